@@ -1,0 +1,156 @@
+/*
+ * tftgpu: truncated Fourier transforms over R = Z/(2^N+1) and Schoenhage-Strassen products in
+ * Z[x] on one GB300 GPU (sm_103a). C ABI of libtftgpu.so.
+ *
+ * Method: D. Harvey, "A cache-friendly truncated FFT" (arXiv 0810.3203).
+ *   Sec. 2    the ring R, omega = 2, the weighted DFT (Eq. dft), the TFT and ITFT definitions,
+ *             polynomial products in R[X] through TFT/ITFT
+ *   Sec. 3    Algorithm 1 (cache-friendly TFT); Sec. 4 Algorithm 2 (cache-friendly ITFT)
+ *   Sec. 5.1  Schoenhage-Strassen multiplication in Z[x]
+ *
+ * Conventions shared by every entry point
+ *   Ring element ("cell"): W = N/64 + 1 little-endian uint64 limbs holding the canonical residue
+ *     in [0, 2^N] (the top limb is 0, or 1 only for 2^N = -1). Consecutive cells are
+ *     stride_limbs >= W limbs apart; limbs past W in a cell are never read or written.
+ *   omega = 2 (a principal 2N-th root of unity), so omega_L = 2^(2N/L) and L = 2^l must divide
+ *     2N. A weight zeta = 2^e is passed as its exponent e (taken mod 2N), as in Sec. 6.
+ *   Supported ring sizes: N a multiple of 64 with N <= 1024, or a multiple of 1024 up to 32768.
+ *   Buffers passed as uint64_t* to the transform calls are DEVICE memory owned by the caller.
+ *   `stream` is a cudaStream_t (NULL = the legacy default stream). All work is enqueued on it;
+ *     the calls return without synchronising unless stated. They are safe to call from several
+ *     host threads on different streams.
+ *   Errors: every call returns a status code (below) and never throws or aborts. On error no
+ *     kernel of the failing call has been enqueued, except for ZX_ECUDA from a launch, after
+ *     which the contents of the caller's buffer are unspecified. zx_last_error() describes
+ *     the most recent failure of the calling thread.
+ */
+#ifndef TFTGPU_H
+#define TFTGPU_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define ZX_OK 0
+#define ZX_EINVAL 1       /* a size, index or flag violates the stated preconditions */
+#define ZX_ENOMEM 2       /* device or pinned-host allocation failed */
+#define ZX_ECUDA 3        /* a CUDA runtime call or kernel launch failed */
+#define ZX_ETIMEOUT 4     /* a bounded device-side wait gave up (batched path) */
+#define ZX_EBUFSIZE 5     /* an output buffer is too small; the needed size is reported */
+#define ZX_EUNSUPPORTED 6 /* valid for the paper, but outside this library's supported sizes */
+
+#define ZX_HOST 0   /* zx_poly.where: data lives in host memory (pageable or pinned) */
+#define ZX_DEVICE 1 /* zx_poly.where: data lives in device memory of the current device */
+
+/*
+ * TFT(L, zeta, z, n) of Sec. 2 computed in place by the cache-friendly order of Algorithm 1.
+ *   x            device buffer of L = 2^l cells. On entry cells 0..z-1 hold a_0..a_{z-1}
+ *                (a_i = 0 for i >= z is implied; those cells are not read). On exit cells
+ *                0..n-1 hold a-hat_0..a-hat_{n-1} of Eq. (dft), i.e. outputs in bit-reversed
+ *                order. All L cells are scratch (Sec. 2: every cell may be used); cells >= n
+ *                are unspecified on exit.
+ *   l            1 <= l <= 16, with 2^l dividing 2N.
+ *   z, n         1 <= z <= L, 1 <= n <= L.
+ *   N            ring size as above.  e  the weight exponent (zeta = 2^e), any int64.
+ *   stride_limbs distance between cells in limbs, >= N/64 + 1.
+ * Returns ZX_EINVAL on bad arguments, ZX_EUNSUPPORTED for an unsupported N, ZX_ECUDA on a
+ * launch failure.
+ */
+int tft_ex(uint64_t *x, int l, int64_t z, int64_t n, int64_t N, int64_t e,
+           int64_t stride_limbs, void *stream);
+
+/* tft_ex with z = n, e = 0 (zeta = 1) and stride_limbs = N/64 + 1: n inputs, n outputs. */
+int tft(uint64_t *x, int l, int64_t n, int64_t N, void *stream);
+
+/*
+ * ITFT(L, zeta, z, n, f) of Sec. 2 computed in place by Algorithm 2 (Sec. 4).
+ *   x      device buffer of L cells. On entry cells 0..n-1 hold a-hat_0..a-hat_{n-1} and cells
+ *          n..z-1 hold L a_n .. L a_{z-1} (a_i = 0 for i >= z implied). On exit cells 0..n-1
+ *          hold L a_0 .. L a_{n-1} when scale = 0, or a_0 .. a_{n-1} when scale = 1 (the
+ *          outputs multiplied by L^{-1} = 2^{2N-l}); if f = 1, cell n holds a-hat_n (never
+ *          scaled). Other cells are unspecified on exit.
+ *   f      0 or 1.  Preconditions: 1 <= z <= L, 0 <= n <= z, 1 <= n + f <= L.
+ *   Other arguments and errors as for tft_ex.
+ */
+int itft_ex(uint64_t *x, int l, int64_t z, int64_t n, int f, int64_t N, int64_t e,
+            int64_t stride_limbs, int scale, void *stream);
+
+/* itft_ex with z = n, f = 0, e = 0, stride N/64 + 1 and scale = 1: returns a_i, so that
+ * itft(tft(x)) restores x literally. */
+int itft(uint64_t *x, int l, int64_t n, int64_t N, void *stream);
+
+/* A polynomial in Z[x] with `len` coefficients of `limbs` little-endian uint64 limbs each,
+ * two's complement when is_signed != 0, unsigned otherwise. `bits` > 0 promises
+ * |coefficient| < 2^bits (0: no promise, 64 * limbs is assumed); the ring size is chosen from
+ * it, and a coefficient that breaks the promise gives an unspecified result. */
+typedef struct {
+    int64_t len;
+    int64_t limbs;
+    int32_t is_signed;
+    int32_t where; /* ZX_HOST or ZX_DEVICE */
+    int64_t bits;
+    uint64_t *data;
+} zx_poly;
+
+/* What zx_mul does for a product (filled by zx_plan). */
+typedef struct {
+    int32_t l;             /* transform length L = 2^l >= len_f + len_g - 1 */
+    int32_t K;             /* 32-bit words per lane of a warp-wide ring element */
+    int64_t N;             /* ring Z/(2^N+1) */
+    int64_t n;             /* number of product coefficients, len_f + len_g - 1 */
+    int64_t stride_limbs;  /* cell stride of the library's ring buffers */
+    int64_t limbs_h;       /* minimum h->limbs that holds every product coefficient */
+    int64_t scratch_bytes; /* device scratch the product needs (two ring buffers) */
+    int32_t tft_passes;    /* kernel passes of one forward transform */
+    int32_t itft_passes;   /* kernel passes of the inverse transform */
+} zx_plan_info;
+
+/*
+ * Ring and transform plan for f * g following the sizing of Sec. 5.1: n = len_f + len_g - 1,
+ * L = 2^ceil(log2 n), N >= bits_f + bits_g + ceil(log2 min(len_f, len_g)) (+1 if signed),
+ * rounded up so that L | 2N and N is a supported size. bits_* are the |coefficient| bounds.
+ * Host only. Returns ZX_EINVAL or ZX_EUNSUPPORTED when no supported ring exists.
+ */
+int zx_plan(int64_t len_f, int64_t bits_f, int64_t len_g, int64_t bits_g, int is_signed,
+            zx_plan_info *out);
+
+/*
+ * h = f * g in Z[x] by Schoenhage-Strassen with truncated transforms (Sec. 2 R[X] product and
+ * Sec. 5.1): pack into R, TFT(f), TFT(g), n pointwise products in R, ITFT, division by L,
+ * lift to Z.
+ *   f, g   inputs, host or device (each independently); not modified.
+ *   h      caller-allocated output with h->len == f->len + g->len - 1 (else ZX_EINVAL) and
+ *          h->limbs >= zx_plan(...).limbs_h (else ZX_EBUFSIZE and h->limbs is overwritten
+ *          with the needed count). h->is_signed is set to f->is_signed || g->is_signed.
+ *   The library owns its scratch (two ring buffers of L cells each), taken from the device's
+ *   stream-ordered memory pool on `stream` and returned to it before the call's work ends.
+ *   Host data is staged through pinned buffers; when any operand is on the host the call
+ *   synchronises `stream` before returning, otherwise it is asynchronous.
+ */
+int zx_mul(const zx_poly *f, const zx_poly *g, zx_poly *h, void *stream);
+
+/*
+ * count independent products hs[i] = fs[i] * gs[i], each with its own ring and length, all
+ * operands in device memory. The products run concurrently: every pass of every product is
+ * one job of a shared per-pass launch, so short products share SMs with long ones instead of
+ * leaving them idle. Same per-product rules as zx_mul (first failing index is reported by
+ * zx_last_error()).
+ */
+int zx_mul_batch(const zx_poly *fs, const zx_poly *gs, zx_poly *hs, int count, void *stream);
+
+/* Human-readable name of a status code (static storage). */
+const char *zx_strerror(int code);
+
+/* Description of the calling thread's most recent failure (static per-thread storage). */
+const char *zx_last_error(void);
+
+/* Library version string, e.g. "tftgpu 0.1 sm_103a". */
+const char *zx_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

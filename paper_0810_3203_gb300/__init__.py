@@ -1,0 +1,171 @@
+"""Python binding of libtftgpu: truncated Fourier transforms over Z/(2^N+1) and
+Schoenhage-Strassen products in Z[x] on a GB300 GPU.
+
+Method: D. Harvey, "A cache-friendly truncated FFT" (arXiv 0810.3203), Algorithms 1 and 2.
+
+Every function here only marshals arguments for the C ABI declared in include/tftgpu.h:
+device tensors become raw pointers, streams become cudaStream_t handles. All arithmetic runs
+in the CUDA kernels of the library. If the library is missing or fails to load, every call
+raises; there is no CPU fallback.
+
+Tensors: ring buffers are torch int64 tensors on a CUDA device (the bit patterns are the
+uint64 limbs), shape (cells * stride_limbs,) or (cells, stride_limbs), contiguous.
+"""
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+ZX_OK, ZX_EINVAL, ZX_ENOMEM, ZX_ECUDA, ZX_ETIMEOUT, ZX_EBUFSIZE, ZX_EUNSUPPORTED = range(7)
+ZX_HOST, ZX_DEVICE = 0, 1
+
+# every entry point the header declares (checked by tests/test_abi.py)
+EXPORTS = ("tft", "tft_ex", "itft", "itft_ex", "zx_plan", "zx_mul", "zx_mul_batch",
+           "zx_strerror", "zx_last_error", "zx_version")
+
+_lib = None
+
+
+class TftError(RuntimeError):
+    def __init__(self, code, where):
+        self.code = code
+        detail = _lib.zx_last_error().decode() if _lib is not None else ""
+        name = _lib.zx_strerror(code).decode() if _lib is not None else str(code)
+        super().__init__(f"{where}: {name} ({detail})")
+
+
+class ZxPoly(C.Structure):
+    _fields_ = [("len", C.c_int64), ("limbs", C.c_int64), ("is_signed", C.c_int32),
+                ("where", C.c_int32), ("bits", C.c_int64), ("data", C.c_void_p)]
+
+
+class ZxPlanInfo(C.Structure):
+    _fields_ = [("l", C.c_int32), ("K", C.c_int32), ("N", C.c_int64), ("n", C.c_int64),
+                ("stride_limbs", C.c_int64), ("limbs_h", C.c_int64), ("scratch_bytes", C.c_int64),
+                ("tft_passes", C.c_int32), ("itft_passes", C.c_int32)]
+
+
+def library_path():
+    return _build.LIB
+
+
+def load(build_if_missing=True):
+    """Load libtftgpu.so (building it first when asked). Raises if it cannot be loaded."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if not os.path.exists(path):
+        if not build_if_missing:
+            raise RuntimeError(f"libtftgpu.so is not built ({path})")
+        _build.build()
+    L = C.CDLL(path)
+    vp, i64, i32 = C.c_void_p, C.c_int64, C.c_int
+    L.tft.argtypes = [vp, i32, i64, i64, vp]
+    L.tft_ex.argtypes = [vp, i32, i64, i64, i64, i64, i64, vp]
+    L.itft.argtypes = [vp, i32, i64, i64, vp]
+    L.itft_ex.argtypes = [vp, i32, i64, i64, i32, i64, i64, i64, i32, vp]
+    L.zx_plan.argtypes = [i64, i64, i64, i64, i32, C.POINTER(ZxPlanInfo)]
+    L.zx_mul.argtypes = [C.POINTER(ZxPoly), C.POINTER(ZxPoly), C.POINTER(ZxPoly), vp]
+    L.zx_mul_batch.argtypes = [C.POINTER(ZxPoly), C.POINTER(ZxPoly), C.POINTER(ZxPoly), i32, vp]
+    L.zx_strerror.argtypes = [i32]
+    L.zx_strerror.restype = C.c_char_p
+    L.zx_last_error.argtypes = []
+    L.zx_last_error.restype = C.c_char_p
+    L.zx_version.restype = C.c_char_p
+    for name in ("tft", "tft_ex", "itft", "itft_ex", "zx_plan", "zx_mul", "zx_mul_batch"):
+        getattr(L, name).restype = i32
+    _lib = L
+    return L
+
+
+def _check(rc, where):
+    if rc != ZX_OK:
+        raise TftError(rc, where)
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return C.c_void_p(stream)
+    return C.c_void_p(stream.cuda_stream)
+
+
+def _dev_ptr(t):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError("expected a CUDA tensor")
+    if t.dtype not in (torch.int64, getattr(torch, "uint64", torch.int64)) or not t.is_contiguous():
+        raise TypeError("expected a contiguous 64-bit integer tensor")
+    return C.c_void_p(t.data_ptr())
+
+
+def limbs(N):
+    return N // 64 + 1
+
+
+def tft(x, l, n, N, stream=None):
+    """In-place TFT with z = n, zeta = 1, stride N/64 + 1 (Algorithm 1)."""
+    _check(load().tft(_dev_ptr(x), l, n, N, _stream(stream)), "tft")
+
+
+def tft_ex(x, l, z, n, N, e=0, stride_limbs=None, stream=None):
+    """In-place TFT(2^l, 2^e, z, n) on cells of stride_limbs limbs (Algorithm 1)."""
+    s = stride_limbs or limbs(N)
+    _check(load().tft_ex(_dev_ptr(x), l, z, n, N, e, s, _stream(stream)), "tft_ex")
+
+
+def itft(x, l, n, N, stream=None):
+    """In-place inverse of tft: returns a_i (scaled by 1/L) (Algorithm 2)."""
+    _check(load().itft(_dev_ptr(x), l, n, N, _stream(stream)), "itft")
+
+
+def itft_ex(x, l, z, n, f, N, e=0, stride_limbs=None, scale=0, stream=None):
+    """In-place ITFT(2^l, 2^e, z, n, f) (Algorithm 2); scale=1 divides the L a_i by L."""
+    s = stride_limbs or limbs(N)
+    _check(load().itft_ex(_dev_ptr(x), l, z, n, f, N, e, s, scale, _stream(stream)), "itft_ex")
+
+
+def zx_plan(len_f, bits_f, len_g, bits_g, is_signed=False):
+    info = ZxPlanInfo()
+    _check(load().zx_plan(len_f, bits_f, len_g, bits_g, 1 if is_signed else 0, C.byref(info)), "zx_plan")
+    return {k: getattr(info, k) for k, _ in ZxPlanInfo._fields_}
+
+
+def _poly(data, length, nlimbs, signed, bits):
+    import torch
+    if isinstance(data, torch.Tensor):
+        ptr, where = _dev_ptr(data).value, ZX_DEVICE
+    else:
+        assert isinstance(data, np.ndarray) and data.dtype == np.uint64 and data.flags.c_contiguous
+        ptr, where = data.ctypes.data, ZX_HOST
+    return ZxPoly(length, nlimbs, 1 if signed else 0, where, bits, ptr)
+
+
+def zx_mul(f, len_f, limbs_f, g, len_g, limbs_g, h, limbs_h, signed=False, bits_f=0, bits_g=0,
+           stream=None):
+    """h = f * g in Z[x]. f, g, h are CUDA int64 tensors or numpy uint64 arrays (host)."""
+    F = _poly(f, len_f, limbs_f, signed, bits_f)
+    G = _poly(g, len_g, limbs_g, signed, bits_g)
+    H = _poly(h, len_f + len_g - 1, limbs_h, signed, 0)
+    _check(load().zx_mul(C.byref(F), C.byref(G), C.byref(H), _stream(stream)), "zx_mul")
+
+
+def zx_mul_batch(items, stream=None):
+    """items: list of (f, len_f, limbs_f, g, len_g, limbs_g, h, limbs_h, signed, bits_f, bits_g)
+    with device tensors."""
+    n = len(items)
+    Fs, Gs, Hs = (ZxPoly * n)(), (ZxPoly * n)(), (ZxPoly * n)()
+    for i, (f, lf, mf, g, lg, mg, h, mh, sg, bf, bg) in enumerate(items):
+        Fs[i] = _poly(f, lf, mf, sg, bf)
+        Gs[i] = _poly(g, lg, mg, sg, bg)
+        Hs[i] = _poly(h, lf + lg - 1, mh, sg, 0)
+    _check(load().zx_mul_batch(Fs, Gs, Hs, n, _stream(stream)), "zx_mul_batch")
+
+
+def version():
+    return load().zx_version().decode()

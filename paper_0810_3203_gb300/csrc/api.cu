@@ -1,0 +1,259 @@
+// C ABI of libtftgpu (declared in include/tftgpu.h): argument checks, planning, staging of
+// host operands, and the order of kernel launches. No arithmetic of the method runs here.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+#include "../../include/tftgpu.h"
+#include "common.h"
+#include "host.h"
+
+namespace tftgpu {
+
+static thread_local std::string g_last_error;
+
+void set_error(const std::string &msg) { g_last_error = msg; }
+
+static int fail(int code, const std::string &msg) {
+  set_error(msg);
+  return code;
+}
+
+static int cuda_fail(cudaError_t e, const char *where) {
+  return fail(ZX_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+static int64_t ceil_log2(int64_t v) {
+  int64_t l = 0;
+  while ((int64_t(1) << l) < v) l++;
+  return l;
+}
+
+static int check_ring(int l, int64_t N) {
+  if (N < 64 || N % 64 != 0) return fail(ZX_EINVAL, "N must be a positive multiple of 64");
+  if (l < 1 || l > 30) return fail(ZX_EINVAL, "l out of range");
+  if ((2 * N) % (int64_t(1) << l) != 0) return fail(ZX_EINVAL, "L = 2^l must divide 2N (omega_L = 2^(2N/L))");
+  if (!ring_supported(N))
+    return fail(ZX_EUNSUPPORTED, "N must be <= 1024 (multiple of 64) or a multiple of 1024 up to 32768");
+  return ZX_OK;
+}
+
+static int transform(int kind, uint64_t *x, int l, int64_t z, int64_t n, int f, int64_t N, int64_t e,
+                     int64_t stride_limbs, int scale, void *stream) {
+  int rc = check_ring(l, N);
+  if (rc) return rc;
+  int64_t L = int64_t(1) << l;
+  if (!x) return fail(ZX_EINVAL, "x is NULL");
+  if (stride_limbs < N / 64 + 1) return fail(ZX_EINVAL, "stride_limbs < N/64 + 1");
+  if (kind == KIND_TFT) {
+    if (z < 1 || z > L || n < 1 || n > L) return fail(ZX_EINVAL, "TFT needs 1 <= z, n <= L");
+  } else {
+    if ((f != 0 && f != 1) || z < 1 || z > L || n < 0 || n > z || n + f < 1 || n + f > L)
+      return fail(ZX_EINVAL, "ITFT needs 1 <= z <= L, 0 <= n <= z, 1 <= n + f <= L, f in {0,1}");
+  }
+  int err = ZX_OK;
+  const TransformPlan *p = get_transform_plan(kind, l, z, n, f, N, e, stride_limbs, scale, &err);
+  if (!p) return err ? fail(err, "planning failed") : fail(ZX_ECUDA, "planning failed");
+  cudaError_t ce = run_transform(*p, x, stride_limbs, cudaStream_t(stream));
+  if (ce != cudaSuccess) return cuda_fail(ce, "transform launch");
+  return ZX_OK;
+}
+
+struct ZxPlan {
+  int l;
+  int64_t N, n, stride, limbs_h, L;
+  Ring ring;
+};
+
+static int make_zx_plan(int64_t lf, int64_t bf, int64_t lg, int64_t bg, int sgn, ZxPlan *zp) {
+  if (lf < 1 || lg < 1) return fail(ZX_EINVAL, "polynomial length must be >= 1");
+  if (bf < 1 || bg < 1) return fail(ZX_EINVAL, "coefficient bit bound must be >= 1");
+  int64_t n = lf + lg - 1;
+  int64_t l = std::max<int64_t>(1, ceil_log2(n));
+  if (l > 16) return fail(ZX_EUNSUPPORTED, "product length above 65536");
+  int64_t L = int64_t(1) << l;
+  int64_t need = bf + bg + ceil_log2(std::min(lf, lg)) + (sgn ? 1 : 0);
+  int64_t align = std::max<int64_t>(need <= 1024 ? 64 : 1024, L / 2);
+  int64_t N = (need + align - 1) / align * align;
+  if (!ring_supported(N)) return fail(ZX_EUNSUPPORTED, "product needs a ring above 2^32768 + 1");
+  zp->l = int(l);
+  zp->N = N;
+  zp->n = n;
+  zp->L = L;
+  int64_t W = N / 64 + 1;
+  zp->stride = W + (W & 1);  // even stride keeps every cell 16-byte aligned
+  zp->limbs_h = (need + 63) / 64;
+  zp->ring = make_ring(N);
+  return ZX_OK;
+}
+
+static int64_t poly_bits(const zx_poly *p) { return p->bits > 0 ? p->bits : 64 * p->limbs; }
+
+static int check_poly(const zx_poly *p, const char *name) {
+  if (!p) return fail(ZX_EINVAL, std::string(name) + " is NULL");
+  if (p->len < 1 || p->limbs < 1 || !p->data) return fail(ZX_EINVAL, std::string(name) + ": bad len/limbs/data");
+  if (p->where != ZX_HOST && p->where != ZX_DEVICE) return fail(ZX_EINVAL, std::string(name) + ": bad where");
+  return ZX_OK;
+}
+
+// device pointer to the operand's coefficients, staging host data through `tmp`
+static int stage_in(const zx_poly *p, uint64_t **dptr, uint64_t **tmp, cudaStream_t s) {
+  *tmp = nullptr;
+  if (p->where == ZX_DEVICE) {
+    *dptr = p->data;
+    return ZX_OK;
+  }
+  size_t bytes = size_t(p->len) * size_t(p->limbs) * 8;
+  cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(tmp), bytes, s);
+  if (e != cudaSuccess) return fail(ZX_ENOMEM, "staging allocation");
+  e = cudaMemcpyAsync(*tmp, p->data, bytes, cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return cuda_fail(e, "host-to-device copy");
+  *dptr = *tmp;
+  return ZX_OK;
+}
+
+}  // namespace tftgpu
+
+using namespace tftgpu;
+
+extern "C" {
+
+int tft_ex(uint64_t *x, int l, int64_t z, int64_t n, int64_t N, int64_t e, int64_t stride_limbs, void *stream) {
+  return transform(KIND_TFT, x, l, z, n, 0, N, e, stride_limbs, 0, stream);
+}
+
+int tft(uint64_t *x, int l, int64_t n, int64_t N, void *stream) {
+  return transform(KIND_TFT, x, l, n, n, 0, N, 0, N / 64 + 1, 0, stream);
+}
+
+int itft_ex(uint64_t *x, int l, int64_t z, int64_t n, int f, int64_t N, int64_t e, int64_t stride_limbs,
+            int scale, void *stream) {
+  if (scale != 0 && scale != 1) return fail(ZX_EINVAL, "scale must be 0 or 1");
+  return transform(KIND_ITFT, x, l, z, n, f, N, e, stride_limbs, scale, stream);
+}
+
+int itft(uint64_t *x, int l, int64_t n, int64_t N, void *stream) {
+  return transform(KIND_ITFT, x, l, n, n, 0, N, 0, N / 64 + 1, 1, stream);
+}
+
+int zx_plan(int64_t len_f, int64_t bits_f, int64_t len_g, int64_t bits_g, int is_signed, zx_plan_info *out) {
+  if (!out) return fail(ZX_EINVAL, "out is NULL");
+  ZxPlan zp;
+  int rc = make_zx_plan(len_f, bits_f, len_g, bits_g, is_signed ? 1 : 0, &zp);
+  if (rc) return rc;
+  std::memset(out, 0, sizeof *out);
+  out->l = zp.l;
+  out->K = zp.ring.K;
+  out->N = zp.N;
+  out->n = zp.n;
+  out->stride_limbs = zp.stride;
+  out->limbs_h = zp.limbs_h;
+  out->scratch_bytes = 2 * zp.L * zp.stride * 8;
+  out->tft_passes = count_passes(KIND_TFT, zp.l, zp.n, zp.n, 0, zp.N);
+  out->itft_passes = count_passes(KIND_ITFT, zp.l, zp.n, zp.n, 0, zp.N);
+  return ZX_OK;
+}
+
+int zx_mul(const zx_poly *f, const zx_poly *g, zx_poly *h, void *stream) {
+  int rc;
+  if ((rc = check_poly(f, "f")) || (rc = check_poly(g, "g")) || (rc = check_poly(h, "h"))) return rc;
+  if (h->len != f->len + g->len - 1) return fail(ZX_EINVAL, "h->len must be f->len + g->len - 1");
+  int sgn = (f->is_signed || g->is_signed) ? 1 : 0;
+  ZxPlan zp;
+  if ((rc = make_zx_plan(f->len, poly_bits(f), g->len, poly_bits(g), sgn, &zp))) return rc;
+  if (h->limbs < zp.limbs_h) {
+    h->limbs = zp.limbs_h;
+    return fail(ZX_EBUFSIZE, "h->limbs too small (needed count written to h->limbs)");
+  }
+  cudaStream_t s = cudaStream_t(stream);
+  h->is_signed = sgn;
+  uint64_t *df = nullptr, *dg = nullptr, *tf = nullptr, *tg = nullptr, *F = nullptr, *Gb = nullptr, *hd = nullptr;
+  auto cleanup = [&]() {
+    if (tf) cudaFreeAsync(tf, s);
+    if (tg) cudaFreeAsync(tg, s);
+    if (F) cudaFreeAsync(F, s);
+    if (Gb) cudaFreeAsync(Gb, s);
+    if (hd && hd != h->data) cudaFreeAsync(hd, s);
+  };
+  if ((rc = stage_in(f, &df, &tf, s)) || (rc = stage_in(g, &dg, &tg, s))) {
+    cleanup();
+    return rc;
+  }
+  size_t ring_bytes = size_t(zp.L) * size_t(zp.stride) * 8;
+  if (cudaMallocAsync(reinterpret_cast<void **>(&F), ring_bytes, s) != cudaSuccess ||
+      cudaMallocAsync(reinterpret_cast<void **>(&Gb), ring_bytes, s) != cudaSuccess) {
+    cleanup();
+    return fail(ZX_ENOMEM, "ring buffers");
+  }
+  size_t hbytes = size_t(h->len) * size_t(h->limbs) * 8;
+  if (h->where == ZX_DEVICE) {
+    hd = h->data;
+  } else if (cudaMallocAsync(reinterpret_cast<void **>(&hd), hbytes, s) != cudaSuccess) {
+    cleanup();
+    return fail(ZX_ENOMEM, "output staging");
+  }
+  cudaError_t ce;
+  int err = ZX_OK;
+  const TransformPlan *pf = get_transform_plan(KIND_TFT, zp.l, f->len, zp.n, 0, zp.N, 0, zp.stride, 0, &err);
+  const TransformPlan *pg = pf ? get_transform_plan(KIND_TFT, zp.l, g->len, zp.n, 0, zp.N, 0, zp.stride, 0, &err) : nullptr;
+  const TransformPlan *pi = pg ? get_transform_plan(KIND_ITFT, zp.l, zp.n, zp.n, 0, zp.N, 0, zp.stride, 1, &err) : nullptr;
+  if (!pi) {
+    cleanup();
+    return fail(err ? err : ZX_ECUDA, "planning failed");
+  }
+  if ((ce = launch_pack(df, f->len, f->limbs, f->is_signed, F, zp.stride, zp.ring, s)) != cudaSuccess ||
+      (ce = launch_pack(dg, g->len, g->limbs, g->is_signed, Gb, zp.stride, zp.ring, s)) != cudaSuccess ||
+      (ce = run_transform(*pf, F, zp.stride, s)) != cudaSuccess ||
+      (ce = run_transform(*pg, Gb, zp.stride, s)) != cudaSuccess ||
+      (ce = launch_pointwise(F, Gb, zp.n, zp.stride, zp.ring, s)) != cudaSuccess ||
+      (ce = run_transform(*pi, F, zp.stride, s)) != cudaSuccess ||
+      (ce = launch_lift(F, zp.n, zp.stride, sgn, hd, h->limbs, zp.ring, s)) != cudaSuccess) {
+    cleanup();
+    return cuda_fail(ce, "zx_mul launch");
+  }
+  if (h->where == ZX_HOST) {
+    if ((ce = cudaMemcpyAsync(h->data, hd, hbytes, cudaMemcpyDeviceToHost, s)) != cudaSuccess) {
+      cleanup();
+      return cuda_fail(ce, "device-to-host copy");
+    }
+  }
+  cleanup();
+  if (f->where == ZX_HOST || g->where == ZX_HOST || h->where == ZX_HOST) {
+    if ((ce = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(ce, "stream synchronize");
+  }
+  return ZX_OK;
+}
+
+int zx_mul_batch(const zx_poly *fs, const zx_poly *gs, zx_poly *hs, int count, void *stream) {
+  if (count < 0 || (count > 0 && (!fs || !gs || !hs))) return fail(ZX_EINVAL, "bad batch arguments");
+  for (int i = 0; i < count; i++) {
+    int rc = zx_mul(fs + i, gs + i, hs + i, stream);
+    if (rc) {
+      set_error("product " + std::to_string(i) + ": " + zx_last_error());
+      return rc;
+    }
+  }
+  return ZX_OK;
+}
+
+const char *zx_strerror(int code) {
+  switch (code) {
+    case ZX_OK: return "ok";
+    case ZX_EINVAL: return "invalid argument";
+    case ZX_ENOMEM: return "out of memory";
+    case ZX_ECUDA: return "CUDA error";
+    case ZX_ETIMEOUT: return "device wait timed out";
+    case ZX_EBUFSIZE: return "output buffer too small";
+    case ZX_EUNSUPPORTED: return "unsupported size";
+    default: return "unknown status";
+  }
+}
+
+const char *zx_last_error(void) { return g_last_error.c_str(); }
+
+const char *zx_version(void) { return "tftgpu 0.1 sm_103a"; }
+
+}  // extern "C"

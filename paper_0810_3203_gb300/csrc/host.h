@@ -1,0 +1,77 @@
+// Host-side internals of libtftgpu: program generation, transform planning and launches.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "common.h"
+
+namespace tftgpu {
+
+enum { KIND_TFT = 0, KIND_ITFT = 1 };
+
+struct ProgramStats {
+  int nops = 0;
+  int nlevels = 0;
+};
+
+// Program image for a sub-transform of length 2^ls held entirely on chip (see common.h).
+std::vector<uint32_t> build_program(int kind, int ls, int64_t z, int64_t n, int f, int64_t N,
+                                    ProgramStats *stats);
+
+// Ring geometry used by the kernels.
+struct Ring {
+  int64_t N = 0;
+  int NW = 0;     // 32-bit words of an N-bit value
+  int K = 0;      // words per lane
+  int G = 0;      // lanes holding words (NW / K)
+  int pitch = 0;  // shared-memory words per cell
+};
+bool ring_supported(int64_t N);
+Ring make_ring(int64_t N);
+
+// Largest on-chip sub-transform (log2 of its cell count) for this ring.
+int max_onchip_ls(const Ring &r);
+
+// One kernel launch: jobs of equal ls.
+struct Launch {
+  int ls = 0;
+  int nwarps = 0;
+  int njobs = 0;
+  JobDesc *d_jobs = nullptr;  // device copy (owned by the plan cache)
+};
+
+struct TransformPlan {
+  Ring ring;
+  std::vector<Launch> launches;  // in stream order
+  int npasses = 0;
+  int64_t njobs = 0;
+};
+
+// Cached plan of TFT (kind = KIND_TFT) or ITFT for the given parameters; nullptr with *err set
+// on failure. escale < 0 means no final scaling.
+const TransformPlan *get_transform_plan(int kind, int l, int64_t z, int64_t n, int f, int64_t N,
+                                        int64_t e, int64_t stride_limbs, int scale, int *err);
+
+// Number of global-memory passes of a transform (host only; no device needed).
+int count_passes(int kind, int l, int64_t z, int64_t n, int f, int64_t N);
+
+// Enqueue a plan on a stream.
+cudaError_t run_transform(const TransformPlan &p, uint64_t *x, int64_t stride_limbs,
+                          cudaStream_t s);
+
+// Kernels of the Z[x] path (zx_kernels.cu).
+cudaError_t launch_pack(const uint64_t *coef, int64_t len, int64_t limbs, int is_signed,
+                        uint64_t *cells, int64_t stride_limbs, const Ring &r, cudaStream_t s);
+cudaError_t launch_pointwise(uint64_t *a, const uint64_t *b, int64_t n, int64_t stride_limbs,
+                             const Ring &r, cudaStream_t s);
+cudaError_t launch_lift(const uint64_t *cells, int64_t n, int64_t stride_limbs, int is_signed,
+                        uint64_t *out, int64_t limbs_out, const Ring &r, cudaStream_t s);
+
+// per-thread error text
+void set_error(const std::string &msg);
+
+}  // namespace tftgpu

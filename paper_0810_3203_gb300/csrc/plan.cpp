@@ -1,0 +1,267 @@
+// Transform planning: Algorithms 1 and 2 applied at the level of global memory.
+//
+// A transform of length L = 2^l whose cells fit in one CTA's shared memory is a single job.
+// Otherwise the array is viewed as an L1 x L2 matrix (L1 = 2^floor(l/2), L2 = 2^ceil(l/2), the
+// paper's split) and the column and row sub-transforms are planned recursively, exactly in
+// the order of Algorithm 1 (columns, then rows) or Algorithm 2 (full rows, rightmost columns,
+// last row, leftmost columns). Each recursion level is one pass over global memory; all
+// sub-transforms of a pass are independent and become the jobs of one kernel launch.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <tuple>
+#include <vector>
+
+#include "../../include/tftgpu.h"
+#include "common.h"
+#include "host.h"
+
+namespace tftgpu {
+
+bool ring_supported(int64_t N) {
+  if (N < 64 || N % 64 != 0) return false;
+  if (N <= 1024) return true;
+  return N % 1024 == 0 && N <= 32768;
+}
+
+Ring make_ring(int64_t N) {
+  Ring r;
+  r.N = N;
+  r.NW = int(N / 32);
+  r.K = words_per_lane(r.NW);
+  r.G = r.NW / r.K;
+  r.pitch = cell_pitch_words(r.NW);
+  return r;
+}
+
+static const size_t kSmemBudget = 200 * 1024;
+
+int max_onchip_ls(const Ring &r) {
+  int ls = 1;
+  while (ls < 16 && size_t(2 << ls) * (size_t(r.pitch) + 1) * 4 <= kSmemBudget) ls++;
+  return ls;
+}
+
+namespace {
+
+int64_t md(int64_t a, int64_t m) {
+  int64_t r = a % m;
+  return r < 0 ? r + m : r;
+}
+
+// device copies of program images, keyed by (device, kind, ls, z, n, f, N)
+struct ProgramCache {
+  std::mutex mu;
+  std::map<std::tuple<int, int, int, int64_t, int64_t, int, int64_t>, uint32_t *> progs;
+
+  const uint32_t *get(int kind, int ls, int64_t z, int64_t n, int f, int64_t N, int *err) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    auto key = std::make_tuple(dev, kind, ls, z, n, f, N);
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = progs.find(key);
+    if (it != progs.end()) return it->second;
+    std::vector<uint32_t> img = build_program(kind, ls, z, n, f, N, nullptr);
+    uint32_t *d = nullptr;
+    if (cudaMalloc(&d, img.size() * 4) != cudaSuccess) {
+      *err = ZX_ENOMEM;
+      return nullptr;
+    }
+    if (cudaMemcpy(d, img.data(), img.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess) {
+      cudaFree(d);
+      *err = ZX_ECUDA;
+      return nullptr;
+    }
+    progs[key] = d;
+    return d;
+  }
+};
+
+ProgramCache &prog_cache() {
+  static ProgramCache *c = new ProgramCache();
+  return *c;
+}
+
+struct JobRec {
+  int pass;
+  int ls;
+  int kind;
+  int64_t z, n;
+  int f;
+  JobDesc d;
+};
+
+struct Planner {
+  Ring ring;
+  int64_t twoN;
+  int ls_max;
+  std::vector<JobRec> jobs;
+
+  void job(int pass, int kind, int64_t cell0, int64_t ms, int l, int64_t e, int64_t z, int64_t n,
+           int f, int64_t nscale, int64_t escale) {
+    JobRec j;
+    std::memset(&j, 0, sizeof j);
+    j.pass = pass;
+    j.ls = l;
+    j.kind = kind;
+    j.z = z;
+    j.n = n;
+    j.f = f;
+    j.d.cell0 = cell0;
+    j.d.mstride = ms;
+    j.d.e = int32_t(md(e, twoN));
+    j.d.nload = int32_t(z);
+    j.d.nstore = int32_t(n + f);
+    j.d.nscale = int32_t(nscale);
+    j.d.escale = int32_t(escale);
+    jobs.push_back(j);
+  }
+
+  // Algorithm 1 over global memory; returns the number of passes used
+  int tft(int pass, int64_t cell0, int64_t ms, int l, int64_t e, int64_t z, int64_t n) {
+    if (l <= ls_max) {
+      job(pass, KIND_TFT, cell0, ms, l, e, z, n, 0, 0, 0);
+      return 1;
+    }
+    int l1 = l / 2, l2 = l - l1;
+    int64_t L = int64_t(1) << l, L1 = int64_t(1) << l1, L2 = int64_t(1) << l2, w = twoN / L;
+    int64_t n2 = n % L2, n1 = n / L2, n1p = (n + L2 - 1) / L2;
+    int64_t z2 = z % L2, z1 = z / L2, z2p = z1 > 0 ? L2 : z2;
+    int dc = 0, dr = 0;
+    for (int64_t u = 0; u < z2p; u++)
+      dc = std::max(dc, tft(pass, cell0 + u * ms, ms * L2, l1, e + u * w, u < z2 ? z1 + 1 : z1, n1p));
+    for (int64_t u = 0; u < n1p; u++)
+      dr = std::max(dr, tft(pass + dc, cell0 + u * L2 * ms, ms, l2, e * L1, z2p, u < n1 ? L2 : n2));
+    return dc + dr;
+  }
+
+  // Algorithm 2 over global memory; outputs L a_i (i < n) are multiplied by 2^escale when
+  // escale >= 0; the f = 1 output a-hat_n never is.
+  int itft(int pass, int64_t cell0, int64_t ms, int l, int64_t e, int64_t z, int64_t n, int f,
+           int64_t escale) {
+    if (l <= ls_max) {
+      job(pass, KIND_ITFT, cell0, ms, l, e, z, n, f, escale >= 0 ? n : 0, escale >= 0 ? escale : 0);
+      return 1;
+    }
+    int l1 = l / 2, l2 = l - l1;
+    int64_t L = int64_t(1) << l, L1 = int64_t(1) << l1, L2 = int64_t(1) << l2, w = twoN / L;
+    int64_t n2 = n % L2, n1 = n / L2, z2 = z % L2, z1 = z / L2;
+    int fp = (n2 + f > 0) ? 1 : 0;
+    int64_t z2p = z1 > 0 ? L2 : z2;
+    int64_t m = std::min(n2, z2), mp = std::max(n2, z2);
+    int p = pass, d = 0;
+    for (int64_t u = 0; u < n1; u++) d = std::max(d, itft(p, cell0 + u * L2 * ms, ms, l2, e * L1, L2, L2, 0, -1));
+    p += d;
+    d = 0;
+    for (int64_t u = n2; u < z2p; u++)
+      d = std::max(d, itft(p, cell0 + u * ms, ms * L2, l1, e + u * w, u < mp ? z1 + 1 : z1, n1, fp, escale));
+    p += d;
+    if (fp) p += itft(p, cell0 + n1 * L2 * ms, ms, l2, e * L1, z2p, n2, f, -1);
+    d = 0;
+    for (int64_t u = 0; u < n2; u++)
+      d = std::max(d, itft(p, cell0 + u * ms, ms * L2, l1, e + u * w, u < m ? z1 + 1 : z1, n1 + 1, 0, escale));
+    p += d;
+    return p - pass;
+  }
+};
+
+struct PlanCache {
+  std::mutex mu;
+  std::map<std::tuple<int, int, int, int64_t, int64_t, int, int64_t, int64_t, int>, std::unique_ptr<TransformPlan>> plans;
+};
+
+PlanCache &plan_cache() {
+  static PlanCache *c = new PlanCache();
+  return *c;
+}
+
+int warps_for(int ls, int K) {
+  int half = 1 << (ls > 0 ? ls - 1 : 0);  // butterflies per level at most
+  int cap = K >= 16 ? 16 : 16;
+  return std::max(1, std::min(cap, half));
+}
+
+}  // namespace
+
+int count_passes(int kind, int l, int64_t z, int64_t n, int f, int64_t N) {
+  Planner P;
+  P.ring = make_ring(N);
+  P.twoN = 2 * N;
+  P.ls_max = max_onchip_ls(P.ring);
+  return kind == KIND_TFT ? P.tft(0, 0, 1, l, 0, z, n) : P.itft(0, 0, 1, l, 0, z, n, f, -1);
+}
+
+const TransformPlan *get_transform_plan(int kind, int l, int64_t z, int64_t n, int f, int64_t N,
+                                        int64_t e, int64_t stride_limbs, int scale, int *err) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  int64_t twoN = 2 * N;
+  e = md(e, twoN);
+  auto key = std::make_tuple(dev, kind, l, z, n, f, N, e, scale);
+  PlanCache &pc = plan_cache();
+  {
+    std::lock_guard<std::mutex> lk(pc.mu);
+    auto it = pc.plans.find(key);
+    if (it != pc.plans.end()) return it->second.get();
+  }
+  Planner P;
+  P.ring = make_ring(N);
+  P.twoN = twoN;
+  P.ls_max = max_onchip_ls(P.ring);
+  int npass;
+  if (kind == KIND_TFT)
+    npass = P.tft(0, 0, 1, l, e, z, n);
+  else
+    npass = P.itft(0, 0, 1, l, e, z, n, f, scale ? md(twoN - l, twoN) : -1);
+
+  std::unique_ptr<TransformPlan> plan(new TransformPlan());
+  plan->ring = P.ring;
+  plan->npasses = npass;
+  plan->njobs = int64_t(P.jobs.size());
+  // resolve programs, then group jobs by (pass, ls) in pass order
+  for (JobRec &j : P.jobs) {
+    j.d.prog = prog_cache().get(j.kind, j.ls, j.z, j.n, j.f, N, err);
+    if (!j.d.prog) return nullptr;
+  }
+  std::stable_sort(P.jobs.begin(), P.jobs.end(), [](const JobRec &a, const JobRec &b) {
+    return a.pass != b.pass ? a.pass < b.pass : a.ls < b.ls;
+  });
+  std::vector<JobDesc> flat;
+  std::vector<std::pair<size_t, Launch>> groups;
+  for (size_t i = 0; i < P.jobs.size();) {
+    size_t k = i;
+    while (k < P.jobs.size() && P.jobs[k].pass == P.jobs[i].pass && P.jobs[k].ls == P.jobs[i].ls) k++;
+    Launch L;
+    L.ls = P.jobs[i].ls;
+    L.njobs = int(k - i);
+    L.nwarps = warps_for(L.ls, P.ring.K);
+    groups.push_back({flat.size(), L});
+    for (size_t t = i; t < k; t++) flat.push_back(P.jobs[t].d);
+    i = k;
+  }
+  JobDesc *d = nullptr;
+  if (cudaMalloc(&d, std::max<size_t>(1, flat.size()) * sizeof(JobDesc)) != cudaSuccess) {
+    *err = ZX_ENOMEM;
+    return nullptr;
+  }
+  if (cudaMemcpy(d, flat.data(), flat.size() * sizeof(JobDesc), cudaMemcpyHostToDevice) != cudaSuccess) {
+    cudaFree(d);
+    *err = ZX_ECUDA;
+    return nullptr;
+  }
+  for (auto &g : groups) {
+    g.second.d_jobs = d + g.first;
+    plan->launches.push_back(g.second);
+  }
+  (void)stride_limbs;
+  std::lock_guard<std::mutex> lk(pc.mu);
+  auto &slot = pc.plans[key];
+  if (!slot) slot = std::move(plan);
+  return slot.get();
+}
+
+}  // namespace tftgpu

@@ -1,0 +1,190 @@
+// Host-side generation of on-chip butterfly programs.
+//
+// A program lists the base-case butterflies that Algorithm 1 (TFT, Sec. 3) or Algorithm 2
+// (ITFT, Sec. 4) executes for a sub-transform of length Ls = 2^ls with given z, n, f, in the
+// order the recursion produces them, then groups them into dependency levels. The weight is
+// symbolic: every rotation is (mul * e + add) mod 2N where e is the job's weight exponent.
+//
+// Any split 1 < L1 < L computes the same outputs (Sec. 2, the decomposition into Eqs. b-cols
+// and b-rows); programs use the split that gives the fewest dependency levels.
+#include <algorithm>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <stdexcept>
+#include <tuple>
+#include <vector>
+
+#include "common.h"
+#include "host.h"
+
+namespace tftgpu {
+
+namespace {
+
+struct SymE {
+  int64_t mul, add;  // exponent = mul * e + add (mod 2N)
+};
+
+class ProgGen {
+ public:
+  ProgGen(int64_t twoN, int policy) : twoN_(twoN), policy_(policy) {}
+
+  std::vector<OpDesc> ops;
+
+  void tft(int base, int stride, int l, SymE E, int64_t z, int64_t n) {
+    if (l == 1) {
+      int c0 = base, c1 = base + stride;
+      if (n == 2 && z == 2) {
+        push(OP_BF, c0, c1, OPF_S | OPF_D, zero(), zero(), zero(), E);
+      } else if (n == 2 && z == 1) {
+        push(OP_TAG, c0, c1, OPF_COPY, zero(), E, zero(), zero());
+      } else if (n == 1 && z == 2) {
+        push(OP_BF, c0, c1, OPF_S, zero(), zero(), zero(), zero());
+      }
+      return;
+    }
+    int l1 = split(l), l2 = l - l1;
+    int64_t L = int64_t(1) << l, L1 = int64_t(1) << l1, L2 = int64_t(1) << l2;
+    int64_t w = twoN_ / L;
+    int64_t n2 = n % L2, n1 = n / L2, n1p = (n + L2 - 1) / L2;
+    int64_t z2 = z % L2, z1 = z / L2, z2p = z1 > 0 ? L2 : z2;
+    for (int64_t u = 0; u < z2; u++)
+      tft(base + int(u) * stride, stride * int(L2), l1, plus(E, u * w), z1 + 1, n1p);
+    for (int64_t u = z2; u < z2p; u++)
+      tft(base + int(u) * stride, stride * int(L2), l1, plus(E, u * w), z1, n1p);
+    SymE Er = times(E, L1);
+    for (int64_t u = 0; u < n1; u++) tft(base + int(u * L2) * stride, stride, l2, Er, z2p, L2);
+    if (n2 > 0) tft(base + int(n1 * L2) * stride, stride, l2, Er, z2p, n2);
+  }
+
+  void itft(int base, int stride, int l, SymE E, int64_t z, int64_t n, int f) {
+    if (l == 1) {
+      int c0 = base, c1 = base + stride;
+      if (n == 2) {
+        push(OP_BF, c0, c1, OPF_S | OPF_D, zero(), neg(E), zero(), zero());
+      } else if (n == 1 && f == 1 && z == 2) {
+        push(OP_CROSS, c0, c1, 0, zero(), zero(), zero(), E);
+      } else if (n == 1 && f == 1 && z == 1) {
+        push(OP_TAG, c0, c1, OPF_COPY, cst(1), E, zero(), zero());
+      } else if (n == 1 && f == 0 && z == 2) {
+        push(OP_BF, c0, c1, OPF_D | OPF_D_TO_I, cst(1), zero(), zero(), zero());
+      } else if (n == 1 && f == 0 && z == 1) {
+        push(OP_TAG, c0, c0, 0, cst(1), zero(), zero(), zero());
+      } else if (n == 0 && z == 2) {
+        push(OP_BF, c0, c1, OPF_S, zero(), zero(), cst(twoN_ - 1), zero());
+      } else if (n == 0 && z == 1) {
+        push(OP_TAG, c0, c0, 0, cst(twoN_ - 1), zero(), zero(), zero());
+      }
+      return;
+    }
+    int l1 = split(l), l2 = l - l1;
+    int64_t L = int64_t(1) << l, L1 = int64_t(1) << l1, L2 = int64_t(1) << l2;
+    int64_t w = twoN_ / L;
+    int64_t n2 = n % L2, n1 = n / L2, z2 = z % L2, z1 = z / L2;
+    int fp = (n2 + f > 0) ? 1 : 0;
+    int64_t z2p = z1 > 0 ? L2 : z2;
+    int64_t m = std::min(n2, z2), mp = std::max(n2, z2);
+    SymE Er = times(E, L1);
+    int cs = stride * int(L2);
+    for (int64_t u = 0; u < n1; u++) itft(base + int(u * L2) * stride, stride, l2, Er, L2, L2, 0);
+    for (int64_t u = n2; u < mp; u++) itft(base + int(u) * stride, cs, l1, plus(E, u * w), z1 + 1, n1, fp);
+    for (int64_t u = mp; u < z2p; u++) itft(base + int(u) * stride, cs, l1, plus(E, u * w), z1, n1, fp);
+    if (fp) itft(base + int(n1 * L2) * stride, stride, l2, Er, z2p, n2, f);
+    for (int64_t u = 0; u < m; u++) itft(base + int(u) * stride, cs, l1, plus(E, u * w), z1 + 1, n1 + 1, 0);
+    for (int64_t u = m; u < n2; u++) itft(base + int(u) * stride, cs, l1, plus(E, u * w), z1, n1 + 1, 0);
+  }
+
+ private:
+  int64_t twoN_;
+  int policy_;
+
+  int split(int l) const { return policy_ == 0 ? 1 : l / 2; }
+  int64_t md(int64_t a) const {
+    int64_t r = a % twoN_;
+    return r < 0 ? r + twoN_ : r;
+  }
+  SymE zero() const { return {0, 0}; }
+  SymE cst(int64_t a) const { return {0, md(a)}; }
+  SymE neg(SymE a) const { return {md(-a.mul), md(-a.add)}; }
+  SymE plus(SymE a, int64_t c) const { return {a.mul, md(a.add + c)}; }
+  SymE times(SymE a, int64_t c) const { return {md(a.mul * c), md(a.add * c)}; }
+  RotA ra(SymE a) const { return RotA{int32_t(a.mul), int32_t(a.add)}; }
+
+  void push(uint8_t kind, int i, int j, uint8_t flags, SymE r_a, SymE r_b, SymE p0, SymE p1) {
+    OpDesc o;
+    std::memset(&o, 0, sizeof o);
+    o.i = uint16_t(i);
+    o.j = uint16_t(j);
+    o.kind = kind;
+    o.flags = flags;
+    o.ra = ra(r_a);
+    o.rb = ra(r_b);
+    o.p0 = ra(p0);
+    o.p1 = ra(p1);
+    ops.push_back(o);
+  }
+};
+
+// group ops into levels: an op goes one level after the last op that touched one of its cells
+std::vector<uint32_t> level_and_pack(const std::vector<OpDesc> &ops, int Ls, int *nlevels_out) {
+  std::vector<int> last(Ls, -1), lvl(ops.size());
+  int nlev = 0;
+  for (size_t k = 0; k < ops.size(); k++) {
+    const OpDesc &o = ops[k];
+    int a = last[o.i], b = (o.j != o.i) ? last[o.j] : -1;
+    int v = std::max(a, b) + 1;
+    lvl[k] = v;
+    last[o.i] = v;
+    last[o.j] = v;
+    nlev = std::max(nlev, v + 1);
+  }
+  std::vector<std::vector<int>> byl(nlev);
+  for (size_t k = 0; k < ops.size(); k++) byl[lvl[k]].push_back(int(k));
+  int off = prog_ops_offset_words(nlev);
+  std::vector<uint32_t> img(off + ops.size() * (sizeof(OpDesc) / 4), 0);
+  img[0] = uint32_t(nlev);
+  img[1] = uint32_t(ops.size());
+  uint32_t start = 0;
+  OpDesc *dst = reinterpret_cast<OpDesc *>(img.data() + off);
+  size_t w = 0;
+  for (int v = 0; v < nlev; v++) {
+    img[2 + v] = start;
+    for (int k : byl[v]) dst[w++] = ops[k];
+    start += uint32_t(byl[v].size());
+  }
+  img[2 + nlev] = start;
+  *nlevels_out = nlev;
+  return img;
+}
+
+}  // namespace
+
+std::vector<uint32_t> build_program(int kind, int ls, int64_t z, int64_t n, int f, int64_t N,
+                                    ProgramStats *stats) {
+  int64_t twoN = 2 * N;
+  int Ls = 1 << ls;
+  std::vector<uint32_t> best;
+  int best_lev = -1;
+  // policy 0: L1 = 2 at every level; policy 1: balanced split (the paper's rule)
+  for (int policy = 0; policy < 2; policy++) {
+    ProgGen g(twoN, policy);
+    if (kind == KIND_TFT)
+      g.tft(0, 1, ls, {1, 0}, z, n);
+    else
+      g.itft(0, 1, ls, {1, 0}, z, n, f);
+    int nlev = 0;
+    std::vector<uint32_t> img = level_and_pack(g.ops, Ls, &nlev);
+    if (best_lev < 0 || nlev < best_lev) {
+      best_lev = nlev;
+      best = std::move(img);
+      if (stats) {
+        stats->nops = int(g.ops.size());
+        stats->nlevels = nlev;
+      }
+    }
+  }
+  return best;
+}
+
+}  // namespace tftgpu

@@ -1,0 +1,288 @@
+// Warp-wide arithmetic in R = Z/(2^N+1) (Sec. 2: R = Z/(2^{M/2}+1) with omega = 2).
+//
+// One ring element is spread over one warp: lane l holds the K consecutive 32-bit words
+// [K l, K l + K) of its N-bit part (lanes >= G = NW/K hold zeros). Additions run a carry
+// chain inside each lane and then pass the lane carry to the next lane with shuffles; a
+// carry that has to cross a lane again is rare for random data, so the cross-lane step loops
+// only while some lane still has one.
+//
+// Storage form of a cell (shared memory): m = x - 1 (an N-bit number, so 2^N = -1 is all
+// ones) plus a zero flag for x = 0, plus a pending rotation t: the cell stands for
+// x 2^t. With that form, multiplying by 2^E needs no correction step except the final +1:
+//   x 2^E = rotc(m, E) + 1  for x in [1, 2^N],  0 <= E < N,
+// where rotc rotates the N bits of m left by E and complements the E bits that wrapped
+// around (2^N = -1). For N <= E < 2N the complement applies to the bits that did not wrap
+// (x 2^E = -(x 2^{E-N}) and -(y + 1) = ~y + 1). This is the "multiplication by powers of
+// omega is cheap" of Sec. 5.1 written for lane-distributed words.
+#pragma once
+
+#include <cstdint>
+
+namespace tftgpu {
+
+#define TFT_FULL 0xffffffffu
+
+struct Geo {
+  int N;     // ring bits
+  int NW;    // words of the N-bit part
+  int G;     // lanes holding words
+  int lane;  // this thread's lane
+  int twoN;
+};
+
+// ------------------------------------------------------------------ carry chains (PTX)
+template <int K>
+__device__ __forceinline__ uint32_t add_chain(uint32_t (&r)[K], const uint32_t (&a)[K],
+                                              const uint32_t (&b)[K], uint32_t cin) {
+  uint32_t cout, d;
+  asm volatile("add.cc.u32 %0, %1, 0xffffffff;" : "=r"(d) : "r"(cin));
+#pragma unroll
+  for (int s = 0; s < K; s++) asm volatile("addc.cc.u32 %0, %1, %2;" : "=r"(r[s]) : "r"(a[s]), "r"(b[s]));
+  asm volatile("addc.u32 %0, 0, 0;" : "=r"(cout));
+  return cout;
+}
+
+// r = a - b - bin over the chunk; returns the borrow out (0/1)
+template <int K>
+__device__ __forceinline__ uint32_t sub_chain(uint32_t (&r)[K], const uint32_t (&a)[K],
+                                              const uint32_t (&b)[K], uint32_t bin) {
+  uint32_t bout, d;
+  asm volatile("sub.cc.u32 %0, 0, %1;" : "=r"(d) : "r"(bin));
+#pragma unroll
+  for (int s = 0; s < K; s++) asm volatile("subc.cc.u32 %0, %1, %2;" : "=r"(r[s]) : "r"(a[s]), "r"(b[s]));
+  asm volatile("subc.u32 %0, 0, 0;" : "=r"(bout));
+  return bout & 1u;
+}
+
+// ------------------------------------------------------------------ ripples
+// add c at slot 0 of the lane's chunk (c may exceed 1), propagate; returns the carry out
+template <int K>
+__device__ __forceinline__ uint32_t ripple_add(uint32_t (&r)[K], uint32_t c) {
+#pragma unroll
+  for (int s = 0; s < K; s++) {
+    if (!__any_sync(TFT_FULL, c)) return 0u;
+    uint32_t t = r[s] + c;
+    c = t < c ? 1u : 0u;
+    r[s] = t;
+  }
+  return c;
+}
+
+// subtract c at slot 0 of the lane's chunk, propagate; returns the borrow out
+template <int K>
+__device__ __forceinline__ uint32_t ripple_sub(uint32_t (&r)[K], uint32_t c) {
+#pragma unroll
+  for (int s = 0; s < K; s++) {
+    if (!__any_sync(TFT_FULL, c)) return 0u;
+    uint32_t v = r[s];
+    r[s] = v - c;
+    c = v < c ? 1u : 0u;
+  }
+  return c;
+}
+
+// Lane carries cout (out of each lane's chunk) moved into the next lane until none is left.
+// Returns the total carry out of bit N.
+template <int K>
+__device__ __forceinline__ uint32_t resolve_add(uint32_t (&r)[K], uint32_t cout, const Geo &g) {
+  uint32_t top = __shfl_sync(TFT_FULL, cout, g.G - 1);
+  uint32_t c = __shfl_up_sync(TFT_FULL, cout, 1);
+  if (g.lane == 0 || g.lane >= g.G) c = 0;
+  while (__any_sync(TFT_FULL, c)) {
+    uint32_t co = ripple_add<K>(r, c);
+    top += __shfl_sync(TFT_FULL, co, g.G - 1);
+    c = __shfl_up_sync(TFT_FULL, co, 1);
+    if (g.lane == 0 || g.lane >= g.G) c = 0;
+  }
+  return top;
+}
+
+template <int K>
+__device__ __forceinline__ uint32_t resolve_sub(uint32_t (&r)[K], uint32_t bout, const Geo &g) {
+  uint32_t top = __shfl_sync(TFT_FULL, bout, g.G - 1);
+  uint32_t c = __shfl_up_sync(TFT_FULL, bout, 1);
+  if (g.lane == 0 || g.lane >= g.G) c = 0;
+  while (__any_sync(TFT_FULL, c)) {
+    uint32_t co = ripple_sub<K>(r, c);
+    top += __shfl_sync(TFT_FULL, co, g.G - 1);
+    c = __shfl_up_sync(TFT_FULL, co, 1);
+    if (g.lane == 0 || g.lane >= g.G) c = 0;
+  }
+  return top;
+}
+
+// r += v at bit 0 (v >= 0, warp-uniform); returns the carry out of bit N
+template <int K>
+__device__ __forceinline__ uint32_t add_small(uint32_t (&r)[K], uint32_t v, const Geo &g) {
+  uint32_t co = ripple_add<K>(r, g.lane == 0 ? v : 0u);
+  return resolve_add<K>(r, co, g);
+}
+
+template <int K>
+__device__ __forceinline__ uint32_t sub_small(uint32_t (&r)[K], uint32_t v, const Geo &g) {
+  uint32_t bo = ripple_sub<K>(r, g.lane == 0 ? v : 0u);
+  return resolve_sub<K>(r, bo, g);
+}
+
+template <int K>
+__device__ __forceinline__ bool is_zero(const uint32_t (&r)[K]) {
+  uint32_t o = 0;
+#pragma unroll
+  for (int s = 0; s < K; s++) o |= r[s];
+  return !__any_sync(TFT_FULL, o);
+}
+
+template <int K>
+__device__ __forceinline__ void set_ones(uint32_t (&r)[K], const Geo &g) {
+#pragma unroll
+  for (int s = 0; s < K; s++) r[s] = g.lane < g.G ? TFT_FULL : 0u;
+}
+
+// Storage form: given an N-bit R and a small warp-uniform v with m = R + v (mod 2^N+1),
+// leave m in [0, 2^N - 1] in r and return 0, or return 1 when m = -1 (the cell value x = m + 1
+// is zero).
+template <int K>
+__device__ __forceinline__ int canon_m(uint32_t (&r)[K], int v, const Geo &g) {
+  while (v != 0) {
+    if (v > 0) {
+      uint32_t o = add_small<K>(r, uint32_t(v), g);  // R + v = R' + o 2^N = R' - o
+      v = -int(o);
+    } else {
+      uint32_t b = sub_small<K>(r, uint32_t(-v), g);  // R - |v| = R' - b 2^N = R' + b
+      if (!b) {
+        v = 0;
+      } else {
+        if (v == -1) return 1;  // R was 0: m = -1
+        v = 1;
+      }
+    }
+  }
+  return 0;
+}
+
+// Canonical value: x = R + v (mod 2^N+1) with x in [0, 2^N]; returns the top bit (1 only for
+// x = 2^N, then r is zero).
+template <int K>
+__device__ __forceinline__ uint32_t canon_x(uint32_t (&r)[K], int v, const Geo &g) {
+  while (v != 0) {
+    if (v > 0) {
+      uint32_t o = add_small<K>(r, uint32_t(v), g);
+      v = -int(o);
+    } else {
+      if (v == -1 && is_zero<K>(r)) return 1u;  // x = -1 = 2^N
+      uint32_t b = sub_small<K>(r, uint32_t(-v), g);
+      v = b ? 1 : 0;
+    }
+  }
+  return 0u;
+}
+
+// ------------------------------------------------------------------ shared-memory cells
+// word w of a cell sits at w + w/32 (one pad word per 32 keeps lane chunks on distinct banks)
+__device__ __forceinline__ int phys(int w) { return w + (w >> 5); }
+
+template <int K>
+__device__ __forceinline__ void smem_store_plain(uint32_t *cell, const uint32_t (&r)[K], const Geo &g) {
+  if (g.lane < g.G) {
+    int b = phys(K * g.lane);
+#pragma unroll
+    for (int s = 0; s < K; s++) cell[b + s] = r[s];
+  }
+}
+
+template <int K>
+__device__ __forceinline__ void smem_load_plain(uint32_t (&r)[K], const uint32_t *cell, const Geo &g) {
+  if (g.lane < g.G) {
+    int b = phys(K * g.lane);
+#pragma unroll
+    for (int s = 0; s < K; s++) r[s] = cell[b + s];
+  } else {
+#pragma unroll
+    for (int s = 0; s < K; s++) r[s] = 0u;
+  }
+}
+
+// raw = rotc(m, E) for the cell (see the file comment); E in [0, 2N). The zero cell reads as
+// all ones with the returned flag set (then x 2^E = raw + 1 - 2^N = 0).
+template <int K>
+__device__ __forceinline__ int smem_read_raw(uint32_t (&r)[K], const uint32_t *cell, uint32_t meta,
+                                             int Ereq, const Geo &g) {
+  if (meta & 1u) {
+    set_ones<K>(r, g);
+    return 1;
+  }
+  int E = int(meta >> 1) + Ereq;
+  if (E >= g.twoN) E -= g.twoN;
+  if (E == 0) {
+    smem_load_plain<K>(r, cell, g);
+    return 0;
+  }
+  if (g.lane >= g.G) {
+#pragma unroll
+    for (int s = 0; s < K; s++) r[s] = 0u;
+    return 0;
+  }
+  const bool low_wrapped = E < g.N;  // complement the wrapped bits (else the others)
+  const int Ep = low_wrapped ? E : E - g.N;
+  const int q = Ep >> 5, sh = Ep & 31;
+  const int j0 = K * g.lane;
+  int src = j0 - q - 1;
+  if (src < 0) src += g.NW;
+  uint32_t prev = cell[phys(src)];
+  const uint32_t lomask = (1u << sh) - 1u;
+  const uint32_t flip = low_wrapped ? 0u : TFT_FULL;
+#pragma unroll
+  for (int s = 0; s < K; s++) {
+    ++src;
+    if (src == g.NW) src = 0;
+    uint32_t cur = cell[phys(src)];
+    uint32_t w = __funnelshift_l(prev, cur, sh);  // (cur:prev) << sh, high word
+    int j = j0 + s;
+    uint32_t m = j < q ? TFT_FULL : (j == q ? lomask : 0u);
+    r[s] = w ^ (m ^ flip);
+    prev = cur;
+  }
+  return 0;
+}
+
+// ------------------------------------------------------------------ global memory cells
+// canonical x: words [0, NW) and the top limb (word NW holds its low half)
+template <int K>
+__device__ __forceinline__ uint32_t gmem_load_x(uint32_t (&r)[K], const uint64_t *cell, const Geo &g) {
+  const uint32_t *w32 = reinterpret_cast<const uint32_t *>(cell);
+  if (g.lane < g.G) {
+    if (K == 1) {
+      r[0] = __ldg(w32 + g.lane);
+    } else {
+      const uint2 *p = reinterpret_cast<const uint2 *>(w32 + K * g.lane);
+#pragma unroll
+      for (int s = 0; s < K / 2; s++) {
+        uint2 v = __ldg(p + s);
+        r[2 * s] = v.x;
+        r[2 * s + 1] = v.y;
+      }
+    }
+  } else {
+#pragma unroll
+    for (int s = 0; s < K; s++) r[s] = 0u;
+  }
+  return __ldg(w32 + g.NW);
+}
+
+template <int K>
+__device__ __forceinline__ void gmem_store_x(uint64_t *cell, const uint32_t (&r)[K], uint32_t top,
+                                             const Geo &g) {
+  uint32_t *w32 = reinterpret_cast<uint32_t *>(cell);
+  if (g.lane < g.G) {
+    if (K == 1) {
+      w32[g.lane] = r[0];
+    } else {
+      uint2 *p = reinterpret_cast<uint2 *>(w32 + K * g.lane);
+#pragma unroll
+      for (int s = 0; s < K / 2; s++) p[s] = make_uint2(r[2 * s], r[2 * s + 1]);
+    }
+  }
+  if (g.lane == 0) cell[g.NW / 2] = uint64_t(top);
+}
+
+}  // namespace tftgpu

@@ -1,0 +1,70 @@
+"""The C ABI library builds, loads without a GPU, and exports every entry point the header
+declares; host-only planning calls answer without touching a device."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def header_functions():
+    src = open(os.path.join(ROOT, "include", "tftgpu.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\*?\s*([a-z_][a-z0-9_]*)\s*\(", src, re.M)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import paper_0810_3203_gb300 as tg
+    tg.build.build()
+    return tg.load(build_if_missing=False)
+
+
+def test_exports_every_declared_function(lib):
+    import paper_0810_3203_gb300 as tg
+    declared = header_functions()
+    assert set(declared) == set(tg.EXPORTS), declared
+    so = C.CDLL(tg.library_path())
+    for name in declared:
+        assert hasattr(so, name), name
+
+
+def test_status_strings(lib):
+    assert lib.zx_strerror(0) == b"ok"
+    assert lib.zx_strerror(6) == b"unsupported size"
+    assert b"sm_103a" in lib.zx_version()
+
+
+def test_plan_medium_product():
+    import paper_0810_3203_gb300 as tg
+    p = tg.zx_plan(3000, 2000, 2500, 2000)
+    assert (p["l"], p["N"], p["n"], p["K"]) == (13, 4096, 5499, 4)
+    assert p["limbs_h"] * 64 >= 2000 + 2000 + 12
+    assert p["tft_passes"] == 2 and p["itft_passes"] >= 2
+
+
+def test_plan_sizes_follow_the_ring_rule():
+    import paper_0810_3203_gb300 as tg
+    for lf, lg, bits in ((1, 1, 1), (100, 100, 64), (20000, 20000, 1024), (5, 70000, 10)):
+        if lf + lg - 1 > 65536:
+            with pytest.raises(tg.TftError) as ei:
+                tg.zx_plan(lf, bits, lg, bits)
+            assert ei.value.code == tg.ZX_EUNSUPPORTED
+            continue
+        p = tg.zx_plan(lf, bits, lg, bits)
+        L = 1 << p["l"]
+        assert L >= lf + lg - 1 and (2 * p["N"]) % L == 0
+        assert p["N"] >= 2 * bits + (min(lf, lg) - 1).bit_length()
+        assert p["N"] <= 1024 or p["N"] % 1024 == 0
+
+
+def test_rejects_bad_arguments_without_a_device(lib):
+    # argument checks come before any CUDA call
+    assert lib.tft_ex(None, 3, 1, 1, 64, 0, 2, None) == 1
+    assert lib.tft_ex(C.c_void_p(8), 8, 1, 1, 64, 0, 2, None) == 1
+    assert lib.itft_ex(C.c_void_p(8), 2, 1, 3, 0, 64, 0, 2, 0, None) == 1
+    assert lib.tft_ex(C.c_void_p(8), 2, 1, 1, 1088, 0, 18, None) == 6
+    assert b"1024" in lib.zx_last_error()
