@@ -1,0 +1,429 @@
+#!/usr/bin/env python
+"""Benchmark of the truncated transforms over Z/(2^32768+1) at L = 2^16 (n swept over
+32769, 40000, 45000, 52000, 65536), the workload on which the TFT/ITFT throughput is quoted.
+
+One step = for every n of the sweep, a TFT (Algorithm 1) then an ITFT with the final division
+by L (Algorithm 2) on resident device buffers; the round trip restores the inputs, so every
+step sees the same data. Throughput counts the algorithmic bytes of the paper's two-pass
+Bailey schedule: every cell a top-level row or column sub-transform reads or writes, times
+8 (N/64 + 1) bytes per cell (see alg_bytes_tft / alg_bytes_itft), divided by device time.
+
+Prints one JSON line (rank 0). Multi-GPU runs (torchrun) are independent replicas: every
+rank runs the whole sweep on its own GPU, no data moves between GPUs, and the value is the
+bytes of all ranks divided by the slowest rank's time (weak scaling).
+
+--impl reference times the CPU oracle (the paper's recursion on the host cores) on a bounded
+sample of the same workload: one round trip at n = 40000 per step.
+"""
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import workloads  # noqa: E402
+
+METRIC = "TFT/ITFT GB/s vs HBM peak; batched Z[x] products/s vs plain, bit-exact"
+WORKLOAD = workloads.TRANSFORM_LARGE
+FALLBACK_HBM_GBS = 6800.0
+
+
+# ---------------------------------------------------------------- algorithmic bytes
+def _split(l):
+    l1 = l // 2
+    return l1, l - l1
+
+
+def alg_cells_tft(l, z, n):
+    """Cells read + written by the two passes of Algorithm 1's top level (Sec. 3)."""
+    _, l2 = _split(l)
+    L2 = 1 << l2
+    n1p = -(-n // L2)
+    z1, z2 = divmod(z, L2)
+    z2p = L2 if z1 > 0 else z2
+    return (z + n1p * z2p) + (n1p * z2p + n)
+
+
+def alg_cells_itft(l, z, n, f=0):
+    """Cells read + written by the four phases of Algorithm 2's top level (Sec. 4)."""
+    _, l2 = _split(l)
+    L2 = 1 << l2
+    n1, n2 = divmod(n, L2)
+    z1, z2 = divmod(z, L2)
+    fp = 1 if n2 + f > 0 else 0
+    z2p = L2 if z1 > 0 else z2
+    m, mp = min(n2, z2), max(n2, z2)
+    cells = n1 * 2 * L2  # full rows
+    for u in range(n2, z2p):  # rightmost columns
+        cells += (z1 + 1 if u < mp else z1) + n1 + fp
+    if fp:  # last row
+        cells += z2p + n2 + f
+    for u in range(n2):  # leftmost columns
+        cells += (z1 + 1 if u < m else z1) + n1 + 1
+    return cells
+
+
+def cell_bytes(N):
+    return 8 * (N // 64 + 1)
+
+
+def step_bytes(N, l, ns):
+    return sum((alg_cells_tft(l, n, n) + alg_cells_itft(l, n, n)) * cell_bytes(N) for n in ns)
+
+
+# ---------------------------------------------------------------- environment
+def measured_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_0810_3203_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        h.update(f.encode())
+        h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic():
+    """Per-launch DRAM bytes of the dominant kernel from the committed ncu summary, if the
+    kernels have not changed since it was taken."""
+    p = os.path.join(ROOT, "profiles", "traffic_job_kernel_l16_N32768.json")
+    try:
+        d = json.load(open(p))
+        if d.get("kernel_source_hash") == kernel_source_hash():
+            return d
+    except Exception:
+        pass
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi samples (every 200 ms) while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- distributed helpers
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def dist_init(backend):
+    import torch.distributed as dist
+    ws, rank, _ = dist_env()
+    if ws > 1 and not dist.is_initialized():
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group(backend=backend, rank=rank, world_size=ws)
+    return ws, rank
+
+
+def max_over_ranks(value, device=None):
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()):
+        return value
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(device=None):
+    import torch.distributed as dist
+    if dist.is_available() and dist.is_initialized():
+        if device is not None and device.type == "cuda":
+            dist.barrier(device_ids=[device.index])
+        else:
+            dist.barrier()
+
+
+def timed_steps(step, steps, warmup, sync, device=None):
+    """W untimed steps, then exactly K steps bracketed by barrier + device sync on both sides;
+    returns the slowest rank's elapsed seconds."""
+    for _ in range(warmup):
+        step()
+    sync()
+    barrier(device)
+    sync()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        step()
+    sync()
+    barrier(device)
+    sync()
+    return max_over_ranks(time.perf_counter() - t0, device)
+
+
+# ---------------------------------------------------------------- CPU oracle legs
+def oracle_roundtrip_seconds(n, N, l):
+    import oracle
+    x = workloads.residues(WORKLOAD["seed"], n, N, cells=1 << l)
+    t0 = time.perf_counter()
+    oracle.tft(x, l, n, n, 0, N)
+    oracle.itft(x, l, n, n, 0, 0, N)
+    return time.perf_counter() - t0
+
+
+def cpu_baseline(N, l):
+    n = 40000
+    secs = oracle_roundtrip_seconds(n, N, l)
+    b = (alg_cells_tft(l, n, n) + alg_cells_itft(l, n, n)) * cell_bytes(N)
+    return {"value": round(b / secs / 1e9, 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
+            "sample": f"one TFT + ITFT round trip at n = {n} (l = {l}, N = {N}), single thread, "
+                      f"{secs:.1f} s"}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    N, l = WORKLOAD["N"], WORKLOAD["l"]
+    n = 40000
+    secs = []
+
+    def step():
+        secs.append(oracle_roundtrip_seconds(n, N, l))
+
+    for _ in range(args.warmup):
+        step()
+    secs.clear()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    elapsed = time.perf_counter() - t0
+    b = (alg_cells_tft(l, n, n) + alg_cells_itft(l, n, n)) * cell_bytes(N)
+    value = b * args.steps / elapsed / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": "GB/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(elapsed / args.steps * 1e3, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": {"workload": "TFT+ITFT round trip over Z/(2^32768+1), L = 2^16, n = 40000 "
+                               "(bounded sample of the n sweep)", "N": N, "l": l, "ns": [n],
+                   "seed": WORKLOAD["seed"]},
+        "cpu_baseline": {"value": round(value, 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
+                         "sample": f"{args.steps} round trips at n = {n}, single thread"},
+        "e2e": {"value": round(value, 4), "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------- GPU leg
+def run_gpu(args):
+    import numpy as np
+    import torch
+
+    import paper_0810_3203_gb300 as tg
+
+    ws, rank, local = dist_env()
+    device = torch.device("cuda", local)
+    torch.cuda.set_device(device)
+    dist_init("nccl")
+    tg.load()
+    N, l, ns = WORKLOAD["N"], WORKLOAD["l"], list(WORKLOAD["ns"])
+    W = N // 64 + 1
+    stride = W + (W & 1)  # 16-byte aligned cells
+    L = 1 << l
+    stream = torch.cuda.current_stream(device)
+    host = {n: workloads.residues(WORKLOAD["seed"], n, N, stride=stride, cells=L) for n in ns}
+    dev = {n: torch.from_numpy(host[n].view(np.int64)).to(device) for n in ns}
+    torch.cuda.synchronize(device)
+
+    def mk():
+        return torch.cuda.Event(enable_timing=True)
+
+    ev = [{n: (mk(), mk(), mk()) for n in ns} for _ in range(args.steps)]
+
+    def step(rec=None):
+        for n in ns:
+            if rec is not None:
+                rec[n][0].record(stream)
+            tg.tft_ex(dev[n], l, n, n, N, 0, stride, stream=stream)
+            if rec is not None:
+                rec[n][1].record(stream)
+            tg.itft_ex(dev[n], l, n, n, 0, N, 0, stride, 1, stream=stream)
+            if rec is not None:
+                rec[n][2].record(stream)
+
+    def sync():
+        torch.cuda.synchronize(device)
+
+    clocks = ClockSampler(local)
+    # warm-up, then exactly K timed steps between barriers and device syncs
+    for _ in range(args.warmup):
+        step()
+    sync()
+    barrier(device)
+    sync()
+    clocks.start()
+    start, stop = mk(), mk()
+    t0 = time.perf_counter()
+    start.record(stream)
+    for k in range(args.steps):
+        step(ev[k])
+    stop.record(stream)
+    sync()
+    barrier(device)
+    sync()
+    wall = time.perf_counter() - t0
+    clk = clocks.stop()
+    dev_ms = start.elapsed_time(stop)
+    elapsed = max_over_ranks(dev_ms / 1e3, device)
+    per_n = {n: [0.0, 0.0] for n in ns}
+    for k in range(args.steps):
+        for n in ns:
+            per_n[n][0] += ev[k][n][0].elapsed_time(ev[k][n][1])
+            per_n[n][1] += ev[k][n][1].elapsed_time(ev[k][n][2])
+
+    # correctness of the timed data: the round trips restore the inputs
+    ok = True
+    for n in ns:
+        back = dev[n].view(-1, stride)[:n, :W].cpu().numpy().view(np.uint64)
+        ok &= bool(np.array_equal(back, host[n].reshape(-1, stride)[:n, :W]))
+
+    sb = step_bytes(N, l, ns)
+    value = sb * args.steps * ws / elapsed / 1e9
+    ktime = sum(a + b for a, b in per_n.values()) / 1e3  # seconds of transform calls
+    achieved = sb * args.steps / ktime / 1e9
+    peak, peak_kind = measured_peak()
+    launches_per_step = sum(tg.transform_plan(0, l, n, n, N)["launches"] + tg.transform_plan(1, l, n, n, N)["launches"]
+                            for n in ns)
+    traffic = recorded_traffic()
+
+    # end to end through the C ABI with host buffers: H2D inputs, TFT, ITFT, D2H results
+    pinned = {n: torch.from_numpy(host[n].view(np.int64)).pin_memory() for n in ns}
+    outp = {n: torch.empty_like(pinned[n]).pin_memory() for n in ns}
+    h2d = sum(pinned[n].numel() * 8 for n in ns)
+
+    def e2e_step():
+        for n in ns:
+            dev[n].copy_(pinned[n], non_blocking=True)
+            tg.tft_ex(dev[n], l, n, n, N, 0, stride, stream=stream)
+            tg.itft_ex(dev[n], l, n, n, 0, N, 0, stride, 1, stream=stream)
+            outp[n].copy_(dev[n], non_blocking=True)
+
+    e2e_secs = timed_steps(e2e_step, max(1, args.steps // 2), 1, sync, device)
+    e2e_value = sb * max(1, args.steps // 2) * ws / e2e_secs / 1e9
+    for n in ns:
+        ok &= bool(np.array_equal(outp[n].numpy().view(np.uint64).reshape(-1, stride)[:n, :W],
+                                  host[n].reshape(-1, stride)[:n, :W]))
+
+    if rank != 0:
+        return 0 if ok else 1
+    cpu = None if args.no_cpu_baseline else cpu_baseline(N, l)
+    line = {
+        "metric": METRIC, "value": round(value, 2), "unit": "GB/s", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(elapsed / args.steps * 1e3, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": "TFT+ITFT round trips over Z/(2^32768+1), L = 2^16, n in "
+                               "{32769, 40000, 45000, 52000, 65536}",
+                   "N": N, "l": l, "ns": ns, "seed": WORKLOAD["seed"], "stride_limbs": stride,
+                   "bytes_per_step": sb, "l2": "inputs larger than L2 (269 MB per buffer)",
+                   "parallelism": f"replicas x{ws}"},
+        "roofline": {"bound": "hbm", "achieved": round(achieved, 2), "peak": peak, "unit": "GB/s",
+                     "frac": round(achieved / peak, 4), "peak_kind": f"{peak_kind} hbm_gbs (burst copy)",
+                     "traffic": traffic.get("dram_bytes_per_launch") if traffic else None,
+                     "kernel": "job_kernel<32> (every launch of the TFT and ITFT calls)"},
+        "per_n_ms": {str(n): [round(a / args.steps, 3), round(b / args.steps, 3)] for n, (a, b) in per_n.items()},
+        "smoothness": {str(n): round((per_n[n][0] + per_n[n][1]) / (per_n[ns[-1]][0] + per_n[ns[-1]][1]), 4)
+                       for n in ns},
+        "e2e": {"value": round(e2e_value, 2), "unit": "GB/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": h2d},
+        "gpu_launches": launches_per_step * args.steps,
+        "clocks": clk,
+        "bit_exact_roundtrip": ok,
+        "wall_s": round(wall, 3),
+    }
+    if cpu is not None:
+        line["cpu_baseline"] = cpu
+    print(json.dumps(line), flush=True)
+    return 0 if ok else 1
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -127,8 +127,9 @@ int zx_plan(int64_t len_f, int64_t bits_f, int64_t len_g, int64_t bits_g, int is
  *          with the needed count). h->is_signed is set to f->is_signed || g->is_signed.
  *   The library owns its scratch (two ring buffers of L cells each), taken from the device's
  *   stream-ordered memory pool on `stream` and returned to it before the call's work ends.
- *   Host data is staged through pinned buffers; when any operand is on the host the call
- *   synchronises `stream` before returning, otherwise it is asynchronous.
+ *   Host operands are copied with cudaMemcpyAsync on `stream` (pinned host memory makes those
+ *   copies asynchronous); when any operand is on the host the call synchronises `stream`
+ *   before returning, otherwise it is asynchronous.
  */
 int zx_mul(const zx_poly *f, const zx_poly *g, zx_poly *h, void *stream);
 
@@ -140,6 +141,19 @@ int zx_mul(const zx_poly *f, const zx_poly *g, zx_poly *h, void *stream);
  * zx_last_error()).
  */
 int zx_mul_batch(const zx_poly *fs, const zx_poly *gs, zx_poly *hs, int count, void *stream);
+
+/* Shape of the launch plan of one transform (host only, no device needed). */
+typedef struct {
+    int32_t passes;    /* passes over global memory */
+    int32_t launches;  /* kernel launches */
+    int64_t jobs;      /* on-chip sub-transforms (one CTA each) */
+    int32_t onchip_l;  /* log2 of the largest sub-transform held in one CTA's shared memory */
+    int32_t K;         /* 32-bit words per lane of a ring element */
+} zx_transform_info;
+
+/* Launch plan of tft_ex (kind = 0) or itft_ex (kind = 1) for these sizes; the weight and
+ * stride do not change it. Same argument checks and status codes as the transform calls. */
+int zx_transform_plan(int kind, int l, int64_t z, int64_t n, int f, int64_t N, zx_transform_info *out);
 
 /* Human-readable name of a status code (static storage). */
 const char *zx_strerror(int code);

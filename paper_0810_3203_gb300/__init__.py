@@ -23,7 +23,7 @@ ZX_HOST, ZX_DEVICE = 0, 1
 
 # every entry point the header declares (checked by tests/test_abi.py)
 EXPORTS = ("tft", "tft_ex", "itft", "itft_ex", "zx_plan", "zx_mul", "zx_mul_batch",
-           "zx_strerror", "zx_last_error", "zx_version")
+           "zx_transform_plan", "zx_strerror", "zx_last_error", "zx_version")
 
 _lib = None
 
@@ -45,6 +45,11 @@ class ZxPlanInfo(C.Structure):
     _fields_ = [("l", C.c_int32), ("K", C.c_int32), ("N", C.c_int64), ("n", C.c_int64),
                 ("stride_limbs", C.c_int64), ("limbs_h", C.c_int64), ("scratch_bytes", C.c_int64),
                 ("tft_passes", C.c_int32), ("itft_passes", C.c_int32)]
+
+
+class ZxTransformInfo(C.Structure):
+    _fields_ = [("passes", C.c_int32), ("launches", C.c_int32), ("jobs", C.c_int64),
+                ("onchip_l", C.c_int32), ("K", C.c_int32)]
 
 
 def library_path():
@@ -70,12 +75,14 @@ def load(build_if_missing=True):
     L.zx_plan.argtypes = [i64, i64, i64, i64, i32, C.POINTER(ZxPlanInfo)]
     L.zx_mul.argtypes = [C.POINTER(ZxPoly), C.POINTER(ZxPoly), C.POINTER(ZxPoly), vp]
     L.zx_mul_batch.argtypes = [C.POINTER(ZxPoly), C.POINTER(ZxPoly), C.POINTER(ZxPoly), i32, vp]
+    L.zx_transform_plan.argtypes = [i32, i32, i64, i64, i32, i64, C.POINTER(ZxTransformInfo)]
     L.zx_strerror.argtypes = [i32]
     L.zx_strerror.restype = C.c_char_p
     L.zx_last_error.argtypes = []
     L.zx_last_error.restype = C.c_char_p
     L.zx_version.restype = C.c_char_p
-    for name in ("tft", "tft_ex", "itft", "itft_ex", "zx_plan", "zx_mul", "zx_mul_batch"):
+    for name in ("tft", "tft_ex", "itft", "itft_ex", "zx_plan", "zx_mul", "zx_mul_batch",
+                 "zx_transform_plan"):
         getattr(L, name).restype = i32
     _lib = L
     return L
@@ -134,6 +141,13 @@ def zx_plan(len_f, bits_f, len_g, bits_g, is_signed=False):
     info = ZxPlanInfo()
     _check(load().zx_plan(len_f, bits_f, len_g, bits_g, 1 if is_signed else 0, C.byref(info)), "zx_plan")
     return {k: getattr(info, k) for k, _ in ZxPlanInfo._fields_}
+
+
+def transform_plan(kind, l, z, n, N, f=0):
+    """Launch plan of a TFT (kind 0) or ITFT (kind 1): passes, launches, jobs, onchip_l, K."""
+    info = ZxTransformInfo()
+    _check(load().zx_transform_plan(kind, l, z, n, f, N, C.byref(info)), "zx_transform_plan")
+    return {k: getattr(info, k) for k, _ in ZxTransformInfo._fields_}
 
 
 def _poly(data, length, nlimbs, signed, bits):

@@ -41,19 +41,24 @@ static int check_ring(int l, int64_t N) {
   return ZX_OK;
 }
 
-static int transform(int kind, uint64_t *x, int l, int64_t z, int64_t n, int f, int64_t N, int64_t e,
-                     int64_t stride_limbs, int scale, void *stream) {
-  int rc = check_ring(l, N);
-  if (rc) return rc;
+static int check_sizes(int kind, int l, int64_t z, int64_t n, int f) {
   int64_t L = int64_t(1) << l;
-  if (!x) return fail(ZX_EINVAL, "x is NULL");
-  if (stride_limbs < N / 64 + 1) return fail(ZX_EINVAL, "stride_limbs < N/64 + 1");
   if (kind == KIND_TFT) {
     if (z < 1 || z > L || n < 1 || n > L) return fail(ZX_EINVAL, "TFT needs 1 <= z, n <= L");
   } else {
     if ((f != 0 && f != 1) || z < 1 || z > L || n < 0 || n > z || n + f < 1 || n + f > L)
       return fail(ZX_EINVAL, "ITFT needs 1 <= z <= L, 0 <= n <= z, 1 <= n + f <= L, f in {0,1}");
   }
+  return ZX_OK;
+}
+
+static int transform(int kind, uint64_t *x, int l, int64_t z, int64_t n, int f, int64_t N, int64_t e,
+                     int64_t stride_limbs, int scale, void *stream) {
+  int rc = check_ring(l, N);
+  if (rc) return rc;
+  if (!x) return fail(ZX_EINVAL, "x is NULL");
+  if (stride_limbs < N / 64 + 1) return fail(ZX_EINVAL, "stride_limbs < N/64 + 1");
+  if ((rc = check_sizes(kind, l, z, n, f))) return rc;
   int err = ZX_OK;
   const TransformPlan *p = get_transform_plan(kind, l, z, n, f, N, e, stride_limbs, scale, &err);
   if (!p) return err ? fail(err, "planning failed") : fail(ZX_ECUDA, "planning failed");
@@ -137,6 +142,24 @@ int itft_ex(uint64_t *x, int l, int64_t z, int64_t n, int f, int64_t N, int64_t 
 
 int itft(uint64_t *x, int l, int64_t n, int64_t N, void *stream) {
   return transform(KIND_ITFT, x, l, n, n, 0, N, 0, N / 64 + 1, 1, stream);
+}
+
+int zx_transform_plan(int kind, int l, int64_t z, int64_t n, int f, int64_t N, zx_transform_info *out) {
+  if (!out) return fail(ZX_EINVAL, "out is NULL");
+  if (kind != KIND_TFT && kind != KIND_ITFT) return fail(ZX_EINVAL, "kind must be 0 (TFT) or 1 (ITFT)");
+  int rc = check_ring(l, N);
+  if (rc) return rc;
+  if ((rc = check_sizes(kind, l, z, n, f))) return rc;
+  std::memset(out, 0, sizeof *out);
+  int passes = 0, launches = 0, onchip = 0;
+  int64_t jobs = 0;
+  plan_shape(kind, l, z, n, f, N, &passes, &launches, &jobs, &onchip);
+  out->passes = passes;
+  out->launches = launches;
+  out->jobs = jobs;
+  out->onchip_l = onchip;
+  out->K = make_ring(N).K;
+  return ZX_OK;
 }
 
 int zx_plan(int64_t len_f, int64_t bits_f, int64_t len_g, int64_t bits_g, int is_signed, zx_plan_info *out) {

@@ -58,6 +58,9 @@ const TransformPlan *get_transform_plan(int kind, int l, int64_t z, int64_t n, i
 
 // Number of global-memory passes of a transform (host only; no device needed).
 int count_passes(int kind, int l, int64_t z, int64_t n, int f, int64_t N);
+// passes, launches and jobs of a transform's plan (host only)
+void plan_shape(int kind, int l, int64_t z, int64_t n, int f, int64_t N, int *passes, int *launches,
+                int64_t *jobs, int *onchip_l);
 
 // Enqueue a plan on a stream.
 cudaError_t run_transform(const TransformPlan &p, uint64_t *x, int64_t stride_limbs,

@@ -195,6 +195,22 @@ int count_passes(int kind, int l, int64_t z, int64_t n, int f, int64_t N) {
   return kind == KIND_TFT ? P.tft(0, 0, 1, l, 0, z, n) : P.itft(0, 0, 1, l, 0, z, n, f, -1);
 }
 
+void plan_shape(int kind, int l, int64_t z, int64_t n, int f, int64_t N, int *passes, int *launches,
+                int64_t *jobs, int *onchip_l) {
+  Planner P;
+  P.ring = make_ring(N);
+  P.twoN = 2 * N;
+  P.ls_max = max_onchip_ls(P.ring);
+  *passes = kind == KIND_TFT ? P.tft(0, 0, 1, l, 0, z, n) : P.itft(0, 0, 1, l, 0, z, n, f, -1);
+  std::vector<std::pair<int, int>> groups;
+  for (const JobRec &j : P.jobs) groups.push_back({j.pass, j.ls});
+  std::sort(groups.begin(), groups.end());
+  groups.erase(std::unique(groups.begin(), groups.end()), groups.end());
+  *launches = int(groups.size());
+  *jobs = int64_t(P.jobs.size());
+  *onchip_l = std::min(l, P.ls_max);
+}
+
 const TransformPlan *get_transform_plan(int kind, int l, int64_t z, int64_t n, int f, int64_t N,
                                         int64_t e, int64_t stride_limbs, int scale, int *err) {
   int dev = 0;
