@@ -410,6 +410,29 @@ def run_gpu(args):
     return 0 if ok else 1
 
 
+def run_profile_case(args):
+    """One TFT and one ITFT at n = 40000 on one 269 MB buffer (the case ncu captures)."""
+    import numpy as np
+    import torch
+
+    import paper_0810_3203_gb300 as tg
+
+    tg.load()
+    N, l, n = WORKLOAD["N"], WORKLOAD["l"], 40000
+    W = N // 64 + 1
+    stride = W + (W & 1)
+    x = workloads.residues(WORKLOAD["seed"], n, N, stride=stride, cells=1 << l)
+    d = torch.from_numpy(x.view(np.int64)).cuda()
+    for _ in range(args.profile_reps):
+        tg.tft_ex(d, l, n, n, N, 0, stride)
+        tg.itft_ex(d, l, n, n, 0, N, 0, stride, 1)
+    torch.cuda.synchronize()
+    back = d.view(-1, stride)[:n, :W].cpu().numpy().view(np.uint64)
+    ok = bool(np.array_equal(back, x.reshape(-1, stride)[:n, :W]))
+    print(json.dumps({"profile_case": "tft+itft n=40000 l=16 N=32768", "reps": args.profile_reps, "ok": ok}))
+    return 0 if ok else 1
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -417,7 +440,12 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-case", action="store_true",
+                    help="run one TFT + ITFT at n = 40000 and exit (the case profiled with ncu)")
+    ap.add_argument("--profile-reps", type=int, default=1)
     args = ap.parse_args()
+    if args.profile_case:
+        return run_profile_case(args)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":

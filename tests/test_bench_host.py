@@ -1,0 +1,69 @@
+"""Host logic of bench.py: the algorithmic byte counts and the multi-rank timing (replicas on
+two gloo ranks on the CPU; no GPU)."""
+import os
+import socket
+import time
+
+import pytest
+
+import bench
+
+
+def test_full_transform_moves_every_cell_four_times():
+    # z = n = L: both passes of Algorithm 1 read and write all L cells; Algorithm 2 likewise
+    for l in (2, 5, 8, 16):
+        L = 1 << l
+        assert bench.alg_cells_tft(l, L, L) == 4 * L
+        assert bench.alg_cells_itft(l, L, L) == 4 * L
+
+
+def test_truncated_counts():
+    # L = 2^16, n = z = 40000: 157 partial-height rows of 256 cells after the column pass
+    l, n = 16, 40000
+    assert bench.alg_cells_tft(l, n, n) == n + 157 * 256 + 157 * 256 + n
+    # counts never exceed the full transform and grow with n
+    prev = 0
+    for n in (1, 2, 255, 256, 257, 32769, 40000, 65535, 65536):
+        c = bench.alg_cells_tft(l, n, n)
+        assert prev <= c <= 4 * 65536
+        prev = c
+        assert bench.alg_cells_itft(l, n, n) <= 4 * 65536
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    p = s.getsockname()[1]
+    s.close()
+    return p
+
+
+def _rank_main(rank, world, port, out):
+    os.environ.update(RANK=str(rank), WORLD_SIZE=str(world), LOCAL_RANK=str(rank),
+                      MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    import torch.distributed as dist
+    ws, r = bench.dist_init("gloo")
+    delay = 0.05 * (rank + 1)
+    secs = bench.timed_steps(lambda: time.sleep(delay), steps=3, warmup=3, sync=lambda: None)
+    out.put((r, ws, secs))
+    dist.destroy_process_group()
+
+
+@pytest.mark.timeout(120)
+def test_two_rank_replicas_take_the_slowest_rank():
+    import torch.multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_rank_main, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    res = [q.get(timeout=100) for _ in procs]
+    for p in procs:
+        p.join(timeout=30)
+        assert p.exitcode == 0
+    res.sort()
+    assert [r for r, _, _ in res] == [0, 1] and all(ws == 2 for _, ws, _ in res)
+    # both ranks report the same (slowest) time, at least rank 1's 3 x 0.1 s
+    assert abs(res[0][2] - res[1][2]) < 1e-9
+    assert res[0][2] >= 0.3
