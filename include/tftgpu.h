@@ -142,6 +142,24 @@ int zx_mul(const zx_poly *f, const zx_poly *g, zx_poly *h, void *stream);
  */
 int zx_mul_batch(const zx_poly *fs, const zx_poly *gs, zx_poly *hs, int count, void *stream);
 
+/*
+ * zx_mul without any memory allocation. The paper has no counterpart; this entry point serves
+ * callers that cannot call cudaMalloc, e.g. code whose device memory is entirely reserved by
+ * another allocator, or a loop that must not pay an allocation's latency and implicit
+ * synchronisation. Same product, same rules for h as zx_mul, with these differences:
+ *   - f, g and h must all be in device memory (ZX_EINVAL otherwise);
+ *   - the ring buffers live in a fixed 20 MiB device array of the library (16 MiB for the two
+ *     ring buffers, 4 MiB for launch plans), held by every GPU that loads the library until the
+ *     process exits; a product whose two ring buffers (2 L stride_limbs 8 bytes, see zx_plan)
+ *     exceed 16 MiB is rejected with ZX_EUNSUPPORTED, and ZX_ENOMEM reports a full plan region;
+ *   - the first call on a device looks up that array's address (cudaGetSymbolAddress) with the
+ *     device current, so make the first call on each device before any stream capture;
+ *   - all calls share the array: calls whose GPU work overlaps (different streams or threads
+ *     without ordering between them) race. Order them on one stream.
+ * It calls no cudaMalloc, cudaFree or other allocating routine; the call is asynchronous.
+ */
+int zx_mul_noalloc(const zx_poly *f, const zx_poly *g, zx_poly *h, void *stream);
+
 /* Shape of the launch plan of one transform (host only, no device needed). */
 typedef struct {
     int32_t passes;    /* passes over global memory */

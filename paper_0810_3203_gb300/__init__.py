@@ -23,7 +23,7 @@ ZX_HOST, ZX_DEVICE = 0, 1
 
 # every entry point the header declares (checked by tests/test_abi.py)
 EXPORTS = ("tft", "tft_ex", "itft", "itft_ex", "zx_plan", "zx_mul", "zx_mul_batch",
-           "zx_transform_plan", "zx_strerror", "zx_last_error", "zx_version")
+           "zx_transform_plan", "zx_mul_noalloc", "zx_strerror", "zx_last_error", "zx_version")
 
 _lib = None
 
@@ -76,13 +76,14 @@ def load(build_if_missing=True):
     L.zx_mul.argtypes = [C.POINTER(ZxPoly), C.POINTER(ZxPoly), C.POINTER(ZxPoly), vp]
     L.zx_mul_batch.argtypes = [C.POINTER(ZxPoly), C.POINTER(ZxPoly), C.POINTER(ZxPoly), i32, vp]
     L.zx_transform_plan.argtypes = [i32, i32, i64, i64, i32, i64, C.POINTER(ZxTransformInfo)]
+    L.zx_mul_noalloc.argtypes = [C.POINTER(ZxPoly), C.POINTER(ZxPoly), C.POINTER(ZxPoly), vp]
     L.zx_strerror.argtypes = [i32]
     L.zx_strerror.restype = C.c_char_p
     L.zx_last_error.argtypes = []
     L.zx_last_error.restype = C.c_char_p
     L.zx_version.restype = C.c_char_p
     for name in ("tft", "tft_ex", "itft", "itft_ex", "zx_plan", "zx_mul", "zx_mul_batch",
-                 "zx_transform_plan"):
+                 "zx_transform_plan", "zx_mul_noalloc"):
         getattr(L, name).restype = i32
     _lib = L
     return L
@@ -167,6 +168,16 @@ def zx_mul(f, len_f, limbs_f, g, len_g, limbs_g, h, limbs_h, signed=False, bits_
     G = _poly(g, len_g, limbs_g, signed, bits_g)
     H = _poly(h, len_f + len_g - 1, limbs_h, signed, 0)
     _check(load().zx_mul(C.byref(F), C.byref(G), C.byref(H), _stream(stream)), "zx_mul")
+
+
+def zx_mul_noalloc(f, len_f, limbs_f, g, len_g, limbs_g, h, limbs_h, signed=False, bits_f=0,
+                   bits_g=0, stream=None):
+    """zx_mul for callers that cannot allocate: every operand a CUDA tensor; the library's
+    fixed 20 MiB device array holds the ring buffers (see include/tftgpu.h)."""
+    F = _poly(f, len_f, limbs_f, signed, bits_f)
+    G = _poly(g, len_g, limbs_g, signed, bits_g)
+    H = _poly(h, len_f + len_g - 1, limbs_h, signed, 0)
+    _check(load().zx_mul_noalloc(C.byref(F), C.byref(G), C.byref(H), _stream(stream)), "zx_mul_noalloc")
 
 
 def zx_mul_batch(items, stream=None):

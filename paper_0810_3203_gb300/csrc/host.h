@@ -62,6 +62,22 @@ int count_passes(int kind, int l, int64_t z, int64_t n, int f, int64_t N);
 void plan_shape(int kind, int l, int64_t z, int64_t n, int f, int64_t N, int *passes, int *launches,
                 int64_t *jobs, int *onchip_l);
 
+// Host-side image of a transform plan: the launches with their job lists and the distinct
+// program images they use (JobDesc::prog is left null; prog_index names the image).
+struct HostPlan {
+  struct Group {
+    int ls = 0, nwarps = 0;
+    std::vector<JobDesc> jobs;
+    std::vector<int> prog_index;
+  };
+  Ring ring;
+  int npasses = 0;
+  std::vector<Group> groups;
+  std::vector<std::vector<uint32_t>> programs;
+};
+void build_host_plan(int kind, int l, int64_t z, int64_t n, int f, int64_t N, int64_t e, int scale,
+                     HostPlan *out);
+
 // Enqueue a plan on a stream.
 cudaError_t run_transform(const TransformPlan &p, uint64_t *x, int64_t stride_limbs,
                           cudaStream_t s);

@@ -211,6 +211,47 @@ void plan_shape(int kind, int l, int64_t z, int64_t n, int f, int64_t N, int *pa
   *onchip_l = std::min(l, P.ls_max);
 }
 
+void build_host_plan(int kind, int l, int64_t z, int64_t n, int f, int64_t N, int64_t e, int scale,
+                     HostPlan *out) {
+  int64_t twoN = 2 * N;
+  e = md(e, twoN);
+  Planner P;
+  P.ring = make_ring(N);
+  P.twoN = twoN;
+  P.ls_max = max_onchip_ls(P.ring);
+  out->ring = P.ring;
+  out->npasses = kind == KIND_TFT ? P.tft(0, 0, 1, l, e, z, n)
+                                  : P.itft(0, 0, 1, l, e, z, n, f, scale ? md(twoN - l, twoN) : -1);
+  std::map<std::tuple<int, int, int64_t, int64_t, int>, int> index;
+  std::stable_sort(P.jobs.begin(), P.jobs.end(), [](const JobRec &a, const JobRec &b) {
+    return a.pass != b.pass ? a.pass < b.pass : a.ls < b.ls;
+  });
+  for (size_t i = 0; i < P.jobs.size();) {
+    size_t k = i;
+    while (k < P.jobs.size() && P.jobs[k].pass == P.jobs[i].pass && P.jobs[k].ls == P.jobs[i].ls) k++;
+    HostPlan::Group g;
+    g.ls = P.jobs[i].ls;
+    g.nwarps = warps_for(g.ls, P.ring.K);
+    for (size_t t = i; t < k; t++) {
+      const JobRec &j = P.jobs[t];
+      auto key = std::make_tuple(j.kind, j.ls, j.z, j.n, j.f);
+      auto it = index.find(key);
+      int pi;
+      if (it == index.end()) {
+        pi = int(out->programs.size());
+        out->programs.push_back(build_program(j.kind, j.ls, j.z, j.n, j.f, N, nullptr));
+        index[key] = pi;
+      } else {
+        pi = it->second;
+      }
+      g.jobs.push_back(j.d);
+      g.prog_index.push_back(pi);
+    }
+    out->groups.push_back(std::move(g));
+    i = k;
+  }
+}
+
 const TransformPlan *get_transform_plan(int kind, int l, int64_t z, int64_t n, int f, int64_t N,
                                         int64_t e, int64_t stride_limbs, int scale, int *err) {
   int dev = 0;
