@@ -165,13 +165,27 @@ typedef struct {
     int32_t passes;    /* passes over global memory */
     int32_t launches;  /* kernel launches */
     int64_t jobs;      /* on-chip sub-transforms (one CTA each) */
-    int32_t onchip_l;  /* log2 of the largest sub-transform held in one CTA's shared memory */
+    int32_t onchip_l;  /* log2 of the largest sub-transform held on chip by one job */
     int32_t K;         /* 32-bit words per lane of a ring element */
+    int32_t cluster_l; /* log2 of the CTAs per job (thread-block cluster; 0: single CTA) */
+    int32_t pad;
 } zx_transform_info;
 
 /* Launch plan of tft_ex (kind = 0) or itft_ex (kind = 1) for these sizes; the weight and
  * stride do not change it. Same argument checks and status codes as the transform calls. */
 int zx_transform_plan(int kind, int l, int64_t z, int64_t n, int f, int64_t N, zx_transform_info *out);
+
+/*
+ * The on-chip schedule of one job (host only): a sub-transform of 2^ls cells (TFT: kind 0,
+ * ITFT: kind 1) with the given z, n, f over Z/(2^N+1), spread over 2^lc CTAs of a cluster.
+ * Writes the job image -- header [nstages, C, load layout, store layout], per stage
+ * [type, arg, per-CTA program offsets], then per-CTA programs of leveled base-case butterflies
+ * of Algorithms 1 and 2 (see paper_0810_3203_gb300/csrc/common.h for the word layout) -- into
+ * buf (cap_words uint32 words) and its length into *size_words. ZX_EBUFSIZE when buf is too
+ * small (the needed length is still written), ZX_EINVAL on bad sizes. For inspection and tests.
+ */
+int zx_job_program(int kind, int ls, int lc, int64_t z, int64_t n, int f, int64_t N, uint32_t *buf,
+                   int64_t cap_words, int64_t *size_words);
 
 /* Human-readable name of a status code (static storage). */
 const char *zx_strerror(int code);

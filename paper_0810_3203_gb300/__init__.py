@@ -23,7 +23,8 @@ ZX_HOST, ZX_DEVICE = 0, 1
 
 # every entry point the header declares (checked by tests/test_abi.py)
 EXPORTS = ("tft", "tft_ex", "itft", "itft_ex", "zx_plan", "zx_mul", "zx_mul_batch",
-           "zx_transform_plan", "zx_mul_noalloc", "zx_strerror", "zx_last_error", "zx_version")
+           "zx_transform_plan", "zx_mul_noalloc", "zx_job_program", "zx_strerror", "zx_last_error",
+           "zx_version")
 
 _lib = None
 
@@ -49,7 +50,7 @@ class ZxPlanInfo(C.Structure):
 
 class ZxTransformInfo(C.Structure):
     _fields_ = [("passes", C.c_int32), ("launches", C.c_int32), ("jobs", C.c_int64),
-                ("onchip_l", C.c_int32), ("K", C.c_int32)]
+                ("onchip_l", C.c_int32), ("K", C.c_int32), ("cluster_l", C.c_int32), ("pad", C.c_int32)]
 
 
 def library_path():
@@ -77,13 +78,15 @@ def load(build_if_missing=True):
     L.zx_mul_batch.argtypes = [C.POINTER(ZxPoly), C.POINTER(ZxPoly), C.POINTER(ZxPoly), i32, vp]
     L.zx_transform_plan.argtypes = [i32, i32, i64, i64, i32, i64, C.POINTER(ZxTransformInfo)]
     L.zx_mul_noalloc.argtypes = [C.POINTER(ZxPoly), C.POINTER(ZxPoly), C.POINTER(ZxPoly), vp]
+    L.zx_job_program.argtypes = [i32, i32, i32, i64, i64, i32, i64, C.POINTER(C.c_uint32), i64,
+                                 C.POINTER(C.c_int64)]
     L.zx_strerror.argtypes = [i32]
     L.zx_strerror.restype = C.c_char_p
     L.zx_last_error.argtypes = []
     L.zx_last_error.restype = C.c_char_p
     L.zx_version.restype = C.c_char_p
     for name in ("tft", "tft_ex", "itft", "itft_ex", "zx_plan", "zx_mul", "zx_mul_batch",
-                 "zx_transform_plan", "zx_mul_noalloc"):
+                 "zx_transform_plan", "zx_mul_noalloc", "zx_job_program"):
         getattr(L, name).restype = i32
     _lib = L
     return L
@@ -149,6 +152,17 @@ def transform_plan(kind, l, z, n, N, f=0):
     info = ZxTransformInfo()
     _check(load().zx_transform_plan(kind, l, z, n, f, N, C.byref(info)), "zx_transform_plan")
     return {k: getattr(info, k) for k, _ in ZxTransformInfo._fields_}
+
+
+def job_program(kind, ls, lc, z, n, N, f=0):
+    """Job image of one on-chip sub-transform (see zx_job_program in include/tftgpu.h), as a
+    numpy uint32 array."""
+    size = C.c_int64(0)
+    load().zx_job_program(kind, ls, lc, z, n, f, N, None, 0, C.byref(size))
+    buf = np.zeros(max(1, size.value), np.uint32)
+    _check(load().zx_job_program(kind, ls, lc, z, n, f, N, buf.ctypes.data_as(C.POINTER(C.c_uint32)),
+                                 buf.size, C.byref(size)), "zx_job_program")
+    return buf[:size.value]
 
 
 def _poly(data, length, nlimbs, signed, bits):

@@ -6,6 +6,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <vector>
 
 #include "../../include/tftgpu.h"
 #include "common.h"
@@ -151,14 +152,32 @@ int zx_transform_plan(int kind, int l, int64_t z, int64_t n, int f, int64_t N, z
   if (rc) return rc;
   if ((rc = check_sizes(kind, l, z, n, f))) return rc;
   std::memset(out, 0, sizeof *out);
-  int passes = 0, launches = 0, onchip = 0;
+  int passes = 0, launches = 0, onchip = 0, cl = 0;
   int64_t jobs = 0;
-  plan_shape(kind, l, z, n, f, N, &passes, &launches, &jobs, &onchip);
+  plan_shape(kind, l, z, n, f, N, &passes, &launches, &jobs, &onchip, &cl);
+  out->cluster_l = cl;
   out->passes = passes;
   out->launches = launches;
   out->jobs = jobs;
   out->onchip_l = onchip;
   out->K = make_ring(N).K;
+  return ZX_OK;
+}
+
+int zx_job_program(int kind, int ls, int lc, int64_t z, int64_t n, int f, int64_t N, uint32_t *buf,
+                   int64_t cap_words, int64_t *size_words) {
+  if (!size_words) return fail(ZX_EINVAL, "size_words is NULL");
+  if (kind != KIND_TFT && kind != KIND_ITFT) return fail(ZX_EINVAL, "kind must be 0 (TFT) or 1 (ITFT)");
+  if (lc < 0 || lc > kMaxClusterLog2 || ls < 1 || ls - lc < lc || ls - lc < 1 || ls > 16)
+    return fail(ZX_EINVAL, "need 1 <= ls <= 16 and 0 <= lc <= 4 with 2 lc <= ls");
+  if (N < 64 || N % 64 != 0 || (2 * N) % (int64_t(1) << ls) != 0)
+    return fail(ZX_EINVAL, "N must be a multiple of 64 with 2^ls | 2N");
+  int rc = check_sizes(kind, ls, z, n, f);
+  if (rc) return rc;
+  std::vector<uint32_t> img = build_job_image(kind, ls, lc, z, n, f, N, nullptr);
+  *size_words = int64_t(img.size());
+  if (!buf || cap_words < int64_t(img.size())) return fail(ZX_EBUFSIZE, "buffer too small for the job image");
+  std::memcpy(buf, img.data(), img.size() * 4);
   return ZX_OK;
 }
 

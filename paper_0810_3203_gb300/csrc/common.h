@@ -13,12 +13,12 @@ namespace tftgpu {
 
 // ---------------------------------------------------------------- on-chip programs
 //
-// A sub-transform that fits in one CTA's shared memory is executed as a "program": the
-// butterflies of Algorithm 1 or 2 (recursing down to the L = 2 base cases) listed in
-// dependency levels. Ops of one level touch disjoint cells and run on different warps; a
-// block barrier separates levels. Rotation amounts are affine in the weight exponent e of
-// the job that runs the program: amount = (mul * e + add) mod 2N, because the recursion
-// turns zeta into zeta * omega^u (e + u w) or zeta^{L1} (e L1), both affine in e.
+// A sub-transform held on chip is executed as a "program": the base-case butterflies of
+// Algorithm 1 or 2 (recursing down to L = 2) listed in dependency levels. Ops of one level
+// touch disjoint cells and run on different warps; a block barrier separates levels.
+// Rotation amounts are affine in the weight exponent e of the job that runs the program:
+// amount = (mul * e + add) mod 2N, because the recursion turns zeta into zeta * omega^u
+// (e + u w) or zeta^{L1} (e L1), both affine in e.
 
 enum OpKind : uint8_t {
   OP_BF = 1,     // A = x_i 2^ra, B = x_j 2^rb; outputs S = A + B and/or D = A - B
@@ -46,21 +46,41 @@ struct OpDesc {
 };
 static_assert(sizeof(OpDesc) == 40, "OpDesc layout");
 
-// Program image in device memory (uint32 words):
+// Program image (uint32 words):
 //   [0] nlevels  [1] nops  [2 .. 2+nlevels] level starts (op indices)  then OpDesc[nops]
 // (the op array starts at word 4 + nlevels rounded up to a multiple of 2 for 8-byte alignment)
 TFT_HD inline int prog_ops_offset_words(int nlevels) { return (3 + nlevels + 1) & ~1; }
 
-// ---------------------------------------------------------------- jobs
+// ---------------------------------------------------------------- jobs and stages
 //
-// A job runs one program on Ls = 2^ls cells of the caller's buffer: cell m of the job is
-// cell (cell0 + m * mstride) of the buffer. Cells [0, nload) are read on entry (the others
-// are implicit zeros), cells [0, nstore) are written back; of those, [0, nscale) are
-// multiplied by 2^escale on the way out (the ITFT's final division by L).
+// A job transforms Ls = 2^ls cells of the caller's buffer: cell m of the job is buffer cell
+// (cell0 + m * mstride). It runs on a cluster of C = 2^lc CTAs (C = 1: a single CTA); each CTA
+// holds Ls / C cells in shared memory. For C > 1 the job's sub-transform is split once more
+// into C x (Ls / C) (Eqs. b-cols / b-rows with L1 = C): in "row layout" CTA r holds row r
+// (cells r L2 + k), in "column layout" CTA c holds columns [c b, c b + b) with b = L2 / C
+// (cell j L2 + c b + i at slot j b + i). A job image lists the stages the CTAs run:
+//   STAGE_PROG  every CTA runs its own program (word offset per CTA, 0 = nothing to do)
+//   STAGE_XCHG  switch between row and column layout: CTA x swaps its slots [y b, y b + b)
+//               with CTA y's slots [x b, x b + b) through distributed shared memory
+//   STAGE_SWAP  the same swap restricted to pairs that involve CTA `arg` (brings row `arg`
+//               of the column layout into CTA `arg`, or back)
+//
+// Job image (uint32 words):
+//   [0] nstages [1] C [2] load layout [3] store layout (0 row, 1 column)
+//   then per stage: type, arg, offset[C]; then the program images (8-byte aligned)
+enum StageType : uint32_t { STAGE_PROG = 0, STAGE_XCHG = 1, STAGE_SWAP = 2 };
+enum Layout : uint32_t { LAYOUT_ROW = 0, LAYOUT_COL = 1 };
+
+TFT_HD inline int job_stage_words(int C) { return 2 + C; }
+TFT_HD inline int job_header_words() { return 4; }
+
+// Cells [0, nload) are read on entry (the others are implicit zeros), cells [0, nstore) are
+// written back; of those, [0, nscale) are multiplied by 2^escale on the way out (the ITFT's
+// final division by L).
 struct JobDesc {
   int64_t cell0;
   int64_t mstride;
-  const uint32_t *prog;
+  const uint32_t *image;
   int32_t e;
   int32_t nload;
   int32_t nstore;
@@ -71,8 +91,9 @@ struct JobDesc {
 static_assert(sizeof(JobDesc) == 48, "JobDesc layout");
 
 // shared-memory geometry of one cell: NW = N/32 words, one padding word per 32 so that the
-// lane-chunked accesses of a warp hit 32 different banks
-TFT_HD inline int cell_pitch_words(int NW) { return NW + NW / 32 + 1; }
+// lane-chunked accesses of a warp hit 32 different banks, rounded up to 16 bytes so that every
+// cell can be copied as a block of 16-byte vectors
+TFT_HD inline int cell_pitch_words(int NW) { return (NW + NW / 32 + 1 + 3) & ~3; }
 
 // words per lane (K) for a ring of NW 32-bit words: 1 for NW <= 32, else NW/32 rounded up to
 // a power of two (NW is a multiple of 32 then)

@@ -22,6 +22,13 @@ struct ProgramStats {
 std::vector<uint32_t> build_program(int kind, int ls, int64_t z, int64_t n, int f, int64_t N,
                                     ProgramStats *stats);
 
+// Job image (stage table plus per-CTA programs, see common.h) for a job of 2^ls cells on a
+// cluster of 2^lc CTAs.
+// Largest per-CTA program (words) in a job image.
+int image_max_program_words(const std::vector<uint32_t> &img);
+std::vector<uint32_t> build_job_image(int kind, int ls, int lc, int64_t z, int64_t n, int f, int64_t N,
+                                      ProgramStats *stats);
+
 // Ring geometry used by the kernels.
 struct Ring {
   int64_t N = 0;
@@ -33,14 +40,21 @@ struct Ring {
 bool ring_supported(int64_t N);
 Ring make_ring(int64_t N);
 
-// Largest on-chip sub-transform (log2 of its cell count) for this ring.
+// Largest sub-transform (log2 of its cell count) one CTA holds in shared memory.
 int max_onchip_ls(const Ring &r);
+// Cells (log2) per CTA of a cluster job: small enough that two CTAs share an SM, so that the
+// stages of one job overlap with those of another.
+int cluster_cta_ls(const Ring &r);
+// Largest cluster (log2 of its CTA count) a job may use (16 CTAs: a non-portable size).
+constexpr int kMaxClusterLog2 = 4;
 
 // One kernel launch: jobs of equal ls.
 struct Launch {
   int ls = 0;
+  int lc = 0;  // cluster of 2^lc CTAs per job
   int nwarps = 0;
   int njobs = 0;
+  int prog_words = 0;  // largest per-CTA program of the launch (shared-memory staging size)
   JobDesc *d_jobs = nullptr;  // device copy (owned by the plan cache)
 };
 
@@ -60,13 +74,13 @@ const TransformPlan *get_transform_plan(int kind, int l, int64_t z, int64_t n, i
 int count_passes(int kind, int l, int64_t z, int64_t n, int f, int64_t N);
 // passes, launches and jobs of a transform's plan (host only)
 void plan_shape(int kind, int l, int64_t z, int64_t n, int f, int64_t N, int *passes, int *launches,
-                int64_t *jobs, int *onchip_l);
+                int64_t *jobs, int *onchip_l, int *cluster_l);
 
 // Host-side image of a transform plan: the launches with their job lists and the distinct
 // program images they use (JobDesc::prog is left null; prog_index names the image).
 struct HostPlan {
   struct Group {
-    int ls = 0, nwarps = 0;
+    int ls = 0, lc = 0, nwarps = 0, prog_words = 0;
     std::vector<JobDesc> jobs;
     std::vector<int> prog_index;
   };

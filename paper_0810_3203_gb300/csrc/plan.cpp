@@ -1,11 +1,12 @@
 // Transform planning: Algorithms 1 and 2 applied at the level of global memory.
 //
-// A transform of length L = 2^l whose cells fit in one CTA's shared memory is a single job.
-// Otherwise the array is viewed as an L1 x L2 matrix (L1 = 2^floor(l/2), L2 = 2^ceil(l/2), the
-// paper's split) and the column and row sub-transforms are planned recursively, exactly in
-// the order of Algorithm 1 (columns, then rows) or Algorithm 2 (full rows, rightmost columns,
-// last row, leftmost columns). Each recursion level is one pass over global memory; all
-// sub-transforms of a pass are independent and become the jobs of one kernel launch.
+// A transform of length L = 2^l whose cells fit in the shared memory of one CTA, or of a
+// cluster of up to 8 CTAs, is a single job. Otherwise the array is viewed as an L1 x L2 matrix
+// (L1 = 2^floor(l/2), L2 = 2^ceil(l/2), the paper's split) and the column and row
+// sub-transforms are planned recursively, exactly in the order of Algorithm 1 (columns, then
+// rows) or Algorithm 2 (full rows, rightmost columns, last row, leftmost columns). Each
+// recursion level is one pass over global memory; all sub-transforms of a pass are
+// independent and become the jobs of one kernel launch.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -46,6 +47,12 @@ int max_onchip_ls(const Ring &r) {
   return ls;
 }
 
+int cluster_cta_ls(const Ring &r) {
+  int ls = 1;
+  while (ls < 16 && size_t(2 << ls) * (size_t(r.pitch) + 1) * 4 <= kSmemBudget / 2) ls++;
+  return ls;
+}
+
 namespace {
 
 int64_t md(int64_t a, int64_t m) {
@@ -53,19 +60,26 @@ int64_t md(int64_t a, int64_t m) {
   return r < 0 ? r + m : r;
 }
 
-// device copies of program images, keyed by (device, kind, ls, z, n, f, N)
-struct ProgramCache {
+// device copies of job images, keyed by (device, kind, ls, lc, z, n, f, N)
+struct ImageCache {
   std::mutex mu;
-  std::map<std::tuple<int, int, int, int64_t, int64_t, int, int64_t>, uint32_t *> progs;
+  std::map<std::tuple<int, int, int, int, int64_t, int64_t, int, int64_t>, uint32_t *> images;
+  std::map<const uint32_t *, int> prog_words;  // largest per-CTA program of each image
 
-  const uint32_t *get(int kind, int ls, int64_t z, int64_t n, int f, int64_t N, int *err) {
+  int max_prog(const uint32_t *d) {
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = prog_words.find(d);
+    return it == prog_words.end() ? 0 : it->second;
+  }
+
+  const uint32_t *get(int kind, int ls, int lc, int64_t z, int64_t n, int f, int64_t N, int *err) {
     int dev = 0;
     cudaGetDevice(&dev);
-    auto key = std::make_tuple(dev, kind, ls, z, n, f, N);
+    auto key = std::make_tuple(dev, kind, ls, lc, z, n, f, N);
     std::lock_guard<std::mutex> lk(mu);
-    auto it = progs.find(key);
-    if (it != progs.end()) return it->second;
-    std::vector<uint32_t> img = build_program(kind, ls, z, n, f, N, nullptr);
+    auto it = images.find(key);
+    if (it != images.end()) return it->second;
+    std::vector<uint32_t> img = build_job_image(kind, ls, lc, z, n, f, N, nullptr);
     uint32_t *d = nullptr;
     if (cudaMalloc(&d, img.size() * 4) != cudaSuccess) {
       *err = ZX_ENOMEM;
@@ -76,19 +90,21 @@ struct ProgramCache {
       *err = ZX_ECUDA;
       return nullptr;
     }
-    progs[key] = d;
+    images[key] = d;
+    prog_words[d] = image_max_program_words(img);
     return d;
   }
 };
 
-ProgramCache &prog_cache() {
-  static ProgramCache *c = new ProgramCache();
+ImageCache &image_cache() {
+  static ImageCache *c = new ImageCache();
   return *c;
 }
 
 struct JobRec {
   int pass;
   int ls;
+  int lc;
   int kind;
   int64_t z, n;
   int f;
@@ -98,8 +114,17 @@ struct JobRec {
 struct Planner {
   Ring ring;
   int64_t twoN;
-  int ls_max;
+  int ls_max;  // largest job held by one CTA
+  int ls_c;    // cells (log2) per CTA of a cluster job
   std::vector<JobRec> jobs;
+
+  // single CTA up to ls_max; a cluster of up to 16 CTAs of 2^ls_c cells above that, as long as
+  // every CTA row of the job's split holds at least one cell per CTA (2 lc <= l)
+  int cluster_log2(int l) const { return l <= ls_max ? 0 : l - ls_c; }
+  bool leaf(int l) const {
+    const int lc = cluster_log2(l);
+    return lc == 0 || (lc <= kMaxClusterLog2 && 2 * lc <= l);
+  }
 
   void job(int pass, int kind, int64_t cell0, int64_t ms, int l, int64_t e, int64_t z, int64_t n,
            int f, int64_t nscale, int64_t escale) {
@@ -107,6 +132,7 @@ struct Planner {
     std::memset(&j, 0, sizeof j);
     j.pass = pass;
     j.ls = l;
+    j.lc = cluster_log2(l);
     j.kind = kind;
     j.z = z;
     j.n = n;
@@ -123,7 +149,7 @@ struct Planner {
 
   // Algorithm 1 over global memory; returns the number of passes used
   int tft(int pass, int64_t cell0, int64_t ms, int l, int64_t e, int64_t z, int64_t n) {
-    if (l <= ls_max) {
+    if (leaf(l)) {
       job(pass, KIND_TFT, cell0, ms, l, e, z, n, 0, 0, 0);
       return 1;
     }
@@ -143,7 +169,7 @@ struct Planner {
   // escale >= 0; the f = 1 output a-hat_n never is.
   int itft(int pass, int64_t cell0, int64_t ms, int l, int64_t e, int64_t z, int64_t n, int f,
            int64_t escale) {
-    if (l <= ls_max) {
+    if (leaf(l)) {
       job(pass, KIND_ITFT, cell0, ms, l, e, z, n, f, escale >= 0 ? n : 0, escale >= 0 ? escale : 0);
       return 1;
     }
@@ -179,10 +205,17 @@ PlanCache &plan_cache() {
   return *c;
 }
 
-int warps_for(int ls, int K) {
-  int half = 1 << (ls > 0 ? ls - 1 : 0);  // butterflies per level at most
-  int cap = K >= 16 ? 16 : 16;
-  return std::max(1, std::min(cap, half));
+// warps per CTA: one per butterfly of a full level, at most 16
+int warps_for(int ls, int lc) {
+  int nslots = 1 << (ls - lc);
+  return std::max(1, std::min(16, nslots / 2));
+}
+
+bool same_launch(const JobRec &a, const JobRec &b) { return a.pass == b.pass && a.ls == b.ls && a.lc == b.lc; }
+bool launch_order(const JobRec &a, const JobRec &b) {
+  if (a.pass != b.pass) return a.pass < b.pass;
+  if (a.ls != b.ls) return a.ls < b.ls;
+  return a.lc < b.lc;
 }
 
 }  // namespace
@@ -192,23 +225,29 @@ int count_passes(int kind, int l, int64_t z, int64_t n, int f, int64_t N) {
   P.ring = make_ring(N);
   P.twoN = 2 * N;
   P.ls_max = max_onchip_ls(P.ring);
+  P.ls_c = cluster_cta_ls(P.ring);
   return kind == KIND_TFT ? P.tft(0, 0, 1, l, 0, z, n) : P.itft(0, 0, 1, l, 0, z, n, f, -1);
 }
 
 void plan_shape(int kind, int l, int64_t z, int64_t n, int f, int64_t N, int *passes, int *launches,
-                int64_t *jobs, int *onchip_l) {
+                int64_t *jobs, int *onchip_l, int *cluster_l) {
   Planner P;
   P.ring = make_ring(N);
   P.twoN = 2 * N;
   P.ls_max = max_onchip_ls(P.ring);
+  P.ls_c = cluster_cta_ls(P.ring);
   *passes = kind == KIND_TFT ? P.tft(0, 0, 1, l, 0, z, n) : P.itft(0, 0, 1, l, 0, z, n, f, -1);
-  std::vector<std::pair<int, int>> groups;
-  for (const JobRec &j : P.jobs) groups.push_back({j.pass, j.ls});
-  std::sort(groups.begin(), groups.end());
-  groups.erase(std::unique(groups.begin(), groups.end()), groups.end());
-  *launches = int(groups.size());
+  std::sort(P.jobs.begin(), P.jobs.end(), launch_order);
+  int nl = 0, lcmax = 0, lsmax = 0;
+  for (size_t i = 0; i < P.jobs.size(); i++) {
+    if (i == 0 || !same_launch(P.jobs[i], P.jobs[i - 1])) nl++;
+    lcmax = std::max(lcmax, P.jobs[i].lc);
+    lsmax = std::max(lsmax, P.jobs[i].ls);
+  }
+  *launches = nl;
   *jobs = int64_t(P.jobs.size());
-  *onchip_l = std::min(l, P.ls_max);
+  *onchip_l = lsmax;
+  *cluster_l = lcmax;
 }
 
 void build_host_plan(int kind, int l, int64_t z, int64_t n, int f, int64_t N, int64_t e, int scale,
@@ -219,33 +258,35 @@ void build_host_plan(int kind, int l, int64_t z, int64_t n, int f, int64_t N, in
   P.ring = make_ring(N);
   P.twoN = twoN;
   P.ls_max = max_onchip_ls(P.ring);
+  P.ls_c = cluster_cta_ls(P.ring);
   out->ring = P.ring;
   out->npasses = kind == KIND_TFT ? P.tft(0, 0, 1, l, e, z, n)
                                   : P.itft(0, 0, 1, l, e, z, n, f, scale ? md(twoN - l, twoN) : -1);
-  std::map<std::tuple<int, int, int64_t, int64_t, int>, int> index;
-  std::stable_sort(P.jobs.begin(), P.jobs.end(), [](const JobRec &a, const JobRec &b) {
-    return a.pass != b.pass ? a.pass < b.pass : a.ls < b.ls;
-  });
+  std::map<std::tuple<int, int, int, int64_t, int64_t, int>, int> index;
+  std::stable_sort(P.jobs.begin(), P.jobs.end(), launch_order);
   for (size_t i = 0; i < P.jobs.size();) {
     size_t k = i;
-    while (k < P.jobs.size() && P.jobs[k].pass == P.jobs[i].pass && P.jobs[k].ls == P.jobs[i].ls) k++;
+    while (k < P.jobs.size() && same_launch(P.jobs[k], P.jobs[i])) k++;
     HostPlan::Group g;
     g.ls = P.jobs[i].ls;
-    g.nwarps = warps_for(g.ls, P.ring.K);
+    g.lc = P.jobs[i].lc;
+    g.nwarps = warps_for(g.ls, g.lc);
+    g.prog_words = 0;
     for (size_t t = i; t < k; t++) {
       const JobRec &j = P.jobs[t];
-      auto key = std::make_tuple(j.kind, j.ls, j.z, j.n, j.f);
+      auto key = std::make_tuple(j.kind, j.ls, j.lc, j.z, j.n, j.f);
       auto it = index.find(key);
       int pi;
       if (it == index.end()) {
         pi = int(out->programs.size());
-        out->programs.push_back(build_program(j.kind, j.ls, j.z, j.n, j.f, N, nullptr));
+        out->programs.push_back(build_job_image(j.kind, j.ls, j.lc, j.z, j.n, j.f, N, nullptr));
         index[key] = pi;
       } else {
         pi = it->second;
       }
       g.jobs.push_back(j.d);
       g.prog_index.push_back(pi);
+      g.prog_words = std::max(g.prog_words, image_max_program_words(out->programs[pi]));
     }
     out->groups.push_back(std::move(g));
     i = k;
@@ -269,6 +310,7 @@ const TransformPlan *get_transform_plan(int kind, int l, int64_t z, int64_t n, i
   P.ring = make_ring(N);
   P.twoN = twoN;
   P.ls_max = max_onchip_ls(P.ring);
+  P.ls_c = cluster_cta_ls(P.ring);
   int npass;
   if (kind == KIND_TFT)
     npass = P.tft(0, 0, 1, l, e, z, n);
@@ -279,23 +321,23 @@ const TransformPlan *get_transform_plan(int kind, int l, int64_t z, int64_t n, i
   plan->ring = P.ring;
   plan->npasses = npass;
   plan->njobs = int64_t(P.jobs.size());
-  // resolve programs, then group jobs by (pass, ls) in pass order
+  // resolve job images, then group jobs by (pass, ls, lc) in pass order
   for (JobRec &j : P.jobs) {
-    j.d.prog = prog_cache().get(j.kind, j.ls, j.z, j.n, j.f, N, err);
-    if (!j.d.prog) return nullptr;
+    j.d.image = image_cache().get(j.kind, j.ls, j.lc, j.z, j.n, j.f, N, err);
+    if (!j.d.image) return nullptr;
   }
-  std::stable_sort(P.jobs.begin(), P.jobs.end(), [](const JobRec &a, const JobRec &b) {
-    return a.pass != b.pass ? a.pass < b.pass : a.ls < b.ls;
-  });
+  std::stable_sort(P.jobs.begin(), P.jobs.end(), launch_order);
   std::vector<JobDesc> flat;
   std::vector<std::pair<size_t, Launch>> groups;
   for (size_t i = 0; i < P.jobs.size();) {
     size_t k = i;
-    while (k < P.jobs.size() && P.jobs[k].pass == P.jobs[i].pass && P.jobs[k].ls == P.jobs[i].ls) k++;
+    while (k < P.jobs.size() && same_launch(P.jobs[k], P.jobs[i])) k++;
     Launch L;
     L.ls = P.jobs[i].ls;
+    L.lc = P.jobs[i].lc;
     L.njobs = int(k - i);
-    L.nwarps = warps_for(L.ls, P.ring.K);
+    L.nwarps = warps_for(L.ls, L.lc);
+    for (size_t t = i; t < k; t++) L.prog_words = std::max(L.prog_words, image_cache().max_prog(P.jobs[t].d.image));
     groups.push_back({flat.size(), L});
     for (size_t t = i; t < k; t++) flat.push_back(P.jobs[t].d);
     i = k;

@@ -177,6 +177,99 @@ __device__ __forceinline__ uint32_t canon_x(uint32_t (&r)[K], int v, const Geo &
   return 0u;
 }
 
+// add the signed small value c at slot 0 of the lane's chunk and propagate; returns the signed
+// carry out of the chunk (-1, 0 or +1)
+template <int K>
+__device__ __forceinline__ int ripple_signed(uint32_t (&r)[K], int c) {
+#pragma unroll
+  for (int s = 0; s < K; s++) {
+    if (!__any_sync(TFT_FULL, c != 0)) return 0;
+    uint32_t old = r[s];
+    uint32_t t = old + uint32_t(c);
+    c = c > 0 ? int(t < old) : (c < 0 ? -int(t > old) : 0);
+    r[s] = t;
+  }
+  return c;
+}
+
+// Finish an add or subtract chain in the storage form m = x - 1 (see the file comment).
+// cout is each lane's signed carry out of its chunk (+1 carry, -1 borrow); it enters the next
+// lane, and the carry out of bit N re-enters lane 0 negated (2^N = -1) together with v0.
+// Leaves m in [0, 2^N - 1] and returns 0, or returns 1 when m = -1 (the cell value x is 0):
+// that is the one value whose carries circulate forever, which the iteration bound detects.
+template <int K>
+__device__ __forceinline__ int settle(uint32_t (&r)[K], int cout, int v0, const Geo &g) {
+  int top = __shfl_sync(TFT_FULL, cout, g.G - 1);
+  int c = __shfl_up_sync(TFT_FULL, cout, 1);
+  if (g.lane == 0) c = v0 - top;
+  if (g.lane >= g.G) c = 0;
+  for (int it = 0;; it++) {
+    if (!__any_sync(TFT_FULL, c != 0)) return 0;
+    if (it > 3 * g.G + 3) return 1;
+    int co = ripple_signed<K>(r, c);
+    top = __shfl_sync(TFT_FULL, co, g.G - 1);
+    c = __shfl_up_sync(TFT_FULL, co, 1);
+    if (g.lane == 0) c = -top;
+    if (g.lane >= g.G) c = 0;
+  }
+}
+
+// ------------------------------------------------------------------ chains into shared memory
+// The same chains, but each result word goes straight to this lane's chunk of a shared-memory
+// cell (st.shared leaves the carry flag alone), so no register array holds the result.
+template <int K>
+__device__ __forceinline__ uint32_t add_chain_st(uint32_t *dst, const uint32_t (&a)[K], const uint32_t (&b)[K],
+                                                 uint32_t cin) {
+  uint32_t cout, d, w;
+  asm volatile("add.cc.u32 %0, %1, 0xffffffff;" : "=r"(d) : "r"(cin));
+#pragma unroll
+  for (int s = 0; s < K; s++) {
+    asm volatile("addc.cc.u32 %0, %1, %2;" : "=r"(w) : "r"(a[s]), "r"(b[s]));
+    asm volatile("st.shared.u32 [%0], %1;" ::"r"((uint32_t)__cvta_generic_to_shared(dst + s)), "r"(w) : "memory");
+  }
+  asm volatile("addc.u32 %0, 0, 0;" : "=r"(cout));
+  return cout;
+}
+
+template <int K>
+__device__ __forceinline__ uint32_t sub_chain_st(uint32_t *dst, const uint32_t (&a)[K], const uint32_t (&b)[K],
+                                                 uint32_t bin) {
+  uint32_t bout, d, w;
+  asm volatile("sub.cc.u32 %0, 0, %1;" : "=r"(d) : "r"(bin));
+#pragma unroll
+  for (int s = 0; s < K; s++) {
+    asm volatile("subc.cc.u32 %0, %1, %2;" : "=r"(w) : "r"(a[s]), "r"(b[s]));
+    asm volatile("st.shared.u32 [%0], %1;" ::"r"((uint32_t)__cvta_generic_to_shared(dst + s)), "r"(w) : "memory");
+  }
+  asm volatile("subc.u32 %0, 0, 0;" : "=r"(bout));
+  return bout & 1u;
+}
+
+// settle() for a result that sits in this lane's chunk `chunk` of a shared-memory cell: the
+// carries ripple through shared memory word by word (usually one word), only in the lanes that
+// hold one.
+template <int K>
+__device__ __forceinline__ int settle_smem(uint32_t *chunk, int cout, int v0, const Geo &g) {
+  int top = __shfl_sync(TFT_FULL, cout, g.G - 1);
+  int c = __shfl_up_sync(TFT_FULL, cout, 1);
+  if (g.lane == 0) c = v0 - top;
+  if (g.lane >= g.G) c = 0;
+  for (int it = 0;; it++) {
+    if (!__any_sync(TFT_FULL, c != 0)) return 0;
+    if (it > 3 * g.G + 3) return 1;
+    for (int s = 0; s < K && c != 0; s++) {
+      const uint32_t old = chunk[s];
+      const uint32_t t = old + uint32_t(c);
+      c = c > 0 ? int(t < old) : -int(t > old);
+      chunk[s] = t;
+    }
+    top = __shfl_sync(TFT_FULL, c, g.G - 1);
+    c = __shfl_up_sync(TFT_FULL, c, 1);
+    if (g.lane == 0) c = -top;
+    if (g.lane >= g.G) c = 0;
+  }
+}
+
 // ------------------------------------------------------------------ shared-memory cells
 // word w of a cell sits at w + w/32 (one pad word per 32 keeps lane chunks on distinct banks)
 __device__ __forceinline__ int phys(int w) { return w + (w >> 5); }
@@ -204,6 +297,12 @@ __device__ __forceinline__ void smem_load_plain(uint32_t (&r)[K], const uint32_t
 
 // raw = rotc(m, E) for the cell (see the file comment); E in [0, 2N). The zero cell reads as
 // all ones with the returned flag set (then x 2^E = raw + 1 - 2^N = 0).
+//
+// Output word j of lane l (j = K l + s) is the funnel shift of source words j - q - 1 and
+// j - q (q = E' / 32 words, sh = E' mod 32 bits), each complemented when its logical index
+// is negative (it wrapped past 2^N = -1). A lane's K + 1 source words form one window that
+// crosses at most one 32-word row of the padded cell (or the end of the cell), so the window
+// is two runs of consecutive addresses, each with a lane-uniform complement mask.
 template <int K>
 __device__ __forceinline__ int smem_read_raw(uint32_t (&r)[K], const uint32_t *cell, uint32_t meta,
                                              int Ereq, const Geo &g) {
@@ -225,21 +324,40 @@ __device__ __forceinline__ int smem_read_raw(uint32_t (&r)[K], const uint32_t *c
   const bool low_wrapped = E < g.N;  // complement the wrapped bits (else the others)
   const int Ep = low_wrapped ? E : E - g.N;
   const int q = Ep >> 5, sh = Ep & 31;
-  const int j0 = K * g.lane;
-  int src = j0 - q - 1;
-  if (src < 0) src += g.NW;
-  uint32_t prev = cell[phys(src)];
-  const uint32_t lomask = (1u << sh) - 1u;
+  const int lam0 = K * g.lane - q - 1;  // logical index of window word 0 (negative: wrapped)
+  const int i0 = lam0 < 0 ? lam0 + g.NW : lam0;
+  int tb, baseA, baseB;
+  if (g.NW >= 32) {
+    const int c0 = i0 & 31, r0 = i0 >> 5, rows = g.NW >> 5;
+    const int r1 = (r0 + 1 == rows) ? 0 : r0 + 1;
+    tb = 31 - c0;
+    baseA = 33 * r0 + c0;
+    baseB = 33 * r1 + c0 - 32;
+  } else {
+    tb = g.NW - 1 - i0;
+    baseA = i0;
+    baseB = i0 - g.NW;
+  }
   const uint32_t flip = low_wrapped ? 0u : TFT_FULL;
+  const uint32_t mA = (lam0 < 0 ? TFT_FULL : 0u) ^ flip;
+  const uint32_t mB = (lam0 + tb + 1 < 0 ? TFT_FULL : 0u) ^ flip;
+  if (sh == 0) {
+    // word-aligned rotation: output word j is source word j - q, no funnel shift
+#pragma unroll
+    for (int s = 0; s < K; s++) {
+      const int t = s + 1;
+      const bool inA = t <= tb;
+      r[s] = cell[(inA ? baseA : baseB) + t] ^ (inA ? mA : mB);
+    }
+    return 0;
+  }
+  uint32_t prev = cell[0 <= tb ? baseA : baseB] ^ (0 <= tb ? mA : mB);
 #pragma unroll
   for (int s = 0; s < K; s++) {
-    ++src;
-    if (src == g.NW) src = 0;
-    uint32_t cur = cell[phys(src)];
-    uint32_t w = __funnelshift_l(prev, cur, sh);  // (cur:prev) << sh, high word
-    int j = j0 + s;
-    uint32_t m = j < q ? TFT_FULL : (j == q ? lomask : 0u);
-    r[s] = w ^ (m ^ flip);
+    const int t = s + 1;
+    const bool inA = t <= tb;
+    uint32_t cur = cell[(inA ? baseA : baseB) + t] ^ (inA ? mA : mB);
+    r[s] = __funnelshift_l(prev, cur, sh);  // (cur:prev) << sh, high word
     prev = cur;
   }
   return 0;

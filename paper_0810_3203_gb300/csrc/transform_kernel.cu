@@ -1,21 +1,32 @@
-// The on-chip sub-transform kernel: one CTA runs one job (a TFT or ITFT of 2^ls cells that
-// sits in shared memory), following a program of base-case butterflies generated from
-// Algorithm 1 or 2 (program.cpp). Global memory is touched once per cell on the way in and
-// once on the way out; every butterfly in between works on shared memory.
+// The sub-transform kernel. One job (a TFT or ITFT of Ls = 2^ls cells) runs on a cluster of
+// C = 2^lc CTAs; every CTA keeps Ls / C cells in shared memory for the whole job, so global
+// memory is read once and written once per cell. Inside a CTA the base-case butterflies of
+// Algorithm 1 or 2 run as a program of dependency levels (program.cpp), one warp per
+// butterfly. When C > 1 the cells move between the column layout and the row layout of the
+// job's own C x (Ls / C) split through distributed shared memory (STAGE_XCHG / STAGE_SWAP).
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdio>
 
 #include "common.h"
 #include "host.h"
 #include "ring_warp.cuh"
 
+namespace cg = cooperative_groups;
+
 namespace tftgpu {
 
-__device__ __forceinline__ int rot_amount(RotA a, int e, int twoN) {
-  long long v = (long long)a.mul * e + a.add;
-  v %= twoN;
-  return int(v < 0 ? v + twoN : v);
+struct KGeo {
+  Geo g;
+  uint32_t mask;  // 2N - 1 when 2N is a power of two, else 0
+};
+
+__device__ __forceinline__ int rot_amount(RotA a, int e, const KGeo &k) {
+  if (k.mask) return int((uint32_t(a.mul) * uint32_t(e) + uint32_t(a.add)) & k.mask);
+  long long v = ((long long)a.mul * e + a.add) % k.g.twoN;
+  return int(v);
 }
 
 template <int K>
@@ -25,128 +36,316 @@ __device__ __forceinline__ void write_cell(uint32_t *cell, uint32_t *meta, const
   if (g.lane == 0) *meta = (uint32_t(tag) << 1) | uint32_t(zflag);
 }
 
+// chunk of this lane inside a shared-memory cell
+__device__ __forceinline__ uint32_t *lane_chunk(uint32_t *cell, int K, const Geo &g) {
+  return cell + phys(K * (g.lane < g.G ? g.lane : 0));
+}
+
 template <int K>
-__device__ void exec_op(const OpDesc &op, uint32_t *cells, uint32_t *meta, int P, int e, const Geo &g) {
+__device__ __forceinline__ void set_meta(uint32_t *meta, int zflag, int tag, const Geo &g) {
+  if (g.lane == 0) *meta = (uint32_t(tag) << 1) | uint32_t(zflag);
+}
+
+// S - 1 = rawA + rawB + 1 - (za + zb) 2^N, written to `dst` in storage form
+template <int K>
+__device__ __forceinline__ int sum_to(uint32_t *dst, const uint32_t (&A)[K], const uint32_t (&B)[K], int za,
+                                      int zb, const Geo &g) {
+  uint32_t *ch = lane_chunk(dst, K, g);
+  uint32_t c = 0;
+  if (g.lane < g.G) c = add_chain_st<K>(ch, A, B, g.lane == 0 ? 1u : 0u);
+  return settle_smem<K>(ch, int(c), za + zb, g);
+}
+
+// D - 1 = rawA - rawB - 1 - (za - zb) 2^N, written to `dst` in storage form
+template <int K>
+__device__ __forceinline__ int diff_to(uint32_t *dst, const uint32_t (&A)[K], const uint32_t (&B)[K], int za,
+                                       int zb, const Geo &g) {
+  uint32_t *ch = lane_chunk(dst, K, g);
+  uint32_t b = 0;
+  if (g.lane < g.G) b = sub_chain_st<K>(ch, A, B, g.lane == 0 ? 1u : 0u);
+  return settle_smem<K>(ch, -int(b), za - zb, g);
+}
+
+template <int K>
+__device__ __forceinline__ void exec_op(const OpDesc &op, uint32_t *cells, uint32_t *meta, int P, int e,
+                                        const KGeo &kg) {
+  const Geo &g = kg.g;
   uint32_t *ci = cells + op.i * P, *cj = cells + op.j * P;
-  uint32_t mi = meta[op.i], mj = meta[op.j];
+  const uint32_t mi = meta[op.i], mj = meta[op.j];
   if (op.kind == OP_TAG) {
-    int ra = rot_amount(op.ra, e, g.twoN);
-    int ti = int(mi >> 1);
+    const int ti = int(mi >> 1);
     if (op.flags & OPF_COPY) {
       uint32_t v[K];
       smem_load_plain<K>(v, ci, g);
-      int tj = ti + rot_amount(op.rb, e, g.twoN);
+      int tj = ti + rot_amount(op.rb, e, kg);
       if (tj >= g.twoN) tj -= g.twoN;
       __syncwarp();
       write_cell<K>(cj, meta + op.j, v, int(mi & 1u), tj, g);
     }
-    int tn = ti + ra;
+    int tn = ti + rot_amount(op.ra, e, kg);
     if (tn >= g.twoN) tn -= g.twoN;
     __syncwarp();
     if (g.lane == 0) meta[op.i] = (uint32_t(tn) << 1) | (mi & 1u);
     return;
   }
   uint32_t A[K], B[K];
-  int za = smem_read_raw<K>(A, ci, mi, rot_amount(op.ra, e, g.twoN), g);
-  int zb = (op.kind == OP_BF || op.kind == OP_CROSS)
-               ? smem_read_raw<K>(B, cj, mj, rot_amount(op.rb, e, g.twoN), g)
-               : 0;
+  const int za = smem_read_raw<K>(A, ci, mi, rot_amount(op.ra, e, kg), g);
+  const int zb = smem_read_raw<K>(B, cj, mj, rot_amount(op.rb, e, kg), g);
   __syncwarp();
-  const uint32_t c0 = g.lane == 0 ? 1u : 0u;
   if (op.kind == OP_BF) {
     if (op.flags & OPF_S) {
-      // S - 1 = rawA + rawB + 1 - (za + zb) 2^N
-      uint32_t S[K];
-      uint32_t c = add_chain<K>(S, A, B, c0);
-      uint32_t C = resolve_add<K>(S, c, g);
-      int zs = canon_m<K>(S, za + zb - int(C), g);
-      bool toj = op.flags & OPF_S_TO_J;
-      write_cell<K>(toj ? cj : ci, meta + (toj ? op.j : op.i), S, zs, rot_amount(op.p0, e, g.twoN), g);
+      const bool toj = op.flags & OPF_S_TO_J;
+      const int zs = sum_to<K>(toj ? cj : ci, A, B, za, zb, g);
+      set_meta<K>(meta + (toj ? op.j : op.i), zs, rot_amount(op.p0, e, kg), g);
     }
     if (op.flags & OPF_D) {
-      // D - 1 = rawA - rawB - 1 - (za - zb) 2^N
-      uint32_t b = sub_chain<K>(B, A, B, c0);
-      uint32_t Bo = resolve_sub<K>(B, b, g);
-      int zd = canon_m<K>(B, int(Bo) + za - zb, g);
-      bool toi = op.flags & OPF_D_TO_I;
-      write_cell<K>(toi ? ci : cj, meta + (toi ? op.i : op.j), B, zd, rot_amount(op.p1, e, g.twoN), g);
+      const bool toi = op.flags & OPF_D_TO_I;
+      const int zd = diff_to<K>(toi ? ci : cj, A, B, za, zb, g);
+      set_meta<K>(meta + (toi ? op.i : op.j), zd, rot_amount(op.p1, e, kg), g);
     }
     return;
   }
   // OP_CROSS: D = x_i - x_j -> x_j (pending p1); then x_i <- x_i + D
-  {
-    uint32_t b = sub_chain<K>(B, A, B, c0);
-    uint32_t Bo = resolve_sub<K>(B, b, g);
-    int zd = canon_m<K>(B, int(Bo) + za - zb, g);
-    write_cell<K>(cj, meta + op.j, B, zd, rot_amount(op.p1, e, g.twoN), g);
-    if (zd) set_ones<K>(B, g);
-    uint32_t S[K];
-    uint32_t c = add_chain<K>(S, A, B, c0);
-    uint32_t C = resolve_add<K>(S, c, g);
-    int zs = canon_m<K>(S, za + zd - int(C), g);
-    write_cell<K>(ci, meta + op.i, S, zs, 0, g);
+  const int zd = diff_to<K>(cj, A, B, za, zb, g);
+  set_meta<K>(meta + op.j, zd, rot_amount(op.p1, e, kg), g);
+  __syncwarp();
+  if (zd)
+    set_ones<K>(B, g);
+  else
+    smem_load_plain<K>(B, cj, g);
+  const int zs = sum_to<K>(ci, A, B, za, zd, g);
+  set_meta<K>(meta + op.i, zs, 0, g);
+}
+
+// Copy the N-bit part of a cell between global memory (16-byte aligned when vec16) and a
+// shared-memory cell, with consecutive lanes on consecutive addresses (coalesced); returns the
+// top limb's low word on loads.
+__device__ __forceinline__ uint32_t gmem_to_smem_cell(uint32_t *scell, const uint64_t *gcell, bool vec16,
+                                                      const Geo &g) {
+  const uint32_t *w32 = reinterpret_cast<const uint32_t *>(gcell);
+  if (vec16 && (g.NW & 3) == 0) {
+    const uint4 *src = reinterpret_cast<const uint4 *>(w32);
+    for (int q = g.lane; q < g.NW / 4; q += 32) {
+      const uint4 v = __ldg(src + q);
+      const int w = 4 * q, pw = phys(w);  // 4 words in one 32-word row
+      scell[pw] = v.x;
+      scell[pw + 1] = v.y;
+      scell[pw + 2] = v.z;
+      scell[pw + 3] = v.w;
+    }
+  } else {
+    const uint2 *src = reinterpret_cast<const uint2 *>(w32);
+    for (int q = g.lane; q < g.NW / 2; q += 32) {
+      const uint2 v = __ldg(src + q);
+      const int pw = phys(2 * q);
+      scell[pw] = v.x;
+      scell[pw + 1] = v.y;
+    }
   }
+  return __ldg(w32 + g.NW);
+}
+
+__device__ __forceinline__ void smem_to_gmem_cell(uint64_t *gcell, const uint32_t *scell, uint32_t top, bool vec16,
+                                                  const Geo &g) {
+  uint32_t *w32 = reinterpret_cast<uint32_t *>(gcell);
+  if (vec16 && (g.NW & 3) == 0) {
+    uint4 *dst = reinterpret_cast<uint4 *>(w32);
+    for (int q = g.lane; q < g.NW / 4; q += 32) {
+      const int pw = phys(4 * q);
+      dst[q] = make_uint4(scell[pw], scell[pw + 1], scell[pw + 2], scell[pw + 3]);
+    }
+  } else {
+    uint2 *dst = reinterpret_cast<uint2 *>(w32);
+    for (int q = g.lane; q < g.NW / 2; q += 32) {
+      const int pw = phys(2 * q);
+      dst[q] = make_uint2(scell[pw], scell[pw + 1]);
+    }
+  }
+  if (g.lane == 0) gcell[g.NW / 2] = uint64_t(top);
+}
+
+// cell index of the job held at `slot` of CTA `rank` in the given layout
+__device__ __forceinline__ int job_cell(uint32_t layout, int rank, int slot, int C, int L2, int b) {
+  if (C == 1) return slot;
+  if (layout == LAYOUT_ROW) return rank * L2 + slot;
+  return (slot / b) * L2 + rank * b + (slot % b);
+}
+
+// one op descriptor from shared memory (8-byte aligned) or, when the program did not fit
+// there, from global memory through the read-only path
+__device__ __forceinline__ OpDesc load_op_shared(const uint32_t *p) {
+  const uint2 *q = reinterpret_cast<const uint2 *>(p);
+  uint2 w0 = q[0], w1 = q[1], w2 = q[2], w3 = q[3], w4 = q[4];
+  OpDesc o;
+  uint2 *d = reinterpret_cast<uint2 *>(&o);
+  d[0] = w0;
+  d[1] = w1;
+  d[2] = w2;
+  d[3] = w3;
+  d[4] = w4;
+  return o;
+}
+
+__device__ __forceinline__ OpDesc load_op_global(const uint32_t *p) {
+  const uint2 *q = reinterpret_cast<const uint2 *>(p);
+  OpDesc o;
+  uint2 *d = reinterpret_cast<uint2 *>(&o);
+#pragma unroll
+  for (int k = 0; k < 5; k++) d[k] = __ldg(q + k);
+  return o;
+}
+
+template <int K, bool STAGED>
+__device__ __forceinline__ void run_program(const uint32_t *pg, uint32_t *cells, uint32_t *meta, int P, int e,
+                                            const KGeo &kg, int warp, int nw) {
+  const int nlev = int(pg[0]);
+  const uint32_t *ops = pg + prog_ops_offset_words(nlev);
+  const int ow = int(sizeof(OpDesc) / 4);
+  for (int v = 0; v < nlev; v++) {
+    const int a = int(pg[2 + v]), b = int(pg[3 + v]);
+    for (int o = a + warp; o < b; o += nw) {
+      const OpDesc op = STAGED ? load_op_shared(ops + o * ow) : load_op_global(ops + o * ow);
+      exec_op<K>(op, cells, meta, P, e, kg);
+    }
+    __syncthreads();
+  }
+}
+
+// Cells of CTA `rank` that arrive from partner `y` in a layout exchange: local slots
+// [y b, y b + b) take the partner's slots [rank b, rank b + b). A cell is one block of P words
+// in either CTA, copied whole with 16-byte loads from the partner's shared memory (consecutive
+// lanes on consecutive addresses). The (partner distance r, block offset i) items go in chunks
+// of one cell per warp: read into registers, cluster barrier, write locally. Pairs are
+// symmetric (y = rank ^ r), so when a chunk's barrier is passed every block it touches has
+// been read by its partner, and later chunks touch other blocks. All CTAs run the same number
+// of chunks and barriers.
+constexpr int kXchgVec = 9;  // 16-byte vectors per lane: cells of up to 9 * 32 * 4 = 1152 words
+
+template <int K>
+__device__ __forceinline__ void exchange(uint32_t *cells, uint32_t *meta, int P, int rank, int C, int b, int only,
+                                         const Geo &g, int warp, int nw) {
+  cg::cluster_group cluster = cg::this_cluster();
+  const int items = (C - 1) * b;
+  const int nvec = P / 4;
+  cluster.sync();  // partners finished writing the cells we are about to read
+  for (int base = 0; base < items; base += nw) {
+    const int t = base + warp;
+    const int r = 1 + t / b, i = t % b, y = rank ^ r;
+    const bool mine = t < items && y < C && (only < 0 || rank == only || y == only);
+    uint4 buf[kXchgVec];
+    uint32_t m = 0;
+    if (mine) {
+      const uint4 *src = reinterpret_cast<const uint4 *>(cluster.map_shared_rank(cells, y) + (rank * b + i) * P);
+#pragma unroll
+      for (int k = 0; k < kXchgVec; k++) {
+        const int v = g.lane + 32 * k;
+        if (v < nvec) buf[k] = src[v];
+      }
+      m = *(cluster.map_shared_rank(meta, y) + (rank * b + i));
+    }
+    cluster.sync();
+    if (mine) {
+      uint4 *dst = reinterpret_cast<uint4 *>(cells + (y * b + i) * P);
+#pragma unroll
+      for (int k = 0; k < kXchgVec; k++) {
+        const int v = g.lane + 32 * k;
+        if (v < nvec) dst[v] = buf[k];
+      }
+      if (g.lane == 0) meta[y * b + i] = m;
+    }
+  }
+  __syncthreads();
 }
 
 template <int K>
 __global__ void __launch_bounds__(512) job_kernel(uint64_t *__restrict__ x, int64_t stride_limbs,
-                                                  const JobDesc *__restrict__ jobs, int N, int ls) {
+                                                  const JobDesc *__restrict__ jobs, int N, int ls, int lc,
+                                                  uint32_t mask, int prog_cap) {
   extern __shared__ uint32_t smem[];
-  const JobDesc jd = jobs[blockIdx.x];
-  Geo g;
-  g.N = N;
-  g.NW = N / 32;
-  g.G = g.NW / K;
-  g.lane = threadIdx.x & 31;
-  g.twoN = 2 * N;
-  const int Ls = 1 << ls;
+  const int C = 1 << lc;
+  const int rank = int(blockIdx.x) & (C - 1);
+  const JobDesc jd = jobs[blockIdx.x >> lc];
+  KGeo kg;
+  kg.g.N = N;
+  kg.g.NW = N / 32;
+  kg.g.G = kg.g.NW / K;
+  kg.g.lane = threadIdx.x & 31;
+  kg.g.twoN = 2 * N;
+  kg.mask = mask;
+  const Geo &g = kg.g;
+  const int nslots = 1 << (ls - lc);
+  const int L2 = nslots, b = nslots / C;
   const int P = cell_pitch_words(g.NW);
   uint32_t *cells = smem;
-  uint32_t *meta = smem + Ls * P;
+  uint32_t *meta = smem + nslots * P;
+  // program staging area, 8-byte aligned, after the cells and their metadata
+  uint32_t *pstage = smem + ((nslots * P + nslots + 1) & ~1);
   const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const uint32_t *img = jd.image;
+  const int nstages = int(img[0]);
+  const uint32_t load_layout = img[2], store_layout = img[3];
 
-  // cells never loaded read as the implicit zero inputs
-  for (int m = threadIdx.x; m < Ls; m += blockDim.x)
-    if (m >= jd.nload) meta[m] = 1u;
+  // slots whose cells are not inputs read as the implicit zeros
+  for (int s = threadIdx.x; s < nslots; s += blockDim.x)
+    if (job_cell(load_layout, rank, s, C, L2, b) >= jd.nload) meta[s] = 1u;
 
-  // load: m = x - 1 into shared memory
-  for (int m = warp; m < jd.nload; m += nw) {
+  // load (coalesced) into shared memory, then the storage form m = x - 1
+  const bool vec16 = ((reinterpret_cast<uintptr_t>(x) & 15) == 0) && ((stride_limbs & 1) == 0);
+  for (int s = warp; s < nslots; s += nw) {
+    const int m = job_cell(load_layout, rank, s, C, L2, b);
+    if (m >= jd.nload) continue;
     const uint64_t *gc = x + (jd.cell0 + int64_t(m) * jd.mstride) * stride_limbs;
-    uint32_t r[K];
-    uint32_t T = gmem_load_x<K>(r, gc, g);
-    uint32_t b = sub_small<K>(r, 1u, g);
-    int z = canon_m<K>(r, int(b) - int(T), g);
-    write_cell<K>(cells + m * P, meta + m, r, z, 0, g);
+    const uint32_t T = gmem_to_smem_cell(cells + s * P, gc, vec16, g);
+    __syncwarp();
+    const int z = settle_smem<K>(lane_chunk(cells + s * P, K, g), 0, -1 - int(T), g);
+    set_meta<K>(meta + s, z, 0, g);
   }
   __syncthreads();
 
-  // program
-  const uint32_t *pg = jd.prog;
-  const int nlev = int(pg[0]);
-  const OpDesc *ops = reinterpret_cast<const OpDesc *>(pg + prog_ops_offset_words(nlev));
-  for (int v = 0; v < nlev; v++) {
-    const int a = int(pg[2 + v]), b = int(pg[3 + v]);
-    for (int o = a + warp; o < b; o += nw) {
-      OpDesc op = ops[o];
-      exec_op<K>(op, cells, meta, P, jd.e, g);
+  for (int st = 0; st < nstages; st++) {
+    const uint32_t *ent = img + job_header_words() + st * job_stage_words(C);
+    const uint32_t type = ent[0];
+    if (type == STAGE_PROG) {
+      const uint32_t off = ent[2 + rank];
+      if (off) {
+        // copy this CTA's program into shared memory when it fits (ops are then read from there)
+        const uint32_t *pg = img + off;
+        const int words = prog_ops_offset_words(int(pg[0])) + int(pg[1]) * int(sizeof(OpDesc) / 4);
+        if (words <= prog_cap) {
+          const uint2 *src = reinterpret_cast<const uint2 *>(pg);
+          uint2 *dst = reinterpret_cast<uint2 *>(pstage);
+          for (int w = threadIdx.x; w < (words + 1) / 2; w += blockDim.x) dst[w] = __ldg(src + w);
+          __syncthreads();
+          run_program<K, true>(pstage, cells, meta, P, jd.e, kg, warp, nw);
+        } else {
+          run_program<K, false>(pg, cells, meta, P, jd.e, kg, warp, nw);
+        }
+      }
+    } else {
+      exchange<K>(cells, meta, P, rank, C, b, type == STAGE_SWAP ? int(ent[1]) : -1, g, warp, nw);
     }
-    __syncthreads();
   }
 
   // store: x = rotc(m, t) + 1, with the final scaling where requested
-  for (int m = warp; m < jd.nstore; m += nw) {
+  for (int s = warp; s < nslots; s += nw) {
+    const int m = job_cell(store_layout, rank, s, C, L2, b);
+    if (m >= jd.nstore) continue;
     uint32_t r[K];
-    int E = m < jd.nscale ? jd.escale : 0;
-    int z = smem_read_raw<K>(r, cells + m * P, meta[m], E, g);
+    const int E = m < jd.nscale ? jd.escale : 0;
+    const int z = smem_read_raw<K>(r, cells + s * P, meta[s], E, g);
     uint32_t top = 0;
     if (z) {
 #pragma unroll
-      for (int s = 0; s < K; s++) r[s] = 0u;
+      for (int q = 0; q < K; q++) r[q] = 0u;
     } else {
       top = add_small<K>(r, 1u, g);
     }
+    // through the cell's own slot (no longer needed) so the global writes are coalesced
+    __syncwarp();
+    smem_store_plain<K>(cells + s * P, r, g);
+    __syncwarp();
     uint64_t *gc = x + (jd.cell0 + int64_t(m) * jd.mstride) * stride_limbs;
-    gmem_store_x<K>(gc, r, top, g);
+    smem_to_gmem_cell(gc, cells + s * P, top, vec16, g);
   }
 }
 
@@ -154,17 +353,37 @@ namespace {
 
 template <int K>
 cudaError_t launch_k(const Launch &L, uint64_t *x, int64_t stride_limbs, const Ring &r, cudaStream_t s) {
-  size_t smem = size_t(1 << L.ls) * size_t(r.pitch) * 4 + size_t(1 << L.ls) * 4;
-  static thread_local int configured_dev[8] = {-1, -1, -1, -1, -1, -1, -1, -1};
+  const int nslots = 1 << (L.ls - L.lc);
+  const size_t base_words = (size_t(nslots) * size_t(r.pitch) + size_t(nslots) + 1) & ~size_t(1);
+  const size_t max_words = (227 * 1024) / 4;
+  const int prog_cap = int(std::min<size_t>(size_t(L.prog_words), max_words > base_words ? max_words - base_words : 0));
+  const size_t smem = (base_words + size_t(prog_cap)) * 4;
+  static thread_local int configured[8] = {0, 0, 0, 0, 0, 0, 0, 0};
   int dev = 0;
   cudaGetDevice(&dev);
-  if (dev < 8 && configured_dev[dev] != 1) {
+  if (dev >= 8 || !configured[dev]) {
     cudaError_t e = cudaFuncSetAttribute(job_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
     if (e != cudaSuccess) return e;
-    configured_dev[dev] = 1;
+    e = cudaFuncSetAttribute(job_kernel<K>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e != cudaSuccess) return e;
+    if (dev < 8) configured[dev] = 1;
   }
-  job_kernel<K><<<L.njobs, L.nwarps * 32, smem, s>>>(x, stride_limbs, L.d_jobs, int(r.N), L.ls);
-  return cudaGetLastError();
+  const uint32_t twoN = uint32_t(2 * r.N);
+  const uint32_t mask = (twoN & (twoN - 1)) == 0 ? twoN - 1 : 0u;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(unsigned(L.njobs) << L.lc);
+  cfg.blockDim = dim3(unsigned(L.nwarps * 32));
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = 1u << L.lc;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = L.lc > 0 ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, job_kernel<K>, x, stride_limbs, (const JobDesc *)L.d_jobs, int(r.N), L.ls, L.lc,
+                            mask, prog_cap);
 }
 
 }  // namespace

@@ -106,13 +106,15 @@ int plan_in_scratch(NoAllocDevice &st, int kind, int l, int64_t z, int64_t n, in
   plan->ring = hp.ring;
   plan->npasses = hp.npasses;
   for (auto &g : hp.groups) {
-    for (size_t i = 0; i < g.jobs.size(); i++) g.jobs[i].prog = dprog[g.prog_index[i]];
+    for (size_t i = 0; i < g.jobs.size(); i++) g.jobs[i].image = dprog[g.prog_index[i]];
     uint64_t *d = plan_space(st, g.jobs.size() * sizeof(JobDesc));
     cudaError_t e = cudaMemcpyAsync(d, g.jobs.data(), g.jobs.size() * sizeof(JobDesc), cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) return na_fail(ZX_ECUDA, std::string("plan upload: ") + cudaGetErrorString(e));
     Launch L;
     L.ls = g.ls;
+    L.lc = g.lc;
     L.nwarps = g.nwarps;
+    L.prog_words = g.prog_words;
     L.njobs = int(g.jobs.size());
     L.d_jobs = reinterpret_cast<JobDesc *>(d);
     plan->launches.push_back(L);
