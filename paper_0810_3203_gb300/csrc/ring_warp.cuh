@@ -245,6 +245,50 @@ __device__ __forceinline__ uint32_t sub_chain_st(uint32_t *dst, const uint32_t (
   return bout & 1u;
 }
 
+// dst = a + b + cin (ADD) or a - b - cin (SUB) over this lane's chunk, where a is read from
+// the shared-memory chunk `asrc` (or is all ones when a_ones: the zero cell's raw form) and b
+// sits in registers. Works in groups of 8 words: 8 loads issued together, then 8 chained
+// add/sub and 8 stores, so a needs no register array. asrc and dst may be the same chunk.
+// Returns the carry (ADD) or borrow (SUB) out of the chunk.
+template <int K, bool SUB>
+__device__ __forceinline__ uint32_t chain_stream(uint32_t *dst, const uint32_t *asrc, bool a_ones,
+                                                 const uint32_t (&b)[K], uint32_t cin) {
+  const uint32_t da = (uint32_t)__cvta_generic_to_shared(dst);
+  const uint32_t sa = (uint32_t)__cvta_generic_to_shared(asrc);
+  uint32_t d, cout;
+  if (SUB)
+    asm volatile("sub.cc.u32 %0, 0, %1;" : "=r"(d) : "r"(cin));
+  else
+    asm volatile("add.cc.u32 %0, %1, 0xffffffff;" : "=r"(d) : "r"(cin));
+  constexpr int GRP = K < 8 ? K : 8;
+#pragma unroll
+  for (int g0 = 0; g0 < K; g0 += GRP) {
+    uint32_t a[GRP];
+#pragma unroll
+    for (int k = 0; k < GRP; k++) {
+      if (a_ones)
+        a[k] = 0xffffffffu;
+      else
+        asm volatile("ld.shared.u32 %0, [%1];" : "=r"(a[k]) : "r"(sa + 4u * (g0 + k)));
+    }
+#pragma unroll
+    for (int k = 0; k < GRP; k++) {
+      uint32_t w;
+      if (SUB)
+        asm volatile("subc.cc.u32 %0, %1, %2;" : "=r"(w) : "r"(a[k]), "r"(b[g0 + k]));
+      else
+        asm volatile("addc.cc.u32 %0, %1, %2;" : "=r"(w) : "r"(a[k]), "r"(b[g0 + k]));
+      asm volatile("st.shared.u32 [%0], %1;" ::"r"(da + 4u * (g0 + k)), "r"(w) : "memory");
+    }
+  }
+  if (SUB) {
+    asm volatile("subc.u32 %0, 0, 0;" : "=r"(cout));
+    return cout & 1u;
+  }
+  asm volatile("addc.u32 %0, 0, 0;" : "=r"(cout));
+  return cout;
+}
+
 // settle() for a result that sits in this lane's chunk `chunk` of a shared-memory cell: the
 // carries ripple through shared memory word by word (usually one word), only in the lanes that
 // hold one.
@@ -254,7 +298,26 @@ __device__ __forceinline__ int settle_smem(uint32_t *chunk, int cout, int v0, co
   int c = __shfl_up_sync(TFT_FULL, cout, 1);
   if (g.lane == 0) c = v0 - top;
   if (g.lane >= g.G) c = 0;
+  // first word of each chunk without a loop; almost always no carry survives it
+  if (c != 0) {
+    const uint32_t old = chunk[0];
+    const uint32_t t = old + uint32_t(c);
+    c = c > 0 ? int(t < old) : -int(t > old);
+    chunk[0] = t;
+  }
+  if (!__any_sync(TFT_FULL, c != 0)) return 0;
+  for (int s = 1; s < K && c != 0; s++) {
+    const uint32_t old = chunk[s];
+    const uint32_t t = old + uint32_t(c);
+    c = c > 0 ? int(t < old) : -int(t > old);
+    chunk[s] = t;
+  }
+  // carries that left a chunk: move them on lane by lane (2^N = -1 at the top)
   for (int it = 0;; it++) {
+    top = __shfl_sync(TFT_FULL, c, g.G - 1);
+    c = __shfl_up_sync(TFT_FULL, c, 1);
+    if (g.lane == 0) c = -top;
+    if (g.lane >= g.G) c = 0;
     if (!__any_sync(TFT_FULL, c != 0)) return 0;
     if (it > 3 * g.G + 3) return 1;
     for (int s = 0; s < K && c != 0; s++) {
@@ -263,10 +326,6 @@ __device__ __forceinline__ int settle_smem(uint32_t *chunk, int cout, int v0, co
       c = c > 0 ? int(t < old) : -int(t > old);
       chunk[s] = t;
     }
-    top = __shfl_sync(TFT_FULL, c, g.G - 1);
-    c = __shfl_up_sync(TFT_FULL, c, 1);
-    if (g.lane == 0) c = -top;
-    if (g.lane >= g.G) c = 0;
   }
 }
 
@@ -303,6 +362,18 @@ __device__ __forceinline__ void smem_load_plain(uint32_t (&r)[K], const uint32_t
 // is negative (it wrapped past 2^N = -1). A lane's K + 1 source words form one window that
 // crosses at most one 32-word row of the padded cell (or the end of the cell), so the window
 // is two runs of consecutive addresses, each with a lane-uniform complement mask.
+template <int K>
+__device__ __forceinline__ int smem_read_raw(uint32_t (&r)[K], const uint32_t *cell, uint32_t meta,
+                                             int Ereq, const Geo &g);
+
+// raw = rotc(m, E) with E in [0, 2N) taken as the whole rotation (the cell's pending rotation
+// is ignored: the caller has accounted for it); zflag is the cell's zero flag
+template <int K>
+__device__ __forceinline__ int smem_read_abs(uint32_t (&r)[K], const uint32_t *cell, int zflag, int E,
+                                             const Geo &g) {
+  return smem_read_raw<K>(r, cell, uint32_t(zflag), E, g);
+}
+
 template <int K>
 __device__ __forceinline__ int smem_read_raw(uint32_t (&r)[K], const uint32_t *cell, uint32_t meta,
                                              int Ereq, const Geo &g) {

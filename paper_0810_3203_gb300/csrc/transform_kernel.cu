@@ -46,24 +46,27 @@ __device__ __forceinline__ void set_meta(uint32_t *meta, int zflag, int tag, con
   if (g.lane == 0) *meta = (uint32_t(tag) << 1) | uint32_t(zflag);
 }
 
-// S - 1 = rawA + rawB + 1 - (za + zb) 2^N, written to `dst` in storage form
+// S - 1 = rawA + rawB + 1 - (za + zb) 2^N, written to `dst` in storage form; rawA is the
+// unrotated cell `acell` (all ones when za), rawB is in registers
 template <int K>
-__device__ __forceinline__ int sum_to(uint32_t *dst, const uint32_t (&A)[K], const uint32_t (&B)[K], int za,
+__device__ __forceinline__ int sum_to(uint32_t *dst, const uint32_t *acell, const uint32_t (&B)[K], int za,
                                       int zb, const Geo &g) {
   uint32_t *ch = lane_chunk(dst, K, g);
   uint32_t c = 0;
-  if (g.lane < g.G) c = add_chain_st<K>(ch, A, B, g.lane == 0 ? 1u : 0u);
+  if (g.lane < g.G) c = chain_stream<K, false>(ch, lane_chunk(const_cast<uint32_t *>(acell), K, g), za != 0, B,
+                                                 g.lane == 0 ? 1u : 0u);
   return settle_smem<K>(ch, int(c), za + zb, g);
 }
 
 // D - 1 = rawA - rawB - 1 - (za - zb) 2^N, written to `dst` in storage form
 template <int K>
-__device__ __forceinline__ int diff_to(uint32_t *dst, const uint32_t (&A)[K], const uint32_t (&B)[K], int za,
+__device__ __forceinline__ int diff_to(uint32_t *dst, const uint32_t *acell, const uint32_t (&B)[K], int za,
                                        int zb, const Geo &g) {
   uint32_t *ch = lane_chunk(dst, K, g);
-  uint32_t b = 0;
-  if (g.lane < g.G) b = sub_chain_st<K>(ch, A, B, g.lane == 0 ? 1u : 0u);
-  return settle_smem<K>(ch, -int(b), za - zb, g);
+  uint32_t bo = 0;
+  if (g.lane < g.G) bo = chain_stream<K, true>(ch, lane_chunk(const_cast<uint32_t *>(acell), K, g), za != 0, B,
+                                                 g.lane == 0 ? 1u : 0u);
+  return settle_smem<K>(ch, -int(bo), za - zb, g);
 }
 
 template <int K>
@@ -88,33 +91,51 @@ __device__ __forceinline__ void exec_op(const OpDesc &op, uint32_t *cells, uint3
     if (g.lane == 0) meta[op.i] = (uint32_t(tn) << 1) | (mi & 1u);
     return;
   }
-  uint32_t A[K], B[K];
-  const int za = smem_read_raw<K>(A, ci, mi, rot_amount(op.ra, e, kg), g);
-  const int zb = smem_read_raw<K>(B, cj, mj, rot_amount(op.rb, e, kg), g);
+  // x_i 2^Ei (+-) x_j 2^Ej = 2^Ei (x_i (+-) x_j 2^(Ej - Ei)): read x_i without rotation and
+  // x_j with the difference, and give the outputs Ei more pending rotation
+  int Ei = int(mi >> 1) + rot_amount(op.ra, e, kg);
+  if (Ei >= g.twoN) Ei -= g.twoN;
+  int Ej = int(mj >> 1) + rot_amount(op.rb, e, kg);
+  if (Ej >= g.twoN) Ej -= g.twoN;
+  int Er = Ej - Ei;
+  if (Er < 0) Er += g.twoN;
+  const int za = int(mi & 1u), zb = int(mj & 1u);
+  uint32_t B[K];
+  smem_read_abs<K>(B, cj, zb, Er, g);
   __syncwarp();
+  auto pend = [&](RotA p) {
+    int t = rot_amount(p, e, kg) + Ei;
+    return t >= g.twoN ? t - g.twoN : t;
+  };
   if (op.kind == OP_BF) {
-    if (op.flags & OPF_S) {
-      const bool toj = op.flags & OPF_S_TO_J;
-      const int zs = sum_to<K>(toj ? cj : ci, A, B, za, zb, g);
-      set_meta<K>(meta + (toj ? op.j : op.i), zs, rot_amount(op.p0, e, kg), g);
+    // x_i is streamed from its cell: the difference goes first when it is written to cell j,
+    // so that x_i is still intact for the sum, which then rewrites cell i word by word
+    const bool wantS = op.flags & OPF_S, wantD = op.flags & OPF_D;
+    const bool toj = op.flags & OPF_S_TO_J, toi = op.flags & OPF_D_TO_I;
+    if (wantD && !toi) {
+      const int zd = diff_to<K>(cj, ci, B, za, zb, g);
+      set_meta<K>(meta + op.j, zd, pend(op.p1), g);
     }
-    if (op.flags & OPF_D) {
-      const bool toi = op.flags & OPF_D_TO_I;
-      const int zd = diff_to<K>(toi ? ci : cj, A, B, za, zb, g);
-      set_meta<K>(meta + (toi ? op.i : op.j), zd, rot_amount(op.p1, e, kg), g);
+    if (wantS) {
+      const int zs = sum_to<K>(toj ? cj : ci, ci, B, za, zb, g);
+      set_meta<K>(meta + (toj ? op.j : op.i), zs, pend(op.p0), g);
+    }
+    if (wantD && toi) {
+      const int zd = diff_to<K>(ci, ci, B, za, zb, g);
+      set_meta<K>(meta + op.i, zd, pend(op.p1), g);
     }
     return;
   }
   // OP_CROSS: D = x_i - x_j -> x_j (pending p1); then x_i <- x_i + D
-  const int zd = diff_to<K>(cj, A, B, za, zb, g);
-  set_meta<K>(meta + op.j, zd, rot_amount(op.p1, e, kg), g);
+  const int zd = diff_to<K>(cj, ci, B, za, zb, g);
+  set_meta<K>(meta + op.j, zd, pend(op.p1), g);
   __syncwarp();
   if (zd)
     set_ones<K>(B, g);
   else
     smem_load_plain<K>(B, cj, g);
-  const int zs = sum_to<K>(ci, A, B, za, zd, g);
-  set_meta<K>(meta + op.i, zs, 0, g);
+  const int zs = sum_to<K>(ci, ci, B, za, zd, g);
+  set_meta<K>(meta + op.i, zs, Ei, g);
 }
 
 // Copy the N-bit part of a cell between global memory (16-byte aligned when vec16) and a
@@ -127,7 +148,7 @@ __device__ __forceinline__ uint32_t gmem_to_smem_cell(uint32_t *scell, const uin
     const uint4 *src = reinterpret_cast<const uint4 *>(w32);
     for (int q = g.lane; q < g.NW / 4; q += 32) {
       const uint4 v = __ldg(src + q);
-      const int w = 4 * q, pw = phys(w);  // 4 words in one 32-word row
+      const int pw = phys(4 * q);  // 4 words in one 32-word row
       scell[pw] = v.x;
       scell[pw + 1] = v.y;
       scell[pw + 2] = v.z;
