@@ -278,8 +278,10 @@ __device__ __forceinline__ void exchange(uint32_t *cells, uint32_t *meta, int P,
   __syncthreads();
 }
 
-template <int K>
-__global__ void __launch_bounds__(512) job_kernel(uint64_t *__restrict__ x, int64_t stride_limbs,
+// MINB = 3: jobs of at most 8 warps and 75 KB of shared memory, three CTAs per SM (registers
+// capped at 85 per thread); MINB = 1: up to 16 warps, one CTA per SM
+template <int K, int MINB>
+__global__ void __launch_bounds__(MINB == 3 ? 256 : 512, MINB) job_kernel(uint64_t *__restrict__ x, int64_t stride_limbs,
                                                   const JobDesc *__restrict__ jobs, int N, int ls, int lc,
                                                   uint32_t mask, int prog_cap) {
   extern __shared__ uint32_t smem[];
@@ -372,25 +374,19 @@ __global__ void __launch_bounds__(512) job_kernel(uint64_t *__restrict__ x, int6
 
 namespace {
 
-template <int K>
-cudaError_t launch_k(const Launch &L, uint64_t *x, int64_t stride_limbs, const Ring &r, cudaStream_t s) {
-  const int nslots = 1 << (L.ls - L.lc);
-  const size_t base_words = (size_t(nslots) * size_t(r.pitch) + size_t(nslots) + 1) & ~size_t(1);
-  const size_t max_words = (227 * 1024) / 4;
-  const int prog_cap = int(std::min<size_t>(size_t(L.prog_words), max_words > base_words ? max_words - base_words : 0));
-  const size_t smem = (base_words + size_t(prog_cap)) * 4;
+template <int K, int MINB>
+cudaError_t launch_km(const Launch &L, uint64_t *x, int64_t stride_limbs, const Ring &r, cudaStream_t s,
+                      size_t smem, int prog_cap, uint32_t mask) {
   static thread_local int configured[8] = {0, 0, 0, 0, 0, 0, 0, 0};
   int dev = 0;
   cudaGetDevice(&dev);
   if (dev >= 8 || !configured[dev]) {
-    cudaError_t e = cudaFuncSetAttribute(job_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    cudaError_t e = cudaFuncSetAttribute(job_kernel<K, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(job_kernel<K>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    e = cudaFuncSetAttribute(job_kernel<K, MINB>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     if (e != cudaSuccess) return e;
     if (dev < 8) configured[dev] = 1;
   }
-  const uint32_t twoN = uint32_t(2 * r.N);
-  const uint32_t mask = (twoN & (twoN - 1)) == 0 ? twoN - 1 : 0u;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(unsigned(L.njobs) << L.lc);
   cfg.blockDim = dim3(unsigned(L.nwarps * 32));
@@ -403,8 +399,22 @@ cudaError_t launch_k(const Launch &L, uint64_t *x, int64_t stride_limbs, const R
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = L.lc > 0 ? 1 : 0;
-  return cudaLaunchKernelEx(&cfg, job_kernel<K>, x, stride_limbs, (const JobDesc *)L.d_jobs, int(r.N), L.ls, L.lc,
-                            mask, prog_cap);
+  return cudaLaunchKernelEx(&cfg, job_kernel<K, MINB>, x, stride_limbs, (const JobDesc *)L.d_jobs, int(r.N), L.ls,
+                            L.lc, mask, prog_cap);
+}
+
+template <int K>
+cudaError_t launch_k(const Launch &L, uint64_t *x, int64_t stride_limbs, const Ring &r, cudaStream_t s) {
+  const int nslots = 1 << (L.ls - L.lc);
+  const size_t base_words = (size_t(nslots) * size_t(r.pitch) + size_t(nslots) + 1) & ~size_t(1);
+  const size_t max_words = (227 * 1024) / 4;
+  const int prog_cap = int(std::min<size_t>(size_t(L.prog_words), max_words > base_words ? max_words - base_words : 0));
+  const size_t smem = (base_words + size_t(prog_cap)) * 4;
+  const uint32_t twoN = uint32_t(2 * r.N);
+  const uint32_t mask = (twoN & (twoN - 1)) == 0 ? twoN - 1 : 0u;
+  if (L.nwarps <= 8 && smem <= 75 * 1024)
+    return launch_km<K, 3>(L, x, stride_limbs, r, s, smem, prog_cap, mask);
+  return launch_km<K, 1>(L, x, stride_limbs, r, s, smem, prog_cap, mask);
 }
 
 }  // namespace
