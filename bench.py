@@ -93,7 +93,8 @@ def measured_peak():
 def kernel_source_hash():
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_0810_3203_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
+    # the files that decide what the transform kernel does and which launches a plan makes
+    for f in ("common.h", "host.h", "plan.cpp", "program.cpp", "ring_warp.cuh", "transform_kernel.cu"):
         h.update(f.encode())
         h.update(open(os.path.join(csrc, f), "rb").read())
     return h.hexdigest()[:16]
@@ -410,6 +411,71 @@ def run_gpu(args):
     return 0 if ok else 1
 
 
+def batch_leg(tg, device, stream, steps, warmup):
+    """The 512 mixed products (lengths uniform in [200, 20000], coefficient bits uniform in
+    [64, 1024]) with operands resident on the device: one zx_mul_batch call per step against
+    the same products as 512 zx_mul calls, results compared word for word."""
+    import numpy as np
+    import torch
+
+    shapes = workloads.batch_shapes()
+    seed = workloads.BATCH_MIXED["seed"] * 1000
+    items, outs_plain = [], []
+    for k, (lf, lg, bits) in enumerate(shapes):
+        m = (bits + 63) // 64
+        f = workloads.coefficients(seed + 2 * k, lf, bits, m)
+        g = workloads.coefficients(seed + 2 * k + 1, lg, bits, m)
+        mh = tg.zx_plan(lf, bits, lg, bits)["limbs_h"]
+        F = torch.from_numpy(f.view(np.int64)).to(device)
+        G = torch.from_numpy(g.view(np.int64)).to(device)
+        H = torch.zeros((lf + lg - 1) * mh, dtype=torch.int64, device=device)
+        items.append((F, lf, m, G, lg, m, H, mh, False, bits, bits))
+        outs_plain.append(torch.zeros_like(H))
+    torch.cuda.synchronize(device)
+
+    def batched():
+        tg.zx_mul_batch(items, stream=stream)
+
+    def plain():
+        for (F, lf, m, G, lg, _, _, mh, sg, b, _), Hp in zip(items, outs_plain):
+            tg.zx_mul(F, lf, m, G, lg, m, Hp, mh, sg, b, b, stream=stream)
+
+    def timed(fn, k, w):
+        for _ in range(w):
+            fn()
+        torch.cuda.synchronize(device)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(k):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize(device)
+        return a.elapsed_time(b) / 1e3 / k
+
+    tb = timed(batched, steps, warmup)
+    tp = timed(plain, max(1, steps // 2), 1)
+    same = all(torch.equal(it[6], hp) for it, hp in zip(items, outs_plain))
+    count = len(items)
+    return {"workload": "512 independent Z[x] products, lengths U[200, 20000], coefficient bits U[64, 1024], "
+                        "unsigned, seed 4; each product in its own ring",
+            "products_per_s": round(count / tb, 2), "plain_products_per_s": round(count / tp, 2),
+            "ms_per_batch": round(tb * 1e3, 3), "ms_plain": round(tp * 1e3, 3),
+            "speedup_vs_plain": round(tp / tb, 3), "bit_exact_vs_plain": bool(same)}
+
+
+def run_batch(args):
+    import torch
+
+    import paper_0810_3203_gb300 as tg
+
+    device = torch.device("cuda", 0)
+    torch.cuda.set_device(device)
+    tg.load()
+    res = batch_leg(tg, device, torch.cuda.current_stream(device), args.steps, args.warmup)
+    print(json.dumps(res), flush=True)
+    return 0 if res["bit_exact_vs_plain"] else 1
+
+
 def run_profile_case(args):
     """One TFT and one ITFT at n = 40000 on one 269 MB buffer (the case ncu captures)."""
     import numpy as np
@@ -443,6 +509,8 @@ def main():
     ap.add_argument("--profile-case", action="store_true",
                     help="run one TFT + ITFT at n = 40000 and exit (the case profiled with ncu)")
     ap.add_argument("--profile-reps", type=int, default=1)
+    ap.add_argument("--batch-only", action="store_true",
+                    help="time only the 512-product batch against one-at-a-time products")
     args = ap.parse_args()
     if args.profile_case:
         return run_profile_case(args)
@@ -450,6 +518,8 @@ def main():
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
         return run_reference(args)
+    if args.batch_only:
+        return run_batch(args)
     return run_gpu(args)
 
 

@@ -106,6 +106,9 @@ typedef struct {
     int64_t scratch_bytes; /* device scratch the product needs (two ring buffers) */
     int32_t tft_passes;    /* kernel passes of one forward transform */
     int32_t itft_passes;   /* kernel passes of the inverse transform */
+    int64_t n_fft;         /* transform outputs computed: n rounded up to whole rows of the
+                              top-level row/column split (the zero padding of Sec. 6), n when
+                              one CTA holds the whole transform */
 } zx_plan_info;
 
 /*
@@ -119,8 +122,9 @@ int zx_plan(int64_t len_f, int64_t bits_f, int64_t len_g, int64_t bits_g, int is
 
 /*
  * h = f * g in Z[x] by Schoenhage-Strassen with truncated transforms (Sec. 2 R[X] product and
- * Sec. 5.1): pack into R, TFT(f), TFT(g), n pointwise products in R, ITFT, division by L,
- * lift to Z.
+ * Sec. 5.1): pack into R, TFT(f), TFT(g), n_fft pointwise products in R, ITFT, division by L,
+ * lift to Z. The product's n coefficients are padded with known zeros to n_fft (zx_plan) so
+ * that the ITFT has no partial row (Sec. 6); the padded coefficients are not returned.
  *   f, g   inputs, host or device (each independently); not modified.
  *   h      caller-allocated output with h->len == f->len + g->len - 1 (else ZX_EINVAL) and
  *          h->limbs >= zx_plan(...).limbs_h (else ZX_EBUFSIZE and h->limbs is overwritten

@@ -45,7 +45,7 @@ class ZxPoly(C.Structure):
 class ZxPlanInfo(C.Structure):
     _fields_ = [("l", C.c_int32), ("K", C.c_int32), ("N", C.c_int64), ("n", C.c_int64),
                 ("stride_limbs", C.c_int64), ("limbs_h", C.c_int64), ("scratch_bytes", C.c_int64),
-                ("tft_passes", C.c_int32), ("itft_passes", C.c_int32)]
+                ("tft_passes", C.c_int32), ("itft_passes", C.c_int32), ("n_fft", C.c_int64)]
 
 
 class ZxTransformInfo(C.Structure):

@@ -70,7 +70,7 @@ static int transform(int kind, uint64_t *x, int l, int64_t z, int64_t n, int f, 
 
 struct ZxPlan {
   int l;
-  int64_t N, n, stride, limbs_h, L;
+  int64_t N, n, nf, stride, limbs_h, L;
   Ring ring;
 };
 
@@ -88,6 +88,7 @@ static int make_zx_plan(int64_t lf, int64_t bf, int64_t lg, int64_t bg, int sgn,
   zp->l = int(l);
   zp->N = N;
   zp->n = n;
+  zp->nf = zero_padded_outputs(int(l), n, N);
   zp->L = L;
   int64_t W = N / 64 + 1;
   zp->stride = W + (W & 1);  // even stride keeps every cell 16-byte aligned
@@ -194,8 +195,9 @@ int zx_plan(int64_t len_f, int64_t bits_f, int64_t len_g, int64_t bits_g, int is
   out->stride_limbs = zp.stride;
   out->limbs_h = zp.limbs_h;
   out->scratch_bytes = 2 * zp.L * zp.stride * 8;
-  out->tft_passes = count_passes(KIND_TFT, zp.l, zp.n, zp.n, 0, zp.N);
-  out->itft_passes = count_passes(KIND_ITFT, zp.l, zp.n, zp.n, 0, zp.N);
+  out->tft_passes = count_passes(KIND_TFT, zp.l, zp.nf, zp.nf, 0, zp.N);
+  out->itft_passes = count_passes(KIND_ITFT, zp.l, zp.nf, zp.nf, 0, zp.N);
+  out->n_fft = zp.nf;
   return ZX_OK;
 }
 
@@ -239,9 +241,9 @@ int zx_mul(const zx_poly *f, const zx_poly *g, zx_poly *h, void *stream) {
   }
   cudaError_t ce;
   int err = ZX_OK;
-  const TransformPlan *pf = get_transform_plan(KIND_TFT, zp.l, f->len, zp.n, 0, zp.N, 0, zp.stride, 0, &err);
-  const TransformPlan *pg = pf ? get_transform_plan(KIND_TFT, zp.l, g->len, zp.n, 0, zp.N, 0, zp.stride, 0, &err) : nullptr;
-  const TransformPlan *pi = pg ? get_transform_plan(KIND_ITFT, zp.l, zp.n, zp.n, 0, zp.N, 0, zp.stride, 1, &err) : nullptr;
+  const TransformPlan *pf = get_transform_plan(KIND_TFT, zp.l, f->len, zp.nf, 0, zp.N, 0, zp.stride, 0, &err);
+  const TransformPlan *pg = pf ? get_transform_plan(KIND_TFT, zp.l, g->len, zp.nf, 0, zp.N, 0, zp.stride, 0, &err) : nullptr;
+  const TransformPlan *pi = pg ? get_transform_plan(KIND_ITFT, zp.l, zp.nf, zp.nf, 0, zp.N, 0, zp.stride, 1, &err) : nullptr;
   if (!pi) {
     cleanup();
     return fail(err ? err : ZX_ECUDA, "planning failed");
@@ -250,7 +252,7 @@ int zx_mul(const zx_poly *f, const zx_poly *g, zx_poly *h, void *stream) {
       (ce = launch_pack(dg, g->len, g->limbs, g->is_signed, Gb, zp.stride, zp.ring, s)) != cudaSuccess ||
       (ce = run_transform(*pf, F, zp.stride, s)) != cudaSuccess ||
       (ce = run_transform(*pg, Gb, zp.stride, s)) != cudaSuccess ||
-      (ce = launch_pointwise(F, Gb, zp.n, zp.stride, zp.ring, s)) != cudaSuccess ||
+      (ce = launch_pointwise(F, Gb, zp.nf, zp.stride, zp.ring, s)) != cudaSuccess ||
       (ce = run_transform(*pi, F, zp.stride, s)) != cudaSuccess ||
       (ce = launch_lift(F, zp.n, zp.stride, sgn, hd, h->limbs, zp.ring, s)) != cudaSuccess) {
     cleanup();
@@ -271,13 +273,51 @@ int zx_mul(const zx_poly *f, const zx_poly *g, zx_poly *h, void *stream) {
 
 int zx_mul_batch(const zx_poly *fs, const zx_poly *gs, zx_poly *hs, int count, void *stream) {
   if (count < 0 || (count > 0 && (!fs || !gs || !hs))) return fail(ZX_EINVAL, "bad batch arguments");
+  std::vector<BatchProduct> items(static_cast<size_t>(count));
   for (int i = 0; i < count; i++) {
-    int rc = zx_mul(fs + i, gs + i, hs + i, stream);
-    if (rc) {
-      set_error("product " + std::to_string(i) + ": " + zx_last_error());
+    const zx_poly *f = fs + i, *g = gs + i;
+    zx_poly *h = hs + i;
+    const std::string tag = "product " + std::to_string(i) + ": ";
+    int rc;
+    if ((rc = check_poly(f, "f")) || (rc = check_poly(g, "g")) || (rc = check_poly(h, "h"))) {
+      set_error(tag + g_last_error);
       return rc;
     }
+    if (f->where != ZX_DEVICE || g->where != ZX_DEVICE || h->where != ZX_DEVICE)
+      return fail(ZX_EINVAL, tag + "zx_mul_batch takes device operands only");
+    if (h->len != f->len + g->len - 1) return fail(ZX_EINVAL, tag + "h->len must be f->len + g->len - 1");
+    const int sgn = (f->is_signed || g->is_signed) ? 1 : 0;
+    ZxPlan zp;
+    if ((rc = make_zx_plan(f->len, poly_bits(f), g->len, poly_bits(g), sgn, &zp))) {
+      set_error(tag + g_last_error);
+      return rc;
+    }
+    if (h->limbs < zp.limbs_h) {
+      h->limbs = zp.limbs_h;
+      return fail(ZX_EBUFSIZE, tag + "h->limbs too small (needed count written to h->limbs)");
+    }
+    BatchProduct &b = items[size_t(i)];
+    b.f = f->data;
+    b.g = g->data;
+    b.h = h->data;
+    b.len_f = f->len;
+    b.len_g = g->len;
+    b.limbs_f = f->limbs;
+    b.limbs_g = g->limbs;
+    b.limbs_h = h->limbs;
+    b.signed_f = f->is_signed ? 1 : 0;
+    b.signed_g = g->is_signed ? 1 : 0;
+    b.sgn = sgn;
+    b.l = zp.l;
+    b.N = zp.N;
+    b.n = zp.n;
+    b.nf = zp.nf;
+    b.stride = zp.stride;
   }
+  for (int i = 0; i < count; i++) hs[i].is_signed = items[size_t(i)].sgn;
+  std::string msg;
+  int rc = run_mul_batch(items, cudaStream_t(stream), &msg);
+  if (rc) return fail(rc, msg);
   return ZX_OK;
 }
 

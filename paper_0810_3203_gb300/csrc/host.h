@@ -70,6 +70,11 @@ struct TransformPlan {
 const TransformPlan *get_transform_plan(int kind, int l, int64_t z, int64_t n, int f, int64_t N,
                                         int64_t e, int64_t stride_limbs, int scale, int *err);
 
+// Outputs a product's transforms compute when the product length n is padded with known zero
+// coefficients up to a whole number of rows of the top-level split (Sec. 6): the ITFT then has
+// no partial row and is the TFT's steps reversed. n itself when one CTA holds the transform.
+int64_t zero_padded_outputs(int l, int64_t n, int64_t N);
+
 // Number of global-memory passes of a transform (host only; no device needed).
 int count_passes(int kind, int l, int64_t z, int64_t n, int f, int64_t N);
 // passes, launches and jobs of a transform's plan (host only)
@@ -92,6 +97,18 @@ struct HostPlan {
 void build_host_plan(int kind, int l, int64_t z, int64_t n, int f, int64_t N, int64_t e, int scale,
                      HostPlan *out);
 
+// One job of a plan with its pass index and launch shape; `d.image` is a device pointer into
+// the shared image cache.
+struct PlannedJob {
+  int pass = 0, ls = 0, lc = 0, prog_words = 0;
+  JobDesc d;
+};
+// Jobs of a TFT / ITFT plan (host side, images resolved on the current device). Returns the
+// number of passes, or -1 with *err set.
+int plan_jobs(int kind, int l, int64_t z, int64_t n, int f, int64_t N, int64_t e, int scale,
+              std::vector<PlannedJob> *out, int *err);
+int warps_for_job(int ls, int lc);
+
 // Enqueue a plan on a stream.
 cudaError_t run_transform(const TransformPlan &p, uint64_t *x, int64_t stride_limbs,
                           cudaStream_t s);
@@ -103,6 +120,42 @@ cudaError_t launch_pointwise(uint64_t *a, const uint64_t *b, int64_t n, int64_t 
                              const Ring &r, cudaStream_t s);
 cudaError_t launch_lift(const uint64_t *cells, int64_t n, int64_t stride_limbs, int is_signed,
                         uint64_t *out, int64_t limbs_out, const Ring &r, cudaStream_t s);
+
+// Batched forms over many products of one ring (item descriptors in device memory). Cell
+// arrays are given as limb offsets from `pool`; operands and outputs as device pointers.
+struct PackItem {
+  const uint64_t *coef;
+  int64_t cells;  // limb offset of the first cell in the pool
+  int64_t len, limbs;
+  int32_t is_signed, pad;
+};
+struct PointwiseItem {
+  int64_t a, b;  // limb offsets of the two cell arrays (a <- a * b)
+  int64_t n;
+};
+struct LiftItem {
+  int64_t cells;  // limb offset
+  uint64_t *out;
+  int64_t n, limbs_out;
+  int32_t is_signed, pad;
+};
+cudaError_t launch_pack_batch(const PackItem *d_items, int count, int64_t max_len, int64_t stride_limbs,
+                              const Ring &r, uint64_t *pool, cudaStream_t s);
+cudaError_t launch_pointwise_batch(const PointwiseItem *d_items, int count, int64_t max_n, int64_t stride_limbs,
+                                   const Ring &r, uint64_t *pool, cudaStream_t s);
+cudaError_t launch_lift_batch(const LiftItem *d_items, int count, int64_t max_n, int64_t stride_limbs,
+                              const Ring &r, uint64_t *pool, cudaStream_t s);
+
+// One product of a batch (operands and output in device memory; ring chosen by the caller).
+struct BatchProduct {
+  const uint64_t *f = nullptr, *g = nullptr;
+  uint64_t *h = nullptr;
+  int64_t len_f = 0, len_g = 0, limbs_f = 0, limbs_g = 0, limbs_h = 0;
+  int32_t signed_f = 0, signed_g = 0, sgn = 0, l = 0;
+  int64_t N = 0, n = 0, nf = 0, stride = 0;  // nf: zero-padded transform outputs
+};
+// Enqueue the products on `s` (zx_batch.cu). Returns ZX_OK or a ZX_* status with *msg set.
+int run_mul_batch(const std::vector<BatchProduct> &items, cudaStream_t s, std::string *msg);
 
 // per-thread error text
 void set_error(const std::string &msg);

@@ -205,6 +205,15 @@ PlanCache &plan_cache() {
   return *c;
 }
 
+}  // namespace
+
+int warps_for_job(int ls, int lc) {
+  int nslots = 1 << (ls - lc);
+  return std::max(1, std::min(16, nslots / 2));
+}
+
+namespace {
+
 // warps per CTA: one per butterfly of a full level, at most 16
 int warps_for(int ls, int lc) {
   int nslots = 1 << (ls - lc);
@@ -219,6 +228,22 @@ bool launch_order(const JobRec &a, const JobRec &b) {
 }
 
 }  // namespace
+
+int64_t zero_padded_outputs(int l, int64_t n, int64_t N) {
+  Planner P;
+  P.ring = make_ring(N);
+  P.twoN = 2 * N;
+  P.ls_max = max_onchip_ls(P.ring);
+  P.ls_c = cluster_cta_ls(P.ring);
+  int64_t row;
+  if (!P.leaf(l))
+    row = int64_t(1) << (l - l / 2);  // rows of the top-level split over global memory
+  else if (P.cluster_log2(l) > 0)
+    row = int64_t(1) << (l - P.cluster_log2(l));  // rows of the job's split across its CTAs
+  else
+    return n;  // one CTA holds the whole transform: a partial row costs no extra pass
+  return std::min(int64_t(1) << l, (n + row - 1) / row * row);
+}
 
 int count_passes(int kind, int l, int64_t z, int64_t n, int f, int64_t N) {
   Planner P;
@@ -291,6 +316,33 @@ void build_host_plan(int kind, int l, int64_t z, int64_t n, int f, int64_t N, in
     out->groups.push_back(std::move(g));
     i = k;
   }
+}
+
+int plan_jobs(int kind, int l, int64_t z, int64_t n, int f, int64_t N, int64_t e, int scale,
+              std::vector<PlannedJob> *out, int *err) {
+  int64_t twoN = 2 * N;
+  e = md(e, twoN);
+  Planner P;
+  P.ring = make_ring(N);
+  P.twoN = twoN;
+  P.ls_max = max_onchip_ls(P.ring);
+  P.ls_c = cluster_cta_ls(P.ring);
+  int npass = kind == KIND_TFT ? P.tft(0, 0, 1, l, e, z, n)
+                               : P.itft(0, 0, 1, l, e, z, n, f, scale ? md(twoN - l, twoN) : -1);
+  out->clear();
+  out->reserve(P.jobs.size());
+  for (JobRec &j : P.jobs) {
+    j.d.image = image_cache().get(j.kind, j.ls, j.lc, j.z, j.n, j.f, N, err);
+    if (!j.d.image) return -1;
+    PlannedJob pj;
+    pj.pass = j.pass;
+    pj.ls = j.ls;
+    pj.lc = j.lc;
+    pj.prog_words = image_cache().max_prog(j.d.image);
+    pj.d = j.d;
+    out->push_back(pj);
+  }
+  return npass;
 }
 
 const TransformPlan *get_transform_plan(int kind, int l, int64_t z, int64_t n, int f, int64_t N,

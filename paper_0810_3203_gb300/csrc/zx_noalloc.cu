@@ -159,9 +159,9 @@ extern "C" int zx_mul_noalloc(const zx_poly *f, const zx_poly *g, zx_poly *h, vo
   NoAllocDevice *st = nullptr;
   if ((rc = device_state(&st))) return rc;
   const TransformPlan *pf = nullptr, *pg = nullptr, *pi = nullptr;
-  if ((rc = plan_in_scratch(*st, KIND_TFT, info.l, f->len, info.n, 0, info.N, 0, s, &pf)) ||
-      (rc = plan_in_scratch(*st, KIND_TFT, info.l, g->len, info.n, 0, info.N, 0, s, &pg)) ||
-      (rc = plan_in_scratch(*st, KIND_ITFT, info.l, info.n, info.n, 0, info.N, 1, s, &pi)))
+  if ((rc = plan_in_scratch(*st, KIND_TFT, info.l, f->len, info.n_fft, 0, info.N, 0, s, &pf)) ||
+      (rc = plan_in_scratch(*st, KIND_TFT, info.l, g->len, info.n_fft, 0, info.N, 0, s, &pg)) ||
+      (rc = plan_in_scratch(*st, KIND_ITFT, info.l, info.n_fft, info.n_fft, 0, info.N, 1, s, &pi)))
     return rc;
   uint64_t *F = st->base, *G = st->base + ring;
   const Ring &r = pf->ring;
@@ -171,7 +171,7 @@ extern "C" int zx_mul_noalloc(const zx_poly *f, const zx_poly *g, zx_poly *h, vo
       (ce = launch_pack(g->data, g->len, g->limbs, g->is_signed, G, info.stride_limbs, r, s)) != cudaSuccess ||
       (ce = run_transform(*pf, F, info.stride_limbs, s)) != cudaSuccess ||
       (ce = run_transform(*pg, G, info.stride_limbs, s)) != cudaSuccess ||
-      (ce = launch_pointwise(F, G, info.n, info.stride_limbs, r, s)) != cudaSuccess ||
+      (ce = launch_pointwise(F, G, info.n_fft, info.stride_limbs, r, s)) != cudaSuccess ||
       (ce = run_transform(*pi, F, info.stride_limbs, s)) != cudaSuccess ||
       (ce = launch_lift(F, info.n, info.stride_limbs, sgn, h->data, h->limbs, r, s)) != cudaSuccess)
     return na_fail(ZX_ECUDA, std::string("zx_mul_noalloc launch: ") + cudaGetErrorString(ce));

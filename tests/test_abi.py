@@ -46,6 +46,25 @@ def test_plan_medium_product():
     assert p["tft_passes"] == 2 and p["itft_passes"] >= 2
 
 
+def test_zero_padded_product_length():
+    """Sec. 6: the product's length is padded with known zeros to whole rows of the top-level
+    split, so the ITFT is the TFT's steps reversed: as many passes as the TFT, no last row."""
+    import paper_0810_3203_gb300 as tg
+    p = tg.zx_plan(3000, 2000, 2500, 2000)
+    assert p["n_fft"] == 5504  # 43 rows of 2^7 cells (split 2^6 x 2^7), n = 5499
+    assert p["itft_passes"] == p["tft_passes"] == 2
+    for lf, lg, bits in ((20000, 20000, 1024), (16385, 1, 64), (12000, 9000, 700), (150, 150, 3000)):
+        p = tg.zx_plan(lf, bits, lg, bits)
+        n, nf, L = p["n"], p["n_fft"], 1 << p["l"]
+        assert n <= nf <= L
+        shape = tg.transform_plan(1, p["l"], nf, nf, p["N"])
+        exact = tg.transform_plan(1, p["l"], n, n, p["N"])
+        assert p["itft_passes"] == shape["passes"] <= exact["passes"]
+        assert p["itft_passes"] == p["tft_passes"], (lf, lg, bits, p)
+        if nf > n and exact["passes"] > 1:  # over global memory: rows, then columns, no last row
+            assert shape["passes"] < exact["passes"]
+
+
 def test_plan_sizes_follow_the_ring_rule():
     import paper_0810_3203_gb300 as tg
     for lf, lg, bits in ((1, 1, 1), (100, 100, 64), (20000, 20000, 1024), (5, 70000, 10)):
