@@ -94,7 +94,7 @@ def kernel_source_hash():
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_0810_3203_gb300", "csrc")
     # the files that decide what the transform kernel does and which launches a plan makes
-    for f in ("common.h", "host.h", "plan.cpp", "program.cpp", "ring_warp.cuh", "transform_kernel.cu"):
+    for f in ("common.h", "plan.cpp", "program.cpp", "ring_warp.cuh", "transform_kernel.cu"):
         h.update(f.encode())
         h.update(open(os.path.join(csrc, f), "rb").read())
     return h.hexdigest()[:16]
@@ -379,6 +379,29 @@ def run_gpu(args):
         ok &= bool(np.array_equal(outp[n].numpy().view(np.uint64).reshape(-1, stride)[:n, :W],
                                   host[n].reshape(-1, stride)[:n, :W]))
 
+    # Sec. 6 zero padding (used inside the products): the exact Algorithm 2 ITFT against the ITFT
+    # of n rounded up to whole rows of 2^8 cells (no last-row step), same buffers, timing only
+    padded = {}
+    for n in ns:
+        n_pad = -(-n // 256) * 256
+
+        def exact(n=n):
+            tg.itft_ex(dev[n], l, n, n, 0, N, 0, stride, 1, stream=stream)
+
+        def pad(n=n, n_pad=n_pad):
+            tg.itft_ex(dev[n], l, n_pad, n_pad, 0, N, 0, stride, 1, stream=stream)
+
+        te = timed_steps(exact, 3, 1, sync, device)
+        tp = timed_steps(pad, 3, 1, sync, device)
+        padded[str(n)] = {"n_padded": n_pad, "exact_ms": round(te / 3 * 1e3, 3), "padded_ms": round(tp / 3 * 1e3, 3),
+                          "passes_exact": tg.transform_plan(1, l, n, n, N)["passes"],
+                          "passes_padded": tg.transform_plan(1, l, n_pad, n_pad, N)["passes"]}
+
+    batch = None if args.no_batch else batch_leg(tg, device, stream, 2, 3)
+    ok &= batch is None or batch["bit_exact_vs_plain"]
+    serve = None if args.no_serve else serve_leg(tg, device, stream, args.serve_requests)
+    ok &= serve is None or serve["bit_exact_vs_plain"]
+
     if rank != 0:
         return 0 if ok else 1
     cpu = None if args.no_cpu_baseline else cpu_baseline(N, l)
@@ -405,6 +428,11 @@ def run_gpu(args):
         "bit_exact_roundtrip": ok,
         "wall_s": round(wall, 3),
     }
+    line["zero_padded_itft"] = padded
+    if batch is not None:
+        line["batch"] = batch
+    if serve is not None:
+        line["serve"] = serve
     if cpu is not None:
         line["cpu_baseline"] = cpu
     print(json.dumps(line), flush=True)
@@ -463,6 +491,76 @@ def batch_leg(tg, device, stream, steps, warmup):
             "speedup_vs_plain": round(tp / tb, 3), "bit_exact_vs_plain": bool(same)}
 
 
+def serve_leg(tg, device, stream, count):
+    """Poisson arrivals (mean 2000 requests/s) of products with lengths log-uniform in
+    [2^8, 2^15] and coefficient bits log-uniform in [64, 4096], operands resident on the
+    device. The serving loop (continuous batching) against the plain path, where each request
+    runs alone with zx_mul once the previous one has finished; latency = completion - arrival."""
+    import numpy as np
+    import torch
+
+    reqs = workloads.serve_requests(count)
+    seed = workloads.SERVE_POISSON["seed"] * 1000
+    items, plain_out = [], []
+    for k, (_, lf, lg, bits) in enumerate(reqs):
+        m = (bits + 63) // 64
+        f = workloads.coefficients(seed + 2 * k, lf, bits, m)
+        g = workloads.coefficients(seed + 2 * k + 1, lg, bits, m)
+        mh = tg.zx_plan(lf, bits, lg, bits)["limbs_h"]
+        F = torch.from_numpy(f.view(np.int64)).to(device)
+        G = torch.from_numpy(g.view(np.int64)).to(device)
+        H = torch.zeros((lf + lg - 1) * mh, dtype=torch.int64, device=device)
+        items.append((F, lf, m, G, lg, m, H, mh, False, bits, bits))
+        plain_out.append(torch.zeros_like(H))
+    torch.cuda.synchronize(device)
+    arrivals = [t for t, _, _, _ in reqs]
+
+    def pct(v, q):
+        v = sorted(v)
+        return v[min(len(v) - 1, int(q * len(v)))]
+
+    with tg.Server(slots=3) as srv:
+        for it in items[:16]:  # warm the plan caches
+            srv.submit(*it)
+        srv.drain(600.0)
+        srv.poll(4096)
+        lat = {}
+        t_srv = time.perf_counter()
+        ids = {}
+        for k, it in enumerate(items):
+            while time.perf_counter() - t_srv < arrivals[k]:
+                pass
+            ids[srv.submit(*it)] = k
+        srv.drain(600.0)
+        t_end = time.perf_counter()
+        for rid, st, sec in srv.poll(count + 16):
+            if st != 0:
+                raise RuntimeError(f"request {rid} failed with status {st}")
+            lat[ids[rid]] = sec
+        stats = srv.stats()
+    served = [lat[k] for k in range(count)]
+
+    plain_lat = []
+    t0 = time.perf_counter()
+    for k, ((F, lf, m, G, lg, _, _, mh, sg, b, _), Hp) in enumerate(zip(items, plain_out)):
+        while time.perf_counter() - t0 < arrivals[k]:
+            pass
+        tg.zx_mul(F, lf, m, G, lg, m, Hp, mh, sg, b, b, stream=stream)
+        torch.cuda.synchronize(device)
+        plain_lat.append(time.perf_counter() - t0 - arrivals[k])
+    t_plain = time.perf_counter() - t0
+    same = all(torch.equal(it[6], hp) for it, hp in zip(items, plain_out))
+    return {"workload": f"{count} requests, Poisson arrivals at 2000/s, lengths log-uniform [2^8, 2^15], "
+                        "coefficient bits log-uniform [64, 4096], unsigned, seed 5",
+            "products_per_s": round(count / (t_end - t_srv), 2),
+            "p50_ms": round(pct(served, 0.5) * 1e3, 3), "p99_ms": round(pct(served, 0.99) * 1e3, 3),
+            "plain_products_per_s": round(count / t_plain, 2),
+            "plain_p50_ms": round(pct(plain_lat, 0.5) * 1e3, 3), "plain_p99_ms": round(pct(plain_lat, 0.99) * 1e3, 3),
+            "offered_per_s": round(count / arrivals[-1], 1), "waves": stats["waves"],
+            "max_wave_products": stats["max_wave_products"], "max_waves_in_flight": stats["max_waves_in_flight"],
+            "arena_peak_gb": round(stats["arena_peak_bytes"] / 1e9, 3), "bit_exact_vs_plain": bool(same)}
+
+
 def run_batch(args):
     import torch
 
@@ -472,6 +570,19 @@ def run_batch(args):
     torch.cuda.set_device(device)
     tg.load()
     res = batch_leg(tg, device, torch.cuda.current_stream(device), args.steps, args.warmup)
+    print(json.dumps(res), flush=True)
+    return 0 if res["bit_exact_vs_plain"] else 1
+
+
+def run_serve(args):
+    import torch
+
+    import paper_0810_3203_gb300 as tg
+
+    device = torch.device("cuda", 0)
+    torch.cuda.set_device(device)
+    tg.load()
+    res = serve_leg(tg, device, torch.cuda.current_stream(device), args.serve_requests)
     print(json.dumps(res), flush=True)
     return 0 if res["bit_exact_vs_plain"] else 1
 
@@ -509,6 +620,10 @@ def main():
     ap.add_argument("--profile-case", action="store_true",
                     help="run one TFT + ITFT at n = 40000 and exit (the case profiled with ncu)")
     ap.add_argument("--profile-reps", type=int, default=1)
+    ap.add_argument("--no-batch", action="store_true", help="skip the 512-product batch leg")
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving leg")
+    ap.add_argument("--serve-requests", type=int, default=1000)
+    ap.add_argument("--serve-only", action="store_true", help="time only the serving leg")
     ap.add_argument("--batch-only", action="store_true",
                     help="time only the 512-product batch against one-at-a-time products")
     args = ap.parse_args()
@@ -520,6 +635,8 @@ def main():
         return run_reference(args)
     if args.batch_only:
         return run_batch(args)
+    if args.serve_only:
+        return run_serve(args)
     return run_gpu(args)
 
 

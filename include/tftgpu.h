@@ -107,7 +107,8 @@ typedef struct {
     int32_t tft_passes;    /* kernel passes of one forward transform */
     int32_t itft_passes;   /* kernel passes of the inverse transform */
     int64_t n_fft;         /* transform outputs computed: n rounded up to whole rows of the
-                              top-level row/column split (the zero padding of Sec. 6), n when
+                              top-level row/column split (the zero padding of Sec. 6), and of
+                              the column jobs' own split when that adds at most n/32; n when
                               one CTA holds the whole transform */
 } zx_plan_info;
 
@@ -163,6 +164,39 @@ int zx_mul_batch(const zx_poly *fs, const zx_poly *gs, zx_poly *hs, int count, v
  * It calls no cudaMalloc, cudaFree or other allocating routine; the call is asynchronous.
  */
 int zx_mul_noalloc(const zx_poly *f, const zx_poly *g, zx_poly *h, void *stream);
+
+/*
+ * Serving loop: continuous batching of Z[x] products on the current device (no counterpart in
+ * the paper; it schedules the zx_mul_batch path). zx_server_create reserves a device arena of
+ * arena_bytes (<= 0: half of the free device memory) and `slots` streams (1..8) and starts a
+ * worker thread. zx_server_submit queues h = f * g (every operand in device memory, same rules
+ * as zx_mul; h->is_signed is set) and returns at once with a request id; a product whose ring
+ * buffers exceed the arena is refused with ZX_ENOMEM. The worker admits the longest prefix of
+ * the queue whose ring buffers fit the free arena into a free slot as one batch, so requests
+ * that arrive while others run start as soon as a slot and memory are free and overlap with
+ * them on the GPU. f, g and h must stay valid until the request is returned by zx_server_poll.
+ * zx_server_poll returns up to `max` finished requests (id, status, seconds from submission to
+ * completion; status and latency_s may be NULL). zx_server_drain waits until nothing is queued
+ * or running (timeout_s < 0: no limit; ZX_ETIMEOUT otherwise). zx_server_destroy finishes the
+ * queued work, stops the worker and frees everything; unpolled results are dropped.
+ */
+typedef struct zx_server zx_server;
+
+typedef struct {
+    int64_t submitted, completed, pending;
+    int64_t waves;             /* batches launched */
+    int64_t max_wave_products; /* largest batch */
+    int32_t slots;
+    int32_t max_waves_in_flight;
+    int64_t arena_bytes, arena_peak_bytes;
+} zx_server_info;
+
+int zx_server_create(int64_t arena_bytes, int slots, zx_server **out);
+int zx_server_submit(zx_server *srv, const zx_poly *f, const zx_poly *g, zx_poly *h, int64_t *id);
+int zx_server_poll(zx_server *srv, int64_t *ids, int32_t *status, double *latency_s, int max, int *count);
+int zx_server_drain(zx_server *srv, double timeout_s);
+int zx_server_stats(zx_server *srv, zx_server_info *out);
+int zx_server_destroy(zx_server *srv);
 
 /* Shape of the launch plan of one transform (host only, no device needed). */
 typedef struct {

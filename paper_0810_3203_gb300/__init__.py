@@ -24,7 +24,8 @@ ZX_HOST, ZX_DEVICE = 0, 1
 # every entry point the header declares (checked by tests/test_abi.py)
 EXPORTS = ("tft", "tft_ex", "itft", "itft_ex", "zx_plan", "zx_mul", "zx_mul_batch",
            "zx_transform_plan", "zx_mul_noalloc", "zx_job_program", "zx_strerror", "zx_last_error",
-           "zx_version")
+           "zx_version", "zx_server_create", "zx_server_submit", "zx_server_poll", "zx_server_drain",
+           "zx_server_stats", "zx_server_destroy")
 
 _lib = None
 
@@ -46,6 +47,13 @@ class ZxPlanInfo(C.Structure):
     _fields_ = [("l", C.c_int32), ("K", C.c_int32), ("N", C.c_int64), ("n", C.c_int64),
                 ("stride_limbs", C.c_int64), ("limbs_h", C.c_int64), ("scratch_bytes", C.c_int64),
                 ("tft_passes", C.c_int32), ("itft_passes", C.c_int32), ("n_fft", C.c_int64)]
+
+
+class ZxServerInfo(C.Structure):
+    _fields_ = [("submitted", C.c_int64), ("completed", C.c_int64), ("pending", C.c_int64),
+                ("waves", C.c_int64), ("max_wave_products", C.c_int64), ("slots", C.c_int32),
+                ("max_waves_in_flight", C.c_int32), ("arena_bytes", C.c_int64),
+                ("arena_peak_bytes", C.c_int64)]
 
 
 class ZxTransformInfo(C.Structure):
@@ -80,13 +88,23 @@ def load(build_if_missing=True):
     L.zx_mul_noalloc.argtypes = [C.POINTER(ZxPoly), C.POINTER(ZxPoly), C.POINTER(ZxPoly), vp]
     L.zx_job_program.argtypes = [i32, i32, i32, i64, i64, i32, i64, C.POINTER(C.c_uint32), i64,
                                  C.POINTER(C.c_int64)]
+    L.zx_server_create.argtypes = [i64, i32, C.POINTER(vp)]
+    L.zx_server_submit.argtypes = [vp, C.POINTER(ZxPoly), C.POINTER(ZxPoly), C.POINTER(ZxPoly),
+                                   C.POINTER(C.c_int64)]
+    L.zx_server_poll.argtypes = [vp, C.POINTER(C.c_int64), C.POINTER(C.c_int32), C.POINTER(C.c_double), i32,
+                                 C.POINTER(C.c_int)]
+    L.zx_server_drain.argtypes = [vp, C.c_double]
+    L.zx_server_stats.argtypes = [vp, C.POINTER(ZxServerInfo)]
+    L.zx_server_destroy.argtypes = [vp]
     L.zx_strerror.argtypes = [i32]
     L.zx_strerror.restype = C.c_char_p
     L.zx_last_error.argtypes = []
     L.zx_last_error.restype = C.c_char_p
     L.zx_version.restype = C.c_char_p
     for name in ("tft", "tft_ex", "itft", "itft_ex", "zx_plan", "zx_mul", "zx_mul_batch",
-                 "zx_transform_plan", "zx_mul_noalloc", "zx_job_program"):
+                 "zx_transform_plan", "zx_mul_noalloc", "zx_job_program", "zx_server_create",
+                 "zx_server_submit", "zx_server_poll", "zx_server_drain", "zx_server_stats",
+                 "zx_server_destroy"):
         getattr(L, name).restype = i32
     _lib = L
     return L
@@ -204,6 +222,60 @@ def zx_mul_batch(items, stream=None):
         Gs[i] = _poly(g, lg, mg, sg, bg)
         Hs[i] = _poly(h, lf + lg - 1, mh, sg, 0)
     _check(load().zx_mul_batch(Fs, Gs, Hs, n, _stream(stream)), "zx_mul_batch")
+
+
+class Server:
+    """Continuous-batching request loop on the current device (zx_server_* in the C ABI).
+
+    submit() queues one product of device tensors and returns its id at once; poll() returns
+    finished requests as (id, status, latency_seconds); drain() waits until nothing is queued
+    or running. The tensors of a request must stay alive until poll() has returned it."""
+
+    def __init__(self, arena_bytes=0, slots=3):
+        self._h = C.c_void_p()
+        _check(load().zx_server_create(arena_bytes, slots, C.byref(self._h)), "zx_server_create")
+        self._keep = {}
+
+    def submit(self, f, len_f, limbs_f, g, len_g, limbs_g, h, limbs_h, signed=False, bits_f=0, bits_g=0):
+        F = _poly(f, len_f, limbs_f, signed, bits_f)
+        G = _poly(g, len_g, limbs_g, signed, bits_g)
+        H = _poly(h, len_f + len_g - 1, limbs_h, signed, 0)
+        rid = C.c_int64()
+        _check(load().zx_server_submit(self._h, C.byref(F), C.byref(G), C.byref(H), C.byref(rid)),
+               "zx_server_submit")
+        self._keep[rid.value] = (f, g, h)
+        return rid.value
+
+    def poll(self, max_items=1024):
+        ids = (C.c_int64 * max_items)()
+        st = (C.c_int32 * max_items)()
+        lat = (C.c_double * max_items)()
+        n = C.c_int()
+        _check(load().zx_server_poll(self._h, ids, st, lat, max_items, C.byref(n)), "zx_server_poll")
+        out = [(ids[k], st[k], lat[k]) for k in range(n.value)]
+        for rid, _, _ in out:
+            self._keep.pop(rid, None)
+        return out
+
+    def drain(self, timeout_s=-1.0):
+        _check(load().zx_server_drain(self._h, timeout_s), "zx_server_drain")
+
+    def stats(self):
+        info = ZxServerInfo()
+        _check(load().zx_server_stats(self._h, C.byref(info)), "zx_server_stats")
+        return {k: getattr(info, k) for k, _ in ZxServerInfo._fields_}
+
+    def close(self):
+        if self._h:
+            load().zx_server_destroy(self._h)
+            self._h = C.c_void_p()
+            self._keep.clear()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
 
 
 def version():

@@ -122,6 +122,38 @@ static int stage_in(const zx_poly *p, uint64_t **dptr, uint64_t **tmp, cudaStrea
   return ZX_OK;
 }
 
+int device_product(const zx_poly *f, const zx_poly *g, zx_poly *h, BatchProduct *b) {
+  int rc;
+  if ((rc = check_poly(f, "f")) || (rc = check_poly(g, "g")) || (rc = check_poly(h, "h"))) return rc;
+  if (f->where != ZX_DEVICE || g->where != ZX_DEVICE || h->where != ZX_DEVICE)
+    return fail(ZX_EINVAL, "operands must be in device memory");
+  if (h->len != f->len + g->len - 1) return fail(ZX_EINVAL, "h->len must be f->len + g->len - 1");
+  const int sgn = (f->is_signed || g->is_signed) ? 1 : 0;
+  ZxPlan zp;
+  if ((rc = make_zx_plan(f->len, poly_bits(f), g->len, poly_bits(g), sgn, &zp))) return rc;
+  if (h->limbs < zp.limbs_h) {
+    h->limbs = zp.limbs_h;
+    return fail(ZX_EBUFSIZE, "h->limbs too small (needed count written to h->limbs)");
+  }
+  b->f = f->data;
+  b->g = g->data;
+  b->h = h->data;
+  b->len_f = f->len;
+  b->len_g = g->len;
+  b->limbs_f = f->limbs;
+  b->limbs_g = g->limbs;
+  b->limbs_h = h->limbs;
+  b->signed_f = f->is_signed ? 1 : 0;
+  b->signed_g = g->is_signed ? 1 : 0;
+  b->sgn = sgn;
+  b->l = zp.l;
+  b->N = zp.N;
+  b->n = zp.n;
+  b->nf = zp.nf;
+  b->stride = zp.stride;
+  return ZX_OK;
+}
+
 }  // namespace tftgpu
 
 using namespace tftgpu;
@@ -275,44 +307,11 @@ int zx_mul_batch(const zx_poly *fs, const zx_poly *gs, zx_poly *hs, int count, v
   if (count < 0 || (count > 0 && (!fs || !gs || !hs))) return fail(ZX_EINVAL, "bad batch arguments");
   std::vector<BatchProduct> items(static_cast<size_t>(count));
   for (int i = 0; i < count; i++) {
-    const zx_poly *f = fs + i, *g = gs + i;
-    zx_poly *h = hs + i;
-    const std::string tag = "product " + std::to_string(i) + ": ";
-    int rc;
-    if ((rc = check_poly(f, "f")) || (rc = check_poly(g, "g")) || (rc = check_poly(h, "h"))) {
-      set_error(tag + g_last_error);
+    int rc = device_product(fs + i, gs + i, hs + i, &items[size_t(i)]);
+    if (rc) {
+      set_error("product " + std::to_string(i) + ": " + g_last_error);
       return rc;
     }
-    if (f->where != ZX_DEVICE || g->where != ZX_DEVICE || h->where != ZX_DEVICE)
-      return fail(ZX_EINVAL, tag + "zx_mul_batch takes device operands only");
-    if (h->len != f->len + g->len - 1) return fail(ZX_EINVAL, tag + "h->len must be f->len + g->len - 1");
-    const int sgn = (f->is_signed || g->is_signed) ? 1 : 0;
-    ZxPlan zp;
-    if ((rc = make_zx_plan(f->len, poly_bits(f), g->len, poly_bits(g), sgn, &zp))) {
-      set_error(tag + g_last_error);
-      return rc;
-    }
-    if (h->limbs < zp.limbs_h) {
-      h->limbs = zp.limbs_h;
-      return fail(ZX_EBUFSIZE, tag + "h->limbs too small (needed count written to h->limbs)");
-    }
-    BatchProduct &b = items[size_t(i)];
-    b.f = f->data;
-    b.g = g->data;
-    b.h = h->data;
-    b.len_f = f->len;
-    b.len_g = g->len;
-    b.limbs_f = f->limbs;
-    b.limbs_g = g->limbs;
-    b.limbs_h = h->limbs;
-    b.signed_f = f->is_signed ? 1 : 0;
-    b.signed_g = g->is_signed ? 1 : 0;
-    b.sgn = sgn;
-    b.l = zp.l;
-    b.N = zp.N;
-    b.n = zp.n;
-    b.nf = zp.nf;
-    b.stride = zp.stride;
   }
   for (int i = 0; i < count; i++) hs[i].is_signed = items[size_t(i)].sgn;
   std::string msg;

@@ -7,6 +7,7 @@
 #include <string>
 #include <vector>
 
+#include "../../include/tftgpu.h"
 #include "common.h"
 
 namespace tftgpu {
@@ -72,7 +73,9 @@ const TransformPlan *get_transform_plan(int kind, int l, int64_t z, int64_t n, i
 
 // Outputs a product's transforms compute when the product length n is padded with known zero
 // coefficients up to a whole number of rows of the top-level split (Sec. 6): the ITFT then has
-// no partial row and is the TFT's steps reversed. n itself when one CTA holds the transform.
+// no partial row and is the TFT's steps reversed. Where the column sub-transforms run on
+// clusters, n is padded to whole rows of their in-job split too when that costs at most n/32.
+// n itself when one CTA holds the transform.
 int64_t zero_padded_outputs(int l, int64_t n, int64_t N);
 
 // Number of global-memory passes of a transform (host only; no device needed).
@@ -154,8 +157,35 @@ struct BatchProduct {
   int32_t signed_f = 0, signed_g = 0, sgn = 0, l = 0;
   int64_t N = 0, n = 0, nf = 0, stride = 0;  // nf: zero-padded transform outputs
 };
+// Checks one product of device operands and fills *b (api.cu); ZX_* status with the error
+// text set on failure. h->limbs is overwritten with the needed count on ZX_EBUFSIZE.
+int device_product(const zx_poly *f, const zx_poly *g, zx_poly *h, BatchProduct *b);
+
 // Enqueue the products on `s` (zx_batch.cu). Returns ZX_OK or a ZX_* status with *msg set.
 int run_mul_batch(const std::vector<BatchProduct> &items, cudaStream_t s, std::string *msg);
+
+// Products of one ring laid out in a pool: item arrays and merged per-pass job lists, all as
+// byte offsets into a descriptor image that is copied to the device as one block.
+struct BatchGroup {
+  Ring ring;
+  int64_t stride = 0;
+  int count = 0;
+  int64_t max_len = 0, max_n = 0;
+  size_t pack_off = 0, pw_off = 0, lift_off = 0;
+  std::vector<Launch> tft, itft;  // d_jobs hold descriptor-image byte offsets
+};
+struct BatchLayout {
+  size_t pool_bytes = 0;
+  std::vector<BatchGroup> groups;
+};
+// Ring buffer bytes of one product (two buffers of L cells).
+size_t product_pool_bytes(const BatchProduct &p);
+// Lay out the products idx (any order; grouped by ring inside) in one pool, appending their
+// descriptors to *desc (16-byte aligned). ZX_* status with *msg set on failure.
+int layout_batch(const std::vector<BatchProduct> &items, const std::vector<int> &idx,
+                 std::vector<unsigned char> *desc, BatchLayout *out, std::string *msg);
+// Enqueue one ring group: descriptors at d_desc on the device, ring buffers at pool.
+cudaError_t enqueue_group(const BatchGroup &g, unsigned char *d_desc, unsigned char *pool, cudaStream_t s);
 
 // per-thread error text
 void set_error(const std::string &msg);

@@ -235,14 +235,24 @@ int64_t zero_padded_outputs(int l, int64_t n, int64_t N) {
   P.twoN = 2 * N;
   P.ls_max = max_onchip_ls(P.ring);
   P.ls_c = cluster_cta_ls(P.ring);
-  int64_t row;
-  if (!P.leaf(l))
-    row = int64_t(1) << (l - l / 2);  // rows of the top-level split over global memory
-  else if (P.cluster_log2(l) > 0)
-    row = int64_t(1) << (l - P.cluster_log2(l));  // rows of the job's split across its CTAs
-  else
-    return n;  // one CTA holds the whole transform: a partial row costs no extra pass
-  return std::min(int64_t(1) << l, (n + row - 1) / row * row);
+  const int64_t L = int64_t(1) << l;
+  auto up = [](int64_t v, int64_t m) { return (v + m - 1) / m * m; };
+  if (!P.leaf(l)) {
+    // whole rows of the top-level split over global memory
+    const int l1 = l / 2, l2 = l - l1;
+    const int64_t n_rows = up(n, int64_t(1) << l2);
+    // when the column sub-transforms are cluster jobs, whole in-job rows of those as well (their
+    // partial in-job row is a serial step on one CTA), if that adds at most 1/32 of n
+    const int lc1 = P.cluster_log2(l1);
+    if (lc1 > 0 && P.leaf(l1)) {
+      const int64_t n_full = up(n, int64_t(1) << (l2 + l1 - lc1));
+      if (n_full <= L && (n_full - n) * 32 <= n) return n_full;
+    }
+    return std::min(L, n_rows);
+  }
+  const int lc = P.cluster_log2(l);
+  if (lc > 0) return std::min(L, up(n, int64_t(1) << (l - lc)));  // whole rows of the job's split
+  return n;  // one CTA holds the whole transform: a partial row costs no extra pass
 }
 
 int count_passes(int kind, int l, int64_t z, int64_t n, int f, int64_t N) {

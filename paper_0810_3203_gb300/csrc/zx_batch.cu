@@ -69,21 +69,6 @@ struct MergedPasses {
   }
 };
 
-struct GroupDesc {
-  Ring ring;
-  int64_t stride = 0;
-  int count = 0;
-  int64_t max_len = 0, max_n = 0;
-  size_t pack_off = 0, pw_off = 0, lift_off = 0;
-  std::vector<Launch> tft, itft;  // d_jobs hold byte offsets into the descriptor image
-};
-
-struct SubBatch {
-  size_t pool_bytes = 0;
-  std::vector<int> idx;  // products (indices into the caller's list)
-  std::vector<GroupDesc> groups;
-};
-
 void to_launches(const MergedPasses &m, DescImage *img, std::vector<Launch> *out) {
   for (const auto &kv : m.jobs) {
     Launch L;
@@ -103,84 +88,126 @@ T *rebase(T *off, unsigned char *base) {
   return reinterpret_cast<T *>(base + reinterpret_cast<size_t>(off));
 }
 
-size_t ring_bytes(const BatchProduct &p) { return size_t(p.stride) * 8 * (size_t(1) << p.l); }
-
 }  // namespace
 
-int run_mul_batch(const std::vector<BatchProduct> &items, cudaStream_t s, std::string *msg) {
-  if (items.empty()) return ZX_OK;
-  // order: by ring, largest rings first, then by transform length
-  std::vector<int> order(items.size());
-  for (size_t i = 0; i < order.size(); i++) order[i] = int(i);
-  std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+size_t product_pool_bytes(const BatchProduct &p) { return 2 * size_t(p.stride) * 8 * (size_t(1) << p.l); }
+
+int layout_batch(const std::vector<BatchProduct> &items, const std::vector<int> &idx_in,
+                 std::vector<unsigned char> *desc, BatchLayout *out, std::string *msg) {
+  std::vector<int> idx(idx_in);
+  // by ring, largest rings first, then by transform length
+  std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) {
     if (items[a].N != items[b].N) return items[a].N > items[b].N;
     return items[a].l > items[b].l;
   });
+  DescImage img;
+  img.bytes.swap(*desc);
+  out->groups.clear();
+  int64_t cell_off = 0;  // in cells of the current group's stride, from the pool's start
+  size_t byte_off = 0;
+  for (size_t a = 0; a < idx.size();) {
+    size_t b = a;
+    while (b < idx.size() && items[idx[b]].N == items[idx[a]].N) b++;
+    BatchGroup gd;
+    const BatchProduct &p0 = items[idx[a]];
+    gd.ring = make_ring(p0.N);
+    gd.stride = p0.stride;
+    gd.count = int(b - a);
+    std::vector<PackItem> pk;
+    std::vector<PointwiseItem> pw;
+    std::vector<LiftItem> lf;
+    MergedPasses mt, mi;
+    const size_t cell_bytes = size_t(gd.stride) * 8;
+    cell_off = int64_t((byte_off + cell_bytes - 1) / cell_bytes);  // first whole cell after the last group
+    for (size_t t = a; t < b; t++) {
+      const BatchProduct &p = items[idx[t]];
+      const int64_t L = int64_t(1) << p.l;
+      const int64_t cf = cell_off, cg = cell_off + L;
+      cell_off += 2 * L;
+      const int64_t F = cf * p.stride, G = cg * p.stride;  // limb offsets in the pool
+      pk.push_back(PackItem{p.f, F, p.len_f, p.limbs_f, p.signed_f, 0});
+      pk.push_back(PackItem{p.g, G, p.len_g, p.limbs_g, p.signed_g, 0});
+      pw.push_back(PointwiseItem{F, G, p.nf});
+      lf.push_back(LiftItem{F, p.h, p.n, p.limbs_h, p.sgn, 0});
+      gd.max_len = std::max(gd.max_len, std::max(p.len_f, p.len_g));
+      gd.max_n = std::max(gd.max_n, p.nf);
+      int rc;
+      if ((rc = mt.add(KIND_TFT, p.l, p.len_f, p.nf, p.N, cf, 0)) ||
+          (rc = mt.add(KIND_TFT, p.l, p.len_g, p.nf, p.N, cg, 0)) ||
+          (rc = mi.add(KIND_ITFT, p.l, p.nf, p.nf, p.N, cf, 1))) {
+        *msg = "planning failed for product " + std::to_string(idx[t]);
+        img.bytes.swap(*desc);
+        return rc;
+      }
+    }
+    byte_off = size_t(cell_off) * cell_bytes;
+    gd.pack_off = img.add(pk.data(), pk.size() * sizeof(PackItem));
+    gd.pw_off = img.add(pw.data(), pw.size() * sizeof(PointwiseItem));
+    gd.lift_off = img.add(lf.data(), lf.size() * sizeof(LiftItem));
+    to_launches(mt, &img, &gd.tft);
+    to_launches(mi, &img, &gd.itft);
+    out->groups.push_back(std::move(gd));
+    a = b;
+  }
+  out->pool_bytes = byte_off;
+  img.bytes.swap(*desc);
+  return ZX_OK;
+}
+
+cudaError_t enqueue_group(const BatchGroup &gd, unsigned char *d_desc, unsigned char *pool, cudaStream_t s) {
+  uint64_t *x = reinterpret_cast<uint64_t *>(pool);
+  TransformPlan tp, ip;
+  tp.ring = ip.ring = gd.ring;
+  for (Launch L : gd.tft) {
+    L.d_jobs = rebase(L.d_jobs, d_desc);
+    tp.launches.push_back(L);
+  }
+  for (Launch L : gd.itft) {
+    L.d_jobs = rebase(L.d_jobs, d_desc);
+    ip.launches.push_back(L);
+  }
+  const PackItem *pk = reinterpret_cast<const PackItem *>(d_desc + gd.pack_off);
+  const PointwiseItem *pw = reinterpret_cast<const PointwiseItem *>(d_desc + gd.pw_off);
+  const LiftItem *lf = reinterpret_cast<const LiftItem *>(d_desc + gd.lift_off);
+  cudaError_t ce;
+  if ((ce = launch_pack_batch(pk, 2 * gd.count, gd.max_len, gd.stride, gd.ring, x, s)) != cudaSuccess) return ce;
+  if ((ce = run_transform(tp, x, gd.stride, s)) != cudaSuccess) return ce;
+  if ((ce = launch_pointwise_batch(pw, gd.count, gd.max_n, gd.stride, gd.ring, x, s)) != cudaSuccess) return ce;
+  if ((ce = run_transform(ip, x, gd.stride, s)) != cudaSuccess) return ce;
+  return launch_lift_batch(lf, gd.count, gd.max_n, gd.stride, gd.ring, x, s);
+}
+
+int run_mul_batch(const std::vector<BatchProduct> &items, cudaStream_t s, std::string *msg) {
+  if (items.empty()) return ZX_OK;
   size_t free_b = 0, total_b = 0;
   if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
     *msg = "cudaMemGetInfo failed";
     return ZX_ECUDA;
   }
   const size_t budget = free_b / 2;
-
-  // cut into sub-batches under the memory budget
-  std::vector<SubBatch> subs(1);
+  // cut into sub-batches under the memory budget, largest rings first
+  std::vector<int> order(items.size());
+  for (size_t i = 0; i < order.size(); i++) order[i] = int(i);
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+    if (items[a].N != items[b].N) return items[a].N > items[b].N;
+    return items[a].l > items[b].l;
+  });
+  std::vector<std::vector<int>> parts(1);
+  size_t acc = 0;
   for (int i : order) {
-    size_t need = 2 * ring_bytes(items[i]);
-    if (!subs.back().idx.empty() && subs.back().pool_bytes + need > budget) subs.emplace_back();
-    subs.back().idx.push_back(i);
-    subs.back().pool_bytes += need;
-  }
-
-  // descriptors of every sub-batch (pool offsets are relative to the sub-batch's pool)
-  DescImage img;
-  for (SubBatch &sb : subs) {
-    int64_t cell_off = 0;  // in cells of the current group's stride, from the pool's start
-    size_t byte_off = 0;
-    for (size_t a = 0; a < sb.idx.size();) {
-      size_t b = a;
-      while (b < sb.idx.size() && items[sb.idx[b]].N == items[sb.idx[a]].N) b++;
-      GroupDesc gd;
-      const BatchProduct &p0 = items[sb.idx[a]];
-      gd.ring = make_ring(p0.N);
-      gd.stride = p0.stride;
-      gd.count = int(b - a);
-      std::vector<PackItem> pk;
-      std::vector<PointwiseItem> pw;
-      std::vector<LiftItem> lf;
-      MergedPasses mt, mi;
-      const size_t cell_bytes = size_t(gd.stride) * 8;
-      cell_off = int64_t((byte_off + cell_bytes - 1) / cell_bytes);  // first whole cell after the last group
-      for (size_t t = a; t < b; t++) {
-        const BatchProduct &p = items[sb.idx[t]];
-        const int64_t L = int64_t(1) << p.l;
-        const int64_t cf = cell_off, cg = cell_off + L;
-        cell_off += 2 * L;
-        const int64_t F = cf * p.stride, G = cg * p.stride;  // limb offsets in the pool
-        pk.push_back(PackItem{p.f, F, p.len_f, p.limbs_f, p.signed_f, 0});
-        pk.push_back(PackItem{p.g, G, p.len_g, p.limbs_g, p.signed_g, 0});
-        pw.push_back(PointwiseItem{F, G, p.nf});
-        lf.push_back(LiftItem{F, p.h, p.n, p.limbs_h, p.sgn, 0});
-        gd.max_len = std::max(gd.max_len, std::max(p.len_f, p.len_g));
-        gd.max_n = std::max(gd.max_n, p.nf);
-        int rc;
-        if ((rc = mt.add(KIND_TFT, p.l, p.len_f, p.nf, p.N, cf, 0)) ||
-            (rc = mt.add(KIND_TFT, p.l, p.len_g, p.nf, p.N, cg, 0)) ||
-            (rc = mi.add(KIND_ITFT, p.l, p.nf, p.nf, p.N, cf, 1))) {
-          *msg = "planning failed for product " + std::to_string(sb.idx[t]);
-          return rc;
-        }
-      }
-      byte_off = size_t(cell_off) * size_t(gd.stride) * 8;
-      gd.pack_off = img.add(pk.data(), pk.size() * sizeof(PackItem));
-      gd.pw_off = img.add(pw.data(), pw.size() * sizeof(PointwiseItem));
-      gd.lift_off = img.add(lf.data(), lf.size() * sizeof(LiftItem));
-      to_launches(mt, &img, &gd.tft);
-      to_launches(mi, &img, &gd.itft);
-      sb.groups.push_back(std::move(gd));
-      a = b;
+    const size_t need = product_pool_bytes(items[i]);
+    if (!parts.back().empty() && acc + need > budget) {
+      parts.emplace_back();
+      acc = 0;
     }
-    sb.pool_bytes = byte_off;
+    parts.back().push_back(i);
+    acc += need;
+  }
+  std::vector<unsigned char> desc;
+  std::vector<BatchLayout> lays(parts.size());
+  for (size_t k = 0; k < parts.size(); k++) {
+    int rc = layout_batch(items, parts[k], &desc, &lays[k], msg);
+    if (rc) return rc;
   }
 
   std::lock_guard<std::mutex> lk(g_batch_mu);
@@ -195,20 +222,18 @@ int run_mul_batch(const std::vector<BatchProduct> &items, cudaStream_t s, std::s
       }
     fs.ready = true;
   }
-
   unsigned char *d_desc = nullptr;
-  cudaError_t ce = cudaMallocAsync(reinterpret_cast<void **>(&d_desc), img.bytes.size(), s);
+  cudaError_t ce = cudaMallocAsync(reinterpret_cast<void **>(&d_desc), desc.size(), s);
   if (ce != cudaSuccess) {
     *msg = "descriptor allocation failed";
     return ZX_ENOMEM;
   }
-  ce = cudaMemcpyAsync(d_desc, img.bytes.data(), img.bytes.size(), cudaMemcpyHostToDevice, s);
+  ce = cudaMemcpyAsync(d_desc, desc.data(), desc.size(), cudaMemcpyHostToDevice, s);
   if (ce != cudaSuccess) {
     cudaFreeAsync(d_desc, s);
     *msg = std::string("descriptor upload: ") + cudaGetErrorString(ce);
     return ZX_ECUDA;
   }
-
   int rc = ZX_OK;
   std::vector<cudaEvent_t> events;
   auto new_event = [&](cudaEvent_t *ev) {
@@ -216,49 +241,33 @@ int run_mul_batch(const std::vector<BatchProduct> &items, cudaStream_t s, std::s
     events.push_back(*ev);
     return true;
   };
-  for (SubBatch &sb : subs) {
+  for (const BatchLayout &lay : lays) {
     unsigned char *pool = nullptr;
-    if (cudaMallocAsync(reinterpret_cast<void **>(&pool), sb.pool_bytes, s) != cudaSuccess) {
-      *msg = "ring buffer pool of " + std::to_string(sb.pool_bytes) + " bytes";
+    if (cudaMallocAsync(reinterpret_cast<void **>(&pool), lay.pool_bytes, s) != cudaSuccess) {
+      *msg = "ring buffer pool of " + std::to_string(lay.pool_bytes) + " bytes";
       rc = ZX_ENOMEM;
       break;
     }
-    cudaEvent_t fork;
-    if (!new_event(&fork) || cudaEventRecord(fork, s) != cudaSuccess) {
-      cudaFreeAsync(pool, s);
-      *msg = "event record failed";
-      rc = ZX_ECUDA;
-      break;
+    const bool fork = lay.groups.size() > 1;
+    const int nstreams = std::min<int>(kForkStreams, int(lay.groups.size()));
+    if (fork) {
+      cudaEvent_t ev;
+      if (!new_event(&ev) || cudaEventRecord(ev, s) != cudaSuccess) {
+        cudaFreeAsync(pool, s);
+        *msg = "event record failed";
+        rc = ZX_ECUDA;
+        break;
+      }
+      for (int k = 0; k < nstreams; k++) cudaStreamWaitEvent(fs.s[k], ev, 0);
     }
-    const int nstreams = std::min<int>(kForkStreams, int(sb.groups.size()));
-    for (int k = 0; k < nstreams && sb.groups.size() > 1; k++) cudaStreamWaitEvent(fs.s[k], fork, 0);
-    uint64_t *x = reinterpret_cast<uint64_t *>(pool);
-    for (size_t gi = 0; gi < sb.groups.size() && rc == ZX_OK; gi++) {
-      GroupDesc &gd = sb.groups[gi];
-      cudaStream_t gs = sb.groups.size() > 1 ? fs.s[gi % kForkStreams] : s;
-      TransformPlan tp, ip;
-      tp.ring = ip.ring = gd.ring;
-      for (Launch L : gd.tft) {
-        L.d_jobs = rebase(L.d_jobs, d_desc);
-        tp.launches.push_back(L);
-      }
-      for (Launch L : gd.itft) {
-        L.d_jobs = rebase(L.d_jobs, d_desc);
-        ip.launches.push_back(L);
-      }
-      const PackItem *pk = reinterpret_cast<const PackItem *>(d_desc + gd.pack_off);
-      const PointwiseItem *pw = reinterpret_cast<const PointwiseItem *>(d_desc + gd.pw_off);
-      const LiftItem *lf = reinterpret_cast<const LiftItem *>(d_desc + gd.lift_off);
-      if ((ce = launch_pack_batch(pk, 2 * gd.count, gd.max_len, gd.stride, gd.ring, x, gs)) != cudaSuccess ||
-          (ce = run_transform(tp, x, gd.stride, gs)) != cudaSuccess ||
-          (ce = launch_pointwise_batch(pw, gd.count, gd.max_n, gd.stride, gd.ring, x, gs)) != cudaSuccess ||
-          (ce = run_transform(ip, x, gd.stride, gs)) != cudaSuccess ||
-          (ce = launch_lift_batch(lf, gd.count, gd.max_n, gd.stride, gd.ring, x, gs)) != cudaSuccess) {
+    for (size_t gi = 0; gi < lay.groups.size() && rc == ZX_OK; gi++) {
+      cudaStream_t gs = fork ? fs.s[gi % kForkStreams] : s;
+      if ((ce = enqueue_group(lay.groups[gi], d_desc, pool, gs)) != cudaSuccess) {
         *msg = std::string("batch launch: ") + cudaGetErrorString(ce);
         rc = ZX_ECUDA;
       }
     }
-    if (sb.groups.size() > 1) {
+    if (fork) {
       for (int k = 0; k < nstreams; k++) {
         cudaEvent_t join;
         if (!new_event(&join)) {

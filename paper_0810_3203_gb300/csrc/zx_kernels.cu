@@ -128,144 +128,199 @@ __global__ void lift_batch_kernel(const LiftItem *__restrict__ items, int64_t st
     lift_one<K>(pool + it.cells + i * stride, it.is_signed, it.out + i * it.limbs_out, it.limbs_out, g);
 }
 
-// a <- a * b mod 2^N + 1 for one product, by a schoolbook column product and the reduction
-// P = P_lo + P_hi 2^N = P_lo - P_hi. `ws` is this warp's shared-memory scratch of 8 NW + 8 words.
-template <int K>
-__device__ __forceinline__ void pointwise_one(uint64_t *acell, const uint64_t *bcell, uint32_t *ws,
-                                              const Geo &g) {
-  const int NW = g.NW;
-  uint32_t *A = ws;
-  uint32_t *B = A + NW;
-  uint32_t *C0 = B + NW;       // column sums, low words (2NW)
-  uint32_t *C1 = C0 + 2 * NW;  // middle words
-  uint32_t *C2 = C1 + 2 * NW;  // high words
-  uint32_t ra[K], rb[K];
-  uint32_t Ta = gmem_load_x<K>(ra, acell, g);
-  uint32_t Tb = gmem_load_x<K>(rb, bcell, g);
-  // 2^N = -1: use magnitude 1 and remember the sign
-  const uint32_t neg = (Ta ^ Tb) & 1u;
-  if (Ta) {
+// One multiply-accumulate of column sums: (c2:c1:c0) += a * w (96-bit column accumulator).
+__device__ __forceinline__ void mac96(uint32_t &c0, uint32_t &c1, uint32_t &c2, uint32_t a, uint32_t w) {
+  asm("mad.lo.cc.u32 %0, %3, %4, %0;\n\t"
+      "madc.hi.cc.u32 %1, %3, %4, %1;\n\t"
+      "addc.u32 %2, %2, 0;"
+      : "+r"(c0), "+r"(c1), "+r"(c2)
+      : "r"(a), "r"(w));
+}
+
+// out word w = in word w - D (zero below D) of a lane-chunked number, D = 1 or 2; the words
+// shifted past the top are dropped
+template <int K, int D>
+__device__ __forceinline__ void shift_words_up(uint32_t (&out)[K], const uint32_t (&in)[K], const Geo &g) {
+  const bool act = g.lane < g.G;
+  if (K >= D) {
+    uint32_t from[D];
 #pragma unroll
-    for (int s = 0; s < K; s++) ra[s] = 0u;
-    if (g.lane == 0) ra[0] = 1u;
+    for (int d = 0; d < D; d++) {
+      from[d] = __shfl_up_sync(TFT_FULL, in[K - D + d], 1);
+      if (g.lane == 0) from[d] = 0u;
+    }
+#pragma unroll
+    for (int q = K - 1; q >= D; q--) out[q] = in[q - D];
+#pragma unroll
+    for (int d = 0; d < D; d++) out[d] = act ? from[d] : 0u;
+  } else {  // K = 1, D = 2
+    uint32_t v = __shfl_up_sync(TFT_FULL, in[0], 2);
+    out[0] = (act && g.lane >= 2) ? v : 0u;
   }
+}
+
+// a <- a * b mod 2^N + 1 for one product (one warp), by product scanning with a negacyclic fold:
+// lane l owns the K column sums p = K l + q of
+//   X = sum_{i+j=p} A_i B_j - sum_{i+j=p+NW} A_i B_j    (2^{32 NW} = 2^N = -1),
+// each a 96-bit accumulator. B sits in registers as a window that turns by one word per step
+// i (window word at column p = B_{(p - i) mod NW}); A_i is a broadcast shared-memory read. A
+// word that wraps from the top column to column 0 enters complemented (~w = 2^32 - 1 - w), which
+// turns the subtraction into a multiply-add; the surplus (2^32 - 1) A_i per wrapped word adds up
+// to (2^32 - 1) SA_p per column, SA_p = sum_{i > p} A_i, and is taken off at the end.
+// `As` is this warp's NW words of shared memory.
+template <int K>
+__device__ __forceinline__ void pointwise_one(uint64_t *acell, const uint64_t *bcell, uint32_t *As,
+                                              const Geo &g) {
+  constexpr int U = K < 4 ? K : 4;  // steps per unrolled block
+  const int NW = g.NW;
+  const uint32_t *a32 = reinterpret_cast<const uint32_t *>(acell);
+  const uint32_t Ta = __ldg(a32 + NW) & 1u;
+  uint32_t win[K + U];
+  uint32_t rb[K];
+  const uint32_t Tb = gmem_load_x<K>(rb, bcell, g) & 1u;
+  // 2^N = -1: use magnitude 1 and remember the sign
+  const uint32_t neg = Ta ^ Tb;
+  for (int w = g.lane; w < NW; w += 32) As[w] = Ta ? (w == 0 ? 1u : 0u) : __ldg(a32 + w);
   if (Tb) {
 #pragma unroll
-    for (int s = 0; s < K; s++) rb[s] = 0u;
+    for (int q = 0; q < K; q++) rb[q] = 0u;
     if (g.lane == 0) rb[0] = 1u;
   }
-  if (g.lane < g.G) {
 #pragma unroll
-    for (int s = 0; s < K; s++) {
-      A[K * g.lane + s] = ra[s];
-      B[K * g.lane + s] = rb[s];
-    }
-  }
+  for (int q = 0; q < K; q++) win[U + q] = rb[q];
   __syncwarp();
-  // column k = lane + 32 t, t = 0 .. 2K-1 (k < 2NW - 1); groups of 4 columns per sweep
-  for (int t0 = 0; t0 < 2 * K; t0 += 4) {
-    uint32_t c0[4] = {0, 0, 0, 0}, c1[4] = {0, 0, 0, 0}, c2[4] = {0, 0, 0, 0};
-    int kmin = g.lane + 32 * t0;
-    int ilo = kmin - (NW - 1);
-    if (ilo < 0) ilo = 0;
-    int ihi = kmin + 32 * 3;
-    if (ihi > NW - 1) ihi = NW - 1;
-    for (int ii = ilo; ii <= ihi; ii++) {
-      uint32_t av = A[ii];
+
+  uint32_t c0[K], c1[K], c2[K];
 #pragma unroll
-      for (int u = 0; u < 4; u++) {
-        int j = kmin + 32 * u - ii;
-        if (j >= 0 && j < NW) {
-          uint32_t bv = B[j];
-          asm("mad.lo.cc.u32 %0, %3, %4, %0;\n\t"
-              "madc.hi.cc.u32 %1, %3, %4, %1;\n\t"
-              "addc.u32 %2, %2, 0;"
-              : "+r"(c0[u]), "+r"(c1[u]), "+r"(c2[u])
-              : "r"(av), "r"(bv));
-        }
-      }
+  for (int q = 0; q < K; q++) c0[q] = c1[q] = c2[q] = 0u;
+  const int src = g.lane >= g.G ? g.lane : (g.lane == 0 ? g.G - 1 : g.lane - 1);
+  for (int i0 = 0; i0 < NW; i0 += U) {
+    uint32_t a[U];
+    if (U == 4) {
+      const uint4 v = *reinterpret_cast<const uint4 *>(As + i0);
+      a[0] = v.x;
+      a[1 % U] = v.y;
+      a[2 % U] = v.z;
+      a[3 % U] = v.w;
+    } else {
+#pragma unroll
+      for (int s = 0; s < U; s++) a[s] = As[i0 + s];
     }
 #pragma unroll
-    for (int u = 0; u < 4; u++) {
-      int k = kmin + 32 * u;
-      if (k < 2 * NW) {
-        C0[k] = c0[u];
-        C1[k] = c1[u];
-        C2[k] = c2[u];
-      }
+    for (int s = 0; s < U; s++) {
+#pragma unroll
+      for (int q = 0; q < K; q++) mac96(c0[q], c1[q], c2[q], a[s], win[U - s + q]);
+      const uint32_t x = __shfl_sync(TFT_FULL, win[U - s + K - 1], src);
+      win[U - s - 1] = g.lane == 0 ? ~x : x;
+    }
+#pragma unroll
+    for (int q = K - 1; q >= 0; q--) win[U + q] = win[q];
+  }
+
+  // SA_p = sum_{i > p} A_i for this lane's columns (below 2^42: two words sa0, sa1)
+  uint32_t sa0[K], sa1[K];
+  {
+    uint64_t own = 0;
+    if (g.lane < g.G) {
+#pragma unroll
+      for (int q = 0; q < K; q++) own += As[K * g.lane + q];
+    }
+    uint64_t above = own;  // inclusive suffix over lanes
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const uint64_t t = __shfl_down_sync(TFT_FULL, above, d);
+      if (g.lane + d < 32) above += t;
+    }
+    uint64_t run = above - own;  // lanes above this one
+#pragma unroll
+    for (int q = K - 1; q >= 0; q--) {
+      const bool act = g.lane < g.G;
+      sa0[q] = act ? uint32_t(run) : 0u;
+      sa1[q] = act ? uint32_t(run >> 32) : 0u;
+      if (act) run += As[K * g.lane + q];
     }
   }
-  __syncwarp();
-  // P = L + H 2^N + extra 2^{2N} with L = sum_{w<NW} (C0[w] + C1[w-1] + C2[w-2]) 2^{32w},
-  // H the same sum over words NW .. 2NW-1, and extra = C2[2NW-2] (word 2NW); 2^N = -1.
-  uint32_t L[K], H[K], t1[K], t2[K];
+  // the words past the top that wrap (negated): c1 of column NW-1, c2 of columns NW-2, NW-1
+  const uint32_t h_c1 = __shfl_sync(TFT_FULL, c1[K - 1], g.G - 1);
+  const uint32_t h_c2b = __shfl_sync(TFT_FULL, c2[K - 1], g.G - 1);
+  uint32_t h_c2a;
+  if (K >= 2)
+    h_c2a = __shfl_sync(TFT_FULL, c2[K >= 2 ? K - 2 : 0], g.G - 1);
+  else
+    h_c2a = __shfl_sync(TFT_FULL, c2[0], g.G - 2);
+
+  // X = V0 + V1 + V2 + Qa + Qb - Qc - Qd - H, with V0 = c0, V1 = c1 one word up, V2 = c2 two
+  // words up, Qa = sa0, Qb = sa1 one word up (= SA), Qc = sa0 one word up, Qd = sa1 two words
+  // up (= SA 2^32), H = the wrapped words
+  uint32_t R[K], t[K];
+  int v = 0;
+  shift_words_up<K, 1>(t, c1, g);
+  v -= int(resolve_add<K>(R, add_chain<K>(R, c0, t, 0u), g));
+  shift_words_up<K, 2>(t, c2, g);
+  v -= int(resolve_add<K>(R, add_chain<K>(R, R, t, 0u), g));
+  v -= int(resolve_add<K>(R, add_chain<K>(R, R, sa0, 0u), g));
+  shift_words_up<K, 1>(t, sa1, g);
+  v -= int(resolve_add<K>(R, add_chain<K>(R, R, t, 0u), g));
+  shift_words_up<K, 1>(t, sa0, g);
+  v += int(resolve_sub<K>(R, sub_chain<K>(R, R, t, 0u), g));
+  shift_words_up<K, 2>(t, sa1, g);
+  v += int(resolve_sub<K>(R, sub_chain<K>(R, R, t, 0u), g));
+  {
+    const uint64_t h0 = uint64_t(h_c1) + h_c2a;
+    const uint32_t hw0 = uint32_t(h0), hw1 = uint32_t(h0 >> 32) + h_c2b;
 #pragma unroll
-  for (int s = 0; s < K; s++) {
-    int w = K * g.lane + s;
-    bool act = g.lane < g.G;
-    L[s] = act ? C0[w] : 0u;
-    t1[s] = (act && w >= 1) ? C1[w - 1] : 0u;
-    t2[s] = (act && w >= 2) ? C2[w - 2] : 0u;
+    for (int q = 0; q < K; q++) {
+      const int w = K * g.lane + q;
+      t[q] = w == 0 ? hw0 : (w == 1 ? hw1 : 0u);
+    }
   }
-  uint32_t c = add_chain<K>(L, L, t1, 0u);
-  uint32_t Lt = resolve_add<K>(L, c, g);
-  c = add_chain<K>(L, L, t2, 0u);
-  Lt += resolve_add<K>(L, c, g);
-#pragma unroll
-  for (int s = 0; s < K; s++) {
-    int w = NW + K * g.lane + s;
-    bool act = g.lane < g.G;
-    H[s] = act ? C0[w] : 0u;
-    t1[s] = act ? C1[w - 1] : 0u;
-    t2[s] = act ? C2[w - 2] : 0u;
-  }
-  c = add_chain<K>(H, H, t1, 0u);
-  uint32_t Ht = resolve_add<K>(H, c, g);
-  c = add_chain<K>(H, H, t2, 0u);
-  Ht += resolve_add<K>(H, c, g);
-  uint32_t extra = C2[2 * NW - 2];
-  // X = L + Lt 2^N - H - Ht 2^N + extra 2^{2N} = L - H - Lt + Ht + extra (mod p)
-  uint32_t bo = sub_chain<K>(L, L, H, 0u);
-  uint32_t Bd = resolve_sub<K>(L, bo, g);
-  int v = int(Bd) - int(Lt) + int(Ht) + int(extra);
-  uint32_t T = canon_x<K>(L, v, g);
+  v += int(resolve_sub<K>(R, sub_chain<K>(R, R, t, 0u), g));
+  uint32_t T = canon_x<K>(R, v, g);
   if (neg) {
     // -x: 2^N -> 1, 0 -> 0, else ~x + 2 (N bits)
     if (T) {
 #pragma unroll
-      for (int s = 0; s < K; s++) L[s] = 0u;
-      if (g.lane == 0) L[0] = 1u;
+      for (int q = 0; q < K; q++) R[q] = 0u;
+      if (g.lane == 0) R[0] = 1u;
       T = 0u;
-    } else if (!is_zero<K>(L)) {
+    } else if (!is_zero<K>(R)) {
 #pragma unroll
-      for (int s = 0; s < K; s++) L[s] = g.lane < g.G ? ~L[s] : 0u;
-      T = add_small<K>(L, 2u, g);
+      for (int q = 0; q < K; q++) R[q] = g.lane < g.G ? ~R[q] : 0u;
+      T = add_small<K>(R, 2u, g);
     }
   }
   __syncwarp();
-  gmem_store_x<K>(acell, L, T, g);
+  gmem_store_x<K>(acell, R, T, g);
   __syncwarp();
 }
 
+constexpr int kPointwiseWarps = 4;
+
+__host__ __device__ constexpr int pointwise_warp_words(int NW) { return (NW + 3) & ~3; }
+
 template <int K>
-__global__ void pointwise_kernel(uint64_t *__restrict__ a, const uint64_t *__restrict__ b, int64_t n,
-                                 int64_t stride, int N, int warps_per_block) {
-  extern __shared__ uint32_t sm[];
+__global__ void __launch_bounds__(kPointwiseWarps * 32)
+    pointwise_kernel(uint64_t *__restrict__ a, const uint64_t *__restrict__ b, int64_t n, int64_t stride, int N,
+                     int warps_per_block) {
+  extern __shared__ uint4 sm4[];
+  uint32_t *sm = reinterpret_cast<uint32_t *>(sm4);
   const Geo g = make_geo(N, K);
   const int warp = threadIdx.x >> 5;
-  uint32_t *ws = sm + size_t(warp) * (8 * g.NW + 8);
+  uint32_t *ws = sm + size_t(warp) * pointwise_warp_words(g.NW);
   const int64_t nwarps = int64_t(gridDim.x) * warps_per_block;
   for (int64_t i = int64_t(blockIdx.x) * warps_per_block + warp; i < n; i += nwarps)
     pointwise_one<K>(a + i * stride, b + i * stride, ws, g);
 }
 
 template <int K>
-__global__ void pointwise_batch_kernel(const PointwiseItem *__restrict__ items, int64_t stride, int N,
-                                       int warps_per_block, uint64_t *__restrict__ pool) {
-  extern __shared__ uint32_t sm[];
+__global__ void __launch_bounds__(kPointwiseWarps * 32)
+    pointwise_batch_kernel(const PointwiseItem *__restrict__ items, int64_t stride, int N, int warps_per_block,
+                           uint64_t *__restrict__ pool) {
+  extern __shared__ uint4 sm4[];
+  uint32_t *sm = reinterpret_cast<uint32_t *>(sm4);
   const Geo g = make_geo(N, K);
   const int warp = threadIdx.x >> 5;
-  uint32_t *ws = sm + size_t(warp) * (8 * g.NW + 8);
+  uint32_t *ws = sm + size_t(warp) * pointwise_warp_words(g.NW);
   const PointwiseItem it = items[blockIdx.y];
   const int64_t nwarps = int64_t(gridDim.x) * warps_per_block;
   for (int64_t i = int64_t(blockIdx.x) * warps_per_block + warp; i < it.n; i += nwarps)
@@ -275,11 +330,8 @@ __global__ void pointwise_batch_kernel(const PointwiseItem *__restrict__ items, 
 template <int K>
 cudaError_t pointwise_k(uint64_t *a, const uint64_t *b, int64_t n, int64_t stride, const Ring &r,
                         cudaStream_t s) {
-  size_t per_warp = size_t(8 * r.NW + 8) * 4;
-  int wpb = int(std::min<size_t>(8, std::max<size_t>(1, (96 * 1024) / per_warp)));
-  size_t smem = per_warp * wpb;
-  cudaError_t e = cudaFuncSetAttribute(pointwise_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-  if (e != cudaSuccess) return e;
+  const int wpb = kPointwiseWarps;
+  const size_t smem = size_t(pointwise_warp_words(r.NW)) * 4 * wpb;
   int64_t blocks = (n + wpb - 1) / wpb;
   if (blocks > 152 * 16) blocks = 152 * 16;
   if (blocks < 1) blocks = 1;
@@ -325,17 +377,14 @@ cudaError_t launch_lift(const uint64_t *cells, int64_t n, int64_t stride_limbs, 
 template <int K>
 cudaError_t pointwise_batch_k(const PointwiseItem *items, int count, int64_t max_n, int64_t stride,
                               const Ring &r, uint64_t *pool, cudaStream_t s) {
-  size_t per_warp = size_t(8 * r.NW + 8) * 4;
-  int wpb = int(std::min<size_t>(8, std::max<size_t>(1, (96 * 1024) / per_warp)));
-  size_t smem = per_warp * wpb;
-  cudaError_t e = cudaFuncSetAttribute(pointwise_batch_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       227 * 1024);
-  if (e != cudaSuccess) return e;
+  const int wpb = kPointwiseWarps;
+  const size_t smem = size_t(pointwise_warp_words(r.NW)) * 4 * wpb;
   int64_t bx = (max_n + wpb - 1) / wpb;
   int64_t cap = std::max<int64_t>(1, (152 * 16) / std::max(1, count));
   if (bx > cap) bx = cap;
   if (bx < 1) bx = 1;
-  pointwise_batch_kernel<K><<<dim3(unsigned(bx), unsigned(count)), wpb * 32, smem, s>>>(items, stride, int(r.N), wpb, pool);
+  pointwise_batch_kernel<K><<<dim3(unsigned(bx), unsigned(count)), wpb * 32, smem, s>>>(items, stride, int(r.N), wpb,
+                                                                                      pool);
   return cudaGetLastError();
 }
 
