@@ -198,6 +198,38 @@ int zx_server_drain(zx_server *srv, double timeout_s);
 int zx_server_stats(zx_server *srv, zx_server_info *out);
 int zx_server_destroy(zx_server *srv);
 
+/*
+ * Autotuner for the launch configuration of ring N (no counterpart in the paper, which fixes
+ * the split L1 = 2^floor(l/2) for cache reasons; every configuration computes the same
+ * outputs). Candidates: cells per CTA of a cluster job (2^3 .. 2^6), the largest job held by one
+ * CTA (the shared-memory limit, or the size at which three CTAs share an SM), warps per CTA
+ * (8 or 16) and, for odd l, the top-level split floor or ceil(l/2). For each candidate the call
+ * times `reps` TFT + ITFT round trips (Algorithm 1, then Algorithm 2 with the division by L)
+ * of length n over the caller's device buffer x (L = 2^l cells of stride_limbs >= N/64 + 1
+ * limbs holding canonical residues; the round trips restore it), keeps the fastest for every
+ * later plan over ring N in this process, and reports it. Synchronises `stream`.
+ */
+typedef struct {
+    int32_t ls_max;     /* log2 of the largest job one CTA holds */
+    int32_t ls_c;       /* log2 of the cells per CTA of a cluster job */
+    int32_t max_warps;  /* warps per CTA */
+    int32_t split;      /* 0: L1 = 2^floor(l/2), 1: L1 = 2^ceil(l/2) */
+    int32_t candidates; /* configurations timed */
+    float best_ms;      /* round-trip time of the chosen configuration */
+    float default_ms;   /* round-trip time of the default configuration */
+    int32_t pad;
+} zx_tune_info;
+
+int zx_tune(uint64_t *x, int l, int64_t n, int64_t N, int64_t stride_limbs, int reps, void *stream,
+            zx_tune_info *out);
+
+/* The launch configuration used for ring N (ls_max, ls_c, max_warps, split; the other fields are
+ * zero), and pinning one, e.g. a result of zx_tune saved from an earlier process. zx_config_set
+ * returns ZX_EINVAL for a configuration the ring cannot run (shared memory, warps, split); with
+ * cfg == NULL it restores the default. Host only. */
+int zx_config_get(int64_t N, zx_tune_info *out);
+int zx_config_set(int64_t N, const zx_tune_info *cfg);
+
 /* Shape of the launch plan of one transform (host only, no device needed). */
 typedef struct {
     int32_t passes;    /* passes over global memory */

@@ -25,7 +25,7 @@ ZX_HOST, ZX_DEVICE = 0, 1
 EXPORTS = ("tft", "tft_ex", "itft", "itft_ex", "zx_plan", "zx_mul", "zx_mul_batch",
            "zx_transform_plan", "zx_mul_noalloc", "zx_job_program", "zx_strerror", "zx_last_error",
            "zx_version", "zx_server_create", "zx_server_submit", "zx_server_poll", "zx_server_drain",
-           "zx_server_stats", "zx_server_destroy")
+           "zx_server_stats", "zx_server_destroy", "zx_tune", "zx_config_get", "zx_config_set")
 
 _lib = None
 
@@ -47,6 +47,11 @@ class ZxPlanInfo(C.Structure):
     _fields_ = [("l", C.c_int32), ("K", C.c_int32), ("N", C.c_int64), ("n", C.c_int64),
                 ("stride_limbs", C.c_int64), ("limbs_h", C.c_int64), ("scratch_bytes", C.c_int64),
                 ("tft_passes", C.c_int32), ("itft_passes", C.c_int32), ("n_fft", C.c_int64)]
+
+
+class ZxTuneInfo(C.Structure):
+    _fields_ = [("ls_max", C.c_int32), ("ls_c", C.c_int32), ("max_warps", C.c_int32), ("split", C.c_int32),
+                ("candidates", C.c_int32), ("best_ms", C.c_float), ("default_ms", C.c_float), ("pad", C.c_int32)]
 
 
 class ZxServerInfo(C.Structure):
@@ -96,6 +101,9 @@ def load(build_if_missing=True):
     L.zx_server_drain.argtypes = [vp, C.c_double]
     L.zx_server_stats.argtypes = [vp, C.POINTER(ZxServerInfo)]
     L.zx_server_destroy.argtypes = [vp]
+    L.zx_tune.argtypes = [vp, i32, i64, i64, i64, i32, vp, C.POINTER(ZxTuneInfo)]
+    L.zx_config_get.argtypes = [i64, C.POINTER(ZxTuneInfo)]
+    L.zx_config_set.argtypes = [i64, C.POINTER(ZxTuneInfo)]
     L.zx_strerror.argtypes = [i32]
     L.zx_strerror.restype = C.c_char_p
     L.zx_last_error.argtypes = []
@@ -104,7 +112,7 @@ def load(build_if_missing=True):
     for name in ("tft", "tft_ex", "itft", "itft_ex", "zx_plan", "zx_mul", "zx_mul_batch",
                  "zx_transform_plan", "zx_mul_noalloc", "zx_job_program", "zx_server_create",
                  "zx_server_submit", "zx_server_poll", "zx_server_drain", "zx_server_stats",
-                 "zx_server_destroy"):
+                 "zx_server_destroy", "zx_tune", "zx_config_get", "zx_config_set"):
         getattr(L, name).restype = i32
     _lib = L
     return L
@@ -222,6 +230,31 @@ def zx_mul_batch(items, stream=None):
         Gs[i] = _poly(g, lg, mg, sg, bg)
         Hs[i] = _poly(h, lf + lg - 1, mh, sg, 0)
     _check(load().zx_mul_batch(Fs, Gs, Hs, n, _stream(stream)), "zx_mul_batch")
+
+
+def tune(x, l, n, N, stride_limbs=None, reps=2, stream=None):
+    """Time the launch configurations of ring N on TFT + ITFT round trips of length n over the
+    device buffer x (restored afterwards) and keep the fastest for later plans (zx_tune)."""
+    info = ZxTuneInfo()
+    s = stride_limbs or limbs(N)
+    _check(load().zx_tune(_dev_ptr(x), l, n, N, s, reps, _stream(stream), C.byref(info)), "zx_tune")
+    return {k: getattr(info, k) for k, _ in ZxTuneInfo._fields_ if k != "pad"}
+
+
+def config_get(N):
+    """Launch configuration used for ring N: ls_max, ls_c, max_warps, split."""
+    info = ZxTuneInfo()
+    _check(load().zx_config_get(N, C.byref(info)), "zx_config_get")
+    return {k: getattr(info, k) for k in ("ls_max", "ls_c", "max_warps", "split")}
+
+
+def config_set(N, cfg=None):
+    """Pin the launch configuration of ring N (a dict like config_get's), or restore the default."""
+    if cfg is None:
+        _check(load().zx_config_set(N, None), "zx_config_set")
+        return
+    info = ZxTuneInfo(cfg["ls_max"], cfg["ls_c"], cfg["max_warps"], cfg["split"], 0, 0.0, 0.0, 0)
+    _check(load().zx_config_set(N, C.byref(info)), "zx_config_set")
 
 
 class Server:

@@ -320,6 +320,109 @@ int zx_mul_batch(const zx_poly *fs, const zx_poly *gs, zx_poly *hs, int count, v
   return ZX_OK;
 }
 
+int zx_tune(uint64_t *x, int l, int64_t n, int64_t N, int64_t stride_limbs, int reps, void *stream,
+            zx_tune_info *out) {
+  if (!out || !x) return fail(ZX_EINVAL, "x or out is NULL");
+  int rc = check_ring(l, N);
+  if (rc) return rc;
+  if ((rc = check_sizes(KIND_TFT, l, n, n, 0))) return rc;
+  if (stride_limbs < N / 64 + 1) return fail(ZX_EINVAL, "stride_limbs < N/64 + 1");
+  if (reps < 1 || reps > 100) return fail(ZX_EINVAL, "reps must be in [1, 100]");
+  const Ring r = make_ring(N);
+  const PlanConfig before = plan_config(N), def = default_config(r);
+  // the largest job that still lets three CTAs share an SM
+  int ls3 = 1;
+  while (ls3 < 16 && (size_t(2) << ls3) * (size_t(r.pitch) + 1) * 4 <= size_t(72) * 1024) ls3++;
+  std::vector<PlanConfig> cands;
+  for (int ls_max : {def.ls_max, ls3})
+    for (int ls_c = 3; ls_c <= 6; ls_c++)
+      for (int mw : {8, 16})
+        for (int sp = 0; sp <= (l & 1); sp++) {
+          PlanConfig c;
+          c.ls_max = ls_max;
+          c.ls_c = ls_c;
+          c.max_warps = mw;
+          c.split = sp;
+          if (!config_valid(r, c)) continue;
+          bool dup = false;
+          for (const PlanConfig &o : cands)
+            dup = dup || (o.ls_max == c.ls_max && o.ls_c == c.ls_c && o.max_warps == c.max_warps && o.split == c.split);
+          if (!dup) cands.push_back(c);
+        }
+  cudaStream_t s = cudaStream_t(stream);
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return fail(ZX_ECUDA, "event");
+  auto round_trip = [&]() {
+    int q = transform(KIND_TFT, x, l, n, n, 0, N, 0, stride_limbs, 0, stream);
+    return q ? q : transform(KIND_ITFT, x, l, n, n, 0, N, 0, stride_limbs, 1, stream);
+  };
+  float best = 1e30f, def_ms = -1.0f;
+  PlanConfig chosen = before;
+  for (const PlanConfig &c : cands) {
+    set_plan_config(N, c);
+    if ((rc = round_trip())) break;  // warm-up: plans and job images are built here
+    cudaEventRecord(e0, s);
+    for (int k = 0; k < reps && !rc; k++) rc = round_trip();
+    cudaEventRecord(e1, s);
+    if (rc) break;
+    if (cudaEventSynchronize(e1) != cudaSuccess) {
+      rc = cuda_fail(cudaGetLastError(), "tuning run");
+      break;
+    }
+    float ms = 0.0f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    ms /= float(reps);
+    if (c.ls_max == def.ls_max && c.ls_c == def.ls_c && c.max_warps == def.max_warps && c.split == def.split)
+      def_ms = ms;
+    if (ms < best) {
+      best = ms;
+      chosen = c;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  set_plan_config(N, rc ? before : chosen);
+  if (rc) return rc;
+  std::memset(out, 0, sizeof *out);
+  out->ls_max = chosen.ls_max;
+  out->ls_c = chosen.ls_c;
+  out->max_warps = chosen.max_warps;
+  out->split = chosen.split;
+  out->candidates = int32_t(cands.size());
+  out->best_ms = best;
+  out->default_ms = def_ms;
+  return ZX_OK;
+}
+
+int zx_config_get(int64_t N, zx_tune_info *out) {
+  if (!out) return fail(ZX_EINVAL, "out is NULL");
+  if (!ring_supported(N)) return fail(ZX_EUNSUPPORTED, "unsupported ring size N");
+  const PlanConfig c = plan_config(N);
+  std::memset(out, 0, sizeof *out);
+  out->ls_max = c.ls_max;
+  out->ls_c = c.ls_c;
+  out->max_warps = c.max_warps;
+  out->split = c.split;
+  return ZX_OK;
+}
+
+int zx_config_set(int64_t N, const zx_tune_info *cfg) {
+  if (!ring_supported(N)) return fail(ZX_EUNSUPPORTED, "unsupported ring size N");
+  const Ring r = make_ring(N);
+  if (!cfg) {
+    set_plan_config(N, default_config(r));
+    return ZX_OK;
+  }
+  PlanConfig c;
+  c.ls_max = cfg->ls_max;
+  c.ls_c = cfg->ls_c;
+  c.max_warps = cfg->max_warps;
+  c.split = cfg->split;
+  if (!config_valid(r, c)) return fail(ZX_EINVAL, "configuration not valid for this ring");
+  set_plan_config(N, c);
+  return ZX_OK;
+}
+
 const char *zx_strerror(int code) {
   switch (code) {
     case ZX_OK: return "ok";

@@ -41,6 +41,22 @@ struct Ring {
 bool ring_supported(int64_t N);
 Ring make_ring(int64_t N);
 
+// Launch configuration of the plans over one ring: the largest job one CTA holds (ls_max),
+// the cells per CTA of a cluster job (ls_c, both log2), the warps per CTA (8 or 16) and the
+// top-level split (0: L1 = 2^floor(l/2) as in the paper, 1: L1 = 2^ceil(l/2)). Every choice
+// computes the same outputs; they differ in speed. zx_tune measures the candidates.
+struct PlanConfig {
+  int ls_max = 0, ls_c = 0, max_warps = 16, split = 0;
+};
+PlanConfig default_config(const Ring &r);
+bool config_valid(const Ring &r, const PlanConfig &c);
+// The configuration used for ring N: the tuned one when set, else the default.
+PlanConfig plan_config(int64_t N);
+void set_plan_config(int64_t N, const PlanConfig &c);
+// Warps per CTA of a job of 2^ls cells on 2^lc CTAs: one per butterfly of a full level, at most
+// max_warps.
+int warps_for_job(int ls, int lc, int max_warps);
+
 // Largest sub-transform (log2 of its cell count) one CTA holds in shared memory.
 int max_onchip_ls(const Ring &r);
 // Cells (log2) per CTA of a cluster job: small enough that two CTAs share an SM, so that the
@@ -103,14 +119,13 @@ void build_host_plan(int kind, int l, int64_t z, int64_t n, int f, int64_t N, in
 // One job of a plan with its pass index and launch shape; `d.image` is a device pointer into
 // the shared image cache.
 struct PlannedJob {
-  int pass = 0, ls = 0, lc = 0, prog_words = 0;
+  int pass = 0, ls = 0, lc = 0, prog_words = 0, nwarps = 0;
   JobDesc d;
 };
 // Jobs of a TFT / ITFT plan (host side, images resolved on the current device). Returns the
 // number of passes, or -1 with *err set.
 int plan_jobs(int kind, int l, int64_t z, int64_t n, int f, int64_t N, int64_t e, int scale,
               std::vector<PlannedJob> *out, int *err);
-int warps_for_job(int ls, int lc);
 
 // Enqueue a plan on a stream.
 cudaError_t run_transform(const TransformPlan &p, uint64_t *x, int64_t stride_limbs,

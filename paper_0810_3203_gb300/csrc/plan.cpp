@@ -53,6 +53,48 @@ int cluster_cta_ls(const Ring &r) {
   return ls;
 }
 
+PlanConfig default_config(const Ring &r) {
+  PlanConfig c;
+  c.ls_max = max_onchip_ls(r);
+  c.ls_c = cluster_cta_ls(r);
+  c.max_warps = 16;
+  c.split = 0;
+  return c;
+}
+
+bool config_valid(const Ring &r, const PlanConfig &c) {
+  auto fits = [&](int ls) { return ls >= 1 && ls <= 16 && size_t(1) << ls <= 65536 &&
+                                   (size_t(1) << ls) * (size_t(r.pitch) + 1) * 4 <= kSmemBudget; };
+  return fits(c.ls_max) && fits(c.ls_c) && c.ls_c <= c.ls_max + 1 && (c.max_warps == 8 || c.max_warps == 16) &&
+         (c.split == 0 || c.split == 1);
+}
+
+namespace {
+
+std::mutex g_config_mu;
+std::map<int64_t, PlanConfig> &config_table() {
+  static std::map<int64_t, PlanConfig> *t = new std::map<int64_t, PlanConfig>();
+  return *t;
+}
+
+}  // namespace
+
+PlanConfig plan_config(int64_t N) {
+  std::lock_guard<std::mutex> lk(g_config_mu);
+  auto it = config_table().find(N);
+  return it != config_table().end() ? it->second : default_config(make_ring(N));
+}
+
+void set_plan_config(int64_t N, const PlanConfig &c) {
+  std::lock_guard<std::mutex> lk(g_config_mu);
+  config_table()[N] = c;
+}
+
+int warps_for_job(int ls, int lc, int max_warps) {
+  const int nslots = 1 << (ls - lc);
+  return std::max(1, std::min(max_warps, nslots / 2));
+}
+
 namespace {
 
 int64_t md(int64_t a, int64_t m) {
@@ -116,7 +158,19 @@ struct Planner {
   int64_t twoN;
   int ls_max;  // largest job held by one CTA
   int ls_c;    // cells (log2) per CTA of a cluster job
+  int split;   // 0: L1 = 2^floor(l/2) (the paper's split), 1: L1 = 2^ceil(l/2)
+  PlanConfig cfg;
   std::vector<JobRec> jobs;
+
+  explicit Planner(int64_t N, const PlanConfig *c = nullptr) {
+    ring = make_ring(N);
+    twoN = 2 * N;
+    cfg = c ? *c : plan_config(N);
+    ls_max = cfg.ls_max;
+    ls_c = cfg.ls_c;
+    split = cfg.split;
+  }
+  int top_l1(int l) const { return split ? l - l / 2 : l / 2; }
 
   // single CTA up to ls_max; a cluster of up to 16 CTAs of 2^ls_c cells above that, as long as
   // every CTA row of the job's split holds at least one cell per CTA (2 lc <= l)
@@ -153,7 +207,7 @@ struct Planner {
       job(pass, KIND_TFT, cell0, ms, l, e, z, n, 0, 0, 0);
       return 1;
     }
-    int l1 = l / 2, l2 = l - l1;
+    int l1 = top_l1(l), l2 = l - l1;
     int64_t L = int64_t(1) << l, L1 = int64_t(1) << l1, L2 = int64_t(1) << l2, w = twoN / L;
     int64_t n2 = n % L2, n1 = n / L2, n1p = (n + L2 - 1) / L2;
     int64_t z2 = z % L2, z1 = z / L2, z2p = z1 > 0 ? L2 : z2;
@@ -173,7 +227,7 @@ struct Planner {
       job(pass, KIND_ITFT, cell0, ms, l, e, z, n, f, escale >= 0 ? n : 0, escale >= 0 ? escale : 0);
       return 1;
     }
-    int l1 = l / 2, l2 = l - l1;
+    int l1 = top_l1(l), l2 = l - l1;
     int64_t L = int64_t(1) << l, L1 = int64_t(1) << l1, L2 = int64_t(1) << l2, w = twoN / L;
     int64_t n2 = n % L2, n1 = n / L2, z2 = z % L2, z1 = z / L2;
     int fp = (n2 + f > 0) ? 1 : 0;
@@ -197,7 +251,8 @@ struct Planner {
 
 struct PlanCache {
   std::mutex mu;
-  std::map<std::tuple<int, int, int, int64_t, int64_t, int, int64_t, int64_t, int>, std::unique_ptr<TransformPlan>> plans;
+  std::map<std::tuple<int, int, int, int64_t, int64_t, int, int64_t, int64_t, int, int>, std::unique_ptr<TransformPlan>>
+      plans;
 };
 
 PlanCache &plan_cache() {
@@ -207,18 +262,7 @@ PlanCache &plan_cache() {
 
 }  // namespace
 
-int warps_for_job(int ls, int lc) {
-  int nslots = 1 << (ls - lc);
-  return std::max(1, std::min(16, nslots / 2));
-}
-
 namespace {
-
-// warps per CTA: one per butterfly of a full level, at most 16
-int warps_for(int ls, int lc) {
-  int nslots = 1 << (ls - lc);
-  return std::max(1, std::min(16, nslots / 2));
-}
 
 bool same_launch(const JobRec &a, const JobRec &b) { return a.pass == b.pass && a.ls == b.ls && a.lc == b.lc; }
 bool launch_order(const JobRec &a, const JobRec &b) {
@@ -230,16 +274,12 @@ bool launch_order(const JobRec &a, const JobRec &b) {
 }  // namespace
 
 int64_t zero_padded_outputs(int l, int64_t n, int64_t N) {
-  Planner P;
-  P.ring = make_ring(N);
-  P.twoN = 2 * N;
-  P.ls_max = max_onchip_ls(P.ring);
-  P.ls_c = cluster_cta_ls(P.ring);
+  Planner P(N);
   const int64_t L = int64_t(1) << l;
   auto up = [](int64_t v, int64_t m) { return (v + m - 1) / m * m; };
   if (!P.leaf(l)) {
     // whole rows of the top-level split over global memory
-    const int l1 = l / 2, l2 = l - l1;
+    const int l1 = P.top_l1(l), l2 = l - l1;
     const int64_t n_rows = up(n, int64_t(1) << l2);
     // when the column sub-transforms are cluster jobs, whole in-job rows of those as well (their
     // partial in-job row is a serial step on one CTA), if that adds at most 1/32 of n
@@ -256,21 +296,13 @@ int64_t zero_padded_outputs(int l, int64_t n, int64_t N) {
 }
 
 int count_passes(int kind, int l, int64_t z, int64_t n, int f, int64_t N) {
-  Planner P;
-  P.ring = make_ring(N);
-  P.twoN = 2 * N;
-  P.ls_max = max_onchip_ls(P.ring);
-  P.ls_c = cluster_cta_ls(P.ring);
+  Planner P(N);
   return kind == KIND_TFT ? P.tft(0, 0, 1, l, 0, z, n) : P.itft(0, 0, 1, l, 0, z, n, f, -1);
 }
 
 void plan_shape(int kind, int l, int64_t z, int64_t n, int f, int64_t N, int *passes, int *launches,
                 int64_t *jobs, int *onchip_l, int *cluster_l) {
-  Planner P;
-  P.ring = make_ring(N);
-  P.twoN = 2 * N;
-  P.ls_max = max_onchip_ls(P.ring);
-  P.ls_c = cluster_cta_ls(P.ring);
+  Planner P(N);
   *passes = kind == KIND_TFT ? P.tft(0, 0, 1, l, 0, z, n) : P.itft(0, 0, 1, l, 0, z, n, f, -1);
   std::sort(P.jobs.begin(), P.jobs.end(), launch_order);
   int nl = 0, lcmax = 0, lsmax = 0;
@@ -289,11 +321,7 @@ void build_host_plan(int kind, int l, int64_t z, int64_t n, int f, int64_t N, in
                      HostPlan *out) {
   int64_t twoN = 2 * N;
   e = md(e, twoN);
-  Planner P;
-  P.ring = make_ring(N);
-  P.twoN = twoN;
-  P.ls_max = max_onchip_ls(P.ring);
-  P.ls_c = cluster_cta_ls(P.ring);
+  Planner P(N);
   out->ring = P.ring;
   out->npasses = kind == KIND_TFT ? P.tft(0, 0, 1, l, e, z, n)
                                   : P.itft(0, 0, 1, l, e, z, n, f, scale ? md(twoN - l, twoN) : -1);
@@ -305,7 +333,7 @@ void build_host_plan(int kind, int l, int64_t z, int64_t n, int f, int64_t N, in
     HostPlan::Group g;
     g.ls = P.jobs[i].ls;
     g.lc = P.jobs[i].lc;
-    g.nwarps = warps_for(g.ls, g.lc);
+    g.nwarps = warps_for_job(g.ls, g.lc, P.cfg.max_warps);
     g.prog_words = 0;
     for (size_t t = i; t < k; t++) {
       const JobRec &j = P.jobs[t];
@@ -332,11 +360,7 @@ int plan_jobs(int kind, int l, int64_t z, int64_t n, int f, int64_t N, int64_t e
               std::vector<PlannedJob> *out, int *err) {
   int64_t twoN = 2 * N;
   e = md(e, twoN);
-  Planner P;
-  P.ring = make_ring(N);
-  P.twoN = twoN;
-  P.ls_max = max_onchip_ls(P.ring);
-  P.ls_c = cluster_cta_ls(P.ring);
+  Planner P(N);
   int npass = kind == KIND_TFT ? P.tft(0, 0, 1, l, e, z, n)
                                : P.itft(0, 0, 1, l, e, z, n, f, scale ? md(twoN - l, twoN) : -1);
   out->clear();
@@ -349,6 +373,7 @@ int plan_jobs(int kind, int l, int64_t z, int64_t n, int f, int64_t N, int64_t e
     pj.ls = j.ls;
     pj.lc = j.lc;
     pj.prog_words = image_cache().max_prog(j.d.image);
+    pj.nwarps = warps_for_job(j.ls, j.lc, P.cfg.max_warps);
     pj.d = j.d;
     out->push_back(pj);
   }
@@ -361,18 +386,16 @@ const TransformPlan *get_transform_plan(int kind, int l, int64_t z, int64_t n, i
   cudaGetDevice(&dev);
   int64_t twoN = 2 * N;
   e = md(e, twoN);
-  auto key = std::make_tuple(dev, kind, l, z, n, f, N, e, scale);
+  const PlanConfig cfg = plan_config(N);
+  const int cfg_key = cfg.ls_max | (cfg.ls_c << 5) | (cfg.max_warps << 10) | (cfg.split << 16);
+  auto key = std::make_tuple(dev, kind, l, z, n, f, N, e, scale, cfg_key);
   PlanCache &pc = plan_cache();
   {
     std::lock_guard<std::mutex> lk(pc.mu);
     auto it = pc.plans.find(key);
     if (it != pc.plans.end()) return it->second.get();
   }
-  Planner P;
-  P.ring = make_ring(N);
-  P.twoN = twoN;
-  P.ls_max = max_onchip_ls(P.ring);
-  P.ls_c = cluster_cta_ls(P.ring);
+  Planner P(N, &cfg);
   int npass;
   if (kind == KIND_TFT)
     npass = P.tft(0, 0, 1, l, e, z, n);
@@ -398,7 +421,7 @@ const TransformPlan *get_transform_plan(int kind, int l, int64_t z, int64_t n, i
     L.ls = P.jobs[i].ls;
     L.lc = P.jobs[i].lc;
     L.njobs = int(k - i);
-    L.nwarps = warps_for(L.ls, L.lc);
+    L.nwarps = warps_for_job(L.ls, L.lc, P.cfg.max_warps);
     for (size_t t = i; t < k; t++) L.prog_words = std::max(L.prog_words, image_cache().max_prog(P.jobs[t].d.image));
     groups.push_back({flat.size(), L});
     for (size_t t = i; t < k; t++) flat.push_back(P.jobs[t].d);

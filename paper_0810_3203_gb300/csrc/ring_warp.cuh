@@ -81,32 +81,60 @@ __device__ __forceinline__ uint32_t ripple_sub(uint32_t (&r)[K], uint32_t c) {
   return c;
 }
 
-// Lane carries cout (out of each lane's chunk) moved into the next lane until none is left.
-// Returns the total carry out of bit N.
+// Carry lookahead across the lanes of a warp. Lane l emits a carry out of its chunk (gen) or
+// lets an incoming one through (pass: its chunk is all ones for carries, all zeros for
+// borrows; gen and pass never hold together, since a chunk that has just emitted a carry cannot
+// be all ones). The carry entering lane l is c_l = gen_{l-1} | (pass_{l-1} & c_{l-1}), c_0 = 0,
+// which are the carries of the binary sum A + B with A = gen and B = gen | pass as lane masks:
+// c_l = bit l of (A + B) ^ A ^ B. Returns c_l of this lane and sets *top to the carry out of
+// lane G - 1, which is bit G: when G < 32 the idle lane G sees it as its c_l and must not
+// apply it. O(1) warp operations, however far a carry travels.
+__device__ __forceinline__ uint32_t lookahead_in(bool gen, bool pass, const Geo &g, uint32_t *top) {
+  const uint32_t A = __ballot_sync(TFT_FULL, gen);
+  const uint32_t B = A | __ballot_sync(TFT_FULL, pass);
+  const uint64_t c = (uint64_t(A) + uint64_t(B)) ^ uint64_t(A) ^ uint64_t(B);
+  *top = uint32_t(c >> g.G) & 1u;
+  return uint32_t(c >> g.lane) & 1u;
+}
+
+// Lane carries cout (0/1, out of each lane's chunk) moved into the following lanes. Returns the
+// carry out of bit N.
 template <int K>
 __device__ __forceinline__ uint32_t resolve_add(uint32_t (&r)[K], uint32_t cout, const Geo &g) {
-  uint32_t top = __shfl_sync(TFT_FULL, cout, g.G - 1);
-  uint32_t c = __shfl_up_sync(TFT_FULL, cout, 1);
-  if (g.lane == 0 || g.lane >= g.G) c = 0;
-  while (__any_sync(TFT_FULL, c)) {
-    uint32_t co = ripple_add<K>(r, c);
-    top += __shfl_sync(TFT_FULL, co, g.G - 1);
-    c = __shfl_up_sync(TFT_FULL, co, 1);
-    if (g.lane == 0 || g.lane >= g.G) c = 0;
+  const bool gen = g.lane < g.G && cout != 0;
+  if (!__any_sync(TFT_FULL, gen)) return 0u;
+  bool pass = g.lane < g.G && !gen;
+#pragma unroll
+  for (int s = 0; s < K; s++) pass = pass && r[s] == TFT_FULL;
+  uint32_t top;
+  if (lookahead_in(gen, pass, g, &top) && g.lane < g.G) {
+    uint32_t c = 1u;
+#pragma unroll
+    for (int s = 0; s < K; s++) {
+      r[s] += c;
+      c = (c && r[s] == 0u) ? 1u : 0u;
+    }
   }
   return top;
 }
 
+// Lane borrows bout (0/1) moved into the following lanes. Returns the borrow out of bit N.
 template <int K>
 __device__ __forceinline__ uint32_t resolve_sub(uint32_t (&r)[K], uint32_t bout, const Geo &g) {
-  uint32_t top = __shfl_sync(TFT_FULL, bout, g.G - 1);
-  uint32_t c = __shfl_up_sync(TFT_FULL, bout, 1);
-  if (g.lane == 0 || g.lane >= g.G) c = 0;
-  while (__any_sync(TFT_FULL, c)) {
-    uint32_t co = ripple_sub<K>(r, c);
-    top += __shfl_sync(TFT_FULL, co, g.G - 1);
-    c = __shfl_up_sync(TFT_FULL, co, 1);
-    if (g.lane == 0 || g.lane >= g.G) c = 0;
+  const bool gen = g.lane < g.G && bout != 0;
+  if (!__any_sync(TFT_FULL, gen)) return 0u;
+  bool pass = g.lane < g.G && !gen;
+#pragma unroll
+  for (int s = 0; s < K; s++) pass = pass && r[s] == 0u;
+  uint32_t top;
+  if (lookahead_in(gen, pass, g, &top) && g.lane < g.G) {
+    uint32_t c = 1u;
+#pragma unroll
+    for (int s = 0; s < K; s++) {
+      const uint32_t old = r[s];
+      r[s] = old - c;
+      c = (c && old == 0u) ? 1u : 0u;
+    }
   }
   return top;
 }
@@ -138,28 +166,6 @@ __device__ __forceinline__ void set_ones(uint32_t (&r)[K], const Geo &g) {
   for (int s = 0; s < K; s++) r[s] = g.lane < g.G ? TFT_FULL : 0u;
 }
 
-// Storage form: given an N-bit R and a small warp-uniform v with m = R + v (mod 2^N+1),
-// leave m in [0, 2^N - 1] in r and return 0, or return 1 when m = -1 (the cell value x = m + 1
-// is zero).
-template <int K>
-__device__ __forceinline__ int canon_m(uint32_t (&r)[K], int v, const Geo &g) {
-  while (v != 0) {
-    if (v > 0) {
-      uint32_t o = add_small<K>(r, uint32_t(v), g);  // R + v = R' + o 2^N = R' - o
-      v = -int(o);
-    } else {
-      uint32_t b = sub_small<K>(r, uint32_t(-v), g);  // R - |v| = R' - b 2^N = R' + b
-      if (!b) {
-        v = 0;
-      } else {
-        if (v == -1) return 1;  // R was 0: m = -1
-        v = 1;
-      }
-    }
-  }
-  return 0;
-}
-
 // Canonical value: x = R + v (mod 2^N+1) with x in [0, 2^N]; returns the top bit (1 only for
 // x = 2^N, then r is zero).
 template <int K>
@@ -177,79 +183,13 @@ __device__ __forceinline__ uint32_t canon_x(uint32_t (&r)[K], int v, const Geo &
   return 0u;
 }
 
-// add the signed small value c at slot 0 of the lane's chunk and propagate; returns the signed
-// carry out of the chunk (-1, 0 or +1)
-template <int K>
-__device__ __forceinline__ int ripple_signed(uint32_t (&r)[K], int c) {
-#pragma unroll
-  for (int s = 0; s < K; s++) {
-    if (!__any_sync(TFT_FULL, c != 0)) return 0;
-    uint32_t old = r[s];
-    uint32_t t = old + uint32_t(c);
-    c = c > 0 ? int(t < old) : (c < 0 ? -int(t > old) : 0);
-    r[s] = t;
-  }
-  return c;
-}
-
-// Finish an add or subtract chain in the storage form m = x - 1 (see the file comment).
-// cout is each lane's signed carry out of its chunk (+1 carry, -1 borrow); it enters the next
-// lane, and the carry out of bit N re-enters lane 0 negated (2^N = -1) together with v0.
-// Leaves m in [0, 2^N - 1] and returns 0, or returns 1 when m = -1 (the cell value x is 0):
-// that is the one value whose carries circulate forever, which the iteration bound detects.
-template <int K>
-__device__ __forceinline__ int settle(uint32_t (&r)[K], int cout, int v0, const Geo &g) {
-  int top = __shfl_sync(TFT_FULL, cout, g.G - 1);
-  int c = __shfl_up_sync(TFT_FULL, cout, 1);
-  if (g.lane == 0) c = v0 - top;
-  if (g.lane >= g.G) c = 0;
-  for (int it = 0;; it++) {
-    if (!__any_sync(TFT_FULL, c != 0)) return 0;
-    if (it > 3 * g.G + 3) return 1;
-    int co = ripple_signed<K>(r, c);
-    top = __shfl_sync(TFT_FULL, co, g.G - 1);
-    c = __shfl_up_sync(TFT_FULL, co, 1);
-    if (g.lane == 0) c = -top;
-    if (g.lane >= g.G) c = 0;
-  }
-}
-
 // ------------------------------------------------------------------ chains into shared memory
-// The same chains, but each result word goes straight to this lane's chunk of a shared-memory
-// cell (st.shared leaves the carry flag alone), so no register array holds the result.
-template <int K>
-__device__ __forceinline__ uint32_t add_chain_st(uint32_t *dst, const uint32_t (&a)[K], const uint32_t (&b)[K],
-                                                 uint32_t cin) {
-  uint32_t cout, d, w;
-  asm volatile("add.cc.u32 %0, %1, 0xffffffff;" : "=r"(d) : "r"(cin));
-#pragma unroll
-  for (int s = 0; s < K; s++) {
-    asm volatile("addc.cc.u32 %0, %1, %2;" : "=r"(w) : "r"(a[s]), "r"(b[s]));
-    asm volatile("st.shared.u32 [%0], %1;" ::"r"((uint32_t)__cvta_generic_to_shared(dst + s)), "r"(w) : "memory");
-  }
-  asm volatile("addc.u32 %0, 0, 0;" : "=r"(cout));
-  return cout;
-}
-
-template <int K>
-__device__ __forceinline__ uint32_t sub_chain_st(uint32_t *dst, const uint32_t (&a)[K], const uint32_t (&b)[K],
-                                                 uint32_t bin) {
-  uint32_t bout, d, w;
-  asm volatile("sub.cc.u32 %0, 0, %1;" : "=r"(d) : "r"(bin));
-#pragma unroll
-  for (int s = 0; s < K; s++) {
-    asm volatile("subc.cc.u32 %0, %1, %2;" : "=r"(w) : "r"(a[s]), "r"(b[s]));
-    asm volatile("st.shared.u32 [%0], %1;" ::"r"((uint32_t)__cvta_generic_to_shared(dst + s)), "r"(w) : "memory");
-  }
-  asm volatile("subc.u32 %0, 0, 0;" : "=r"(bout));
-  return bout & 1u;
-}
-
 // dst = a + b + cin (ADD) or a - b - cin (SUB) over this lane's chunk, where a is read from
 // the shared-memory chunk `asrc` (or is all ones when a_ones: the zero cell's raw form) and b
-// sits in registers. Works in groups of 8 words: 8 loads issued together, then 8 chained
-// add/sub and 8 stores, so a needs no register array. asrc and dst may be the same chunk.
-// Returns the carry (ADD) or borrow (SUB) out of the chunk.
+// sits in registers. Works in groups of up to 8 words: the group's loads issued together, then
+// its chained add/sub and stores, so a needs no register array. Each group's accesses use one
+// base address and immediate offsets. asrc and dst may be the same chunk. Returns the carry
+// (ADD) or borrow (SUB) out of the chunk.
 template <int K, bool SUB>
 __device__ __forceinline__ uint32_t chain_stream(uint32_t *dst, const uint32_t *asrc, bool a_ones,
                                                  const uint32_t (&b)[K], uint32_t cin) {
@@ -260,25 +200,72 @@ __device__ __forceinline__ uint32_t chain_stream(uint32_t *dst, const uint32_t *
     asm volatile("sub.cc.u32 %0, 0, %1;" : "=r"(d) : "r"(cin));
   else
     asm volatile("add.cc.u32 %0, %1, 0xffffffff;" : "=r"(d) : "r"(cin));
-  constexpr int GRP = K < 8 ? K : 8;
+  if (K >= 8) {
 #pragma unroll
-  for (int g0 = 0; g0 < K; g0 += GRP) {
-    uint32_t a[GRP];
+    for (int g0 = 0; g0 < K; g0 += 8) {
+      const uint32_t sg = sa + 4u * g0, dg = da + 4u * g0;
+      uint32_t a0, a1, a2, a3, a4, a5, a6, a7;
+      if (a_ones) {
+        a0 = a1 = a2 = a3 = a4 = a5 = a6 = a7 = 0xffffffffu;
+      } else {
+        asm volatile(
+            "ld.shared.u32 %0, [%8];\n\t"
+            "ld.shared.u32 %1, [%8+4];\n\t"
+            "ld.shared.u32 %2, [%8+8];\n\t"
+            "ld.shared.u32 %3, [%8+12];\n\t"
+            "ld.shared.u32 %4, [%8+16];\n\t"
+            "ld.shared.u32 %5, [%8+20];\n\t"
+            "ld.shared.u32 %6, [%8+24];\n\t"
+            "ld.shared.u32 %7, [%8+28];"
+            : "=r"(a0), "=r"(a1), "=r"(a2), "=r"(a3), "=r"(a4), "=r"(a5), "=r"(a6), "=r"(a7)
+            : "r"(sg));
+      }
+      if (SUB)
+        asm volatile(
+            "{\n\t.reg .u32 w;\n\t"
+            "subc.cc.u32 w, %0, %8;\n\tst.shared.u32 [%16], w;\n\t"
+            "subc.cc.u32 w, %1, %9;\n\tst.shared.u32 [%16+4], w;\n\t"
+            "subc.cc.u32 w, %2, %10;\n\tst.shared.u32 [%16+8], w;\n\t"
+            "subc.cc.u32 w, %3, %11;\n\tst.shared.u32 [%16+12], w;\n\t"
+            "subc.cc.u32 w, %4, %12;\n\tst.shared.u32 [%16+16], w;\n\t"
+            "subc.cc.u32 w, %5, %13;\n\tst.shared.u32 [%16+20], w;\n\t"
+            "subc.cc.u32 w, %6, %14;\n\tst.shared.u32 [%16+24], w;\n\t"
+            "subc.cc.u32 w, %7, %15;\n\tst.shared.u32 [%16+28], w;\n\t}"
+            ::"r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(a4), "r"(a5), "r"(a6), "r"(a7), "r"(b[g0]), "r"(b[g0 + 1]),
+            "r"(b[g0 + 2]), "r"(b[g0 + 3]), "r"(b[g0 + 4]), "r"(b[g0 + 5]), "r"(b[g0 + 6]), "r"(b[g0 + 7]), "r"(dg)
+            : "memory");
+      else
+        asm volatile(
+            "{\n\t.reg .u32 w;\n\t"
+            "addc.cc.u32 w, %0, %8;\n\tst.shared.u32 [%16], w;\n\t"
+            "addc.cc.u32 w, %1, %9;\n\tst.shared.u32 [%16+4], w;\n\t"
+            "addc.cc.u32 w, %2, %10;\n\tst.shared.u32 [%16+8], w;\n\t"
+            "addc.cc.u32 w, %3, %11;\n\tst.shared.u32 [%16+12], w;\n\t"
+            "addc.cc.u32 w, %4, %12;\n\tst.shared.u32 [%16+16], w;\n\t"
+            "addc.cc.u32 w, %5, %13;\n\tst.shared.u32 [%16+20], w;\n\t"
+            "addc.cc.u32 w, %6, %14;\n\tst.shared.u32 [%16+24], w;\n\t"
+            "addc.cc.u32 w, %7, %15;\n\tst.shared.u32 [%16+28], w;\n\t}"
+            ::"r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(a4), "r"(a5), "r"(a6), "r"(a7), "r"(b[g0]), "r"(b[g0 + 1]),
+            "r"(b[g0 + 2]), "r"(b[g0 + 3]), "r"(b[g0 + 4]), "r"(b[g0 + 5]), "r"(b[g0 + 6]), "r"(b[g0 + 7]), "r"(dg)
+            : "memory");
+    }
+  } else {
+    uint32_t a[K];
 #pragma unroll
-    for (int k = 0; k < GRP; k++) {
+    for (int k = 0; k < K; k++) {
       if (a_ones)
         a[k] = 0xffffffffu;
       else
-        asm volatile("ld.shared.u32 %0, [%1];" : "=r"(a[k]) : "r"(sa + 4u * (g0 + k)));
+        asm volatile("ld.shared.u32 %0, [%1];" : "=r"(a[k]) : "r"(sa + 4u * k));
     }
 #pragma unroll
-    for (int k = 0; k < GRP; k++) {
+    for (int k = 0; k < K; k++) {
       uint32_t w;
       if (SUB)
-        asm volatile("subc.cc.u32 %0, %1, %2;" : "=r"(w) : "r"(a[k]), "r"(b[g0 + k]));
+        asm volatile("subc.cc.u32 %0, %1, %2;" : "=r"(w) : "r"(a[k]), "r"(b[k]));
       else
-        asm volatile("addc.cc.u32 %0, %1, %2;" : "=r"(w) : "r"(a[k]), "r"(b[g0 + k]));
-      asm volatile("st.shared.u32 [%0], %1;" ::"r"(da + 4u * (g0 + k)), "r"(w) : "memory");
+        asm volatile("addc.cc.u32 %0, %1, %2;" : "=r"(w) : "r"(a[k]), "r"(b[k]));
+      asm volatile("st.shared.u32 [%0], %1;" ::"r"(da + 4u * k), "r"(w) : "memory");
     }
   }
   if (SUB) {
@@ -289,16 +276,66 @@ __device__ __forceinline__ uint32_t chain_stream(uint32_t *dst, const uint32_t *
   return cout;
 }
 
-// settle() for a result that sits in this lane's chunk `chunk` of a shared-memory cell: the
-// carries ripple through shared memory word by word (usually one word), only in the lanes that
-// hold one.
+// Rest of settle_smem once some carry has survived the first word of a chunk: c (-1, 0 or +1)
+// is pending at word `start` of this lane's chunk. Each round ripples the pending carries
+// through the lanes' own chunks, moves the carries that leave a chunk across lanes with the
+// lookahead (one sign at a time, each over whole chunks that pass it on), and puts the net
+// carry out of bit N back in at bit 0 with the opposite sign (2^N = -1). A legitimate result
+// settles within two rounds; carries that still circulate after six mean the value is -1 (the
+// zero cell), reported by returning 1.
+template <int K>
+__device__ __noinline__ int settle_smem_slow(uint32_t *chunk, int c, const Geo &g) {
+  int start = 1;
+  for (int round = 0; round < 6; round++) {
+    for (int s = start; s < K && c != 0; s++) {
+      const uint32_t old = chunk[s];
+      const uint32_t t = old + uint32_t(c);
+      c = c > 0 ? int(t < old) : -int(t > old);
+      chunk[s] = t;
+    }
+    if (!__any_sync(TFT_FULL, c != 0)) return 0;
+    // Lanes above 0 carry the chain's sign, lane 0 may carry the other one. That sign goes
+    // first: its emitters are then untouched when they emit, so no lane ever has to pass on
+    // two carries of one sign (which the lookahead cannot express); in the second phase only
+    // lane 0 emits, and nothing enters lane 0.
+    int wrap = 0;
+    const bool plus_first = __any_sync(TFT_FULL, g.lane > 0 && c > 0);
+    for (int ph = 0; ph < 2; ph++) {
+      const bool plus = (ph == 0) == plus_first;
+      const bool gen = plus ? c > 0 : c < 0;
+      if (!__any_sync(TFT_FULL, gen)) continue;
+      const uint32_t pattern = plus ? TFT_FULL : 0u;  // a chunk that passes the carry on
+      bool pass = g.lane < g.G && !gen;
+      for (int s = 0; s < K && pass; s++) pass = chunk[s] == pattern;
+      uint32_t top;
+      if (lookahead_in(gen, pass, g, &top) && g.lane < g.G) {
+        for (int s = 0; s < K; s++) {
+          const uint32_t old = chunk[s];
+          chunk[s] = plus ? old + 1u : old - 1u;
+          if (old != pattern) break;
+        }
+      }
+      wrap += plus ? -int(top) : int(top);
+    }
+    if (wrap == 0) return 0;
+    c = g.lane == 0 ? wrap : 0;
+    start = 0;
+  }
+  return 1;
+}
+
+// settle() for a result that sits in this lane's chunk `chunk` of a shared-memory cell: cout is
+// each lane's carry out of its chunk (all of one sign); it enters the next lane, and the carry
+// out of bit N re-enters lane 0 negated (2^N = -1) together with v0. Leaves m in [0, 2^N - 1]
+// and returns 0, or returns 1 when m = -1 (the cell value x is zero). Carries are applied to
+// the first word of each chunk without a loop; for random data none survives that, and the
+// rest (long runs of ones or zeros, common in structured data) goes to the lookahead path.
 template <int K>
 __device__ __forceinline__ int settle_smem(uint32_t *chunk, int cout, int v0, const Geo &g) {
-  int top = __shfl_sync(TFT_FULL, cout, g.G - 1);
+  const int top = __shfl_sync(TFT_FULL, cout, g.G - 1);
   int c = __shfl_up_sync(TFT_FULL, cout, 1);
   if (g.lane == 0) c = v0 - top;
   if (g.lane >= g.G) c = 0;
-  // first word of each chunk without a loop; almost always no carry survives it
   if (c != 0) {
     const uint32_t old = chunk[0];
     const uint32_t t = old + uint32_t(c);
@@ -306,27 +343,7 @@ __device__ __forceinline__ int settle_smem(uint32_t *chunk, int cout, int v0, co
     chunk[0] = t;
   }
   if (!__any_sync(TFT_FULL, c != 0)) return 0;
-  for (int s = 1; s < K && c != 0; s++) {
-    const uint32_t old = chunk[s];
-    const uint32_t t = old + uint32_t(c);
-    c = c > 0 ? int(t < old) : -int(t > old);
-    chunk[s] = t;
-  }
-  // carries that left a chunk: move them on lane by lane (2^N = -1 at the top)
-  for (int it = 0;; it++) {
-    top = __shfl_sync(TFT_FULL, c, g.G - 1);
-    c = __shfl_up_sync(TFT_FULL, c, 1);
-    if (g.lane == 0) c = -top;
-    if (g.lane >= g.G) c = 0;
-    if (!__any_sync(TFT_FULL, c != 0)) return 0;
-    if (it > 3 * g.G + 3) return 1;
-    for (int s = 0; s < K && c != 0; s++) {
-      const uint32_t old = chunk[s];
-      const uint32_t t = old + uint32_t(c);
-      c = c > 0 ? int(t < old) : -int(t > old);
-      chunk[s] = t;
-    }
-  }
+  return settle_smem_slow<K>(chunk, c, g);
 }
 
 // ------------------------------------------------------------------ shared-memory cells

@@ -279,8 +279,9 @@ __device__ __forceinline__ void exchange(uint32_t *cells, uint32_t *meta, int P,
 }
 
 // MINB = 3: jobs of at most 8 warps and 75 KB of shared memory, three CTAs per SM (registers
-// capped at 85 per thread); MINB = 1: up to 16 warps, one CTA per SM
-template <int K, int MINB>
+// capped at 85 per thread); MINB = 1: up to 16 warps, one CTA per SM. FULL: all 32 lanes hold
+// words (NW = 32 K), which lets the compiler drop the idle-lane cases.
+template <int K, int MINB, bool FULL>
 __global__ void __launch_bounds__(MINB == 3 ? 256 : 512, MINB) job_kernel(uint64_t *__restrict__ x, int64_t stride_limbs,
                                                   const JobDesc *__restrict__ jobs, int N, int ls, int lc,
                                                   uint32_t mask, int prog_cap) {
@@ -291,7 +292,7 @@ __global__ void __launch_bounds__(MINB == 3 ? 256 : 512, MINB) job_kernel(uint64
   KGeo kg;
   kg.g.N = N;
   kg.g.NW = N / 32;
-  kg.g.G = kg.g.NW / K;
+  kg.g.G = FULL ? 32 : kg.g.NW / K;
   kg.g.lane = threadIdx.x & 31;
   kg.g.twoN = 2 * N;
   kg.mask = mask;
@@ -374,16 +375,16 @@ __global__ void __launch_bounds__(MINB == 3 ? 256 : 512, MINB) job_kernel(uint64
 
 namespace {
 
-template <int K, int MINB>
+template <int K, int MINB, bool FULL>
 cudaError_t launch_km(const Launch &L, uint64_t *x, int64_t stride_limbs, const Ring &r, cudaStream_t s,
                       size_t smem, int prog_cap, uint32_t mask) {
   static thread_local int configured[8] = {0, 0, 0, 0, 0, 0, 0, 0};
   int dev = 0;
   cudaGetDevice(&dev);
   if (dev >= 8 || !configured[dev]) {
-    cudaError_t e = cudaFuncSetAttribute(job_kernel<K, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    cudaError_t e = cudaFuncSetAttribute(job_kernel<K, MINB, FULL>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(job_kernel<K, MINB>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    e = cudaFuncSetAttribute(job_kernel<K, MINB, FULL>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     if (e != cudaSuccess) return e;
     if (dev < 8) configured[dev] = 1;
   }
@@ -399,7 +400,7 @@ cudaError_t launch_km(const Launch &L, uint64_t *x, int64_t stride_limbs, const 
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = L.lc > 0 ? 1 : 0;
-  return cudaLaunchKernelEx(&cfg, job_kernel<K, MINB>, x, stride_limbs, (const JobDesc *)L.d_jobs, int(r.N), L.ls,
+  return cudaLaunchKernelEx(&cfg, job_kernel<K, MINB, FULL>, x, stride_limbs, (const JobDesc *)L.d_jobs, int(r.N), L.ls,
                             L.lc, mask, prog_cap);
 }
 
@@ -413,8 +414,10 @@ cudaError_t launch_k(const Launch &L, uint64_t *x, int64_t stride_limbs, const R
   const uint32_t twoN = uint32_t(2 * r.N);
   const uint32_t mask = (twoN & (twoN - 1)) == 0 ? twoN - 1 : 0u;
   if (L.nwarps <= 8 && smem <= 75 * 1024)
-    return launch_km<K, 3>(L, x, stride_limbs, r, s, smem, prog_cap, mask);
-  return launch_km<K, 1>(L, x, stride_limbs, r, s, smem, prog_cap, mask);
+    return r.G == 32 ? launch_km<K, 3, true>(L, x, stride_limbs, r, s, smem, prog_cap, mask)
+                     : launch_km<K, 3, false>(L, x, stride_limbs, r, s, smem, prog_cap, mask);
+  return r.G == 32 ? launch_km<K, 1, true>(L, x, stride_limbs, r, s, smem, prog_cap, mask)
+                   : launch_km<K, 1, false>(L, x, stride_limbs, r, s, smem, prog_cap, mask);
 }
 
 }  // namespace

@@ -54,6 +54,7 @@ struct DescImage {
 struct MergedPasses {
   std::map<std::tuple<int, int, int>, std::vector<JobDesc>> jobs;
   std::map<std::tuple<int, int, int>, int> prog_words;
+  std::map<std::tuple<int, int, int>, int> nwarps;
   int add(int kind, int l, int64_t z, int64_t n, int64_t N, int64_t cell_off, int scale) {
     std::vector<PlannedJob> pj;
     int err = ZX_OK;
@@ -64,6 +65,7 @@ struct MergedPasses {
       jobs[key].push_back(j.d);
       int &w = prog_words[key];
       w = std::max(w, j.prog_words);
+      nwarps[key] = j.nwarps;
     }
     return ZX_OK;
   }
@@ -74,7 +76,7 @@ void to_launches(const MergedPasses &m, DescImage *img, std::vector<Launch> *out
     Launch L;
     L.ls = std::get<1>(kv.first);
     L.lc = std::get<2>(kv.first);
-    L.nwarps = warps_for_job(L.ls, L.lc);
+    L.nwarps = m.nwarps.at(kv.first);
     L.njobs = int(kv.second.size());
     L.prog_words = m.prog_words.at(kv.first);
     size_t off = img->add(kv.second.data(), kv.second.size() * sizeof(JobDesc));

@@ -87,3 +87,22 @@ def test_rejects_bad_arguments_without_a_device(lib):
     assert lib.itft_ex(C.c_void_p(8), 2, 1, 3, 0, 64, 0, 2, 0, None) == 1
     assert lib.tft_ex(C.c_void_p(8), 2, 1, 1, 1088, 0, 18, None) == 6
     assert b"1024" in lib.zx_last_error()
+
+
+def test_launch_configuration_get_set_without_a_device():
+    import paper_0810_3203_gb300 as tg
+    N = 32768
+    default = tg.config_get(N)
+    assert default["max_warps"] in (8, 16) and default["split"] in (0, 1)
+    shape = tg.transform_plan(0, 16, 40000, 40000, N)
+    try:
+        tg.config_set(N, {"ls_max": 4, "ls_c": 3, "max_warps": 8, "split": 1})
+        assert tg.config_get(N)["ls_c"] == 3
+        assert tg.transform_plan(0, 16, 40000, 40000, N)["passes"] > shape["passes"]
+        with pytest.raises(tg.TftError) as ei:
+            tg.config_set(N, {"ls_max": 9, "ls_c": 3, "max_warps": 8, "split": 0})  # 512 cells of 4 KB
+        assert ei.value.code == tg.ZX_EINVAL
+    finally:
+        tg.config_set(N)
+    assert tg.config_get(N) == default
+    assert tg.transform_plan(0, 16, 40000, 40000, N) == shape

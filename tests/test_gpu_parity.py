@@ -110,6 +110,31 @@ def test_itft_parity(tg, orc, N, l):
         assert bad.size == 0, f"N={N} l={l} z={z} n={n} f={f} e={e}: {bad.size} cells differ, first {bad[:5]}"
 
 
+@pytest.mark.parametrize("N,l", [(128, 5), (1024, 8), (4096, 10), (8192, 7), (32768, 7), (32768, 12)])
+def test_structured_inputs(tg, orc, N, l):
+    """Inputs with long runs of equal bits (0, 2^N, 2^N - 1, runs of ones, small packed-like
+    values): carries and borrows cross many words and lanes, and some results are the zero cell."""
+    L = 1 << l
+    W = limbs(N)
+    rng = random.Random(N + l)
+    for t in range(3):
+        z = [L, rng.randint(1, L), max(1, L // 2 + 1)][t]
+        n = [L, rng.randint(1, z), rng.randint(1, L)][t]
+        e = [0, rng.randrange(2 * N), 1][t]
+        x = workloads.structured_residues(7000 + 10 * t + l, z, N, cells=L)
+        ref = x.copy()
+        orc.tft(ref, l, z, n, e, N)
+        got = gpu_tft(tg, x, l, z, n, e, N, W)
+        bad = cells_eq(got, ref, n, W, W)
+        assert bad.size == 0, f"TFT N={N} l={l} z={z} n={n} e={e}: {bad.size} cells differ, first {bad[:5]}"
+        nn = min(n, z)
+        ref = x.copy()
+        orc.itft(ref, l, z, nn, 0, e, N)
+        got = gpu_itft(tg, x, l, z, nn, 0, e, N, W)
+        bad = cells_eq(got, ref, nn, W, W)
+        assert bad.size == 0, f"ITFT N={N} l={l} z={z} n={nn} e={e}: {bad.size} cells differ, first {bad[:5]}"
+
+
 def test_exhaustive_small(tg, orc):
     """Every (z, n) and (z, n, f) for L = 16 over Z/(2^64+1)."""
     N, l = 64, 4

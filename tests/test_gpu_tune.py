@@ -1,0 +1,95 @@
+"""GPU parity under every launch configuration, and the autotuner (zx_tune).
+
+Any split and any job size give the same outputs (Sec. 2 decomposition), so the transforms
+must match the oracle word for word whatever configuration a ring runs with; the tuner must
+leave its buffer restored and the fastest configuration in place.
+"""
+import random
+
+import numpy as np
+import pytest
+
+import workloads
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def tg():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_0810_3203_gb300 as m
+    m.load()
+    return m
+
+
+def cells(a, count, W):
+    return a[:count * W].reshape(count, W)
+
+
+def configs(N):
+    out = []
+    for ls_max in (4, 5, 6, 8):
+        for ls_c in (3, 4, 5):
+            for mw in (8, 16):
+                for sp in (0, 1):
+                    out.append({"ls_max": ls_max, "ls_c": ls_c, "max_warps": mw, "split": sp})
+    return out
+
+
+@pytest.mark.parametrize("N,l", [(1024, 11), (4096, 11), (32768, 9)])
+def test_parity_under_every_configuration(tg, orc, N, l):
+    L, W = 1 << l, N // 64 + 1
+    rng = random.Random(N + l)
+    tried = 0
+    try:
+        for cfg in configs(N):
+            try:
+                tg.config_set(N, cfg)
+            except tg.TftError:
+                continue  # does not fit this ring
+            tried += 1
+            z, n = rng.randint(L // 2, L), rng.randint(1, L)
+            e = rng.randrange(2 * N)
+            x = workloads.residues(100 + tried, z, N, cells=L)
+            ref = x.copy()
+            orc.tft(ref, l, z, n, e, N)
+            d = torch.from_numpy(x.view(np.int64)).cuda()
+            tg.tft_ex(d, l, z, n, N, e)
+            got = d.cpu().numpy().view(np.uint64)
+            assert np.array_equal(cells(got, n, W), cells(ref, n, W)), (cfg, z, n, e)
+            nn = min(n, z)
+            ref = x.copy()
+            orc.itft(ref, l, z, nn, 1 if nn < z else 0, e, N)
+            d = torch.from_numpy(x.view(np.int64)).cuda()
+            f = 1 if nn < z else 0
+            tg.itft_ex(d, l, z, nn, f, N, e)
+            got = d.cpu().numpy().view(np.uint64)
+            assert np.array_equal(cells(got, nn + f, W), cells(ref, nn + f, W)), (cfg, z, nn, f, e)
+    finally:
+        tg.config_set(N)
+    assert tried >= 8
+
+
+def test_tune_restores_buffer_and_keeps_fastest(tg, orc):
+    N, l, n = 4096, 12, 3000
+    W = N // 64 + 1
+    x = workloads.residues(77, n, N, cells=1 << l)
+    d = torch.from_numpy(x.view(np.int64)).cuda()
+    try:
+        info = tg.tune(d, l, n, N, reps=1)
+        torch.cuda.synchronize()
+        back = d.cpu().numpy().view(np.uint64)
+        assert np.array_equal(cells(back, n, W), cells(x, n, W))
+        assert info["candidates"] >= 4 and info["best_ms"] > 0
+        assert tg.config_get(N) == {k: info[k] for k in ("ls_max", "ls_c", "max_warps", "split")}
+        # the tuned configuration computes the same transform as the oracle
+        ref = x.copy()
+        orc.tft(ref, l, n, n, 0, N)
+        tg.tft(d, l, n, N)
+        got = d.cpu().numpy().view(np.uint64)
+        assert np.array_equal(cells(got, n, W), cells(ref, n, W))
+    finally:
+        tg.config_set(N)

@@ -58,6 +58,46 @@ def residues(seed, count, N, stride=None, cells=None, offset=0):
     return x.reshape(-1)
 
 
+def structured_residues(seed, count, N, stride=None, cells=None):
+    """`count` residues in [0, 2^N] drawn from shapes with long runs of equal bits, which make
+    carries and borrows travel far: 0, 1, 2^N, 2^N - 1, powers of two, 2^N - 2^k, runs of ones
+    (2^a - 1) 2^b, small values (below 2^64 or 2^1024, like packed coefficients) and uniform
+    values. Same cell layout as residues()."""
+    W = limbs_for(N)
+    stride = stride or W
+    cells = cells if cells is not None else count
+    x = np.zeros((cells, stride), dtype=np.uint64)
+    words = splitmix64(seed, 4 * count).tolist()
+    for i in range(count):
+        kind, a, b, c = (int(v) for v in words[4 * i:4 * i + 4])
+        kind %= 10
+        if kind == 0:
+            v = 0
+        elif kind == 1:
+            v = 1
+        elif kind == 2:
+            v = 1 << N
+        elif kind == 3:
+            v = (1 << N) - 1
+        elif kind == 4:
+            v = 1 << (a % N)
+        elif kind == 5:
+            v = (1 << N) - (1 << (a % N))
+        elif kind == 6:
+            lo, hi = sorted((a % N, b % N))
+            v = ((1 << (hi - lo + 1)) - 1) << lo
+            v = min(v, (1 << N) - 1)
+        elif kind == 7:
+            v = c
+        elif kind == 8:
+            v = int.from_bytes(np.asarray(splitmix64(c, 16), dtype=np.uint64).tobytes(), "little") % (1 << min(N, 1024))
+        else:
+            v = int.from_bytes(np.asarray(splitmix64(c, W - 1), dtype=np.uint64).tobytes(), "little")
+        for t in range(W):
+            x[i, t] = np.uint64((v >> (64 * t)) & 0xFFFFFFFFFFFFFFFF)
+    return x.reshape(-1)
+
+
 def coefficients(seed, length, bits, limbs, signed=False, offset=0):
     """`length` coefficients uniform in [0, 2^bits) (signed: |c| < 2^bits, random sign),
     stored in `limbs` little-endian uint64 limbs, two's complement when signed."""
