@@ -300,6 +300,11 @@ def run_gpu(args):
     dev = {n: torch.from_numpy(host[n].view(np.int64)).to(device) for n in ns}
     torch.cuda.synchronize(device)
 
+    # launch configuration of the ring: the autotuner's pick, on one of the sweep's buffers (the
+    # round trips restore it), outside every timed region
+    tuned = None if args.no_tune else tg.tune(dev[40000 if 40000 in dev else ns[0]], l, 40000 if 40000 in dev else ns[0],
+                                              N, stride, reps=2, stream=stream)
+
     def mk():
         return torch.cuda.Event(enable_timing=True)
 
@@ -397,9 +402,9 @@ def run_gpu(args):
                           "passes_exact": tg.transform_plan(1, l, n, n, N)["passes"],
                           "passes_padded": tg.transform_plan(1, l, n_pad, n_pad, N)["passes"]}
 
-    batch = None if args.no_batch else batch_leg(tg, device, stream, 2, 3)
+    batch = None if args.no_batch else batch_leg(tg, device, stream, 2, 3, not args.no_tune)
     ok &= batch is None or batch["bit_exact_vs_plain"]
-    serve = None if args.no_serve else serve_leg(tg, device, stream, args.serve_requests)
+    serve = None if args.no_serve else serve_leg(tg, device, stream, args.serve_requests, not args.no_tune)
     ok &= serve is None or serve["bit_exact_vs_plain"]
 
     if rank != 0:
@@ -417,7 +422,9 @@ def run_gpu(args):
                    "parallelism": f"replicas x{ws}"},
         "roofline": {"bound": "hbm", "achieved": round(achieved, 2), "peak": peak, "unit": "GB/s",
                      "frac": round(achieved / peak, 4), "peak_kind": f"{peak_kind} hbm_gbs (burst copy)",
-                     "traffic": traffic.get("dram_bytes_per_launch") if traffic else None,
+                     "traffic": traffic.get("dram_bytes_per_tft") if traffic else None,
+                     "traffic_unit": "DRAM bytes of one TFT call at n = 40000 (ncu), against "
+                                     f"{traffic.get('alg_bytes_per_tft') if traffic else None} algorithmic",
                      "kernel": "job_kernel<32> (every launch of the TFT and ITFT calls)"},
         "per_n_ms": {str(n): [round(a / args.steps, 3), round(b / args.steps, 3)] for n, (a, b) in per_n.items()},
         "smoothness": {str(n): round((per_n[n][0] + per_n[n][1]) / (per_n[ns[-1]][0] + per_n[ns[-1]][1]), 4)
@@ -429,6 +436,8 @@ def run_gpu(args):
         "wall_s": round(wall, 3),
     }
     line["zero_padded_itft"] = padded
+    if tuned is not None:
+        line["tuned_config"] = tuned
     if batch is not None:
         line["batch"] = batch
     if serve is not None:
@@ -439,7 +448,37 @@ def run_gpu(args):
     return 0 if ok else 1
 
 
-def batch_leg(tg, device, stream, steps, warmup):
+def tune_rings(tg, device, stream, shapes, enabled, top=4):
+    """Run the autotuner for the rings that carry most of the work of these products (the
+    heaviest `top` by estimated cells x ring size), each on a scratch buffer of random residues
+    at the largest transform length and median product length seen for it."""
+    import numpy as np
+    import torch
+
+    if not enabled:
+        return None
+    rings = {}
+    for lf, bf, lg, bg in shapes:
+        p = tg.zx_plan(lf, bf, lg, bg)
+        r = rings.setdefault(p["N"], {"l": 0, "n": [], "work": 0})
+        r["l"] = max(r["l"], p["l"])
+        r["n"].append(p["n_fft"])
+        r["work"] += p["n_fft"] * p["N"]
+    out = {}
+    for N, r in sorted(rings.items(), key=lambda kv: -kv[1]["work"])[:top]:
+        l, n = r["l"], sorted(r["n"])[len(r["n"]) // 2]
+        n = min(n, 1 << l)
+        W = N // 64 + 1
+        stride = W + (W & 1)
+        x = torch.from_numpy(workloads.residues(11, n, N, stride=stride, cells=1 << l).view(np.int64)).to(device)
+        info = tg.tune(x, l, n, N, stride, reps=1, stream=stream)
+        out[str(N)] = {k: info[k] for k in ("ls_max", "ls_c", "max_warps", "split", "best_ms", "default_ms")}
+        del x
+    torch.cuda.synchronize(device)
+    return out
+
+
+def batch_leg(tg, device, stream, steps, warmup, tune=True):
     """The 512 mixed products (lengths uniform in [200, 20000], coefficient bits uniform in
     [64, 1024]) with operands resident on the device: one zx_mul_batch call per step against
     the same products as 512 zx_mul calls, results compared word for word."""
@@ -460,6 +499,7 @@ def batch_leg(tg, device, stream, steps, warmup):
         items.append((F, lf, m, G, lg, m, H, mh, False, bits, bits))
         outs_plain.append(torch.zeros_like(H))
     torch.cuda.synchronize(device)
+    tuned = tune_rings(tg, device, stream, [(lf, bits, lg, bits) for lf, lg, bits in shapes], tune)
 
     def batched():
         tg.zx_mul_batch(items, stream=stream)
@@ -488,10 +528,10 @@ def batch_leg(tg, device, stream, steps, warmup):
                         "unsigned, seed 4; each product in its own ring",
             "products_per_s": round(count / tb, 2), "plain_products_per_s": round(count / tp, 2),
             "ms_per_batch": round(tb * 1e3, 3), "ms_plain": round(tp * 1e3, 3),
-            "speedup_vs_plain": round(tp / tb, 3), "bit_exact_vs_plain": bool(same)}
+            "speedup_vs_plain": round(tp / tb, 3), "bit_exact_vs_plain": bool(same), "tuned": tuned}
 
 
-def serve_leg(tg, device, stream, count):
+def serve_leg(tg, device, stream, count, tune=True):
     """Poisson arrivals (mean 2000 requests/s) of products with lengths log-uniform in
     [2^8, 2^15] and coefficient bits log-uniform in [64, 4096], operands resident on the
     device. The serving loop (continuous batching) against the plain path, where each request
@@ -514,6 +554,7 @@ def serve_leg(tg, device, stream, count):
         plain_out.append(torch.zeros_like(H))
     torch.cuda.synchronize(device)
     arrivals = [t for t, _, _, _ in reqs]
+    tuned = tune_rings(tg, device, stream, [(lf, bits, lg, bits) for _, lf, lg, bits in reqs], tune)
 
     def pct(v, q):
         v = sorted(v)
@@ -558,7 +599,8 @@ def serve_leg(tg, device, stream, count):
             "plain_p50_ms": round(pct(plain_lat, 0.5) * 1e3, 3), "plain_p99_ms": round(pct(plain_lat, 0.99) * 1e3, 3),
             "offered_per_s": round(count / arrivals[-1], 1), "waves": stats["waves"],
             "max_wave_products": stats["max_wave_products"], "max_waves_in_flight": stats["max_waves_in_flight"],
-            "arena_peak_gb": round(stats["arena_peak_bytes"] / 1e9, 3), "bit_exact_vs_plain": bool(same)}
+            "arena_peak_gb": round(stats["arena_peak_bytes"] / 1e9, 3), "bit_exact_vs_plain": bool(same),
+            "tuned": tuned}
 
 
 def run_batch(args):
@@ -569,7 +611,7 @@ def run_batch(args):
     device = torch.device("cuda", 0)
     torch.cuda.set_device(device)
     tg.load()
-    res = batch_leg(tg, device, torch.cuda.current_stream(device), args.steps, args.warmup)
+    res = batch_leg(tg, device, torch.cuda.current_stream(device), args.steps, args.warmup, not args.no_tune)
     print(json.dumps(res), flush=True)
     return 0 if res["bit_exact_vs_plain"] else 1
 
@@ -582,7 +624,7 @@ def run_serve(args):
     device = torch.device("cuda", 0)
     torch.cuda.set_device(device)
     tg.load()
-    res = serve_leg(tg, device, torch.cuda.current_stream(device), args.serve_requests)
+    res = serve_leg(tg, device, torch.cuda.current_stream(device), args.serve_requests, not args.no_tune)
     print(json.dumps(res), flush=True)
     return 0 if res["bit_exact_vs_plain"] else 1
 
@@ -596,6 +638,9 @@ def run_profile_case(args):
 
     tg.load()
     N, l, n = WORKLOAD["N"], WORKLOAD["l"], 40000
+    if args.config:
+        ls_max, ls_c, mw, sp = (int(v) for v in args.config.split(","))
+        tg.config_set(N, {"ls_max": ls_max, "ls_c": ls_c, "max_warps": mw, "split": sp})
     W = N // 64 + 1
     stride = W + (W & 1)
     x = workloads.residues(WORKLOAD["seed"], n, N, stride=stride, cells=1 << l)
@@ -620,7 +665,10 @@ def main():
     ap.add_argument("--profile-case", action="store_true",
                     help="run one TFT + ITFT at n = 40000 and exit (the case profiled with ncu)")
     ap.add_argument("--profile-reps", type=int, default=1)
+    ap.add_argument("--config", default="",
+                    help="ls_max,ls_c,max_warps,split: launch configuration for --profile-case")
     ap.add_argument("--no-batch", action="store_true", help="skip the 512-product batch leg")
+    ap.add_argument("--no-tune", action="store_true", help="keep the default launch configurations")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving leg")
     ap.add_argument("--serve-requests", type=int, default=1000)
     ap.add_argument("--serve-only", action="store_true", help="time only the serving leg")

@@ -334,6 +334,7 @@ int zx_tune(uint64_t *x, int l, int64_t n, int64_t N, int64_t stride_limbs, int 
   int ls3 = 1;
   while (ls3 < 16 && (size_t(2) << ls3) * (size_t(r.pitch) + 1) * 4 <= size_t(72) * 1024) ls3++;
   std::vector<PlanConfig> cands;
+  cands.push_back(def);
   for (int ls_max : {def.ls_max, ls3})
     for (int ls_c = 3; ls_c <= 6; ls_c++)
       for (int mw : {8, 16})

@@ -90,6 +90,17 @@ struct JobDesc {
 };
 static_assert(sizeof(JobDesc) == 48, "JobDesc layout");
 
+// One segment of a merged launch: the jobs of one cached plan launch, applied to a buffer that
+// starts `cell_off` cells after the launch's base pointer. Segment s covers the CTAs
+// [first_cta, first_cta + (njobs << lc)) of the launch.
+struct Segment {
+  const JobDesc *jobs;
+  int64_t cell_off;
+  int32_t njobs;
+  int32_t first_cta;
+};
+static_assert(sizeof(Segment) == 24, "Segment layout");
+
 // shared-memory geometry of one cell: NW = N/32 words, one padding word per 32 so that the
 // lane-chunked accesses of a warp hit 32 different banks, rounded up to 16 bytes so that every
 // cell can be copied as a block of 16-byte vectors

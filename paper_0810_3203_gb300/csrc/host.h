@@ -67,12 +67,15 @@ constexpr int kMaxClusterLog2 = 4;
 
 // One kernel launch: jobs of equal ls.
 struct Launch {
+  int pass = 0;  // global-memory pass of the plan this launch belongs to
   int ls = 0;
   int lc = 0;  // cluster of 2^lc CTAs per job
   int nwarps = 0;
-  int njobs = 0;
+  int njobs = 0;       // jobs of the launch (all segments together when d_segs is set)
   int prog_words = 0;  // largest per-CTA program of the launch (shared-memory staging size)
-  JobDesc *d_jobs = nullptr;  // device copy (owned by the plan cache)
+  JobDesc *d_jobs = nullptr;         // device copy (owned by the plan cache)
+  const Segment *d_segs = nullptr;   // merged launch: segments in device memory (d_jobs unused)
+  int nsegs = 0;
 };
 
 struct TransformPlan {
@@ -115,17 +118,6 @@ struct HostPlan {
 };
 void build_host_plan(int kind, int l, int64_t z, int64_t n, int f, int64_t N, int64_t e, int scale,
                      HostPlan *out);
-
-// One job of a plan with its pass index and launch shape; `d.image` is a device pointer into
-// the shared image cache.
-struct PlannedJob {
-  int pass = 0, ls = 0, lc = 0, prog_words = 0, nwarps = 0;
-  JobDesc d;
-};
-// Jobs of a TFT / ITFT plan (host side, images resolved on the current device). Returns the
-// number of passes, or -1 with *err set.
-int plan_jobs(int kind, int l, int64_t z, int64_t n, int f, int64_t N, int64_t e, int scale,
-              std::vector<PlannedJob> *out, int *err);
 
 // Enqueue a plan on a stream.
 cudaError_t run_transform(const TransformPlan &p, uint64_t *x, int64_t stride_limbs,
@@ -187,7 +179,7 @@ struct BatchGroup {
   int count = 0;
   int64_t max_len = 0, max_n = 0;
   size_t pack_off = 0, pw_off = 0, lift_off = 0;
-  std::vector<Launch> tft, itft;  // d_jobs hold descriptor-image byte offsets
+  std::vector<Launch> tft, itft;  // merged launches; d_segs hold descriptor-image byte offsets
 };
 struct BatchLayout {
   size_t pool_bytes = 0;

@@ -53,11 +53,15 @@ int cluster_cta_ls(const Ring &r) {
   return ls;
 }
 
+// Default: the largest single-CTA job the shared memory allows, eight cells per CTA of a cluster
+// job and at most eight warps per CTA, the paper's split. Measured on GB300 (zx_tune): small
+// clusters and CTAs that three or more share an SM beat fewer, larger jobs with fewer passes,
+// because a job's time is set by the latency of its dependency levels.
 PlanConfig default_config(const Ring &r) {
   PlanConfig c;
   c.ls_max = max_onchip_ls(r);
-  c.ls_c = cluster_cta_ls(r);
-  c.max_warps = 16;
+  c.ls_c = std::min(3, cluster_cta_ls(r));
+  c.max_warps = 8;
   c.split = 0;
   return c;
 }
@@ -277,22 +281,30 @@ int64_t zero_padded_outputs(int l, int64_t n, int64_t N) {
   Planner P(N);
   const int64_t L = int64_t(1) << l;
   auto up = [](int64_t v, int64_t m) { return (v + m - 1) / m * m; };
-  if (!P.leaf(l)) {
-    // whole rows of the top-level split over global memory
-    const int l1 = P.top_l1(l), l2 = l - l1;
-    const int64_t n_rows = up(n, int64_t(1) << l2);
-    // when the column sub-transforms are cluster jobs, whole in-job rows of those as well (their
-    // partial in-job row is a serial step on one CTA), if that adds at most 1/32 of n
-    const int lc1 = P.cluster_log2(l1);
-    if (lc1 > 0 && P.leaf(l1)) {
-      const int64_t n_full = up(n, int64_t(1) << (l2 + l1 - lc1));
-      if (n_full <= L && (n_full - n) * 32 <= n) return n_full;
+  // Granularities that make the rows of one more recursion level whole: the top split's rows
+  // (L2), then the rows of the column sub-transforms' own split (their n is n / L2), and so on
+  // down to the jobs (a cluster job's in-job rows; a single CTA needs nothing).
+  std::vector<int64_t> grains;
+  int64_t g = 1;
+  for (int ll = l;;) {
+    if (P.leaf(ll)) {
+      const int lc = P.cluster_log2(ll);
+      if (lc > 0) grains.push_back(g << (ll - lc));
+      break;
     }
-    return std::min(L, n_rows);
+    const int l1 = P.top_l1(ll);
+    g <<= (ll - l1);
+    grains.push_back(g);
+    ll = l1;
   }
-  const int lc = P.cluster_log2(l);
-  if (lc > 0) return std::min(L, up(n, int64_t(1) << (l - lc)));  // whole rows of the job's split
-  return n;  // one CTA holds the whole transform: a partial row costs no extra pass
+  if (grains.empty()) return n;
+  // the top level's whole rows always (they remove a pass); finer ones while they add at most n/32
+  int64_t best = std::min(L, up(n, grains[0]));
+  for (size_t k = 1; k < grains.size(); k++) {
+    const int64_t c = up(n, grains[k]);
+    if (c <= L && (c - n) * 32 <= n) best = c;
+  }
+  return best;
 }
 
 int count_passes(int kind, int l, int64_t z, int64_t n, int f, int64_t N) {
@@ -356,30 +368,6 @@ void build_host_plan(int kind, int l, int64_t z, int64_t n, int f, int64_t N, in
   }
 }
 
-int plan_jobs(int kind, int l, int64_t z, int64_t n, int f, int64_t N, int64_t e, int scale,
-              std::vector<PlannedJob> *out, int *err) {
-  int64_t twoN = 2 * N;
-  e = md(e, twoN);
-  Planner P(N);
-  int npass = kind == KIND_TFT ? P.tft(0, 0, 1, l, e, z, n)
-                               : P.itft(0, 0, 1, l, e, z, n, f, scale ? md(twoN - l, twoN) : -1);
-  out->clear();
-  out->reserve(P.jobs.size());
-  for (JobRec &j : P.jobs) {
-    j.d.image = image_cache().get(j.kind, j.ls, j.lc, j.z, j.n, j.f, N, err);
-    if (!j.d.image) return -1;
-    PlannedJob pj;
-    pj.pass = j.pass;
-    pj.ls = j.ls;
-    pj.lc = j.lc;
-    pj.prog_words = image_cache().max_prog(j.d.image);
-    pj.nwarps = warps_for_job(j.ls, j.lc, P.cfg.max_warps);
-    pj.d = j.d;
-    out->push_back(pj);
-  }
-  return npass;
-}
-
 const TransformPlan *get_transform_plan(int kind, int l, int64_t z, int64_t n, int f, int64_t N,
                                         int64_t e, int64_t stride_limbs, int scale, int *err) {
   int dev = 0;
@@ -418,6 +406,7 @@ const TransformPlan *get_transform_plan(int kind, int l, int64_t z, int64_t n, i
     size_t k = i;
     while (k < P.jobs.size() && same_launch(P.jobs[k], P.jobs[i])) k++;
     Launch L;
+    L.pass = P.jobs[i].pass;
     L.ls = P.jobs[i].ls;
     L.lc = P.jobs[i].lc;
     L.njobs = int(k - i);

@@ -284,11 +284,27 @@ __device__ __forceinline__ void exchange(uint32_t *cells, uint32_t *meta, int P,
 template <int K, int MINB, bool FULL>
 __global__ void __launch_bounds__(MINB == 3 ? 256 : 512, MINB) job_kernel(uint64_t *__restrict__ x, int64_t stride_limbs,
                                                   const JobDesc *__restrict__ jobs, int N, int ls, int lc,
-                                                  uint32_t mask, int prog_cap) {
+                                                  uint32_t mask, int prog_cap,
+                                                  const Segment *__restrict__ segs, int nsegs) {
   extern __shared__ uint32_t smem[];
   const int C = 1 << lc;
   const int rank = int(blockIdx.x) & (C - 1);
-  const JobDesc jd = jobs[blockIdx.x >> lc];
+  JobDesc jd;
+  if (nsegs == 0) {
+    jd = jobs[blockIdx.x >> lc];
+  } else {
+    // merged launch: the last segment that starts at or before this CTA (segments hold whole
+    // clusters, so the CTAs of one cluster agree)
+    int lo = 0, hi = nsegs - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (segs[mid].first_cta <= int(blockIdx.x)) lo = mid;
+      else hi = mid - 1;
+    }
+    const Segment sg = segs[lo];
+    jd = sg.jobs[(int(blockIdx.x) - sg.first_cta) >> lc];
+    jd.cell0 += sg.cell_off;
+  }
   KGeo kg;
   kg.g.N = N;
   kg.g.NW = N / 32;
@@ -401,7 +417,7 @@ cudaError_t launch_km(const Launch &L, uint64_t *x, int64_t stride_limbs, const 
   cfg.attrs = attr;
   cfg.numAttrs = L.lc > 0 ? 1 : 0;
   return cudaLaunchKernelEx(&cfg, job_kernel<K, MINB, FULL>, x, stride_limbs, (const JobDesc *)L.d_jobs, int(r.N), L.ls,
-                            L.lc, mask, prog_cap);
+                            L.lc, mask, prog_cap, L.d_segs, L.nsegs);
 }
 
 template <int K>

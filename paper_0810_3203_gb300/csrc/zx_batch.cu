@@ -50,44 +50,51 @@ struct DescImage {
   }
 };
 
-// Jobs of many transforms over one ring buffer pool, merged by (pass, ls, lc).
-struct MergedPasses {
-  std::map<std::tuple<int, int, int>, std::vector<JobDesc>> jobs;
-  std::map<std::tuple<int, int, int>, int> prog_words;
-  std::map<std::tuple<int, int, int>, int> nwarps;
-  int add(int kind, int l, int64_t z, int64_t n, int64_t N, int64_t cell_off, int scale) {
-    std::vector<PlannedJob> pj;
+// Launches of many transforms over one ring buffer pool, merged by (pass, ls, lc): each
+// product's transform uses its cached plan (job lists stay in device memory), and a merged
+// launch is a table of segments, one per product launch, with the product's cell offset.
+struct MergedSegs {
+  struct Acc {
+    std::vector<Segment> segs;
+    int nwarps = 0, prog_words = 0, ctas = 0, njobs = 0;
+  };
+  std::map<std::tuple<int, int, int>, Acc> m;
+  int add(int kind, int l, int64_t z, int64_t n, int64_t N, int64_t stride, int64_t cell_off, int scale) {
     int err = ZX_OK;
-    if (plan_jobs(kind, l, z, n, 0, N, 0, scale, &pj, &err) < 0) return err ? err : ZX_ECUDA;
-    for (PlannedJob &j : pj) {
-      auto key = std::make_tuple(j.pass, j.ls, j.lc);
-      j.d.cell0 += cell_off;
-      jobs[key].push_back(j.d);
-      int &w = prog_words[key];
-      w = std::max(w, j.prog_words);
-      nwarps[key] = j.nwarps;
+    const TransformPlan *p = get_transform_plan(kind, l, z, n, 0, N, 0, stride, scale, &err);
+    if (!p) return err ? err : ZX_ECUDA;
+    for (const Launch &L : p->launches) {
+      Acc &a = m[std::make_tuple(L.pass, L.ls, L.lc)];
+      a.segs.push_back(Segment{L.d_jobs, cell_off, int32_t(L.njobs), int32_t(a.ctas)});
+      a.ctas += L.njobs << L.lc;
+      a.njobs += L.njobs;
+      a.nwarps = L.nwarps;
+      a.prog_words = std::max(a.prog_words, L.prog_words);
     }
     return ZX_OK;
   }
 };
 
-void to_launches(const MergedPasses &m, DescImage *img, std::vector<Launch> *out) {
-  for (const auto &kv : m.jobs) {
+void to_launches(const MergedSegs &m, DescImage *img, std::vector<Launch> *out) {
+  for (const auto &kv : m.m) {
+    const MergedSegs::Acc &a = kv.second;
     Launch L;
+    L.pass = std::get<0>(kv.first);
     L.ls = std::get<1>(kv.first);
     L.lc = std::get<2>(kv.first);
-    L.nwarps = m.nwarps.at(kv.first);
-    L.njobs = int(kv.second.size());
-    L.prog_words = m.prog_words.at(kv.first);
-    size_t off = img->add(kv.second.data(), kv.second.size() * sizeof(JobDesc));
-    L.d_jobs = reinterpret_cast<JobDesc *>(off);
+    L.nwarps = a.nwarps;
+    L.njobs = a.njobs;
+    L.prog_words = a.prog_words;
+    L.d_jobs = nullptr;
+    L.nsegs = int(a.segs.size());
+    L.d_segs = reinterpret_cast<const Segment *>(img->add(a.segs.data(), a.segs.size() * sizeof(Segment)));
     out->push_back(L);
   }
 }
 
 template <class T>
-T *rebase(T *off, unsigned char *base) {
-  return reinterpret_cast<T *>(base + reinterpret_cast<size_t>(off));
+const T *rebase(const T *off, unsigned char *base) {
+  return reinterpret_cast<const T *>(base + reinterpret_cast<size_t>(off));
 }
 
 }  // namespace
@@ -118,7 +125,7 @@ int layout_batch(const std::vector<BatchProduct> &items, const std::vector<int> 
     std::vector<PackItem> pk;
     std::vector<PointwiseItem> pw;
     std::vector<LiftItem> lf;
-    MergedPasses mt, mi;
+    MergedSegs mt, mi;
     const size_t cell_bytes = size_t(gd.stride) * 8;
     cell_off = int64_t((byte_off + cell_bytes - 1) / cell_bytes);  // first whole cell after the last group
     for (size_t t = a; t < b; t++) {
@@ -134,9 +141,9 @@ int layout_batch(const std::vector<BatchProduct> &items, const std::vector<int> 
       gd.max_len = std::max(gd.max_len, std::max(p.len_f, p.len_g));
       gd.max_n = std::max(gd.max_n, p.nf);
       int rc;
-      if ((rc = mt.add(KIND_TFT, p.l, p.len_f, p.nf, p.N, cf, 0)) ||
-          (rc = mt.add(KIND_TFT, p.l, p.len_g, p.nf, p.N, cg, 0)) ||
-          (rc = mi.add(KIND_ITFT, p.l, p.nf, p.nf, p.N, cf, 1))) {
+      if ((rc = mt.add(KIND_TFT, p.l, p.len_f, p.nf, p.N, p.stride, cf, 0)) ||
+          (rc = mt.add(KIND_TFT, p.l, p.len_g, p.nf, p.N, p.stride, cg, 0)) ||
+          (rc = mi.add(KIND_ITFT, p.l, p.nf, p.nf, p.N, p.stride, cf, 1))) {
         *msg = "planning failed for product " + std::to_string(idx[t]);
         img.bytes.swap(*desc);
         return rc;
@@ -161,11 +168,11 @@ cudaError_t enqueue_group(const BatchGroup &gd, unsigned char *d_desc, unsigned 
   TransformPlan tp, ip;
   tp.ring = ip.ring = gd.ring;
   for (Launch L : gd.tft) {
-    L.d_jobs = rebase(L.d_jobs, d_desc);
+    L.d_segs = rebase(L.d_segs, d_desc);
     tp.launches.push_back(L);
   }
   for (Launch L : gd.itft) {
-    L.d_jobs = rebase(L.d_jobs, d_desc);
+    L.d_segs = rebase(L.d_segs, d_desc);
     ip.launches.push_back(L);
   }
   const PackItem *pk = reinterpret_cast<const PackItem *>(d_desc + gd.pack_off);

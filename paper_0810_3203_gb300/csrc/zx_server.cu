@@ -263,13 +263,14 @@ void worker_main(zx_server *S) {
 
 // upper bound on the descriptor bytes of one product inside a wave
 size_t desc_bound(const BatchProduct &p) {
-  int passes = 0, launches = 0, onchip = 0, cl = 0;
-  int64_t jt = 0, ji = 0;
-  plan_shape(KIND_TFT, p.l, std::max(p.len_f, p.len_g), p.nf, 0, p.N, &passes, &launches, &jt, &onchip, &cl);
-  plan_shape(KIND_ITFT, p.l, p.nf, p.nf, 0, p.N, &passes, &launches, &ji, &onchip, &cl);
-  // pack (2), pointwise and lift items, jobs of two TFTs and one ITFT, 16-byte alignment slack
-  return 2 * sizeof(PackItem) + sizeof(PointwiseItem) + sizeof(LiftItem) + size_t(2 * jt + ji) * sizeof(JobDesc) +
-         8 * 16;
+  int passes = 0, lt = 0, li = 0, onchip = 0, cl = 0;
+  int64_t jobs = 0;
+  plan_shape(KIND_TFT, p.l, std::max(p.len_f, p.len_g), p.nf, 0, p.N, &passes, &lt, &jobs, &onchip, &cl);
+  plan_shape(KIND_ITFT, p.l, p.nf, p.nf, 0, p.N, &passes, &li, &jobs, &onchip, &cl);
+  // pack (2), pointwise and lift items, one segment per launch of two TFTs and one ITFT, and
+  // 16-byte alignment slack (the job lists themselves stay in the plan cache)
+  return 2 * sizeof(PackItem) + sizeof(PointwiseItem) + sizeof(LiftItem) + size_t(2 * lt + li) * sizeof(Segment) +
+         16 * 16;
 }
 
 }  // namespace
