@@ -40,6 +40,13 @@ def lib():
         L.orc_itft.argtypes = [_u64p, i64, i32, i64, i64, i32, i64, i64, i32, i32, u64, _i64p]
         L.orc_tft_phases.argtypes = [_u64p, i64, i32, i32, i64, i64, i64, i64, i32]
         L.orc_itft_phases.argtypes = [_u64p, i64, i32, i32, i64, i64, i32, i64, i64, i32]
+        for name in ("orc_sn_add", "orc_sn_sub", "orc_sn_mul"):
+            getattr(L, name).argtypes = [_u64p, _u64p, _u64p, i64, u64]
+        L.orc_sn_ypow.argtypes = [_u64p, _u64p, i64, i64, u64]
+        L.orc_sn_half.argtypes = [_u64p, _u64p, i64, u64]
+        L.orc_sn_dft_brute.argtypes = [_u64p, _u64p, i64, i32, i64, i64, i64, i64, u64]
+        L.orc_sn_tft.argtypes = [_u64p, i64, i32, i64, i64, i64, i64, u64, i32, i32, u64, _i64p]
+        L.orc_sn_itft.argtypes = [_u64p, i64, i32, i64, i64, i32, i64, i64, u64, i32, i32, u64, _i64p]
         L.orc_zx_mul.argtypes = [C.POINTER(_Poly)] * 3 + [C.POINTER(i32), _i64p]
         L.orc_zx_plan.argtypes = [i64, i64, i64, i64, i32, C.POINTER(i32), _i64p]
         L.orc_zx_schoolbook.argtypes = [C.POINTER(_Poly)] * 3
@@ -208,3 +215,74 @@ def zx_schoolbook(f, len_f, limbs_f, g, len_g, limbs_g, limbs_h, signed=False):
 def poly_eval_mod(f, length, nlimbs, signed, t, P):
     F = _poly(f, length, nlimbs, signed)
     return int(lib().orc_poly_eval_mod(C.byref(F), t, P))
+
+
+# ---------------------------------------------------------------- S[y]/(y^{M/2}+1), S = Z/mZ
+def sn_cells(vals, M, count=None, stride=None):
+    """Elements given as lists of M/2 ints mod m -> uint64 cells (zero-filled to `count`)."""
+    H = M // 2
+    stride = stride or H
+    count = count if count is not None else len(vals)
+    x = np.zeros(count * stride, dtype=np.uint64)
+    for i, v in enumerate(vals):
+        x[i * stride:i * stride + H] = np.asarray(v, dtype=np.uint64)
+    return x
+
+
+def sn_vals(x, M, count, stride=None):
+    H = M // 2
+    stride = stride or H
+    return [[int(w) for w in x[i * stride:i * stride + H]] for i in range(count)]
+
+
+def _sn2(name, a, b, M, m):
+    r = np.zeros(M // 2, dtype=np.uint64)
+    _check(getattr(lib(), name)(_p(r), _p(np.asarray(a, dtype=np.uint64)), _p(np.asarray(b, dtype=np.uint64)), M, m), name)
+    return [int(w) for w in r]
+
+
+def sn_add(a, b, M, m):
+    return _sn2("orc_sn_add", a, b, M, m)
+
+
+def sn_sub(a, b, M, m):
+    return _sn2("orc_sn_sub", a, b, M, m)
+
+
+def sn_mul(a, b, M, m):
+    return _sn2("orc_sn_mul", a, b, M, m)
+
+
+def sn_ypow(a, k, M, m):
+    r = np.zeros(M // 2, dtype=np.uint64)
+    _check(lib().orc_sn_ypow(_p(r), _p(np.asarray(a, dtype=np.uint64)), k, M, m), "orc_sn_ypow")
+    return [int(w) for w in r]
+
+
+def sn_half(a, M, m):
+    r = np.zeros(M // 2, dtype=np.uint64)
+    _check(lib().orc_sn_half(_p(r), _p(np.asarray(a, dtype=np.uint64)), M, m), "orc_sn_half")
+    return [int(w) for w in r]
+
+
+def sn_dft_brute(x, l, z, n, e, M, m, stride=None):
+    stride = stride or M // 2
+    out = np.zeros_like(x)
+    _check(lib().orc_sn_dft_brute(_p(out), _p(x), stride, l, z, n, e, M, m), "orc_sn_dft_brute")
+    return out
+
+
+def sn_tft(x, l, z, n, e, M, m, stride=None, policy=SPLIT_BALANCED, top_l1=0, seed=0):
+    """In place: Algorithm 1 over S[y]/(y^{M/2}+1). Returns the base-case count."""
+    cnt = C.c_int64(0)
+    _check(lib().orc_sn_tft(_p(x), stride or M // 2, l, z, n, e, M, m, policy, top_l1, seed, C.byref(cnt)),
+           "orc_sn_tft")
+    return cnt.value
+
+
+def sn_itft(x, l, z, n, f, e, M, m, stride=None, policy=SPLIT_BALANCED, top_l1=0, seed=0):
+    """In place: Algorithm 2 over S[y]/(y^{M/2}+1): L a_0 .. L a_{n-1} (then a-hat_n if f)."""
+    cnt = C.c_int64(0)
+    _check(lib().orc_sn_itft(_p(x), stride or M // 2, l, z, n, f, e, M, m, policy, top_l1, seed, C.byref(cnt)),
+           "orc_sn_itft")
+    return cnt.value

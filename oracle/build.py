@@ -7,7 +7,7 @@ import os
 import subprocess
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-SOURCES = ["ring.c", "transforms.c", "zx.c"]
+SOURCES = ["ring.c", "transforms.c", "zx.c", "sn.c"]
 LIB = os.path.join(HERE, "_build", "liboracle.so")
 
 

@@ -105,6 +105,26 @@ int orc_zx_schoolbook(orc_poly *h, const orc_poly *f, const orc_poly *g);
 /* sum_i c_i t^i mod P for a 61-bit prime P (Schwartz-Zippel spot checks of big products). */
 uint64_t orc_poly_eval_mod(const orc_poly *f, uint64_t t, uint64_t P);
 
+/* ------------------------------------------------------------------ Schoenhage-Nussbaumer ring
+ * R = S[y]/(y^{M/2}+1), S = Z/mZ (Sec. 5.2): M a power of two >= 2, m odd with 3 <= m < 2^63.
+ * An element is M/2 coefficients in [0, m), stored as uint64; omega = y is a principal M-th
+ * root of unity, omega_L = y^{M/L} (L | M), and zeta = y^e. */
+int orc_sn_add(uint64_t *r, const uint64_t *a, const uint64_t *b, int64_t M, uint64_t m);
+int orc_sn_sub(uint64_t *r, const uint64_t *a, const uint64_t *b, int64_t M, uint64_t m);
+/* r = y^k a (negacyclic shift), k mod M; r may alias a */
+int orc_sn_ypow(uint64_t *r, const uint64_t *a, int64_t k, int64_t M, uint64_t m);
+int orc_sn_half(uint64_t *r, const uint64_t *a, int64_t M, uint64_t m);
+/* r = a b in R (negacyclic schoolbook product modulo m); test use only */
+int orc_sn_mul(uint64_t *r, const uint64_t *a, const uint64_t *b, int64_t M, uint64_t m);
+/* Eq. (dft), Algorithm 1 and Algorithm 2 over R, same conventions as the Z/(2^N+1) versions
+ * (cells of stride >= M/2 words). */
+int orc_sn_dft_brute(uint64_t *out, const uint64_t *in, int64_t stride, int l, int64_t z, int64_t n,
+                     int64_t e, int64_t M, uint64_t m);
+int orc_sn_tft(uint64_t *x, int64_t stride, int l, int64_t z, int64_t n, int64_t e, int64_t M, uint64_t m,
+               int policy, int top_l1, uint64_t seed, int64_t *count);
+int orc_sn_itft(uint64_t *x, int64_t stride, int l, int64_t z, int64_t n, int f, int64_t e, int64_t M,
+                uint64_t m, int policy, int top_l1, uint64_t seed, int64_t *count);
+
 #ifdef __cplusplus
 }
 #endif

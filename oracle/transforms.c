@@ -18,7 +18,9 @@
 #include <string.h>
 
 typedef struct {
-    int64_t N, W, twoN;
+    int kind;       /* 0: Z/(2^N+1) with omega = 2; 1: S[y]/(y^{M/2}+1), S = Z/mZ, omega = y */
+    uint64_t m;     /* kind 1: the modulus of S */
+    int64_t N, W, twoN; /* kind 1: N = M/2 coefficients, W = M/2 words, twoN = M */
     int policy;
     int top_l1;     /* ORC_SPLIT_TOP: l1 at the outermost level */
     int depth;      /* current recursion depth (0 = outermost) */
@@ -60,10 +62,27 @@ static int choose_l1(ctx_t *c, int l)
 
 /* ring helpers on cells */
 static void cp(ctx_t *c, uint64_t *d, const uint64_t *s) { memmove(d, s, (size_t)c->W * 8); }
-static void add(ctx_t *c, uint64_t *r, const uint64_t *a, const uint64_t *b) { orc_ring_add(r, a, b, c->N); }
-static void sub(ctx_t *c, uint64_t *r, const uint64_t *a, const uint64_t *b) { orc_ring_sub(r, a, b, c->N); }
-static void rot(ctx_t *c, uint64_t *r, const uint64_t *a, int64_t k) { orc_ring_mul2exp(r, a, emod(k, c->twoN), c->N); }
-static void half(ctx_t *c, uint64_t *r, const uint64_t *a) { orc_ring_div2(r, a, c->N); }
+static void add(ctx_t *c, uint64_t *r, const uint64_t *a, const uint64_t *b)
+{
+    if (c->kind) orc_sn_add(r, a, b, c->twoN, c->m);
+    else orc_ring_add(r, a, b, c->N);
+}
+static void sub(ctx_t *c, uint64_t *r, const uint64_t *a, const uint64_t *b)
+{
+    if (c->kind) orc_sn_sub(r, a, b, c->twoN, c->m);
+    else orc_ring_sub(r, a, b, c->N);
+}
+/* r = omega^k a: a rotation by k bits (kind 0) or a negacyclic shift by k places (kind 1) */
+static void rot(ctx_t *c, uint64_t *r, const uint64_t *a, int64_t k)
+{
+    if (c->kind) orc_sn_ypow(r, a, emod(k, c->twoN), c->twoN, c->m);
+    else orc_ring_mul2exp(r, a, emod(k, c->twoN), c->N);
+}
+static void half(ctx_t *c, uint64_t *r, const uint64_t *a)
+{
+    if (c->kind) orc_sn_half(r, a, c->twoN, c->m);
+    else orc_ring_div2(r, a, c->N);
+}
 
 static unsigned bitrev(uint64_t j, int l)
 {
@@ -72,27 +91,39 @@ static unsigned bitrev(uint64_t j, int l)
     return (unsigned)r;
 }
 
+/* Eq. (dft) term by term: zeta^{j'} omega_L^{i j'} = omega^{e j' + w i j'} with w = twoN / L */
+static void dft_brute(ctx_t *c, uint64_t *out, const uint64_t *in, int64_t stride, int l, int64_t z, int64_t n,
+                      int64_t e)
+{
+    int64_t L = (int64_t)1 << l, W = c->W, twoN = c->twoN;
+    int64_t w = twoN / L;
+    uint64_t *acc = calloc((size_t)W, 8), *term = calloc((size_t)W, 8);
+    for (int64_t j = 0; j < n; j++) {
+        int64_t jr = bitrev((uint64_t)j, l);
+        memset(acc, 0, (size_t)W * 8);
+        for (int64_t i = 0; i < z; i++) {
+            int64_t k = emod(emod(e, twoN) * jr + w * emod(i * jr, L), twoN);
+            rot(c, term, in + i * stride, k);
+            add(c, acc, acc, term);
+        }
+        memcpy(out + j * stride, acc, (size_t)W * 8);
+    }
+    free(acc);
+    free(term);
+}
+
 int orc_dft_brute(uint64_t *out, const uint64_t *in, int64_t stride, int l, int64_t z, int64_t n,
                   int64_t e, int64_t N)
 {
     if (!n_ok(N) || l < 1 || l > 30) return -1;
     int64_t L = (int64_t)1 << l, W = N / 64 + 1, twoN = 2 * N;
     if (twoN % L != 0 || z < 0 || z > L || n < 0 || n > L || stride < W) return -1;
-    int64_t w = twoN / L; /* omega_L = 2^w */
-    uint64_t *acc = calloc((size_t)W, 8), *term = calloc((size_t)W, 8);
-    for (int64_t j = 0; j < n; j++) {
-        int64_t jr = bitrev((uint64_t)j, l);
-        memset(acc, 0, (size_t)W * 8);
-        for (int64_t i = 0; i < z; i++) {
-            /* zeta^{j'} omega_L^{i j'} = 2^{e j' + w i j'} */
-            int64_t k = emod(emod(e, twoN) * jr + w * emod(i * jr, L), twoN);
-            orc_ring_mul2exp(term, in + i * stride, k, N);
-            orc_ring_add(acc, acc, term, N);
-        }
-        memcpy(out + j * stride, acc, (size_t)W * 8);
-    }
-    free(acc);
-    free(term);
+    ctx_t c;
+    memset(&c, 0, sizeof c);
+    c.N = N;
+    c.W = W;
+    c.twoN = twoN;
+    dft_brute(&c, out, in, stride, l, z, n, e);
     return 0;
 }
 
@@ -304,6 +335,68 @@ int orc_itft_phases(uint64_t *x, int64_t s, int l, int l1, int64_t z, int64_t n,
         for (int64_t u = 0; u < m; u++) itft_rec(&c, x + u * s, s * L2, l1, emod(e + u * w, c.twoN), z1 + 1, n1 + 1, 0);
         for (int64_t u = m; u < n2; u++) itft_rec(&c, x + u * s, s * L2, l1, emod(e + u * w, c.twoN), z1, n1 + 1, 0);
     }
+    free(c.tmp);
+    return 0;
+}
+
+/* ------------------------------------------------------------------ the ring S[y]/(y^{M/2}+1) */
+
+static int setup_sn(ctx_t *c, int64_t M, uint64_t m, int64_t stride, int l, int policy, int top_l1,
+                    uint64_t seed, int need_x)
+{
+    memset(c, 0, sizeof *c);
+    if (M < 2 || (M & (M - 1)) != 0 || !(m & 1u) || m < 3 || m >= ((uint64_t)1 << 63)) return -1;
+    if (l < 1 || l > 30 || M % ((int64_t)1 << l) != 0) return -1; /* omega_L = y^{M/L}: L | M */
+    c->kind = 1;
+    c->m = m;
+    c->N = M / 2;
+    c->W = M / 2;
+    c->twoN = M;
+    if (need_x && stride < c->W) return -1;
+    c->policy = policy;
+    c->top_l1 = top_l1;
+    c->rng = seed;
+    c->tmp = calloc((size_t)(2 * c->W), 8);
+    return 0;
+}
+
+int orc_sn_dft_brute(uint64_t *out, const uint64_t *in, int64_t stride, int l, int64_t z, int64_t n,
+                     int64_t e, int64_t M, uint64_t m)
+{
+    ctx_t c;
+    if (setup_sn(&c, M, m, stride, l, ORC_SPLIT_BALANCED, 0, 0, 1)) return -1;
+    int64_t L = (int64_t)1 << l;
+    if (z < 0 || z > L || n < 0 || n > L) { free(c.tmp); return -1; }
+    dft_brute(&c, out, in, stride, l, z, n, e);
+    free(c.tmp);
+    return 0;
+}
+
+int orc_sn_tft(uint64_t *x, int64_t stride, int l, int64_t z, int64_t n, int64_t e, int64_t M, uint64_t m,
+               int policy, int top_l1, uint64_t seed, int64_t *count)
+{
+    ctx_t c;
+    if (setup_sn(&c, M, m, stride, l, policy, top_l1, seed, x != NULL)) return -1;
+    int64_t L = (int64_t)1 << l;
+    if (z < 1 || z > L || n < 1 || n > L) { free(c.tmp); return -1; }
+    tft_rec(&c, x, stride, l, emod(e, c.twoN), z, n);
+    if (count) *count += c.count;
+    free(c.tmp);
+    return 0;
+}
+
+int orc_sn_itft(uint64_t *x, int64_t stride, int l, int64_t z, int64_t n, int f, int64_t e, int64_t M,
+                uint64_t m, int policy, int top_l1, uint64_t seed, int64_t *count)
+{
+    ctx_t c;
+    if (setup_sn(&c, M, m, stride, l, policy, top_l1, seed, x != NULL)) return -1;
+    int64_t L = (int64_t)1 << l;
+    if ((f != 0 && f != 1) || z < 1 || z > L || n < 0 || n + f < 1 || n + f > L || z < n) {
+        free(c.tmp);
+        return -1;
+    }
+    itft_rec(&c, x, stride, l, emod(e, c.twoN), z, n, f);
+    if (count) *count += c.count;
     free(c.tmp);
     return 0;
 }
