@@ -230,6 +230,25 @@ int zx_tune(uint64_t *x, int l, int64_t n, int64_t N, int64_t stride_limbs, int 
 int zx_config_get(int64_t N, zx_tune_info *out);
 int zx_config_set(int64_t N, const zx_tune_info *cfg);
 
+/*
+ * Truncated transforms over the Schoenhage-Nussbaumer coefficient ring (Sec. 5.2):
+ * R = S[y]/(y^(M/2) + 1), S = Z/mZ, with omega = y a principal M-th root of unity, so the
+ * twiddles are negacyclic shifts of the coefficients. Same semantics as tft_ex / itft_ex with
+ * omega_L = y^(M/L) and zeta = y^e:
+ *   x       device buffer of L = 2^l cells, cell i at x + i * stride (stride >= M/2 uint64);
+ *           a cell is the M/2 coefficients of an element, each in [0, m) (canonical)
+ *   M       a power of two, 2 <= M <= 2048 (ZX_EUNSUPPORTED above), with L | M
+ *   m       odd modulus, 3 <= m < 2^63
+ *   sn_itft returns L a_i (scale = 0) or a_i (scale = 1: multiplied by L^-1 mod m), then
+ *           a-hat_n when f = 1.
+ * The products of the Schoenhage-Nussbaumer algorithm (Kronecker substitution or
+ * Nussbaumer's method on the pointwise step) are outside this library.
+ */
+int sn_tft(uint64_t *x, int l, int64_t z, int64_t n, int64_t M, uint64_t m, int64_t e, int64_t stride,
+           void *stream);
+int sn_itft(uint64_t *x, int l, int64_t z, int64_t n, int f, int64_t M, uint64_t m, int64_t e, int64_t stride,
+            int scale, void *stream);
+
 /* Shape of the launch plan of one transform (host only, no device needed). */
 typedef struct {
     int32_t passes;    /* passes over global memory */

@@ -25,7 +25,7 @@ ZX_HOST, ZX_DEVICE = 0, 1
 EXPORTS = ("tft", "tft_ex", "itft", "itft_ex", "zx_plan", "zx_mul", "zx_mul_batch",
            "zx_transform_plan", "zx_mul_noalloc", "zx_job_program", "zx_strerror", "zx_last_error",
            "zx_version", "zx_server_create", "zx_server_submit", "zx_server_poll", "zx_server_drain",
-           "zx_server_stats", "zx_server_destroy", "zx_tune", "zx_config_get", "zx_config_set")
+           "zx_server_stats", "zx_server_destroy", "zx_tune", "zx_config_get", "zx_config_set", "sn_tft", "sn_itft")
 
 _lib = None
 
@@ -104,6 +104,8 @@ def load(build_if_missing=True):
     L.zx_tune.argtypes = [vp, i32, i64, i64, i64, i32, vp, C.POINTER(ZxTuneInfo)]
     L.zx_config_get.argtypes = [i64, C.POINTER(ZxTuneInfo)]
     L.zx_config_set.argtypes = [i64, C.POINTER(ZxTuneInfo)]
+    L.sn_tft.argtypes = [vp, i32, i64, i64, i64, C.c_uint64, i64, i64, vp]
+    L.sn_itft.argtypes = [vp, i32, i64, i64, i32, i64, C.c_uint64, i64, i64, i32, vp]
     L.zx_strerror.argtypes = [i32]
     L.zx_strerror.restype = C.c_char_p
     L.zx_last_error.argtypes = []
@@ -112,7 +114,7 @@ def load(build_if_missing=True):
     for name in ("tft", "tft_ex", "itft", "itft_ex", "zx_plan", "zx_mul", "zx_mul_batch",
                  "zx_transform_plan", "zx_mul_noalloc", "zx_job_program", "zx_server_create",
                  "zx_server_submit", "zx_server_poll", "zx_server_drain", "zx_server_stats",
-                 "zx_server_destroy", "zx_tune", "zx_config_get", "zx_config_set"):
+                 "zx_server_destroy", "zx_tune", "zx_config_get", "zx_config_set", "sn_tft", "sn_itft"):
         getattr(L, name).restype = i32
     _lib = L
     return L
@@ -239,6 +241,16 @@ def tune(x, l, n, N, stride_limbs=None, reps=2, stream=None):
     s = stride_limbs or limbs(N)
     _check(load().zx_tune(_dev_ptr(x), l, n, N, s, reps, _stream(stream), C.byref(info)), "zx_tune")
     return {k: getattr(info, k) for k, _ in ZxTuneInfo._fields_ if k != "pad"}
+
+
+def sn_tft(x, l, z, n, M, m, e=0, stride=None, stream=None):
+    """In-place TFT over S[y]/(y^(M/2)+1), S = Z/mZ (Algorithm 1 with omega = y, zeta = y^e)."""
+    _check(load().sn_tft(_dev_ptr(x), l, z, n, M, m, e, stride or M // 2, _stream(stream)), "sn_tft")
+
+
+def sn_itft(x, l, z, n, f, M, m, e=0, stride=None, scale=0, stream=None):
+    """In-place ITFT over S[y]/(y^(M/2)+1) (Algorithm 2); scale=1 multiplies by L^-1 mod m."""
+    _check(load().sn_itft(_dev_ptr(x), l, z, n, f, M, m, e, stride or M // 2, scale, _stream(stream)), "sn_itft")
 
 
 def config_get(N):

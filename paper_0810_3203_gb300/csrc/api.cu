@@ -395,6 +395,35 @@ int zx_tune(uint64_t *x, int l, int64_t n, int64_t N, int64_t stride_limbs, int 
   return ZX_OK;
 }
 
+static int sn_transform(int kind, uint64_t *x, int l, int64_t z, int64_t n, int f, int64_t M, uint64_t m, int64_t e,
+                        int64_t stride, int scale, void *stream) {
+  if (!x) return fail(ZX_EINVAL, "x is NULL");
+  if (M < 2 || (M & (M - 1)) != 0) return fail(ZX_EINVAL, "M must be a power of two >= 2");
+  if (M > 2048) return fail(ZX_EUNSUPPORTED, "M above 2048 (elements of more than 1024 coefficients)");
+  if (l < 1 || l > 11 || M % (int64_t(1) << l) != 0) return fail(ZX_EINVAL, "L = 2^l must divide M (omega_L = y^(M/L))");
+  if (!(m & 1u) || m < 3 || m >= (uint64_t(1) << 63)) return fail(ZX_EINVAL, "m must be odd with 3 <= m < 2^63");
+  if (stride < M / 2) return fail(ZX_EINVAL, "stride < M/2");
+  int rc = check_sizes(kind, l, z, n, f);
+  if (rc) return rc;
+  int err = ZX_OK;
+  const TransformPlan *p = get_sn_plan(kind, l, z, n, f, M / 2, e, scale, &err);
+  if (!p) return err ? fail(err, "planning failed") : fail(ZX_ECUDA, "planning failed");
+  cudaError_t ce = run_sn_transform(*p, x, stride, M / 2, m, cudaStream_t(stream));
+  if (ce != cudaSuccess) return cuda_fail(ce, "transform launch");
+  return ZX_OK;
+}
+
+int sn_tft(uint64_t *x, int l, int64_t z, int64_t n, int64_t M, uint64_t m, int64_t e, int64_t stride,
+           void *stream) {
+  return sn_transform(KIND_TFT, x, l, z, n, 0, M, m, e, stride, 0, stream);
+}
+
+int sn_itft(uint64_t *x, int l, int64_t z, int64_t n, int f, int64_t M, uint64_t m, int64_t e, int64_t stride,
+            int scale, void *stream) {
+  if (scale != 0 && scale != 1) return fail(ZX_EINVAL, "scale must be 0 or 1");
+  return sn_transform(KIND_ITFT, x, l, z, n, f, M, m, e, stride, scale, stream);
+}
+
 int zx_config_get(int64_t N, zx_tune_info *out) {
   if (!out) return fail(ZX_EINVAL, "out is NULL");
   if (!ring_supported(N)) return fail(ZX_EUNSUPPORTED, "unsupported ring size N");

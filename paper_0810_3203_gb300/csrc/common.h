@@ -34,6 +34,15 @@ enum OpFlags : uint8_t {
   OPF_COPY = 16,   // OP_TAG: copy x_i into x_j
 };
 
+// Scalar flags of an op (OpDesc::pad), used over S[y]/(y^{M/2}+1) only, where the ITFT base
+// case's factors 2 and 1/2 are not powers of omega: A (x_i, or the tagged cell of OP_TAG) is
+// doubled or halved as it is read, S is halved as it is written.
+enum OpScalar : uint16_t {
+  OPS_A_DOUBLE = 1,
+  OPS_A_HALVE = 2,
+  OPS_S_HALVE = 4,
+};
+
 struct RotA {  // affine rotation amount: (mul * e + add) mod 2N
   int32_t mul, add;
 };
@@ -41,7 +50,7 @@ struct RotA {  // affine rotation amount: (mul * e + add) mod 2N
 struct OpDesc {
   uint16_t i, j;
   uint8_t kind, flags;
-  uint16_t pad;
+  uint16_t pad;  // OpScalar flags (S[y]/(y^{M/2}+1) programs), else 0
   RotA ra, rb, p0, p1;  // read rotations of x_i, x_j; pending rotations of the S and D outputs
 };
 static_assert(sizeof(OpDesc) == 40, "OpDesc layout");

@@ -20,15 +20,16 @@ struct ProgramStats {
 };
 
 // Program image for a sub-transform of length 2^ls held entirely on chip (see common.h).
+// sn: programs for S[y]/(y^{N}+1) (2N = M), where doublings and halvings are scalar flags.
 std::vector<uint32_t> build_program(int kind, int ls, int64_t z, int64_t n, int f, int64_t N,
-                                    ProgramStats *stats);
+                                    ProgramStats *stats, bool sn = false);
 
 // Job image (stage table plus per-CTA programs, see common.h) for a job of 2^ls cells on a
 // cluster of 2^lc CTAs.
 // Largest per-CTA program (words) in a job image.
 int image_max_program_words(const std::vector<uint32_t> &img);
 std::vector<uint32_t> build_job_image(int kind, int ls, int lc, int64_t z, int64_t n, int f, int64_t N,
-                                      ProgramStats *stats);
+                                      ProgramStats *stats, bool sn = false);
 
 // Ring geometry used by the kernels.
 struct Ring {
@@ -118,6 +119,17 @@ struct HostPlan {
 };
 void build_host_plan(int kind, int l, int64_t z, int64_t n, int f, int64_t N, int64_t e, int scale,
                      HostPlan *out);
+
+// Plans over S[y]/(y^{M/2}+1), H = M/2 coefficients per element (single-CTA jobs; the ITFT's
+// final division by L is escale = l halvings). nullptr with *err set on failure.
+int sn_max_onchip_ls(int64_t H);
+const TransformPlan *get_sn_plan(int kind, int l, int64_t z, int64_t n, int f, int64_t H, int64_t e, int scale,
+                                 int *err);
+void sn_plan_shape(int kind, int l, int64_t z, int64_t n, int f, int64_t H, int *passes, int *launches,
+                   int64_t *jobs);
+// Enqueue an S[y]/(y^{M/2}+1) plan (sn_kernel.cu).
+cudaError_t run_sn_transform(const TransformPlan &p, uint64_t *x, int64_t stride, int64_t H, uint64_t m,
+                             cudaStream_t s);
 
 // Enqueue a plan on a stream.
 cudaError_t run_transform(const TransformPlan &p, uint64_t *x, int64_t stride_limbs,

@@ -109,7 +109,7 @@ int64_t md(int64_t a, int64_t m) {
 // device copies of job images, keyed by (device, kind, ls, lc, z, n, f, N)
 struct ImageCache {
   std::mutex mu;
-  std::map<std::tuple<int, int, int, int, int64_t, int64_t, int, int64_t>, uint32_t *> images;
+  std::map<std::tuple<int, int, int, int, int64_t, int64_t, int, int64_t, int>, uint32_t *> images;
   std::map<const uint32_t *, int> prog_words;  // largest per-CTA program of each image
 
   int max_prog(const uint32_t *d) {
@@ -118,14 +118,14 @@ struct ImageCache {
     return it == prog_words.end() ? 0 : it->second;
   }
 
-  const uint32_t *get(int kind, int ls, int lc, int64_t z, int64_t n, int f, int64_t N, int *err) {
+  const uint32_t *get(int kind, int ls, int lc, int64_t z, int64_t n, int f, int64_t N, int *err, bool sn = false) {
     int dev = 0;
     cudaGetDevice(&dev);
-    auto key = std::make_tuple(dev, kind, ls, lc, z, n, f, N);
+    auto key = std::make_tuple(dev, kind, ls, lc, z, n, f, N, sn ? 1 : 0);
     std::lock_guard<std::mutex> lk(mu);
     auto it = images.find(key);
     if (it != images.end()) return it->second;
-    std::vector<uint32_t> img = build_job_image(kind, ls, lc, z, n, f, N, nullptr);
+    std::vector<uint32_t> img = build_job_image(kind, ls, lc, z, n, f, N, nullptr, sn);
     uint32_t *d = nullptr;
     if (cudaMalloc(&d, img.size() * 4) != cudaSuccess) {
       *err = ZX_ENOMEM;
@@ -435,6 +435,115 @@ const TransformPlan *get_transform_plan(int kind, int l, int64_t z, int64_t n, i
   auto &slot = pc.plans[key];
   if (!slot) slot = std::move(plan);
   return slot.get();
+}
+
+// ---------------------------------------------------------------- S[y]/(y^{M/2}+1) plans
+// Algorithms 1 and 2 over global memory exactly as for Z/(2^N+1), with omega = y (rotations
+// mod M = 2H) and single-CTA jobs only: an element is H = M/2 coefficients of 8 bytes.
+
+int sn_max_onchip_ls(int64_t H) {
+  int ls = 1;
+  while (ls < 16 && (size_t(2) << ls) * (size_t(H) * 8 + 4) <= size_t(72) * 1024) ls++;
+  return ls;
+}
+
+namespace {
+struct SnPlanCache {
+  std::mutex mu;
+  std::map<std::tuple<int, int, int, int64_t, int64_t, int, int64_t, int64_t, int>, std::unique_ptr<TransformPlan>> plans;
+};
+SnPlanCache &sn_plan_cache() {
+  static SnPlanCache *c = new SnPlanCache();
+  return *c;
+}
+}  // namespace
+
+const TransformPlan *get_sn_plan(int kind, int l, int64_t z, int64_t n, int f, int64_t H, int64_t e, int scale,
+                                 int *err) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const int64_t M = 2 * H;
+  e = md(e, M);
+  auto key = std::make_tuple(dev, kind, l, z, n, f, H, e, scale);
+  SnPlanCache &pc = sn_plan_cache();
+  {
+    std::lock_guard<std::mutex> lk(pc.mu);
+    auto it = pc.plans.find(key);
+    if (it != pc.plans.end()) return it->second.get();
+  }
+  PlanConfig cfg;
+  cfg.ls_max = sn_max_onchip_ls(H);
+  cfg.ls_c = -64;  // no cluster jobs: sub-transforms above ls_max recurse
+  cfg.max_warps = 8;
+  cfg.split = 0;
+  Planner P(H, &cfg);
+  // the final division by L: l halvings of every coefficient (escale counts them)
+  const int npass = kind == KIND_TFT ? P.tft(0, 0, 1, l, e, z, n) : P.itft(0, 0, 1, l, e, z, n, f, scale ? l : -1);
+  std::unique_ptr<TransformPlan> plan(new TransformPlan());
+  plan->ring = make_ring(64);
+  plan->ring.N = H;
+  plan->npasses = npass;
+  plan->njobs = int64_t(P.jobs.size());
+  for (JobRec &j : P.jobs) {
+    if (j.lc != 0) {
+      *err = ZX_EUNSUPPORTED;
+      return nullptr;
+    }
+    j.d.image = image_cache().get(j.kind, j.ls, j.lc, j.z, j.n, j.f, H, err, true);
+    if (!j.d.image) return nullptr;
+  }
+  std::stable_sort(P.jobs.begin(), P.jobs.end(), launch_order);
+  std::vector<JobDesc> flat;
+  std::vector<std::pair<size_t, Launch>> groups;
+  for (size_t i = 0; i < P.jobs.size();) {
+    size_t k = i;
+    while (k < P.jobs.size() && same_launch(P.jobs[k], P.jobs[i])) k++;
+    Launch L;
+    L.pass = P.jobs[i].pass;
+    L.ls = P.jobs[i].ls;
+    L.lc = 0;
+    L.njobs = int(k - i);
+    L.nwarps = warps_for_job(L.ls, 0, cfg.max_warps);
+    for (size_t t = i; t < k; t++) L.prog_words = std::max(L.prog_words, image_cache().max_prog(P.jobs[t].d.image));
+    groups.push_back({flat.size(), L});
+    for (size_t t = i; t < k; t++) flat.push_back(P.jobs[t].d);
+    i = k;
+  }
+  JobDesc *d = nullptr;
+  if (cudaMalloc(&d, std::max<size_t>(1, flat.size()) * sizeof(JobDesc)) != cudaSuccess) {
+    *err = ZX_ENOMEM;
+    return nullptr;
+  }
+  if (cudaMemcpy(d, flat.data(), flat.size() * sizeof(JobDesc), cudaMemcpyHostToDevice) != cudaSuccess) {
+    cudaFree(d);
+    *err = ZX_ECUDA;
+    return nullptr;
+  }
+  for (auto &g : groups) {
+    g.second.d_jobs = d + g.first;
+    plan->launches.push_back(g.second);
+  }
+  std::lock_guard<std::mutex> lk(pc.mu);
+  auto &slot = pc.plans[key];
+  if (!slot) slot = std::move(plan);
+  return slot.get();
+}
+
+void sn_plan_shape(int kind, int l, int64_t z, int64_t n, int f, int64_t H, int *passes, int *launches,
+                   int64_t *jobs) {
+  PlanConfig cfg;
+  cfg.ls_max = sn_max_onchip_ls(H);
+  cfg.ls_c = -64;
+  cfg.max_warps = 8;
+  cfg.split = 0;
+  Planner P(H, &cfg);
+  *passes = kind == KIND_TFT ? P.tft(0, 0, 1, l, 0, z, n) : P.itft(0, 0, 1, l, 0, z, n, f, -1);
+  std::sort(P.jobs.begin(), P.jobs.end(), launch_order);
+  int nl = 0;
+  for (size_t i = 0; i < P.jobs.size(); i++)
+    if (i == 0 || !same_launch(P.jobs[i], P.jobs[i - 1])) nl++;
+  *launches = nl;
+  *jobs = int64_t(P.jobs.size());
 }
 
 }  // namespace tftgpu

@@ -33,7 +33,9 @@ struct SymE {
 // Emits the base cases of Algorithm 1 / 2 on cell indices base + i * stride.
 class ProgGen {
  public:
-  ProgGen(int64_t twoN, int policy) : twoN_(twoN), policy_(policy) {}
+  // sn: the ring is S[y]/(y^{M/2}+1) (twoN = M, omega = y); there 2 is not a power of omega, so
+  // the ITFT base case's doublings and halvings become scalar flags (OPS_*) instead of rotations
+  ProgGen(int64_t twoN, int policy, bool sn = false) : twoN_(twoN), policy_(policy), sn_(sn) {}
 
   std::vector<OpDesc> ops;
 
@@ -72,20 +74,24 @@ class ProgGen {
   void itft(int base, int stride, int l, SymE E, int64_t z, int64_t n, int f) {
     if (l == 1) {
       int c0 = base, c1 = base + stride;
+      // doubling / halving: 2 = omega and 1/2 = omega^{2N-1} over Z/(2^N+1); scalar flags
+      // over S[y]/(y^{M/2}+1)
+      const SymE two = sn_ ? zero() : cst(1), half = sn_ ? zero() : cst(twoN_ - 1);
+      const uint16_t a2 = sn_ ? OPS_A_DOUBLE : 0, ah = sn_ ? OPS_A_HALVE : 0, sh = sn_ ? OPS_S_HALVE : 0;
       if (n == 2) {
         push(OP_BF, c0, c1, OPF_S | OPF_D, zero(), neg(E), zero(), zero());
       } else if (n == 1 && f == 1 && z == 2) {
         push(OP_CROSS, c0, c1, 0, zero(), zero(), zero(), E);
       } else if (n == 1 && f == 1 && z == 1) {
-        push(OP_TAG, c0, c1, OPF_COPY, cst(1), E, zero(), zero());
+        push(OP_TAG, c0, c1, OPF_COPY, two, E, zero(), zero(), a2);
       } else if (n == 1 && f == 0 && z == 2) {
-        push(OP_BF, c0, c1, OPF_D | OPF_D_TO_I, cst(1), zero(), zero(), zero());
+        push(OP_BF, c0, c1, OPF_D | OPF_D_TO_I, two, zero(), zero(), zero(), a2);
       } else if (n == 1 && f == 0 && z == 1) {
-        push(OP_TAG, c0, c0, 0, cst(1), zero(), zero(), zero());
+        push(OP_TAG, c0, c0, 0, two, zero(), zero(), zero(), a2);
       } else if (n == 0 && z == 2) {
-        push(OP_BF, c0, c1, OPF_S, zero(), zero(), cst(twoN_ - 1), zero());
+        push(OP_BF, c0, c1, OPF_S, zero(), zero(), half, zero(), sh);
       } else if (n == 0 && z == 1) {
-        push(OP_TAG, c0, c0, 0, cst(twoN_ - 1), zero(), zero(), zero());
+        push(OP_TAG, c0, c0, 0, half, zero(), zero(), zero(), ah);
       }
       return;
     }
@@ -109,6 +115,7 @@ class ProgGen {
  private:
   int64_t twoN_;
   int policy_;
+  bool sn_;
 
   int split(int l) const { return policy_ == 0 ? 1 : l / 2; }
   int64_t md(int64_t a) const {
@@ -117,13 +124,14 @@ class ProgGen {
   }
   RotA ra(SymE a) const { return RotA{int32_t(a.mul), int32_t(a.add)}; }
 
-  void push(uint8_t kind, int i, int j, uint8_t flags, SymE r_a, SymE r_b, SymE p0, SymE p1) {
+  void push(uint8_t kind, int i, int j, uint8_t flags, SymE r_a, SymE r_b, SymE p0, SymE p1, uint16_t scal = 0) {
     OpDesc o;
     std::memset(&o, 0, sizeof o);
     o.i = uint16_t(i);
     o.j = uint16_t(j);
     o.kind = kind;
     o.flags = flags;
+    o.pad = scal;
     o.ra = ra(r_a);
     o.rb = ra(r_b);
     o.p0 = ra(p0);
@@ -167,11 +175,11 @@ std::vector<uint32_t> level_and_pack(const std::vector<OpDesc> &ops, int nslots,
 // Generate with both split policies (through `emit`) and keep the image with fewer levels.
 // `slot` maps a generated cell index to the local slot of the CTA that runs the program.
 std::vector<uint32_t> best_program(int64_t twoN, int nslots, const std::function<void(ProgGen &)> &emit,
-                                   const std::function<int(int)> &slot, ProgramStats *stats) {
+                                   const std::function<int(int)> &slot, ProgramStats *stats, bool sn = false) {
   std::vector<uint32_t> best;
   int best_lev = -1;
   for (int policy = 0; policy < 2; policy++) {
-    ProgGen g(twoN, policy);
+    ProgGen g(twoN, policy, sn);
     emit(g);
     if (g.ops.empty()) return {};
     for (OpDesc &o : g.ops) {
@@ -195,7 +203,7 @@ std::vector<uint32_t> best_program(int64_t twoN, int nslots, const std::function
 }  // namespace
 
 std::vector<uint32_t> build_program(int kind, int ls, int64_t z, int64_t n, int f, int64_t N,
-                                    ProgramStats *stats) {
+                                    ProgramStats *stats, bool sn) {
   int64_t twoN = 2 * N;
   auto emit = [&](ProgGen &g) {
     if (kind == KIND_TFT)
@@ -203,11 +211,11 @@ std::vector<uint32_t> build_program(int kind, int ls, int64_t z, int64_t n, int 
     else
       g.itft(0, 1, ls, {1, 0}, z, n, f);
   };
-  return best_program(twoN, 1 << ls, emit, [](int c) { return c; }, stats);
+  return best_program(twoN, 1 << ls, emit, [](int c) { return c; }, stats, sn);
 }
 
 std::vector<uint32_t> build_job_image(int kind, int ls, int lc, int64_t z, int64_t n, int f, int64_t N,
-                                      ProgramStats *stats) {
+                                      ProgramStats *stats, bool sn) {
   const int64_t twoN = 2 * N;
   const int C = 1 << lc;
   struct Stage {
@@ -217,7 +225,7 @@ std::vector<uint32_t> build_job_image(int kind, int ls, int lc, int64_t z, int64
   std::vector<Stage> stages;
   uint32_t load_layout = LAYOUT_ROW, store_layout = LAYOUT_ROW;
   if (lc == 0) {
-    Stage s{STAGE_PROG, 0, {build_program(kind, ls, z, n, f, N, stats)}};
+    Stage s{STAGE_PROG, 0, {build_program(kind, ls, z, n, f, N, stats, sn)}};
     stages.push_back(std::move(s));
   } else {
     const int l2 = ls - lc;
