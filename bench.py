@@ -402,6 +402,8 @@ def run_gpu(args):
                           "passes_exact": tg.transform_plan(1, l, n, n, N)["passes"],
                           "passes_padded": tg.transform_plan(1, l, n_pad, n_pad, N)["passes"]}
 
+    sn = sn_leg(tg, device, stream, 10)
+    ok &= sn["bit_exact_roundtrip"]
     batch = None if args.no_batch else batch_leg(tg, device, stream, 2, 3, not args.no_tune)
     ok &= batch is None or batch["bit_exact_vs_plain"]
     serve = None if args.no_serve else serve_leg(tg, device, stream, args.serve_requests, not args.no_tune)
@@ -436,6 +438,7 @@ def run_gpu(args):
         "wall_s": round(wall, 3),
     }
     line["zero_padded_itft"] = padded
+    line["sn"] = sn
     if tuned is not None:
         line["tuned_config"] = tuned
     if batch is not None:
@@ -601,6 +604,41 @@ def serve_leg(tg, device, stream, count, tune=True):
             "max_wave_products": stats["max_wave_products"], "max_waves_in_flight": stats["max_waves_in_flight"],
             "arena_peak_gb": round(stats["arena_peak_bytes"] / 1e9, 3), "bit_exact_vs_plain": bool(same),
             "tuned": tuned}
+
+
+def sn_leg(tg, device, stream, steps):
+    """Round trips over S[y]/(y^(M/2)+1) (Sec. 5.2 workload shape): TFT then ITFT with the
+    division by L at M = 2048 (elements of 1024 coefficients, 8 KB), L = 2^11, n = 2000,
+    resident buffer; algorithmic bytes of the paper's two-pass schedule as for Z/(2^N+1)."""
+    import numpy as np
+    import torch
+
+    w = workloads.SN_TRANSFORM
+    M, m, l, n = w["M"], w["m"], w["l"], w["n"]
+    L, H = 1 << l, M // 2
+    x = workloads.sn_elements(w["seed"], n, M, m, cells=L)
+    d = torch.from_numpy(x.view(np.int64)).to(device)
+
+    def step():
+        tg.sn_tft(d, l, n, n, M, m, 0, stream=stream)
+        tg.sn_itft(d, l, n, n, 0, M, m, 0, scale=1, stream=stream)
+
+    for _ in range(3):
+        step()
+    torch.cuda.synchronize(device)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(steps):
+        step()
+    b.record(stream)
+    torch.cuda.synchronize(device)
+    sec = a.elapsed_time(b) / 1e3 / steps
+    ok = bool(np.array_equal(d.cpu().numpy().view(np.uint64)[:n * H], x[:n * H]))
+    cells = alg_cells_tft(l, n, n) + alg_cells_itft(l, n, n)
+    gbs = cells * H * 8 / sec / 1e9
+    return {"workload": f"S[y]/(y^{H}+1) over Z/mZ, m = 2^40 + 15, L = 2^{l}, n = {n}, pieces of {M // 4} "
+                        "coefficients, seed 7", "ms_per_round_trip": round(sec * 1e3, 3),
+            "gbs_algorithmic": round(gbs, 2), "bit_exact_roundtrip": ok}
 
 
 def run_batch(args):

@@ -47,6 +47,9 @@ def lib():
         L.orc_sn_dft_brute.argtypes = [_u64p, _u64p, i64, i32, i64, i64, i64, i64, u64]
         L.orc_sn_tft.argtypes = [_u64p, i64, i32, i64, i64, i64, i64, u64, i32, i32, u64, _i64p]
         L.orc_sn_itft.argtypes = [_u64p, i64, i32, i64, i64, i32, i64, i64, u64, i32, i32, u64, _i64p]
+        L.orc_sqrt2_dft_brute.argtypes = [_u64p, _u64p, i64, i32, i64, i64, i64, i64]
+        L.orc_sqrt2_tft.argtypes = [_u64p, i64, i32, i64, i64, i64, i64, i32, i32, u64, _i64p]
+        L.orc_sqrt2_itft.argtypes = [_u64p, i64, i32, i64, i64, i32, i64, i64, i32, i32, u64, _i64p]
         L.orc_zx_mul.argtypes = [C.POINTER(_Poly)] * 3 + [C.POINTER(i32), _i64p]
         L.orc_zx_plan.argtypes = [i64, i64, i64, i64, i32, C.POINTER(i32), _i64p]
         L.orc_zx_schoolbook.argtypes = [C.POINTER(_Poly)] * 3
@@ -285,4 +288,26 @@ def sn_itft(x, l, z, n, f, e, M, m, stride=None, policy=SPLIT_BALANCED, top_l1=0
     cnt = C.c_int64(0)
     _check(lib().orc_sn_itft(_p(x), stride or M // 2, l, z, n, f, e, M, m, policy, top_l1, seed, C.byref(cnt)),
            "orc_sn_itft")
+    return cnt.value
+
+
+# ---------------------------------------------------------------- omega = sqrt2 over Z/(2^N+1)
+def sqrt2_dft_brute(x, l, z, n, e, N, stride=None):
+    stride = stride or limbs(N)
+    out = np.zeros_like(x)
+    _check(lib().orc_sqrt2_dft_brute(_p(out), _p(x), stride, l, z, n, e, N), "orc_sqrt2_dft_brute")
+    return out
+
+
+def sqrt2_tft(x, l, z, n, e, N, stride=None, policy=SPLIT_BALANCED, top_l1=0, seed=0):
+    cnt = C.c_int64(0)
+    _check(lib().orc_sqrt2_tft(_p(x), stride or limbs(N), l, z, n, e, N, policy, top_l1, seed, C.byref(cnt)),
+           "orc_sqrt2_tft")
+    return cnt.value
+
+
+def sqrt2_itft(x, l, z, n, f, e, N, stride=None, policy=SPLIT_BALANCED, top_l1=0, seed=0):
+    cnt = C.c_int64(0)
+    _check(lib().orc_sqrt2_itft(_p(x), stride or limbs(N), l, z, n, f, e, N, policy, top_l1, seed, C.byref(cnt)),
+           "orc_sqrt2_itft")
     return cnt.value

@@ -125,6 +125,17 @@ int orc_sn_tft(uint64_t *x, int64_t stride, int l, int64_t z, int64_t n, int64_t
 int orc_sn_itft(uint64_t *x, int64_t stride, int l, int64_t z, int64_t n, int f, int64_t e, int64_t M,
                 uint64_t m, int policy, int top_l1, uint64_t seed, int64_t *count);
 
+/* ------------------------------------------------------------------ omega = sqrt2 over Z/(2^N+1)
+ * sqrt2 = 2^{3N/4} - 2^{N/4} squares to 2 and is a principal 4N-th root of unity, so transforms
+ * of any length L | 4N exist. Exponents (e, and those of omega_L = sqrt2^{4N/L}) are in units of
+ * sqrt2, mod 4N; otherwise as orc_dft_brute / orc_tft / orc_itft. Not in the paper. */
+int orc_sqrt2_dft_brute(uint64_t *out, const uint64_t *in, int64_t stride, int l, int64_t z, int64_t n,
+                        int64_t e, int64_t N);
+int orc_sqrt2_tft(uint64_t *x, int64_t stride, int l, int64_t z, int64_t n, int64_t e, int64_t N, int policy,
+                  int top_l1, uint64_t seed, int64_t *count);
+int orc_sqrt2_itft(uint64_t *x, int64_t stride, int l, int64_t z, int64_t n, int f, int64_t e, int64_t N,
+                   int policy, int top_l1, uint64_t seed, int64_t *count);
+
 #ifdef __cplusplus
 }
 #endif

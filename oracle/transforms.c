@@ -18,7 +18,8 @@
 #include <string.h>
 
 typedef struct {
-    int kind;       /* 0: Z/(2^N+1) with omega = 2; 1: S[y]/(y^{M/2}+1), S = Z/mZ, omega = y */
+    int kind;       /* 0: Z/(2^N+1) with omega = 2; 1: S[y]/(y^{M/2}+1), S = Z/mZ, omega = y;
+                       2: Z/(2^N+1) with omega = sqrt2 = 2^{3N/4} - 2^{N/4} (order 4N) */
     uint64_t m;     /* kind 1: the modulus of S */
     int64_t N, W, twoN; /* kind 1: N = M/2 coefficients, W = M/2 words, twoN = M */
     int policy;
@@ -64,23 +65,41 @@ static int choose_l1(ctx_t *c, int l)
 static void cp(ctx_t *c, uint64_t *d, const uint64_t *s) { memmove(d, s, (size_t)c->W * 8); }
 static void add(ctx_t *c, uint64_t *r, const uint64_t *a, const uint64_t *b)
 {
-    if (c->kind) orc_sn_add(r, a, b, c->twoN, c->m);
+    if (c->kind == 1) orc_sn_add(r, a, b, c->twoN, c->m);
     else orc_ring_add(r, a, b, c->N);
 }
 static void sub(ctx_t *c, uint64_t *r, const uint64_t *a, const uint64_t *b)
 {
-    if (c->kind) orc_sn_sub(r, a, b, c->twoN, c->m);
+    if (c->kind == 1) orc_sn_sub(r, a, b, c->twoN, c->m);
     else orc_ring_sub(r, a, b, c->N);
 }
-/* r = omega^k a: a rotation by k bits (kind 0) or a negacyclic shift by k places (kind 1) */
+/* r = sqrt2^k a over Z/(2^N+1), k mod 4N: 2^{k/2} a for even k, and for odd k
+ * 2^{(k-1)/2} (2^{3N/4} - 2^{N/4}) a, a difference of two rotations */
+static void rot_sqrt2(ctx_t *c, uint64_t *r, const uint64_t *a, int64_t k)
+{
+    k = emod(k, 4 * c->N);
+    int64_t h = k >> 1;
+    if (!(k & 1)) {
+        orc_ring_mul2exp(r, a, emod(h, 2 * c->N), c->N);
+        return;
+    }
+    uint64_t *t = c->tmp + 2 * c->W;
+    orc_ring_mul2exp(t, a, emod(h + 3 * c->N / 4, 2 * c->N), c->N);
+    orc_ring_mul2exp(r, a, emod(h + c->N / 4, 2 * c->N), c->N);
+    orc_ring_sub(r, t, r, c->N);
+}
+
+/* r = omega^k a: a rotation by k bits (kind 0), a negacyclic shift by k places (kind 1), or a
+ * power of sqrt2 (kind 2) */
 static void rot(ctx_t *c, uint64_t *r, const uint64_t *a, int64_t k)
 {
-    if (c->kind) orc_sn_ypow(r, a, emod(k, c->twoN), c->twoN, c->m);
+    if (c->kind == 1) orc_sn_ypow(r, a, emod(k, c->twoN), c->twoN, c->m);
+    else if (c->kind == 2) rot_sqrt2(c, r, a, k);
     else orc_ring_mul2exp(r, a, emod(k, c->twoN), c->N);
 }
 static void half(ctx_t *c, uint64_t *r, const uint64_t *a)
 {
-    if (c->kind) orc_sn_half(r, a, c->twoN, c->m);
+    if (c->kind == 1) orc_sn_half(r, a, c->twoN, c->m);
     else orc_ring_div2(r, a, c->N);
 }
 
@@ -244,7 +263,7 @@ static int setup(ctx_t *c, int64_t N, int64_t stride, int l, int policy, int top
     c->policy = policy;
     c->top_l1 = top_l1;
     c->rng = seed;
-    c->tmp = calloc((size_t)(2 * c->W), 8);
+    c->tmp = calloc((size_t)(3 * c->W), 8);
     return 0;
 }
 
@@ -356,7 +375,7 @@ static int setup_sn(ctx_t *c, int64_t M, uint64_t m, int64_t stride, int l, int 
     c->policy = policy;
     c->top_l1 = top_l1;
     c->rng = seed;
-    c->tmp = calloc((size_t)(2 * c->W), 8);
+    c->tmp = calloc((size_t)(3 * c->W), 8);
     return 0;
 }
 
@@ -390,6 +409,59 @@ int orc_sn_itft(uint64_t *x, int64_t stride, int l, int64_t z, int64_t n, int f,
 {
     ctx_t c;
     if (setup_sn(&c, M, m, stride, l, policy, top_l1, seed, x != NULL)) return -1;
+    int64_t L = (int64_t)1 << l;
+    if ((f != 0 && f != 1) || z < 1 || z > L || n < 0 || n + f < 1 || n + f > L || z < n) {
+        free(c.tmp);
+        return -1;
+    }
+    itft_rec(&c, x, stride, l, emod(e, c.twoN), z, n, f);
+    if (count) *count += c.count;
+    free(c.tmp);
+    return 0;
+}
+
+/* ------------------------------------------------------------------ Z/(2^N+1) with omega = sqrt2 */
+
+static int setup_sqrt2(ctx_t *c, int64_t N, int64_t stride, int l, int policy, int top_l1, uint64_t seed,
+                       int need_x)
+{
+    if (setup(c, N, stride, 1, policy, top_l1, seed, need_x)) return -1; /* L | 4N is checked here */
+    if (l < 1 || l > 30 || (4 * N) % ((int64_t)1 << l) != 0) { free(c->tmp); return -1; } /* L | 4N */
+    c->kind = 2;
+    c->twoN = 4 * N; /* the order of omega */
+    return 0;
+}
+
+int orc_sqrt2_dft_brute(uint64_t *out, const uint64_t *in, int64_t stride, int l, int64_t z, int64_t n,
+                        int64_t e, int64_t N)
+{
+    ctx_t c;
+    if (setup_sqrt2(&c, N, stride, l, ORC_SPLIT_BALANCED, 0, 0, 1)) return -1;
+    int64_t L = (int64_t)1 << l;
+    if (z < 0 || z > L || n < 0 || n > L) { free(c.tmp); return -1; }
+    dft_brute(&c, out, in, stride, l, z, n, e);
+    free(c.tmp);
+    return 0;
+}
+
+int orc_sqrt2_tft(uint64_t *x, int64_t stride, int l, int64_t z, int64_t n, int64_t e, int64_t N, int policy,
+                  int top_l1, uint64_t seed, int64_t *count)
+{
+    ctx_t c;
+    if (setup_sqrt2(&c, N, stride, l, policy, top_l1, seed, x != NULL)) return -1;
+    int64_t L = (int64_t)1 << l;
+    if (z < 1 || z > L || n < 1 || n > L) { free(c.tmp); return -1; }
+    tft_rec(&c, x, stride, l, emod(e, c.twoN), z, n);
+    if (count) *count += c.count;
+    free(c.tmp);
+    return 0;
+}
+
+int orc_sqrt2_itft(uint64_t *x, int64_t stride, int l, int64_t z, int64_t n, int f, int64_t e, int64_t N,
+                   int policy, int top_l1, uint64_t seed, int64_t *count)
+{
+    ctx_t c;
+    if (setup_sqrt2(&c, N, stride, l, policy, top_l1, seed, x != NULL)) return -1;
     int64_t L = (int64_t)1 << l;
     if ((f != 0 && f != 1) || z < 1 || z > L || n < 0 || n + f < 1 || n + f > L || z < n) {
         free(c.tmp);

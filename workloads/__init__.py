@@ -26,6 +26,10 @@ TRANSFORM_LARGE = dict(N=32768, l=16, ns=(32769, 40000, 45000, 52000, 65536), se
 BATCH_MIXED = dict(count=512, len_lo=200, len_hi=20000, bits_lo=64, bits_hi=1024, seed=4)
 SERVE_POISSON = dict(rate=2000.0, len_lo=2 ** 8, len_hi=2 ** 15, bits_lo=64, bits_hi=4096, seed=5)
 SMOOTHNESS_SWEEP = dict(len_lo=512, len_hi=16384, step=1.05, bits=8000, seed=6)
+# Sec. 5.2 shape: a polynomial of about 5 * 10^5 coefficients modulo a 41-bit odd modulus, cut
+# into pieces of M/4 coefficients, each piece an element of S[y]/(y^(M/2)+1) with its upper
+# half zero; transform length 2^11 = M, n = 2000 nonzero elements
+SN_TRANSFORM = dict(M=2048, m=(1 << 40) + 15, l=11, n=2000, seed=7)
 
 
 def splitmix64(seed, count, offset=0):
@@ -95,6 +99,20 @@ def structured_residues(seed, count, N, stride=None, cells=None):
             v = int.from_bytes(np.asarray(splitmix64(c, W - 1), dtype=np.uint64).tobytes(), "little")
         for t in range(W):
             x[i, t] = np.uint64((v >> (64 * t)) & 0xFFFFFFFFFFFFFFFF)
+    return x.reshape(-1)
+
+
+def sn_elements(seed, count, M, m, cells=None, nonzero=None):
+    """`count` elements of S[y]/(y^(M/2)+1), S = Z/mZ: the first `nonzero` coefficients
+    (default M/4, a piece of the input polynomial) uniform in [0, m), the rest zero; cells of
+    M/2 uint64, `cells` cells in all (the ones past `count` zero)."""
+    H = M // 2
+    nonzero = M // 4 if nonzero is None else nonzero
+    cells = cells if cells is not None else count
+    x = np.zeros((cells, H), dtype=np.uint64)
+    if count and nonzero:
+        w = splitmix64(seed, count * nonzero).reshape(count, nonzero)
+        x[:count, :nonzero] = w % np.uint64(m)
     return x.reshape(-1)
 
 
