@@ -82,6 +82,16 @@ int itft_ex(uint64_t *x, int l, int64_t z, int64_t n, int f, int64_t N, int64_t 
  * itft(tft(x)) restores x literally. */
 int itft(uint64_t *x, int l, int64_t n, int64_t N, void *stream);
 
+/*
+ * The same transforms with omega = sqrt2 = 2^(3N/4) - 2^(N/4), a principal 4N-th root of unity
+ * in Z/(2^N+1) (the sqrt2 trick; not in the paper): L = 2^l only has to divide 4N, so a product
+ * of length L can use a ring of L/4 bits instead of L/2. omega_L = sqrt2^(4N/L), zeta = sqrt2^e
+ * with e taken mod 4N; otherwise as tft_ex / itft_ex (itft_sqrt2 with scale = 1 divides by L).
+ */
+int tft_sqrt2(uint64_t *x, int l, int64_t z, int64_t n, int64_t N, int64_t e, int64_t stride_limbs, void *stream);
+int itft_sqrt2(uint64_t *x, int l, int64_t z, int64_t n, int f, int64_t N, int64_t e, int64_t stride_limbs,
+               int scale, void *stream);
+
 /* A polynomial in Z[x] with `len` coefficients of `limbs` little-endian uint64 limbs each,
  * two's complement when is_signed != 0, unsigned otherwise. `bits` > 0 promises
  * |coefficient| < 2^bits (0: no promise, 64 * limbs is assumed); the ring size is chosen from
@@ -110,6 +120,9 @@ typedef struct {
                               top-level row/column split (the zero padding of Sec. 6), and of
                               the column jobs' own split when that adds at most n/32; n when
                               one CTA holds the whole transform */
+    int32_t sqrt2;         /* 1: the transforms use omega = sqrt2 (L | 4N), which allowed a
+                              ring half the size of the L | 2N rule; 0: omega = 2 */
+    int32_t pad;
 } zx_plan_info;
 
 /*
@@ -249,7 +262,8 @@ int sn_tft(uint64_t *x, int l, int64_t z, int64_t n, int64_t M, uint64_t m, int6
 int sn_itft(uint64_t *x, int l, int64_t z, int64_t n, int f, int64_t M, uint64_t m, int64_t e, int64_t stride,
             int scale, void *stream);
 
-/* Shape of the launch plan of one transform (host only, no device needed). */
+/* Shape of the launch plan of one transform (host only, no device needed); the same for omega = 2
+ * (L | 2N) and omega = sqrt2 (L | 4N), so only L | 4N is required. */
 typedef struct {
     int32_t passes;    /* passes over global memory */
     int32_t launches;  /* kernel launches */
@@ -266,14 +280,17 @@ int zx_transform_plan(int kind, int l, int64_t z, int64_t n, int f, int64_t N, z
 
 /*
  * The on-chip schedule of one job (host only): a sub-transform of 2^ls cells (TFT: kind 0,
- * ITFT: kind 1) with the given z, n, f over Z/(2^N+1), spread over 2^lc CTAs of a cluster.
+ * ITFT: kind 1) with the given z, n, f, spread over 2^lc CTAs of a cluster, over
+ * Z/(2^N+1) with omega = 2 (mode 0), S[y]/(y^N+1) with omega = y (mode 1: rotations mod 2N,
+ * the ITFT's doublings and halvings as scalar flags) or Z/(2^N+1) with omega = sqrt2 (mode 2:
+ * rotations mod 4N).
  * Writes the job image -- header [nstages, C, load layout, store layout], per stage
  * [type, arg, per-CTA program offsets], then per-CTA programs of leveled base-case butterflies
  * of Algorithms 1 and 2 (see paper_0810_3203_gb300/csrc/common.h for the word layout) -- into
  * buf (cap_words uint32 words) and its length into *size_words. ZX_EBUFSIZE when buf is too
  * small (the needed length is still written), ZX_EINVAL on bad sizes. For inspection and tests.
  */
-int zx_job_program(int kind, int ls, int lc, int64_t z, int64_t n, int f, int64_t N, uint32_t *buf,
+int zx_job_program(int kind, int ls, int lc, int64_t z, int64_t n, int f, int64_t N, int mode, uint32_t *buf,
                    int64_t cap_words, int64_t *size_words);
 
 /* Human-readable name of a status code (static storage). */

@@ -25,7 +25,7 @@ ZX_HOST, ZX_DEVICE = 0, 1
 EXPORTS = ("tft", "tft_ex", "itft", "itft_ex", "zx_plan", "zx_mul", "zx_mul_batch",
            "zx_transform_plan", "zx_mul_noalloc", "zx_job_program", "zx_strerror", "zx_last_error",
            "zx_version", "zx_server_create", "zx_server_submit", "zx_server_poll", "zx_server_drain",
-           "zx_server_stats", "zx_server_destroy", "zx_tune", "zx_config_get", "zx_config_set", "sn_tft", "sn_itft")
+           "zx_server_stats", "zx_server_destroy", "zx_tune", "zx_config_get", "zx_config_set", "sn_tft", "sn_itft", "tft_sqrt2", "itft_sqrt2")
 
 _lib = None
 
@@ -46,7 +46,8 @@ class ZxPoly(C.Structure):
 class ZxPlanInfo(C.Structure):
     _fields_ = [("l", C.c_int32), ("K", C.c_int32), ("N", C.c_int64), ("n", C.c_int64),
                 ("stride_limbs", C.c_int64), ("limbs_h", C.c_int64), ("scratch_bytes", C.c_int64),
-                ("tft_passes", C.c_int32), ("itft_passes", C.c_int32), ("n_fft", C.c_int64)]
+                ("tft_passes", C.c_int32), ("itft_passes", C.c_int32), ("n_fft", C.c_int64),
+                ("sqrt2", C.c_int32), ("pad", C.c_int32)]
 
 
 class ZxTuneInfo(C.Structure):
@@ -91,7 +92,7 @@ def load(build_if_missing=True):
     L.zx_mul_batch.argtypes = [C.POINTER(ZxPoly), C.POINTER(ZxPoly), C.POINTER(ZxPoly), i32, vp]
     L.zx_transform_plan.argtypes = [i32, i32, i64, i64, i32, i64, C.POINTER(ZxTransformInfo)]
     L.zx_mul_noalloc.argtypes = [C.POINTER(ZxPoly), C.POINTER(ZxPoly), C.POINTER(ZxPoly), vp]
-    L.zx_job_program.argtypes = [i32, i32, i32, i64, i64, i32, i64, C.POINTER(C.c_uint32), i64,
+    L.zx_job_program.argtypes = [i32, i32, i32, i64, i64, i32, i64, i32, C.POINTER(C.c_uint32), i64,
                                  C.POINTER(C.c_int64)]
     L.zx_server_create.argtypes = [i64, i32, C.POINTER(vp)]
     L.zx_server_submit.argtypes = [vp, C.POINTER(ZxPoly), C.POINTER(ZxPoly), C.POINTER(ZxPoly),
@@ -104,6 +105,8 @@ def load(build_if_missing=True):
     L.zx_tune.argtypes = [vp, i32, i64, i64, i64, i32, vp, C.POINTER(ZxTuneInfo)]
     L.zx_config_get.argtypes = [i64, C.POINTER(ZxTuneInfo)]
     L.zx_config_set.argtypes = [i64, C.POINTER(ZxTuneInfo)]
+    L.tft_sqrt2.argtypes = [vp, i32, i64, i64, i64, i64, i64, vp]
+    L.itft_sqrt2.argtypes = [vp, i32, i64, i64, i32, i64, i64, i64, i32, vp]
     L.sn_tft.argtypes = [vp, i32, i64, i64, i64, C.c_uint64, i64, i64, vp]
     L.sn_itft.argtypes = [vp, i32, i64, i64, i32, i64, C.c_uint64, i64, i64, i32, vp]
     L.zx_strerror.argtypes = [i32]
@@ -114,7 +117,7 @@ def load(build_if_missing=True):
     for name in ("tft", "tft_ex", "itft", "itft_ex", "zx_plan", "zx_mul", "zx_mul_batch",
                  "zx_transform_plan", "zx_mul_noalloc", "zx_job_program", "zx_server_create",
                  "zx_server_submit", "zx_server_poll", "zx_server_drain", "zx_server_stats",
-                 "zx_server_destroy", "zx_tune", "zx_config_get", "zx_config_set", "sn_tft", "sn_itft"):
+                 "zx_server_destroy", "zx_tune", "zx_config_get", "zx_config_set", "sn_tft", "sn_itft", "tft_sqrt2", "itft_sqrt2"):
         getattr(L, name).restype = i32
     _lib = L
     return L
@@ -182,13 +185,13 @@ def transform_plan(kind, l, z, n, N, f=0):
     return {k: getattr(info, k) for k, _ in ZxTransformInfo._fields_}
 
 
-def job_program(kind, ls, lc, z, n, N, f=0):
+def job_program(kind, ls, lc, z, n, N, f=0, mode=0):
     """Job image of one on-chip sub-transform (see zx_job_program in include/tftgpu.h), as a
-    numpy uint32 array."""
+    numpy uint32 array. mode: 0 omega = 2, 1 omega = y over S[y]/(y^N+1), 2 omega = sqrt2."""
     size = C.c_int64(0)
-    load().zx_job_program(kind, ls, lc, z, n, f, N, None, 0, C.byref(size))
+    load().zx_job_program(kind, ls, lc, z, n, f, N, mode, None, 0, C.byref(size))
     buf = np.zeros(max(1, size.value), np.uint32)
-    _check(load().zx_job_program(kind, ls, lc, z, n, f, N, buf.ctypes.data_as(C.POINTER(C.c_uint32)),
+    _check(load().zx_job_program(kind, ls, lc, z, n, f, N, mode, buf.ctypes.data_as(C.POINTER(C.c_uint32)),
                                  buf.size, C.byref(size)), "zx_job_program")
     return buf[:size.value]
 
@@ -241,6 +244,18 @@ def tune(x, l, n, N, stride_limbs=None, reps=2, stream=None):
     s = stride_limbs or limbs(N)
     _check(load().zx_tune(_dev_ptr(x), l, n, N, s, reps, _stream(stream), C.byref(info)), "zx_tune")
     return {k: getattr(info, k) for k, _ in ZxTuneInfo._fields_ if k != "pad"}
+
+
+def tft_sqrt2(x, l, z, n, N, e=0, stride_limbs=None, stream=None):
+    """In-place TFT with omega = sqrt2 (L | 4N); e is the exponent of zeta in units of sqrt2."""
+    s = stride_limbs or limbs(N)
+    _check(load().tft_sqrt2(_dev_ptr(x), l, z, n, N, e, s, _stream(stream)), "tft_sqrt2")
+
+
+def itft_sqrt2(x, l, z, n, f, N, e=0, stride_limbs=None, scale=0, stream=None):
+    """In-place ITFT with omega = sqrt2 (L | 4N); scale=1 divides the L a_i by L."""
+    s = stride_limbs or limbs(N)
+    _check(load().itft_sqrt2(_dev_ptr(x), l, z, n, f, N, e, s, scale, _stream(stream)), "itft_sqrt2")
 
 
 def sn_tft(x, l, z, n, M, m, e=0, stride=None, stream=None):

@@ -33,10 +33,12 @@ static int64_t ceil_log2(int64_t v) {
   return l;
 }
 
-static int check_ring(int l, int64_t N) {
+static int check_ring(int l, int64_t N, int mode = RING_FERMAT) {
   if (N < 64 || N % 64 != 0) return fail(ZX_EINVAL, "N must be a positive multiple of 64");
   if (l < 1 || l > 30) return fail(ZX_EINVAL, "l out of range");
-  if ((2 * N) % (int64_t(1) << l) != 0) return fail(ZX_EINVAL, "L = 2^l must divide 2N (omega_L = 2^(2N/L))");
+  if (omega_order(N, mode) % (int64_t(1) << l) != 0)
+    return fail(ZX_EINVAL, mode == RING_SQRT2 ? "L = 2^l must divide 4N (omega_L = sqrt2^(4N/L))"
+                                              : "L = 2^l must divide 2N (omega_L = 2^(2N/L))");
   if (!ring_supported(N))
     return fail(ZX_EUNSUPPORTED, "N must be <= 1024 (multiple of 64) or a multiple of 1024 up to 32768");
   return ZX_OK;
@@ -54,14 +56,14 @@ static int check_sizes(int kind, int l, int64_t z, int64_t n, int f) {
 }
 
 static int transform(int kind, uint64_t *x, int l, int64_t z, int64_t n, int f, int64_t N, int64_t e,
-                     int64_t stride_limbs, int scale, void *stream) {
-  int rc = check_ring(l, N);
+                     int64_t stride_limbs, int scale, void *stream, int mode = RING_FERMAT) {
+  int rc = check_ring(l, N, mode);
   if (rc) return rc;
   if (!x) return fail(ZX_EINVAL, "x is NULL");
   if (stride_limbs < N / 64 + 1) return fail(ZX_EINVAL, "stride_limbs < N/64 + 1");
   if ((rc = check_sizes(kind, l, z, n, f))) return rc;
   int err = ZX_OK;
-  const TransformPlan *p = get_transform_plan(kind, l, z, n, f, N, e, stride_limbs, scale, &err);
+  const TransformPlan *p = get_transform_plan(kind, l, z, n, f, N, e, stride_limbs, scale, &err, mode);
   if (!p) return err ? fail(err, "planning failed") : fail(ZX_ECUDA, "planning failed");
   cudaError_t ce = run_transform(*p, x, stride_limbs, cudaStream_t(stream));
   if (ce != cudaSuccess) return cuda_fail(ce, "transform launch");
@@ -70,6 +72,7 @@ static int transform(int kind, uint64_t *x, int l, int64_t z, int64_t n, int f, 
 
 struct ZxPlan {
   int l;
+  int mode;  // RING_FERMAT, or RING_SQRT2 when omega = sqrt2 allows a smaller ring
   int64_t N, n, nf, stride, limbs_h, L;
   Ring ring;
 };
@@ -82,10 +85,19 @@ static int make_zx_plan(int64_t lf, int64_t bf, int64_t lg, int64_t bg, int sgn,
   if (l > 16) return fail(ZX_EUNSUPPORTED, "product length above 65536");
   int64_t L = int64_t(1) << l;
   int64_t need = bf + bg + ceil_log2(std::min(lf, lg)) + (sgn ? 1 : 0);
-  int64_t align = std::max<int64_t>(need <= 1024 ? 64 : 1024, L / 2);
+  // omega = 2 needs L | 2N; omega = sqrt2 (4 | N) needs only L | 4N, a ring up to half the size
+  const int64_t unit = need <= 1024 ? 64 : 1024;
+  const int64_t align = std::max<int64_t>(unit, L / 2), align4 = std::max<int64_t>(unit, L / 4);
   int64_t N = (need + align - 1) / align * align;
+  const int64_t N4 = (need + align4 - 1) / align4 * align4;
+  int mode = RING_FERMAT;
+  if (N4 < N && ring_supported(N4)) {
+    N = N4;
+    mode = RING_SQRT2;
+  }
   if (!ring_supported(N)) return fail(ZX_EUNSUPPORTED, "product needs a ring above 2^32768 + 1");
   zp->l = int(l);
+  zp->mode = mode;
   zp->N = N;
   zp->n = n;
   zp->nf = zero_padded_outputs(int(l), n, N);
@@ -151,6 +163,7 @@ int device_product(const zx_poly *f, const zx_poly *g, zx_poly *h, BatchProduct 
   b->n = zp.n;
   b->nf = zp.nf;
   b->stride = zp.stride;
+  b->mode = zp.mode;
   return ZX_OK;
 }
 
@@ -174,6 +187,16 @@ int itft_ex(uint64_t *x, int l, int64_t z, int64_t n, int f, int64_t N, int64_t 
   return transform(KIND_ITFT, x, l, z, n, f, N, e, stride_limbs, scale, stream);
 }
 
+int tft_sqrt2(uint64_t *x, int l, int64_t z, int64_t n, int64_t N, int64_t e, int64_t stride_limbs, void *stream) {
+  return transform(KIND_TFT, x, l, z, n, 0, N, e, stride_limbs, 0, stream, RING_SQRT2);
+}
+
+int itft_sqrt2(uint64_t *x, int l, int64_t z, int64_t n, int f, int64_t N, int64_t e, int64_t stride_limbs,
+               int scale, void *stream) {
+  if (scale != 0 && scale != 1) return fail(ZX_EINVAL, "scale must be 0 or 1");
+  return transform(KIND_ITFT, x, l, z, n, f, N, e, stride_limbs, scale, stream, RING_SQRT2);
+}
+
 int itft(uint64_t *x, int l, int64_t n, int64_t N, void *stream) {
   return transform(KIND_ITFT, x, l, n, n, 0, N, 0, N / 64 + 1, 1, stream);
 }
@@ -181,7 +204,7 @@ int itft(uint64_t *x, int l, int64_t n, int64_t N, void *stream) {
 int zx_transform_plan(int kind, int l, int64_t z, int64_t n, int f, int64_t N, zx_transform_info *out) {
   if (!out) return fail(ZX_EINVAL, "out is NULL");
   if (kind != KIND_TFT && kind != KIND_ITFT) return fail(ZX_EINVAL, "kind must be 0 (TFT) or 1 (ITFT)");
-  int rc = check_ring(l, N);
+  int rc = check_ring(l, N, RING_SQRT2);  // the shape is the same for omega = 2 and sqrt2
   if (rc) return rc;
   if ((rc = check_sizes(kind, l, z, n, f))) return rc;
   std::memset(out, 0, sizeof *out);
@@ -197,17 +220,19 @@ int zx_transform_plan(int kind, int l, int64_t z, int64_t n, int f, int64_t N, z
   return ZX_OK;
 }
 
-int zx_job_program(int kind, int ls, int lc, int64_t z, int64_t n, int f, int64_t N, uint32_t *buf,
+int zx_job_program(int kind, int ls, int lc, int64_t z, int64_t n, int f, int64_t N, int mode, uint32_t *buf,
                    int64_t cap_words, int64_t *size_words) {
   if (!size_words) return fail(ZX_EINVAL, "size_words is NULL");
   if (kind != KIND_TFT && kind != KIND_ITFT) return fail(ZX_EINVAL, "kind must be 0 (TFT) or 1 (ITFT)");
+  if (mode != RING_FERMAT && mode != RING_SN && mode != RING_SQRT2) return fail(ZX_EINVAL, "mode must be 0, 1 or 2");
   if (lc < 0 || lc > kMaxClusterLog2 || ls < 1 || ls - lc < lc || ls - lc < 1 || ls > 16)
     return fail(ZX_EINVAL, "need 1 <= ls <= 16 and 0 <= lc <= 4 with 2 lc <= ls");
-  if (N < 64 || N % 64 != 0 || (2 * N) % (int64_t(1) << ls) != 0)
-    return fail(ZX_EINVAL, "N must be a multiple of 64 with 2^ls | 2N");
+  if (mode == RING_SN ? (N < 1 || (N & (N - 1)) != 0) : (N < 64 || N % 64 != 0))
+    return fail(ZX_EINVAL, "N must be a multiple of 64 (a power of two for mode 1)");
+  if (omega_order(N, mode) % (int64_t(1) << ls) != 0) return fail(ZX_EINVAL, "2^ls must divide the order of omega");
   int rc = check_sizes(kind, ls, z, n, f);
   if (rc) return rc;
-  std::vector<uint32_t> img = build_job_image(kind, ls, lc, z, n, f, N, nullptr);
+  std::vector<uint32_t> img = build_job_image(kind, ls, lc, z, n, f, N, nullptr, mode);
   *size_words = int64_t(img.size());
   if (!buf || cap_words < int64_t(img.size())) return fail(ZX_EBUFSIZE, "buffer too small for the job image");
   std::memcpy(buf, img.data(), img.size() * 4);
@@ -230,6 +255,7 @@ int zx_plan(int64_t len_f, int64_t bits_f, int64_t len_g, int64_t bits_g, int is
   out->tft_passes = count_passes(KIND_TFT, zp.l, zp.nf, zp.nf, 0, zp.N);
   out->itft_passes = count_passes(KIND_ITFT, zp.l, zp.nf, zp.nf, 0, zp.N);
   out->n_fft = zp.nf;
+  out->sqrt2 = zp.mode == RING_SQRT2 ? 1 : 0;
   return ZX_OK;
 }
 
@@ -273,9 +299,11 @@ int zx_mul(const zx_poly *f, const zx_poly *g, zx_poly *h, void *stream) {
   }
   cudaError_t ce;
   int err = ZX_OK;
-  const TransformPlan *pf = get_transform_plan(KIND_TFT, zp.l, f->len, zp.nf, 0, zp.N, 0, zp.stride, 0, &err);
-  const TransformPlan *pg = pf ? get_transform_plan(KIND_TFT, zp.l, g->len, zp.nf, 0, zp.N, 0, zp.stride, 0, &err) : nullptr;
-  const TransformPlan *pi = pg ? get_transform_plan(KIND_ITFT, zp.l, zp.nf, zp.nf, 0, zp.N, 0, zp.stride, 1, &err) : nullptr;
+  const TransformPlan *pf = get_transform_plan(KIND_TFT, zp.l, f->len, zp.nf, 0, zp.N, 0, zp.stride, 0, &err, zp.mode);
+  const TransformPlan *pg =
+      pf ? get_transform_plan(KIND_TFT, zp.l, g->len, zp.nf, 0, zp.N, 0, zp.stride, 0, &err, zp.mode) : nullptr;
+  const TransformPlan *pi =
+      pg ? get_transform_plan(KIND_ITFT, zp.l, zp.nf, zp.nf, 0, zp.N, 0, zp.stride, 1, &err, zp.mode) : nullptr;
   if (!pi) {
     cleanup();
     return fail(err ? err : ZX_ECUDA, "planning failed");

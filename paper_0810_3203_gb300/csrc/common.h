@@ -34,6 +34,12 @@ enum OpFlags : uint8_t {
   OPF_COPY = 16,   // OP_TAG: copy x_i into x_j
 };
 
+// Rings of a program: Z/(2^N+1) with omega = 2 (order 2N), S[y]/(y^N+1) with omega = y (order
+// M = 2N), Z/(2^N+1) with omega = sqrt2 = 2^{3N/4} - 2^{N/4} (order 4N). Rotation amounts of
+// programs, jobs and cell tags are exponents of omega.
+enum RingMode : int { RING_FERMAT = 0, RING_SN = 1, RING_SQRT2 = 2 };
+TFT_HD inline int64_t omega_order(int64_t N, int mode) { return mode == RING_SQRT2 ? 4 * N : 2 * N; }
+
 // Scalar flags of an op (OpDesc::pad), used over S[y]/(y^{M/2}+1) only, where the ITFT base
 // case's factors 2 and 1/2 are not powers of omega: A (x_i, or the tagged cell of OP_TAG) is
 // doubled or halved as it is read, S is halved as it is written.

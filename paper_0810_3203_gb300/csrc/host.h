@@ -20,16 +20,17 @@ struct ProgramStats {
 };
 
 // Program image for a sub-transform of length 2^ls held entirely on chip (see common.h).
-// sn: programs for S[y]/(y^{N}+1) (2N = M), where doublings and halvings are scalar flags.
+// mode (RingMode): RING_SN programs are for S[y]/(y^{N}+1) (2N = M), where doublings and
+// halvings are scalar flags; RING_SQRT2 programs take exponents of sqrt2 (mod 4N).
 std::vector<uint32_t> build_program(int kind, int ls, int64_t z, int64_t n, int f, int64_t N,
-                                    ProgramStats *stats, bool sn = false);
+                                    ProgramStats *stats, int mode = RING_FERMAT);
 
 // Job image (stage table plus per-CTA programs, see common.h) for a job of 2^ls cells on a
 // cluster of 2^lc CTAs.
 // Largest per-CTA program (words) in a job image.
 int image_max_program_words(const std::vector<uint32_t> &img);
 std::vector<uint32_t> build_job_image(int kind, int ls, int lc, int64_t z, int64_t n, int f, int64_t N,
-                                      ProgramStats *stats, bool sn = false);
+                                      ProgramStats *stats, int mode = RING_FERMAT);
 
 // Ring geometry used by the kernels.
 struct Ring {
@@ -81,6 +82,7 @@ struct Launch {
 
 struct TransformPlan {
   Ring ring;
+  int mode = RING_FERMAT;  // RingMode of the rotation amounts
   std::vector<Launch> launches;  // in stream order
   int npasses = 0;
   int64_t njobs = 0;
@@ -89,7 +91,8 @@ struct TransformPlan {
 // Cached plan of TFT (kind = KIND_TFT) or ITFT for the given parameters; nullptr with *err set
 // on failure. escale < 0 means no final scaling.
 const TransformPlan *get_transform_plan(int kind, int l, int64_t z, int64_t n, int f, int64_t N,
-                                        int64_t e, int64_t stride_limbs, int scale, int *err);
+                                        int64_t e, int64_t stride_limbs, int scale, int *err,
+                                        int mode = RING_FERMAT);
 
 // Outputs a product's transforms compute when the product length n is padded with known zero
 // coefficients up to a whole number of rows of the top-level split (Sec. 6): the ITFT then has
@@ -118,7 +121,7 @@ struct HostPlan {
   std::vector<std::vector<uint32_t>> programs;
 };
 void build_host_plan(int kind, int l, int64_t z, int64_t n, int f, int64_t N, int64_t e, int scale,
-                     HostPlan *out);
+                     HostPlan *out, int mode = RING_FERMAT);
 
 // Plans over S[y]/(y^{M/2}+1), H = M/2 coefficients per element (single-CTA jobs; the ITFT's
 // final division by L is escale = l halvings). nullptr with *err set on failure.
@@ -175,6 +178,7 @@ struct BatchProduct {
   int64_t len_f = 0, len_g = 0, limbs_f = 0, limbs_g = 0, limbs_h = 0;
   int32_t signed_f = 0, signed_g = 0, sgn = 0, l = 0;
   int64_t N = 0, n = 0, nf = 0, stride = 0;  // nf: zero-padded transform outputs
+  int mode = RING_FERMAT;                      // omega = 2, or sqrt2 (RING_SQRT2)
 };
 // Checks one product of device operands and fills *b (api.cu); ZX_* status with the error
 // text set on failure. h->limbs is overwritten with the needed count on ZX_EBUFSIZE.
@@ -187,6 +191,7 @@ int run_mul_batch(const std::vector<BatchProduct> &items, cudaStream_t s, std::s
 // byte offsets into a descriptor image that is copied to the device as one block.
 struct BatchGroup {
   Ring ring;
+  int mode = RING_FERMAT;
   int64_t stride = 0;
   int count = 0;
   int64_t max_len = 0, max_n = 0;

@@ -118,14 +118,15 @@ struct ImageCache {
     return it == prog_words.end() ? 0 : it->second;
   }
 
-  const uint32_t *get(int kind, int ls, int lc, int64_t z, int64_t n, int f, int64_t N, int *err, bool sn = false) {
+  const uint32_t *get(int kind, int ls, int lc, int64_t z, int64_t n, int f, int64_t N, int *err,
+                      int mode = RING_FERMAT) {
     int dev = 0;
     cudaGetDevice(&dev);
-    auto key = std::make_tuple(dev, kind, ls, lc, z, n, f, N, sn ? 1 : 0);
+    auto key = std::make_tuple(dev, kind, ls, lc, z, n, f, N, mode);
     std::lock_guard<std::mutex> lk(mu);
     auto it = images.find(key);
     if (it != images.end()) return it->second;
-    std::vector<uint32_t> img = build_job_image(kind, ls, lc, z, n, f, N, nullptr, sn);
+    std::vector<uint32_t> img = build_job_image(kind, ls, lc, z, n, f, N, nullptr, mode);
     uint32_t *d = nullptr;
     if (cudaMalloc(&d, img.size() * 4) != cudaSuccess) {
       *err = ZX_ENOMEM;
@@ -166,9 +167,12 @@ struct Planner {
   PlanConfig cfg;
   std::vector<JobRec> jobs;
 
-  explicit Planner(int64_t N, const PlanConfig *c = nullptr) {
+  int mode;   // RingMode: twoN is the order of omega (2N, or 4N for sqrt2)
+
+  explicit Planner(int64_t N, const PlanConfig *c = nullptr, int mode_ = RING_FERMAT) {
     ring = make_ring(N);
-    twoN = 2 * N;
+    mode = mode_;
+    twoN = omega_order(N, mode_);
     cfg = c ? *c : plan_config(N);
     ls_max = cfg.ls_max;
     ls_c = cfg.ls_c;
@@ -329,14 +333,19 @@ void plan_shape(int kind, int l, int64_t z, int64_t n, int f, int64_t N, int *pa
   *cluster_l = lcmax;
 }
 
+// the exponent of 1/L in powers of omega (2^{-l} = omega^{-l u}, u = 1, or 2 for sqrt2)
+static int64_t inv_l_exponent(int l, int64_t twoN, int mode) {
+  return md(twoN - int64_t(l) * (mode == RING_SQRT2 ? 2 : 1), twoN);
+}
+
 void build_host_plan(int kind, int l, int64_t z, int64_t n, int f, int64_t N, int64_t e, int scale,
-                     HostPlan *out) {
-  int64_t twoN = 2 * N;
+                     HostPlan *out, int mode) {
+  const int64_t twoN = omega_order(N, mode);
   e = md(e, twoN);
-  Planner P(N);
+  Planner P(N, nullptr, mode);
   out->ring = P.ring;
   out->npasses = kind == KIND_TFT ? P.tft(0, 0, 1, l, e, z, n)
-                                  : P.itft(0, 0, 1, l, e, z, n, f, scale ? md(twoN - l, twoN) : -1);
+                                  : P.itft(0, 0, 1, l, e, z, n, f, scale ? inv_l_exponent(l, twoN, mode) : -1);
   std::map<std::tuple<int, int, int, int64_t, int64_t, int>, int> index;
   std::stable_sort(P.jobs.begin(), P.jobs.end(), launch_order);
   for (size_t i = 0; i < P.jobs.size();) {
@@ -354,7 +363,7 @@ void build_host_plan(int kind, int l, int64_t z, int64_t n, int f, int64_t N, in
       int pi;
       if (it == index.end()) {
         pi = int(out->programs.size());
-        out->programs.push_back(build_job_image(j.kind, j.ls, j.lc, j.z, j.n, j.f, N, nullptr));
+        out->programs.push_back(build_job_image(j.kind, j.ls, j.lc, j.z, j.n, j.f, N, nullptr, mode));
         index[key] = pi;
       } else {
         pi = it->second;
@@ -369,13 +378,13 @@ void build_host_plan(int kind, int l, int64_t z, int64_t n, int f, int64_t N, in
 }
 
 const TransformPlan *get_transform_plan(int kind, int l, int64_t z, int64_t n, int f, int64_t N,
-                                        int64_t e, int64_t stride_limbs, int scale, int *err) {
+                                        int64_t e, int64_t stride_limbs, int scale, int *err, int mode) {
   int dev = 0;
   cudaGetDevice(&dev);
-  int64_t twoN = 2 * N;
+  const int64_t twoN = omega_order(N, mode);
   e = md(e, twoN);
   const PlanConfig cfg = plan_config(N);
-  const int cfg_key = cfg.ls_max | (cfg.ls_c << 5) | (cfg.max_warps << 10) | (cfg.split << 16);
+  const int cfg_key = cfg.ls_max | (cfg.ls_c << 5) | (cfg.max_warps << 10) | (cfg.split << 16) | (mode << 20);
   auto key = std::make_tuple(dev, kind, l, z, n, f, N, e, scale, cfg_key);
   PlanCache &pc = plan_cache();
   {
@@ -383,20 +392,21 @@ const TransformPlan *get_transform_plan(int kind, int l, int64_t z, int64_t n, i
     auto it = pc.plans.find(key);
     if (it != pc.plans.end()) return it->second.get();
   }
-  Planner P(N, &cfg);
+  Planner P(N, &cfg, mode);
   int npass;
   if (kind == KIND_TFT)
     npass = P.tft(0, 0, 1, l, e, z, n);
   else
-    npass = P.itft(0, 0, 1, l, e, z, n, f, scale ? md(twoN - l, twoN) : -1);
+    npass = P.itft(0, 0, 1, l, e, z, n, f, scale ? inv_l_exponent(l, twoN, mode) : -1);
 
   std::unique_ptr<TransformPlan> plan(new TransformPlan());
   plan->ring = P.ring;
+  plan->mode = mode;
   plan->npasses = npass;
   plan->njobs = int64_t(P.jobs.size());
   // resolve job images, then group jobs by (pass, ls, lc) in pass order
   for (JobRec &j : P.jobs) {
-    j.d.image = image_cache().get(j.kind, j.ls, j.lc, j.z, j.n, j.f, N, err);
+    j.d.image = image_cache().get(j.kind, j.ls, j.lc, j.z, j.n, j.f, N, err, mode);
     if (!j.d.image) return nullptr;
   }
   std::stable_sort(P.jobs.begin(), P.jobs.end(), launch_order);
@@ -489,7 +499,7 @@ const TransformPlan *get_sn_plan(int kind, int l, int64_t z, int64_t n, int f, i
       *err = ZX_EUNSUPPORTED;
       return nullptr;
     }
-    j.d.image = image_cache().get(j.kind, j.ls, j.lc, j.z, j.n, j.f, H, err, true);
+    j.d.image = image_cache().get(j.kind, j.ls, j.lc, j.z, j.n, j.f, H, err, RING_SN);
     if (!j.d.image) return nullptr;
   }
   std::stable_sort(P.jobs.begin(), P.jobs.end(), launch_order);

@@ -33,9 +33,10 @@ struct SymE {
 // Emits the base cases of Algorithm 1 / 2 on cell indices base + i * stride.
 class ProgGen {
  public:
-  // sn: the ring is S[y]/(y^{M/2}+1) (twoN = M, omega = y); there 2 is not a power of omega, so
-  // the ITFT base case's doublings and halvings become scalar flags (OPS_*) instead of rotations
-  ProgGen(int64_t twoN, int policy, bool sn = false) : twoN_(twoN), policy_(policy), sn_(sn) {}
+  // mode RING_SN: the ring is S[y]/(y^{M/2}+1) (twoN = M, omega = y); there 2 is not a power of
+  // omega, so the ITFT base case's doublings and halvings become scalar flags (OPS_*) instead of
+  // rotations. RING_SQRT2: omega = sqrt2 over Z/(2^N+1) (twoN = 4N), so 2 = omega^2.
+  ProgGen(int64_t twoN, int policy, int mode = RING_FERMAT) : twoN_(twoN), policy_(policy), mode_(mode) {}
 
   std::vector<OpDesc> ops;
 
@@ -76,8 +77,10 @@ class ProgGen {
       int c0 = base, c1 = base + stride;
       // doubling / halving: 2 = omega and 1/2 = omega^{2N-1} over Z/(2^N+1); scalar flags
       // over S[y]/(y^{M/2}+1)
-      const SymE two = sn_ ? zero() : cst(1), half = sn_ ? zero() : cst(twoN_ - 1);
-      const uint16_t a2 = sn_ ? OPS_A_DOUBLE : 0, ah = sn_ ? OPS_A_HALVE : 0, sh = sn_ ? OPS_S_HALVE : 0;
+      const bool sn = mode_ == RING_SN;
+      const int64_t u = mode_ == RING_SQRT2 ? 2 : 1;  // the exponent of 2 in powers of omega
+      const SymE two = sn ? zero() : cst(u), half = sn ? zero() : cst(twoN_ - u);
+      const uint16_t a2 = sn ? OPS_A_DOUBLE : 0, ah = sn ? OPS_A_HALVE : 0, sh = sn ? OPS_S_HALVE : 0;
       if (n == 2) {
         push(OP_BF, c0, c1, OPF_S | OPF_D, zero(), neg(E), zero(), zero());
       } else if (n == 1 && f == 1 && z == 2) {
@@ -115,7 +118,7 @@ class ProgGen {
  private:
   int64_t twoN_;
   int policy_;
-  bool sn_;
+  int mode_;
 
   int split(int l) const { return policy_ == 0 ? 1 : l / 2; }
   int64_t md(int64_t a) const {
@@ -175,11 +178,11 @@ std::vector<uint32_t> level_and_pack(const std::vector<OpDesc> &ops, int nslots,
 // Generate with both split policies (through `emit`) and keep the image with fewer levels.
 // `slot` maps a generated cell index to the local slot of the CTA that runs the program.
 std::vector<uint32_t> best_program(int64_t twoN, int nslots, const std::function<void(ProgGen &)> &emit,
-                                   const std::function<int(int)> &slot, ProgramStats *stats, bool sn = false) {
+                                   const std::function<int(int)> &slot, ProgramStats *stats, int mode = RING_FERMAT) {
   std::vector<uint32_t> best;
   int best_lev = -1;
   for (int policy = 0; policy < 2; policy++) {
-    ProgGen g(twoN, policy, sn);
+    ProgGen g(twoN, policy, mode);
     emit(g);
     if (g.ops.empty()) return {};
     for (OpDesc &o : g.ops) {
@@ -203,20 +206,20 @@ std::vector<uint32_t> best_program(int64_t twoN, int nslots, const std::function
 }  // namespace
 
 std::vector<uint32_t> build_program(int kind, int ls, int64_t z, int64_t n, int f, int64_t N,
-                                    ProgramStats *stats, bool sn) {
-  int64_t twoN = 2 * N;
+                                    ProgramStats *stats, int mode) {
+  const int64_t twoN = omega_order(N, mode);
   auto emit = [&](ProgGen &g) {
     if (kind == KIND_TFT)
       g.tft(0, 1, ls, {1, 0}, z, n);
     else
       g.itft(0, 1, ls, {1, 0}, z, n, f);
   };
-  return best_program(twoN, 1 << ls, emit, [](int c) { return c; }, stats, sn);
+  return best_program(twoN, 1 << ls, emit, [](int c) { return c; }, stats, mode);
 }
 
 std::vector<uint32_t> build_job_image(int kind, int ls, int lc, int64_t z, int64_t n, int f, int64_t N,
-                                      ProgramStats *stats, bool sn) {
-  const int64_t twoN = 2 * N;
+                                      ProgramStats *stats, int mode) {
+  const int64_t twoN = omega_order(N, mode);
   const int C = 1 << lc;
   struct Stage {
     uint32_t type, arg;
@@ -225,7 +228,7 @@ std::vector<uint32_t> build_job_image(int kind, int ls, int lc, int64_t z, int64
   std::vector<Stage> stages;
   uint32_t load_layout = LAYOUT_ROW, store_layout = LAYOUT_ROW;
   if (lc == 0) {
-    Stage s{STAGE_PROG, 0, {build_program(kind, ls, z, n, f, N, stats, sn)}};
+    Stage s{STAGE_PROG, 0, {build_program(kind, ls, z, n, f, N, stats, mode)}};
     stages.push_back(std::move(s));
   } else {
     const int l2 = ls - lc;
@@ -242,7 +245,7 @@ std::vector<uint32_t> build_job_image(int kind, int ls, int lc, int64_t z, int64
         auto e = [&](ProgGen &g) { emit(g, c); };
         s.progs.push_back(best_program(twoN, nslots, e, cols ? std::function<int(int)>(col_slot)
                                                               : std::function<int(int)>(row_slot),
-                                       stats));
+                                       stats, mode));
       }
       stages.push_back(std::move(s));
     };

@@ -451,6 +451,83 @@ __device__ __forceinline__ int smem_read_raw(uint32_t (&r)[K], const uint32_t *c
   return 0;
 }
 
+// r = r - rotc(m, E) - bin over this lane's chunk, as one borrow chain (E in [0, 2N), m the
+// cell's N-bit storage form): the rotated words come out of the same two-run window as in
+// smem_read_raw and feed subc directly, so the second operand needs no register array.
+// Returns the borrow out of the chunk. Lanes >= G subtract nothing.
+template <int K>
+__device__ __forceinline__ uint32_t smem_sub_rotated(uint32_t (&r)[K], const uint32_t *cell, int E, uint32_t bin,
+                                                     const Geo &g) {
+  if (g.lane >= g.G) return 0u;
+  uint32_t d, bout;
+  asm volatile("sub.cc.u32 %0, 0, %1;" : "=r"(d) : "r"(bin));
+  if (E == 0) {
+    const int b = phys(K * g.lane);
+#pragma unroll
+    for (int s = 0; s < K; s++) asm volatile("subc.cc.u32 %0, %0, %1;" : "+r"(r[s]) : "r"(cell[b + s]));
+  } else {
+    const bool low_wrapped = E < g.N;
+    const int Ep = low_wrapped ? E : E - g.N;
+    const int q = Ep >> 5, sh = Ep & 31;
+    const int lam0 = K * g.lane - q - 1;
+    const int i0 = lam0 < 0 ? lam0 + g.NW : lam0;
+    int tb, baseA, baseB;
+    if (g.NW >= 32) {
+      const int c0 = i0 & 31, r0 = i0 >> 5, rows = g.NW >> 5;
+      const int r1 = (r0 + 1 == rows) ? 0 : r0 + 1;
+      tb = 31 - c0;
+      baseA = 33 * r0 + c0;
+      baseB = 33 * r1 + c0 - 32;
+    } else {
+      tb = g.NW - 1 - i0;
+      baseA = i0;
+      baseB = i0 - g.NW;
+    }
+    const uint32_t flip = low_wrapped ? 0u : TFT_FULL;
+    const uint32_t mA = (lam0 < 0 ? TFT_FULL : 0u) ^ flip;
+    const uint32_t mB = (lam0 + tb + 1 < 0 ? TFT_FULL : 0u) ^ flip;
+    uint32_t prev = cell[0 <= tb ? baseA : baseB] ^ (0 <= tb ? mA : mB);
+#pragma unroll
+    for (int s = 0; s < K; s++) {
+      const int t = s + 1;
+      const bool inA = t <= tb;
+      const uint32_t cur = cell[(inA ? baseA : baseB) + t] ^ (inA ? mA : mB);
+      const uint32_t w = sh ? __funnelshift_l(prev, cur, sh) : cur;
+      asm volatile("subc.cc.u32 %0, %0, %1;" : "+r"(r[s]) : "r"(w));
+      prev = cur;
+    }
+  }
+  asm volatile("subc.u32 %0, 0, 0;" : "=r"(bout));
+  return bout & 1u;
+}
+
+// raw form of x sqrt2^E over Z/(2^N+1), E in [0, 4N) (sqrt2 = 2^{3N/4} - 2^{N/4}): for even E
+// the rotation rotc(m, E/2); for odd E = 2h + 1, x 2^h sqrt2 = x 2^{h+3N/4} - x 2^{h+N/4}, whose
+// storage form is rotc(m, h + 3N/4) - rotc(m, h + N/4) - 1 (the +1 of x = m + 1 cancels), made
+// canonical. Returns 1 for the zero cell (r all ones), like smem_read_abs.
+template <int K>
+__device__ __forceinline__ int smem_read_pow(uint32_t (&r)[K], const uint32_t *cell, int zflag, int E,
+                                             const Geo &g) {
+  if (zflag) {
+    set_ones<K>(r, g);
+    return 1;
+  }
+  const int h = E >> 1;
+  if (!(E & 1)) return smem_read_abs<K>(r, cell, 0, h, g);
+  int e1 = h + 3 * (g.N >> 2), e2 = h + (g.N >> 2);
+  if (e1 >= g.twoN) e1 -= g.twoN;
+  if (e2 >= g.twoN) e2 -= g.twoN;
+  smem_read_abs<K>(r, cell, 0, e1, g);
+  const uint32_t bo = smem_sub_rotated<K>(r, cell, e2, g.lane == 0 ? 1u : 0u, g);
+  // r - T 2^N = r + T (mod 2^N + 1), T the borrow out of bit N
+  const uint32_t T = resolve_sub<K>(r, bo, g);
+  if (T && add_small<K>(r, 1u, g)) {  // r + 1 = 2^N would be the value 0: not for x != 0
+    set_ones<K>(r, g);
+    return 1;
+  }
+  return 0;
+}
+
 // ------------------------------------------------------------------ global memory cells
 // canonical x: words [0, NW) and the top limb (word NW holds its low half)
 template <int K>

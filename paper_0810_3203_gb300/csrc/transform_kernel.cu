@@ -20,13 +20,22 @@ namespace tftgpu {
 
 struct KGeo {
   Geo g;
-  uint32_t mask;  // 2N - 1 when 2N is a power of two, else 0
+  int ord;        // order of omega: 2N (omega = 2) or 4N (omega = sqrt2); exponents are mod ord
+  uint32_t mask;  // ord - 1 when ord is a power of two, else 0
 };
 
 __device__ __forceinline__ int rot_amount(RotA a, int e, const KGeo &k) {
   if (k.mask) return int((uint32_t(a.mul) * uint32_t(e) + uint32_t(a.add)) & k.mask);
-  long long v = ((long long)a.mul * e + a.add) % k.g.twoN;
+  long long v = ((long long)a.mul * e + a.add) % k.ord;
   return int(v);
+}
+
+// raw form of x omega^E (E in [0, ord)): a rotation for omega = 2, a power of sqrt2 otherwise
+template <int K, bool SQ>
+__device__ __forceinline__ int read_omega_pow(uint32_t (&r)[K], const uint32_t *cell, int zflag, int E,
+                                              const Geo &g) {
+  if (SQ) return smem_read_pow<K>(r, cell, zflag, E, g);
+  return smem_read_abs<K>(r, cell, zflag, E, g);
 }
 
 template <int K>
@@ -69,7 +78,7 @@ __device__ __forceinline__ int diff_to(uint32_t *dst, const uint32_t *acell, con
   return settle_smem<K>(ch, -int(bo), za - zb, g);
 }
 
-template <int K>
+template <int K, bool SQ>
 __device__ __forceinline__ void exec_op(const OpDesc &op, uint32_t *cells, uint32_t *meta, int P, int e,
                                         const KGeo &kg) {
   const Geo &g = kg.g;
@@ -81,12 +90,12 @@ __device__ __forceinline__ void exec_op(const OpDesc &op, uint32_t *cells, uint3
       uint32_t v[K];
       smem_load_plain<K>(v, ci, g);
       int tj = ti + rot_amount(op.rb, e, kg);
-      if (tj >= g.twoN) tj -= g.twoN;
+      if (tj >= kg.ord) tj -= kg.ord;
       __syncwarp();
       write_cell<K>(cj, meta + op.j, v, int(mi & 1u), tj, g);
     }
     int tn = ti + rot_amount(op.ra, e, kg);
-    if (tn >= g.twoN) tn -= g.twoN;
+    if (tn >= kg.ord) tn -= kg.ord;
     __syncwarp();
     if (g.lane == 0) meta[op.i] = (uint32_t(tn) << 1) | (mi & 1u);
     return;
@@ -94,18 +103,18 @@ __device__ __forceinline__ void exec_op(const OpDesc &op, uint32_t *cells, uint3
   // x_i 2^Ei (+-) x_j 2^Ej = 2^Ei (x_i (+-) x_j 2^(Ej - Ei)): read x_i without rotation and
   // x_j with the difference, and give the outputs Ei more pending rotation
   int Ei = int(mi >> 1) + rot_amount(op.ra, e, kg);
-  if (Ei >= g.twoN) Ei -= g.twoN;
+  if (Ei >= kg.ord) Ei -= kg.ord;
   int Ej = int(mj >> 1) + rot_amount(op.rb, e, kg);
-  if (Ej >= g.twoN) Ej -= g.twoN;
+  if (Ej >= kg.ord) Ej -= kg.ord;
   int Er = Ej - Ei;
-  if (Er < 0) Er += g.twoN;
+  if (Er < 0) Er += kg.ord;
   const int za = int(mi & 1u), zb = int(mj & 1u);
   uint32_t B[K];
-  smem_read_abs<K>(B, cj, zb, Er, g);
+  read_omega_pow<K, SQ>(B, cj, zb, Er, g);
   __syncwarp();
   auto pend = [&](RotA p) {
     int t = rot_amount(p, e, kg) + Ei;
-    return t >= g.twoN ? t - g.twoN : t;
+    return t >= kg.ord ? t - kg.ord : t;
   };
   if (op.kind == OP_BF) {
     // x_i is streamed from its cell: the difference goes first when it is written to cell j,
@@ -216,7 +225,7 @@ __device__ __forceinline__ OpDesc load_op_global(const uint32_t *p) {
   return o;
 }
 
-template <int K, bool STAGED>
+template <int K, bool STAGED, bool SQ>
 __device__ __forceinline__ void run_program(const uint32_t *pg, uint32_t *cells, uint32_t *meta, int P, int e,
                                             const KGeo &kg, int warp, int nw) {
   const int nlev = int(pg[0]);
@@ -226,7 +235,7 @@ __device__ __forceinline__ void run_program(const uint32_t *pg, uint32_t *cells,
     const int a = int(pg[2 + v]), b = int(pg[3 + v]);
     for (int o = a + warp; o < b; o += nw) {
       const OpDesc op = STAGED ? load_op_shared(ops + o * ow) : load_op_global(ops + o * ow);
-      exec_op<K>(op, cells, meta, P, e, kg);
+      exec_op<K, SQ>(op, cells, meta, P, e, kg);
     }
     __syncthreads();
   }
@@ -281,7 +290,7 @@ __device__ __forceinline__ void exchange(uint32_t *cells, uint32_t *meta, int P,
 // MINB = 3: jobs of at most 8 warps and 75 KB of shared memory, three CTAs per SM (registers
 // capped at 85 per thread); MINB = 1: up to 16 warps, one CTA per SM. FULL: all 32 lanes hold
 // words (NW = 32 K), which lets the compiler drop the idle-lane cases.
-template <int K, int MINB, bool FULL>
+template <int K, int MINB, bool FULL, bool SQ>
 __global__ void __launch_bounds__(MINB == 3 ? 256 : 512, MINB) job_kernel(uint64_t *__restrict__ x, int64_t stride_limbs,
                                                   const JobDesc *__restrict__ jobs, int N, int ls, int lc,
                                                   uint32_t mask, int prog_cap,
@@ -311,6 +320,7 @@ __global__ void __launch_bounds__(MINB == 3 ? 256 : 512, MINB) job_kernel(uint64
   kg.g.G = FULL ? 32 : kg.g.NW / K;
   kg.g.lane = threadIdx.x & 31;
   kg.g.twoN = 2 * N;
+  kg.ord = SQ ? 4 * N : 2 * N;
   kg.mask = mask;
   const Geo &g = kg.g;
   const int nslots = 1 << (ls - lc);
@@ -356,9 +366,9 @@ __global__ void __launch_bounds__(MINB == 3 ? 256 : 512, MINB) job_kernel(uint64
           uint2 *dst = reinterpret_cast<uint2 *>(pstage);
           for (int w = threadIdx.x; w < (words + 1) / 2; w += blockDim.x) dst[w] = __ldg(src + w);
           __syncthreads();
-          run_program<K, true>(pstage, cells, meta, P, jd.e, kg, warp, nw);
+          run_program<K, true, SQ>(pstage, cells, meta, P, jd.e, kg, warp, nw);
         } else {
-          run_program<K, false>(pg, cells, meta, P, jd.e, kg, warp, nw);
+          run_program<K, false, SQ>(pg, cells, meta, P, jd.e, kg, warp, nw);
         }
       }
     } else {
@@ -371,8 +381,9 @@ __global__ void __launch_bounds__(MINB == 3 ? 256 : 512, MINB) job_kernel(uint64
     const int m = job_cell(store_layout, rank, s, C, L2, b);
     if (m >= jd.nstore) continue;
     uint32_t r[K];
-    const int E = m < jd.nscale ? jd.escale : 0;
-    const int z = smem_read_raw<K>(r, cells + s * P, meta[s], E, g);
+    int E = int(meta[s] >> 1) + (m < jd.nscale ? jd.escale : 0);
+    if (E >= kg.ord) E -= kg.ord;
+    const int z = read_omega_pow<K, SQ>(r, cells + s * P, int(meta[s] & 1u), E, g);
     uint32_t top = 0;
     if (z) {
 #pragma unroll
@@ -391,16 +402,16 @@ __global__ void __launch_bounds__(MINB == 3 ? 256 : 512, MINB) job_kernel(uint64
 
 namespace {
 
-template <int K, int MINB, bool FULL>
+template <int K, int MINB, bool FULL, bool SQ>
 cudaError_t launch_km(const Launch &L, uint64_t *x, int64_t stride_limbs, const Ring &r, cudaStream_t s,
                       size_t smem, int prog_cap, uint32_t mask) {
   static thread_local int configured[8] = {0, 0, 0, 0, 0, 0, 0, 0};
   int dev = 0;
   cudaGetDevice(&dev);
   if (dev >= 8 || !configured[dev]) {
-    cudaError_t e = cudaFuncSetAttribute(job_kernel<K, MINB, FULL>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    cudaError_t e = cudaFuncSetAttribute(job_kernel<K, MINB, FULL, SQ>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(job_kernel<K, MINB, FULL>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    e = cudaFuncSetAttribute(job_kernel<K, MINB, FULL, SQ>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     if (e != cudaSuccess) return e;
     if (dev < 8) configured[dev] = 1;
   }
@@ -416,38 +427,39 @@ cudaError_t launch_km(const Launch &L, uint64_t *x, int64_t stride_limbs, const 
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = L.lc > 0 ? 1 : 0;
-  return cudaLaunchKernelEx(&cfg, job_kernel<K, MINB, FULL>, x, stride_limbs, (const JobDesc *)L.d_jobs, int(r.N), L.ls,
+  return cudaLaunchKernelEx(&cfg, job_kernel<K, MINB, FULL, SQ>, x, stride_limbs, (const JobDesc *)L.d_jobs, int(r.N), L.ls,
                             L.lc, mask, prog_cap, L.d_segs, L.nsegs);
 }
 
-template <int K>
+template <int K, bool SQ>
 cudaError_t launch_k(const Launch &L, uint64_t *x, int64_t stride_limbs, const Ring &r, cudaStream_t s) {
   const int nslots = 1 << (L.ls - L.lc);
   const size_t base_words = (size_t(nslots) * size_t(r.pitch) + size_t(nslots) + 1) & ~size_t(1);
   const size_t max_words = (227 * 1024) / 4;
   const int prog_cap = int(std::min<size_t>(size_t(L.prog_words), max_words > base_words ? max_words - base_words : 0));
   const size_t smem = (base_words + size_t(prog_cap)) * 4;
-  const uint32_t twoN = uint32_t(2 * r.N);
-  const uint32_t mask = (twoN & (twoN - 1)) == 0 ? twoN - 1 : 0u;
+  const uint32_t ord = uint32_t((SQ ? 4 : 2) * r.N);
+  const uint32_t mask = (ord & (ord - 1)) == 0 ? ord - 1 : 0u;
   if (L.nwarps <= 8 && smem <= 75 * 1024)
-    return r.G == 32 ? launch_km<K, 3, true>(L, x, stride_limbs, r, s, smem, prog_cap, mask)
-                     : launch_km<K, 3, false>(L, x, stride_limbs, r, s, smem, prog_cap, mask);
-  return r.G == 32 ? launch_km<K, 1, true>(L, x, stride_limbs, r, s, smem, prog_cap, mask)
-                   : launch_km<K, 1, false>(L, x, stride_limbs, r, s, smem, prog_cap, mask);
+    return r.G == 32 ? launch_km<K, 3, true, SQ>(L, x, stride_limbs, r, s, smem, prog_cap, mask)
+                     : launch_km<K, 3, false, SQ>(L, x, stride_limbs, r, s, smem, prog_cap, mask);
+  return r.G == 32 ? launch_km<K, 1, true, SQ>(L, x, stride_limbs, r, s, smem, prog_cap, mask)
+                   : launch_km<K, 1, false, SQ>(L, x, stride_limbs, r, s, smem, prog_cap, mask);
 }
 
 }  // namespace
 
 cudaError_t run_transform(const TransformPlan &p, uint64_t *x, int64_t stride_limbs, cudaStream_t s) {
+  const bool sq = p.mode == RING_SQRT2;
   for (const Launch &L : p.launches) {
     cudaError_t e;
     switch (p.ring.K) {
-      case 1: e = launch_k<1>(L, x, stride_limbs, p.ring, s); break;
-      case 2: e = launch_k<2>(L, x, stride_limbs, p.ring, s); break;
-      case 4: e = launch_k<4>(L, x, stride_limbs, p.ring, s); break;
-      case 8: e = launch_k<8>(L, x, stride_limbs, p.ring, s); break;
-      case 16: e = launch_k<16>(L, x, stride_limbs, p.ring, s); break;
-      case 32: e = launch_k<32>(L, x, stride_limbs, p.ring, s); break;
+      case 1: e = sq ? launch_k<1, true>(L, x, stride_limbs, p.ring, s) : launch_k<1, false>(L, x, stride_limbs, p.ring, s); break;
+      case 2: e = sq ? launch_k<2, true>(L, x, stride_limbs, p.ring, s) : launch_k<2, false>(L, x, stride_limbs, p.ring, s); break;
+      case 4: e = sq ? launch_k<4, true>(L, x, stride_limbs, p.ring, s) : launch_k<4, false>(L, x, stride_limbs, p.ring, s); break;
+      case 8: e = sq ? launch_k<8, true>(L, x, stride_limbs, p.ring, s) : launch_k<8, false>(L, x, stride_limbs, p.ring, s); break;
+      case 16: e = sq ? launch_k<16, true>(L, x, stride_limbs, p.ring, s) : launch_k<16, false>(L, x, stride_limbs, p.ring, s); break;
+      case 32: e = sq ? launch_k<32, true>(L, x, stride_limbs, p.ring, s) : launch_k<32, false>(L, x, stride_limbs, p.ring, s); break;
       default: return cudaErrorInvalidValue;
     }
     if (e != cudaSuccess) return e;

@@ -59,9 +59,9 @@ struct MergedSegs {
     int nwarps = 0, prog_words = 0, ctas = 0, njobs = 0;
   };
   std::map<std::tuple<int, int, int>, Acc> m;
-  int add(int kind, int l, int64_t z, int64_t n, int64_t N, int64_t stride, int64_t cell_off, int scale) {
+  int add(int kind, int l, int64_t z, int64_t n, int64_t N, int64_t stride, int64_t cell_off, int scale, int mode) {
     int err = ZX_OK;
-    const TransformPlan *p = get_transform_plan(kind, l, z, n, 0, N, 0, stride, scale, &err);
+    const TransformPlan *p = get_transform_plan(kind, l, z, n, 0, N, 0, stride, scale, &err, mode);
     if (!p) return err ? err : ZX_ECUDA;
     for (const Launch &L : p->launches) {
       Acc &a = m[std::make_tuple(L.pass, L.ls, L.lc)];
@@ -104,9 +104,10 @@ size_t product_pool_bytes(const BatchProduct &p) { return 2 * size_t(p.stride) *
 int layout_batch(const std::vector<BatchProduct> &items, const std::vector<int> &idx_in,
                  std::vector<unsigned char> *desc, BatchLayout *out, std::string *msg) {
   std::vector<int> idx(idx_in);
-  // by ring, largest rings first, then by transform length
+  // by ring (size, then omega), largest rings first, then by transform length
   std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) {
     if (items[a].N != items[b].N) return items[a].N > items[b].N;
+    if (items[a].mode != items[b].mode) return items[a].mode < items[b].mode;
     return items[a].l > items[b].l;
   });
   DescImage img;
@@ -116,10 +117,11 @@ int layout_batch(const std::vector<BatchProduct> &items, const std::vector<int> 
   size_t byte_off = 0;
   for (size_t a = 0; a < idx.size();) {
     size_t b = a;
-    while (b < idx.size() && items[idx[b]].N == items[idx[a]].N) b++;
+    while (b < idx.size() && items[idx[b]].N == items[idx[a]].N && items[idx[b]].mode == items[idx[a]].mode) b++;
     BatchGroup gd;
     const BatchProduct &p0 = items[idx[a]];
     gd.ring = make_ring(p0.N);
+    gd.mode = p0.mode;
     gd.stride = p0.stride;
     gd.count = int(b - a);
     std::vector<PackItem> pk;
@@ -141,9 +143,9 @@ int layout_batch(const std::vector<BatchProduct> &items, const std::vector<int> 
       gd.max_len = std::max(gd.max_len, std::max(p.len_f, p.len_g));
       gd.max_n = std::max(gd.max_n, p.nf);
       int rc;
-      if ((rc = mt.add(KIND_TFT, p.l, p.len_f, p.nf, p.N, p.stride, cf, 0)) ||
-          (rc = mt.add(KIND_TFT, p.l, p.len_g, p.nf, p.N, p.stride, cg, 0)) ||
-          (rc = mi.add(KIND_ITFT, p.l, p.nf, p.nf, p.N, p.stride, cf, 1))) {
+      if ((rc = mt.add(KIND_TFT, p.l, p.len_f, p.nf, p.N, p.stride, cf, 0, p.mode)) ||
+          (rc = mt.add(KIND_TFT, p.l, p.len_g, p.nf, p.N, p.stride, cg, 0, p.mode)) ||
+          (rc = mi.add(KIND_ITFT, p.l, p.nf, p.nf, p.N, p.stride, cf, 1, p.mode))) {
         *msg = "planning failed for product " + std::to_string(idx[t]);
         img.bytes.swap(*desc);
         return rc;
@@ -167,6 +169,7 @@ cudaError_t enqueue_group(const BatchGroup &gd, unsigned char *d_desc, unsigned 
   uint64_t *x = reinterpret_cast<uint64_t *>(pool);
   TransformPlan tp, ip;
   tp.ring = ip.ring = gd.ring;
+  tp.mode = ip.mode = gd.mode;
   for (Launch L : gd.tft) {
     L.d_segs = rebase(L.d_segs, d_desc);
     tp.launches.push_back(L);

@@ -81,15 +81,15 @@ uint64_t *plan_space(NoAllocDevice &st, size_t bytes) {
 }
 
 int plan_in_scratch(NoAllocDevice &st, int kind, int l, int64_t z, int64_t n, int f, int64_t N, int scale,
-                    cudaStream_t s, const TransformPlan **out) {
-  auto key = std::make_tuple(kind, l, z, n, f, N, int64_t(0), scale);
+                    int mode, cudaStream_t s, const TransformPlan **out) {
+  auto key = std::make_tuple(kind, l, z, n, f, N, int64_t(mode), scale);
   auto it = st.plans.find(key);
   if (it != st.plans.end()) {
     *out = it->second.get();
     return ZX_OK;
   }
   HostPlan hp;
-  build_host_plan(kind, l, z, n, f, N, 0, scale, &hp);
+  build_host_plan(kind, l, z, n, f, N, 0, scale, &hp, mode);
   size_t need = 0;
   for (const auto &img : hp.programs) need += (img.size() * 4 + 15) / 16 * 16;
   for (const auto &g : hp.groups) need += (g.jobs.size() * sizeof(JobDesc) + 15) / 16 * 16;
@@ -104,6 +104,7 @@ int plan_in_scratch(NoAllocDevice &st, int kind, int l, int64_t z, int64_t n, in
   }
   std::unique_ptr<TransformPlan> plan(new TransformPlan());
   plan->ring = hp.ring;
+  plan->mode = mode;
   plan->npasses = hp.npasses;
   for (auto &g : hp.groups) {
     for (size_t i = 0; i < g.jobs.size(); i++) g.jobs[i].image = dprog[g.prog_index[i]];
@@ -159,9 +160,10 @@ extern "C" int zx_mul_noalloc(const zx_poly *f, const zx_poly *g, zx_poly *h, vo
   NoAllocDevice *st = nullptr;
   if ((rc = device_state(&st))) return rc;
   const TransformPlan *pf = nullptr, *pg = nullptr, *pi = nullptr;
-  if ((rc = plan_in_scratch(*st, KIND_TFT, info.l, f->len, info.n_fft, 0, info.N, 0, s, &pf)) ||
-      (rc = plan_in_scratch(*st, KIND_TFT, info.l, g->len, info.n_fft, 0, info.N, 0, s, &pg)) ||
-      (rc = plan_in_scratch(*st, KIND_ITFT, info.l, info.n_fft, info.n_fft, 0, info.N, 1, s, &pi)))
+  const int mode = info.sqrt2 ? RING_SQRT2 : RING_FERMAT;
+  if ((rc = plan_in_scratch(*st, KIND_TFT, info.l, f->len, info.n_fft, 0, info.N, 0, mode, s, &pf)) ||
+      (rc = plan_in_scratch(*st, KIND_TFT, info.l, g->len, info.n_fft, 0, info.N, 0, mode, s, &pg)) ||
+      (rc = plan_in_scratch(*st, KIND_ITFT, info.l, info.n_fft, info.n_fft, 0, info.N, 1, mode, s, &pi)))
     return rc;
   uint64_t *F = st->base, *G = st->base + ring;
   const Ring &r = pf->ring;

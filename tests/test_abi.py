@@ -46,6 +46,18 @@ def test_plan_medium_product():
     assert p["tft_passes"] == 2 and p["itft_passes"] >= 2
 
 
+def test_sqrt2_halves_the_large_rings():
+    """With omega = sqrt2 (L | 4N) a product of length L needs a ring of L/4 bits: the mixed
+    batch's largest products run over Z/(2^16384+1) instead of Z/(2^32768+1)."""
+    import paper_0810_3203_gb300 as tg
+    p = tg.zx_plan(20000, 1024, 20000, 1024)
+    assert (p["l"], p["N"], p["sqrt2"]) == (16, 16384, 1)
+    p = tg.zx_plan(12000, 700, 9000, 700)
+    assert (p["l"], p["N"], p["sqrt2"]) == (15, 8192, 1)
+    p = tg.zx_plan(3000, 2000, 2500, 2000)  # 4012 bits needed: the ring is the same either way
+    assert (p["N"], p["sqrt2"]) == (4096, 0)
+
+
 def test_zero_padded_product_length():
     """Sec. 6: the product's length is padded with known zeros to whole rows of the top-level
     split, so the ITFT is the TFT's steps reversed: as many passes as the TFT, no last row."""
@@ -77,7 +89,10 @@ def test_plan_sizes_follow_the_ring_rule():
             continue
         p = tg.zx_plan(lf, bits, lg, bits)
         L = 1 << p["l"]
-        assert L >= lf + lg - 1 and (2 * p["N"]) % L == 0
+        # omega = 2 needs L | 2N; omega = sqrt2 (chosen when it allows a smaller ring) L | 4N
+        assert L >= lf + lg - 1 and ((4 if p["sqrt2"] else 2) * p["N"]) % L == 0
+        if p["sqrt2"]:
+            assert (2 * p["N"]) % L != 0  # only chosen where omega = 2 would need a bigger ring
         assert p["N"] >= 2 * bits + (min(lf, lg) - 1).bit_length()
         assert p["N"] <= 1024 or p["N"] % 1024 == 0
 

@@ -41,23 +41,79 @@ def ops_of(img, off):
     for k in range(nops):
         w = [int(v) for v in img[base + 10 * k:base + 10 * k + 10]]
         ops.append(dict(i=w[0] & 0xFFFF, j=w[0] >> 16, kind=w[1] & 0xFF, flags=(w[1] >> 8) & 0xFF,
-                        ra=(w[2], w[3]), rb=(w[4], w[5]), p0=(w[6], w[7]), p1=(w[8], w[9])))
+                        scal=w[1] >> 16, ra=(w[2], w[3]), rb=(w[4], w[5]), p0=(w[6], w[7]), p1=(w[8], w[9])))
     return starts, ops
 
 
-def run_image(img, ls, N, e, inputs, nload, nstore, nscale=0, escale=0):
-    """Execute a job image on Python integers; returns the stored cell values {cell: value}."""
-    p, twoN = (1 << N) + 1, 2 * N
+OPS_A_DOUBLE, OPS_A_HALVE, OPS_S_HALVE = 1, 2, 4
+
+
+class Fermat:
+    """Z/(2^N+1) with omega = 2 (mode 0) or omega = sqrt2 (mode 2); values are ints."""
+
+    def __init__(self, N, mode=0):
+        self.p, self.order = (1 << N) + 1, (4 if mode == 2 else 2) * N
+        self.w = ((1 << (3 * N // 4)) - (1 << (N // 4))) % self.p if mode == 2 else 2
+        self.zero = 0
+
+    def pow(self, v, t):
+        return v * pow(self.w, t % self.order, self.p) % self.p
+
+    def add(self, a, b):
+        return (a + b) % self.p
+
+    def sub(self, a, b):
+        return (a - b) % self.p
+
+    def scale(self, v, k):  # times 2^k, k in {-1, 1}
+        return v * pow(2, k, self.p) % self.p
+
+
+class SnRing:
+    """S[y]/(y^H+1), S = Z/mZ (mode 1); values are tuples of H ints."""
+
+    def __init__(self, H, m):
+        self.H, self.m, self.order = H, m, 2 * H
+        self.zero = (0,) * H
+
+    def pow(self, v, t):
+        t %= self.order
+        neg = t >= self.H
+        t -= self.H if neg else 0
+        out = [0] * self.H
+        for i, c in enumerate(v):
+            j, c2 = i + t, c
+            if j >= self.H:
+                j, c2 = j - self.H, -c
+            out[j] = (-c2 if neg else c2) % self.m
+        return tuple(out)
+
+    def add(self, a, b):
+        return tuple((x + y) % self.m for x, y in zip(a, b))
+
+    def sub(self, a, b):
+        return tuple((x - y) % self.m for x, y in zip(a, b))
+
+    def scale(self, v, k):
+        f = pow(2, k, self.m)
+        return tuple(x * f % self.m for x in v)
+
+
+def run_image(img, ls, N, e, inputs, nload, nstore, nscale=0, escale=0, ring=None):
+    """Execute a job image on Python values (ints mod 2^N+1 unless `ring` says otherwise);
+    returns the stored cell values {cell: value}. Scalar flags (mode 1) are applied as read."""
+    R = ring or Fermat(N)
+    twoN = R.order
     nst, C, load_l, store_l = (int(v) for v in img[:4])
     lc = C.bit_length() - 1
     nslots = 1 << (ls - lc)
     L2, b = nslots, nslots // C
     rot = lambda a: (a[0] * e + a[1]) % twoN
-    state = [[(0, 0)] * nslots for _ in range(C)]
+    state = [[(R.zero, 0)] * nslots for _ in range(C)]
     for c in range(C):
         for s in range(nslots):
             m = job_cell(load_l, c, s, C, L2, b)
-            state[c][s] = (inputs[m] if m < nload else 0, 0)
+            state[c][s] = (inputs[m] if m < nload else R.zero, 0)
     for st in range(nst):
         ent = 4 + st * (2 + C)
         typ, arg = int(img[ent]), int(img[ent + 1])
@@ -76,24 +132,28 @@ def run_image(img, ls, N, e, inputs, nload, nstore, nscale=0, escale=0):
                             touched.add(cell)
                         xi, ti = sc[o["i"]]
                         xj, tj = sc[o["j"]]
+                        sa = 1 if o["scal"] & OPS_A_DOUBLE else (-1 if o["scal"] & OPS_A_HALVE else 0)
                         if o["kind"] == OP_TAG:
                             if o["flags"] & OPF_COPY:
                                 sc[o["j"]] = (xi, (ti + rot(o["rb"])) % twoN)
-                            sc[o["i"]] = (xi, (ti + rot(o["ra"])) % twoN)
+                            sc[o["i"]] = (R.scale(xi, sa) if sa else xi, (ti + rot(o["ra"])) % twoN)
                             continue
-                        A = xi * pow(2, ti + rot(o["ra"]), p) % p
-                        B = xj * pow(2, tj + rot(o["rb"]), p) % p
+                        A = R.pow(xi, ti + rot(o["ra"]))
+                        if sa:
+                            A = R.scale(A, sa)
+                        B = R.pow(xj, tj + rot(o["rb"]))
                         if o["kind"] == OP_BF:
                             if o["flags"] & OPF_S:
                                 dst = o["j"] if o["flags"] & OPF_S_TO_J else o["i"]
-                                sc[dst] = ((A + B) % p, rot(o["p0"]))
+                                S = R.add(A, B)
+                                sc[dst] = (R.scale(S, -1) if o["scal"] & OPS_S_HALVE else S, rot(o["p0"]))
                             if o["flags"] & OPF_D:
                                 dst = o["i"] if o["flags"] & OPF_D_TO_I else o["j"]
-                                sc[dst] = ((A - B) % p, rot(o["p1"]))
+                                sc[dst] = (R.sub(A, B), rot(o["p1"]))
                         else:
-                            D = (A - B) % p
+                            D = R.sub(A, B)
                             sc[o["j"]] = (D, rot(o["p1"]))
-                            sc[o["i"]] = ((A + D) % p, 0)
+                            sc[o["i"]] = (R.add(A, D), 0)
         else:
             only = arg if typ == STAGE_SWAP else -1
             new = [list(row) for row in state]
@@ -111,7 +171,7 @@ def run_image(img, ls, N, e, inputs, nload, nstore, nscale=0, escale=0):
             if m < nstore:
                 x, t = state[c][s]
                 t += escale if m < nscale else 0
-                out[m] = x * pow(2, t, p) % p
+                out[m] = R.pow(x, t)
     return out
 
 
@@ -177,3 +237,58 @@ def test_cluster_job_every_itft_case(tg, orc):
                 img = tg.job_program(0, ls, lc, z, n, N)
                 got = run_image(img, ls, N, 7, vals, z, n)
                 assert [got[m] for m in range(n)] == oracle_tft(orc, vals, ls, z, n, 7, N), (z, n)
+
+
+@pytest.mark.parametrize("ls,lc", [(3, 0), (4, 2), (6, 3), (8, 4)])
+def test_sqrt2_images(tg, orc, ls, lc):
+    """Schedules with exponents of sqrt2 (mod 4N) at L = 4N: the odd powers appear."""
+    N = (1 << ls) // 4 if (1 << ls) >= 256 else 64
+    L = 1 << ls
+    R = Fermat(N, mode=2)
+    rng = random.Random(ls * 13 + lc)
+    for t in range(6):
+        z, n, e = rng.randint(1, L), rng.randint(1, L), rng.randrange(4 * N)
+        vals = [rng.randrange(R.p) for _ in range(z)]
+        img = tg.job_program(0, ls, lc, z, n, N, mode=2)
+        got = run_image(img, ls, N, e, vals, z, n, ring=R)
+        x = orc.cells_from_ints(vals, N, count=L)
+        orc.sqrt2_tft(x, ls, z, n, e, N)
+        assert [got[m] for m in range(n)] == orc.cells_to_ints(x, N, n), (z, n, e)
+        f = t % 2
+        nn = rng.randint(1 - f, z - f if z - f >= 1 - f else 1 - f)
+        nn = max(1 - f, min(nn, L - f, z))
+        img = tg.job_program(1, ls, lc, z, nn, N, f, mode=2)
+        esc = (4 * N - 2 * ls) % (4 * N)
+        got = run_image(img, ls, N, e, vals, z, nn + f, nscale=nn, escale=esc, ring=R)
+        x = orc.cells_from_ints(vals, N, count=L)
+        orc.sqrt2_itft(x, ls, z, nn, f, e, N)
+        ref = orc.cells_to_ints(x, N, nn + f)
+        scaled = [R.pow(v, esc) for v in ref[:nn]] + ref[nn:]
+        assert [got[m] for m in range(nn + f)] == scaled, (z, nn, f, e)
+
+
+@pytest.mark.parametrize("ls", [2, 3, 4, 5])
+def test_sn_images(tg, orc, ls):
+    """Schedules over S[y]/(y^H+1): rotations are negacyclic shifts, and the ITFT base case's
+    doublings and halvings are scalar flags."""
+    M, m = 32, 65537
+    H, L = M // 2, 1 << ls
+    R = SnRing(H, m)
+    rng = random.Random(ls)
+    for t in range(6):
+        z = rng.randint(1, L)
+        e = rng.randrange(M)
+        vals = [tuple(rng.randrange(m) for _ in range(H)) for _ in range(z)]
+        f = t % 2
+        n = max(1 - f, min(rng.randint(0, z), L - f))
+        img = tg.job_program(1, ls, 0, z, n, H, f, mode=1)
+        got = run_image(img, ls, H, e, vals, z, n + f, ring=R)
+        x = orc.sn_cells([list(v) for v in vals], M, count=L)
+        orc.sn_itft(x, ls, z, n, f, e, M, m)
+        assert [list(got[i]) for i in range(n + f)] == orc.sn_vals(x, M, n + f), (z, n, f, e)
+        nt = rng.randint(1, L)
+        img = tg.job_program(0, ls, 0, z, nt, H, mode=1)
+        got = run_image(img, ls, H, e, vals, z, nt, ring=R)
+        x = orc.sn_cells([list(v) for v in vals], M, count=L)
+        orc.sn_tft(x, ls, z, nt, e, M, m)
+        assert [list(got[i]) for i in range(nt)] == orc.sn_vals(x, M, nt), (z, nt, e)
