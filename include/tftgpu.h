@@ -216,7 +216,8 @@ int zx_server_destroy(zx_server *srv);
  * the split L1 = 2^floor(l/2) for cache reasons; every configuration computes the same
  * outputs). Candidates: cells per CTA of a cluster job (2^3 .. 2^6), the largest job held by one
  * CTA (the shared-memory limit, or the size at which three CTAs share an SM), warps per CTA
- * (8 or 16) and, for odd l, the top-level split floor or ceil(l/2). For each candidate the call
+ * (8 or 16) and, for odd l, the top-level split floor or ceil(l/2). The round trips use
+ * omega = 2 when L | 2N, else omega = sqrt2 (L | 4N), the transforms products use. For each candidate the call
  * times `reps` TFT + ITFT round trips (Algorithm 1, then Algorithm 2 with the division by L)
  * of length n over the caller's device buffer x (L = 2^l cells of stride_limbs >= N/64 + 1
  * limbs holding canonical residues; the round trips restore it), keeps the fastest for every

@@ -351,7 +351,9 @@ int zx_mul_batch(const zx_poly *fs, const zx_poly *gs, zx_poly *hs, int count, v
 int zx_tune(uint64_t *x, int l, int64_t n, int64_t N, int64_t stride_limbs, int reps, void *stream,
             zx_tune_info *out) {
   if (!out || !x) return fail(ZX_EINVAL, "x or out is NULL");
-  int rc = check_ring(l, N);
+  // the round trips use omega = 2 when L | 2N, else omega = sqrt2 (L | 4N), as products do
+  const int mode = (2 * N) % (int64_t(1) << (l < 1 ? 1 : l)) == 0 ? RING_FERMAT : RING_SQRT2;
+  int rc = check_ring(l, N, mode);
   if (rc) return rc;
   if ((rc = check_sizes(KIND_TFT, l, n, n, 0))) return rc;
   if (stride_limbs < N / 64 + 1) return fail(ZX_EINVAL, "stride_limbs < N/64 + 1");
@@ -382,8 +384,8 @@ int zx_tune(uint64_t *x, int l, int64_t n, int64_t N, int64_t stride_limbs, int 
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return fail(ZX_ECUDA, "event");
   auto round_trip = [&]() {
-    int q = transform(KIND_TFT, x, l, n, n, 0, N, 0, stride_limbs, 0, stream);
-    return q ? q : transform(KIND_ITFT, x, l, n, n, 0, N, 0, stride_limbs, 1, stream);
+    int q = transform(KIND_TFT, x, l, n, n, 0, N, 0, stride_limbs, 0, stream, mode);
+    return q ? q : transform(KIND_ITFT, x, l, n, n, 0, N, 0, stride_limbs, 1, stream, mode);
   };
   float best = 1e30f, def_ms = -1.0f;
   PlanConfig chosen = before;

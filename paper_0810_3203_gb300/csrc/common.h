@@ -101,7 +101,7 @@ struct JobDesc {
   int32_t nstore;
   int32_t nscale;
   int32_t escale;
-  int32_t pad;
+  int32_t pad;  // log2 of the job's cells (0: the launch's ls); single-CTA launches mix sizes
 };
 static_assert(sizeof(JobDesc) == 48, "JobDesc layout");
 

@@ -206,6 +206,7 @@ struct Planner {
     j.d.nstore = int32_t(n + f);
     j.d.nscale = int32_t(nscale);
     j.d.escale = int32_t(escale);
+    j.d.pad = l;  // the job's own size (launches mix single-CTA jobs of different sizes)
     jobs.push_back(j);
   }
 
@@ -272,11 +273,15 @@ PlanCache &plan_cache() {
 
 namespace {
 
-bool same_launch(const JobRec &a, const JobRec &b) { return a.pass == b.pass && a.ls == b.ls && a.lc == b.lc; }
+// Jobs of one pass share a launch: single-CTA jobs of every size together (each job carries its
+// own size, the launch is sized for the largest), cluster jobs by size.
+bool same_launch(const JobRec &a, const JobRec &b) {
+  return a.pass == b.pass && a.lc == b.lc && (a.lc == 0 || a.ls == b.ls);
+}
 bool launch_order(const JobRec &a, const JobRec &b) {
   if (a.pass != b.pass) return a.pass < b.pass;
-  if (a.ls != b.ls) return a.ls < b.ls;
-  return a.lc < b.lc;
+  if (a.lc != b.lc) return a.lc < b.lc;
+  return a.ls < b.ls;
 }
 
 }  // namespace
@@ -352,7 +357,7 @@ void build_host_plan(int kind, int l, int64_t z, int64_t n, int f, int64_t N, in
     size_t k = i;
     while (k < P.jobs.size() && same_launch(P.jobs[k], P.jobs[i])) k++;
     HostPlan::Group g;
-    g.ls = P.jobs[i].ls;
+    g.ls = P.jobs[k - 1].ls;  // the largest job of the launch
     g.lc = P.jobs[i].lc;
     g.nwarps = warps_for_job(g.ls, g.lc, P.cfg.max_warps);
     g.prog_words = 0;
@@ -417,7 +422,7 @@ const TransformPlan *get_transform_plan(int kind, int l, int64_t z, int64_t n, i
     while (k < P.jobs.size() && same_launch(P.jobs[k], P.jobs[i])) k++;
     Launch L;
     L.pass = P.jobs[i].pass;
-    L.ls = P.jobs[i].ls;
+    L.ls = P.jobs[k - 1].ls;  // sorted by size within the launch: the largest
     L.lc = P.jobs[i].lc;
     L.njobs = int(k - i);
     L.nwarps = warps_for_job(L.ls, L.lc, P.cfg.max_warps);
@@ -510,7 +515,7 @@ const TransformPlan *get_sn_plan(int kind, int l, int64_t z, int64_t n, int f, i
     while (k < P.jobs.size() && same_launch(P.jobs[k], P.jobs[i])) k++;
     Launch L;
     L.pass = P.jobs[i].pass;
-    L.ls = P.jobs[i].ls;
+    L.ls = P.jobs[k - 1].ls;
     L.lc = 0;
     L.njobs = int(k - i);
     L.nwarps = warps_for_job(L.ls, 0, cfg.max_warps);

@@ -323,7 +323,7 @@ __global__ void __launch_bounds__(MINB == 3 ? 256 : 512, MINB) job_kernel(uint64
   kg.ord = SQ ? 4 * N : 2 * N;
   kg.mask = mask;
   const Geo &g = kg.g;
-  const int nslots = 1 << (ls - lc);
+  const int nslots = 1 << ((jd.pad > 0 ? jd.pad : ls) - lc);
   const int L2 = nslots, b = nslots / C;
   const int P = cell_pitch_words(g.NW);
   uint32_t *cells = smem;

@@ -93,3 +93,18 @@ def test_tune_restores_buffer_and_keeps_fastest(tg, orc):
         assert np.array_equal(cells(got, n, W), cells(ref, n, W))
     finally:
         tg.config_set(N)
+
+
+def test_tune_sqrt2_ring(tg):
+    """L = 4N: the tuner times the omega = sqrt2 transforms products use on that ring."""
+    N, l, n = 1024, 12, 3000
+    W = N // 64 + 1
+    x = workloads.residues(78, n, N, cells=1 << l)
+    d = torch.from_numpy(x.view(np.int64)).cuda()
+    try:
+        info = tg.tune(d, l, n, N, reps=1)
+        torch.cuda.synchronize()
+        assert info["best_ms"] > 0
+        assert np.array_equal(cells(d.cpu().numpy().view(np.uint64), n, W), cells(x, n, W))
+    finally:
+        tg.config_set(N)
