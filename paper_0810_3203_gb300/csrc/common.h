@@ -116,10 +116,12 @@ struct Segment {
 };
 static_assert(sizeof(Segment) == 24, "Segment layout");
 
-// shared-memory geometry of one cell: NW = N/32 words, one padding word per 32 so that the
-// lane-chunked accesses of a warp hit 32 different banks, rounded up to 16 bytes so that every
-// cell can be copied as a block of 16-byte vectors
-TFT_HD inline int cell_pitch_words(int NW) { return (NW + NW / 32 + 1 + 3) & ~3; }
+// shared-memory geometry of one cell: NW = N/32 words. Rings of more than 64 words (4 or more
+// words per lane; NW is then a multiple of 32) pad each 32-word row to 36 words, which keeps
+// 16-byte vector accesses aligned and free of bank conflicts; smaller rings pad one word per
+// 32 (scalar accesses of a warp on 32 different banks), rounded up to 16 bytes so that every
+// cell can be copied as a block of 16-byte vectors.
+TFT_HD inline int cell_pitch_words(int NW) { return NW > 64 ? (NW / 32) * 36 : (NW + NW / 32 + 1 + 3) & ~3; }
 
 // words per lane (K) for a ring of NW 32-bit words: 1 for NW <= 32, else NW/32 rounded up to
 // a power of two (NW is a multiple of 32 then)

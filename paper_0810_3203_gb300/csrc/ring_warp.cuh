@@ -184,72 +184,107 @@ __device__ __forceinline__ uint32_t canon_x(uint32_t (&r)[K], int v, const Geo &
 }
 
 // ------------------------------------------------------------------ chains into shared memory
+// One group of GW (4 or 8) words of a carry (ADD) or borrow (SUB) chain, o = a +- b[g0 ..] +- c,
+// as one asm block: the chain's carry is kept in the register c between groups (c enters as
+// zero / nonzero and leaves as the carry 0/1, or the borrow 0 / all ones), so that two chains
+// can advance in turns. The outputs are early-clobber: each is written while later inputs of
+// the block are still to be read.
+template <int GW, bool SUB, int K>
+__device__ __forceinline__ void chain_group(uint32_t (&o)[GW], const uint32_t (&a)[GW], const uint32_t (&b)[K],
+                                            int g0, uint32_t &c) {
+  if constexpr (GW == 8) {
+    if (SUB)
+      asm volatile(
+          "{\n\t.reg .u32 t;\n\tsub.cc.u32 t, 0, %8;\n\t"
+          "subc.cc.u32 %0, %9, %17;\n\tsubc.cc.u32 %1, %10, %18;\n\t"
+          "subc.cc.u32 %2, %11, %19;\n\tsubc.cc.u32 %3, %12, %20;\n\t"
+          "subc.cc.u32 %4, %13, %21;\n\tsubc.cc.u32 %5, %14, %22;\n\t"
+          "subc.cc.u32 %6, %15, %23;\n\tsubc.cc.u32 %7, %16, %24;\n\t"
+          "subc.u32 %8, 0, 0;\n\t}"
+          : "=&r"(o[0]), "=&r"(o[1]), "=&r"(o[2]), "=&r"(o[3]), "=&r"(o[4]), "=&r"(o[5]), "=&r"(o[6]), "=&r"(o[7]), "+r"(c)
+          : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(a[4]), "r"(a[5]), "r"(a[6]), "r"(a[7]), "r"(b[g0]),
+            "r"(b[g0 + 1]), "r"(b[g0 + 2]), "r"(b[g0 + 3]), "r"(b[g0 + 4]), "r"(b[g0 + 5]), "r"(b[g0 + 6]),
+            "r"(b[g0 + 7]));
+    else
+      asm volatile(
+          "{\n\t.reg .u32 t;\n\tadd.cc.u32 t, %8, 0xffffffff;\n\t"
+          "addc.cc.u32 %0, %9, %17;\n\taddc.cc.u32 %1, %10, %18;\n\t"
+          "addc.cc.u32 %2, %11, %19;\n\taddc.cc.u32 %3, %12, %20;\n\t"
+          "addc.cc.u32 %4, %13, %21;\n\taddc.cc.u32 %5, %14, %22;\n\t"
+          "addc.cc.u32 %6, %15, %23;\n\taddc.cc.u32 %7, %16, %24;\n\t"
+          "addc.u32 %8, 0, 0;\n\t}"
+          : "=&r"(o[0]), "=&r"(o[1]), "=&r"(o[2]), "=&r"(o[3]), "=&r"(o[4]), "=&r"(o[5]), "=&r"(o[6]), "=&r"(o[7]), "+r"(c)
+          : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(a[4]), "r"(a[5]), "r"(a[6]), "r"(a[7]), "r"(b[g0]),
+            "r"(b[g0 + 1]), "r"(b[g0 + 2]), "r"(b[g0 + 3]), "r"(b[g0 + 4]), "r"(b[g0 + 5]), "r"(b[g0 + 6]),
+            "r"(b[g0 + 7]));
+  } else {
+    if (SUB)
+      asm volatile(
+          "{\n\t.reg .u32 t;\n\tsub.cc.u32 t, 0, %4;\n\t"
+          "subc.cc.u32 %0, %5, %9;\n\tsubc.cc.u32 %1, %6, %10;\n\t"
+          "subc.cc.u32 %2, %7, %11;\n\tsubc.cc.u32 %3, %8, %12;\n\t"
+          "subc.u32 %4, 0, 0;\n\t}"
+          : "=&r"(o[0]), "=&r"(o[1]), "=&r"(o[2]), "=&r"(o[3]), "+r"(c)
+          : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[g0]), "r"(b[g0 + 1]), "r"(b[g0 + 2]), "r"(b[g0 + 3]));
+    else
+      asm volatile(
+          "{\n\t.reg .u32 t;\n\tadd.cc.u32 t, %4, 0xffffffff;\n\t"
+          "addc.cc.u32 %0, %5, %9;\n\taddc.cc.u32 %1, %6, %10;\n\t"
+          "addc.cc.u32 %2, %7, %11;\n\taddc.cc.u32 %3, %8, %12;\n\t"
+          "addc.u32 %4, 0, 0;\n\t}"
+          : "=&r"(o[0]), "=&r"(o[1]), "=&r"(o[2]), "=&r"(o[3]), "+r"(c)
+          : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[g0]), "r"(b[g0 + 1]), "r"(b[g0 + 2]), "r"(b[g0 + 3]));
+  }
+}
+
+// GW words of a 16-byte aligned shared-memory chunk (all ones for a_ones)
+template <int GW>
+__device__ __forceinline__ void load_group(uint32_t (&a)[GW], const uint32_t *src, bool a_ones) {
+#pragma unroll
+  for (int v = 0; v < GW / 4; v++) {
+    const uint4 q = a_ones ? make_uint4(TFT_FULL, TFT_FULL, TFT_FULL, TFT_FULL)
+                           : reinterpret_cast<const uint4 *>(src)[v];
+    a[4 * v] = q.x;
+    a[4 * v + 1] = q.y;
+    a[4 * v + 2] = q.z;
+    a[4 * v + 3] = q.w;
+  }
+}
+
+template <int GW>
+__device__ __forceinline__ void store_group(uint32_t *dst, const uint32_t (&o)[GW]) {
+#pragma unroll
+  for (int v = 0; v < GW / 4; v++)
+    reinterpret_cast<uint4 *>(dst)[v] = make_uint4(o[4 * v], o[4 * v + 1], o[4 * v + 2], o[4 * v + 3]);
+}
+
 // dst = a + b + cin (ADD) or a - b - cin (SUB) over this lane's chunk, where a is read from
 // the shared-memory chunk `asrc` (or is all ones when a_ones: the zero cell's raw form) and b
-// sits in registers. Works in groups of up to 8 words: the group's loads issued together, then
-// its chained add/sub and stores, so a needs no register array. Each group's accesses use one
-// base address and immediate offsets. asrc and dst may be the same chunk. Returns the carry
-// (ADD) or borrow (SUB) out of the chunk.
+// sits in registers. K >= 4: groups of 8 words (4 for K = 4) read and written as 16-byte
+// vectors, so a needs no register array; K <= 2: scalar words. asrc and dst may be the same
+// chunk. Returns the carry (ADD) or borrow (SUB) out of the chunk.
 template <int K, bool SUB>
 __device__ __forceinline__ uint32_t chain_stream(uint32_t *dst, const uint32_t *asrc, bool a_ones,
                                                  const uint32_t (&b)[K], uint32_t cin) {
-  const uint32_t da = (uint32_t)__cvta_generic_to_shared(dst);
-  const uint32_t sa = (uint32_t)__cvta_generic_to_shared(asrc);
-  uint32_t d, cout;
-  if (SUB)
-    asm volatile("sub.cc.u32 %0, 0, %1;" : "=r"(d) : "r"(cin));
-  else
-    asm volatile("add.cc.u32 %0, %1, 0xffffffff;" : "=r"(d) : "r"(cin));
-  if (K >= 8) {
+  if constexpr (K >= 4) {
+    constexpr int GW = K >= 8 ? 8 : 4;
+    uint32_t c = cin;
 #pragma unroll
-    for (int g0 = 0; g0 < K; g0 += 8) {
-      const uint32_t sg = sa + 4u * g0, dg = da + 4u * g0;
-      uint32_t a0, a1, a2, a3, a4, a5, a6, a7;
-      if (a_ones) {
-        a0 = a1 = a2 = a3 = a4 = a5 = a6 = a7 = 0xffffffffu;
-      } else {
-        asm volatile(
-            "ld.shared.u32 %0, [%8];\n\t"
-            "ld.shared.u32 %1, [%8+4];\n\t"
-            "ld.shared.u32 %2, [%8+8];\n\t"
-            "ld.shared.u32 %3, [%8+12];\n\t"
-            "ld.shared.u32 %4, [%8+16];\n\t"
-            "ld.shared.u32 %5, [%8+20];\n\t"
-            "ld.shared.u32 %6, [%8+24];\n\t"
-            "ld.shared.u32 %7, [%8+28];"
-            : "=r"(a0), "=r"(a1), "=r"(a2), "=r"(a3), "=r"(a4), "=r"(a5), "=r"(a6), "=r"(a7)
-            : "r"(sg));
-      }
-      if (SUB)
-        asm volatile(
-            "{\n\t.reg .u32 w;\n\t"
-            "subc.cc.u32 w, %0, %8;\n\tst.shared.u32 [%16], w;\n\t"
-            "subc.cc.u32 w, %1, %9;\n\tst.shared.u32 [%16+4], w;\n\t"
-            "subc.cc.u32 w, %2, %10;\n\tst.shared.u32 [%16+8], w;\n\t"
-            "subc.cc.u32 w, %3, %11;\n\tst.shared.u32 [%16+12], w;\n\t"
-            "subc.cc.u32 w, %4, %12;\n\tst.shared.u32 [%16+16], w;\n\t"
-            "subc.cc.u32 w, %5, %13;\n\tst.shared.u32 [%16+20], w;\n\t"
-            "subc.cc.u32 w, %6, %14;\n\tst.shared.u32 [%16+24], w;\n\t"
-            "subc.cc.u32 w, %7, %15;\n\tst.shared.u32 [%16+28], w;\n\t}"
-            ::"r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(a4), "r"(a5), "r"(a6), "r"(a7), "r"(b[g0]), "r"(b[g0 + 1]),
-            "r"(b[g0 + 2]), "r"(b[g0 + 3]), "r"(b[g0 + 4]), "r"(b[g0 + 5]), "r"(b[g0 + 6]), "r"(b[g0 + 7]), "r"(dg)
-            : "memory");
-      else
-        asm volatile(
-            "{\n\t.reg .u32 w;\n\t"
-            "addc.cc.u32 w, %0, %8;\n\tst.shared.u32 [%16], w;\n\t"
-            "addc.cc.u32 w, %1, %9;\n\tst.shared.u32 [%16+4], w;\n\t"
-            "addc.cc.u32 w, %2, %10;\n\tst.shared.u32 [%16+8], w;\n\t"
-            "addc.cc.u32 w, %3, %11;\n\tst.shared.u32 [%16+12], w;\n\t"
-            "addc.cc.u32 w, %4, %12;\n\tst.shared.u32 [%16+16], w;\n\t"
-            "addc.cc.u32 w, %5, %13;\n\tst.shared.u32 [%16+20], w;\n\t"
-            "addc.cc.u32 w, %6, %14;\n\tst.shared.u32 [%16+24], w;\n\t"
-            "addc.cc.u32 w, %7, %15;\n\tst.shared.u32 [%16+28], w;\n\t}"
-            ::"r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(a4), "r"(a5), "r"(a6), "r"(a7), "r"(b[g0]), "r"(b[g0 + 1]),
-            "r"(b[g0 + 2]), "r"(b[g0 + 3]), "r"(b[g0 + 4]), "r"(b[g0 + 5]), "r"(b[g0 + 6]), "r"(b[g0 + 7]), "r"(dg)
-            : "memory");
+    for (int g0 = 0; g0 < K; g0 += GW) {
+      uint32_t a[GW], o[GW];
+      load_group<GW>(a, asrc + g0, a_ones);
+      chain_group<GW, SUB, K>(o, a, b, g0, c);
+      store_group<GW>(dst + g0, o);
     }
+    return SUB ? (c & 1u) : c;
   } else {
+    const uint32_t da = (uint32_t)__cvta_generic_to_shared(dst);
+    const uint32_t sa = (uint32_t)__cvta_generic_to_shared(asrc);
+    uint32_t d, cout;
+    if (SUB)
+      asm volatile("sub.cc.u32 %0, 0, %1;" : "=r"(d) : "r"(cin));
+    else
+      asm volatile("add.cc.u32 %0, %1, 0xffffffff;" : "=r"(d) : "r"(cin));
     uint32_t a[K];
 #pragma unroll
     for (int k = 0; k < K; k++) {
@@ -267,13 +302,35 @@ __device__ __forceinline__ uint32_t chain_stream(uint32_t *dst, const uint32_t *
         asm volatile("addc.cc.u32 %0, %1, %2;" : "=r"(w) : "r"(a[k]), "r"(b[k]));
       asm volatile("st.shared.u32 [%0], %1;" ::"r"(da + 4u * k), "r"(w) : "memory");
     }
+    if (SUB) {
+      asm volatile("subc.u32 %0, 0, 0;" : "=r"(cout));
+      return cout & 1u;
+    }
+    asm volatile("addc.u32 %0, 0, 0;" : "=r"(cout));
+    return cout;
   }
-  if (SUB) {
-    asm volatile("subc.u32 %0, 0, 0;" : "=r"(cout));
-    return cout & 1u;
+}
+
+// Both outputs of a butterfly in one pass over a (K >= 4): per group of words, the group of a is
+// read once, then D = a - b - cin and S = a + b + cin each advance by one group and are stored
+// (the two chains take turns on the one carry flag). dS or dD may be the chunk of a: each group
+// is read before it is written. Sets the carry out of S and the borrow out of D.
+template <int K>
+__device__ __forceinline__ void bf_stream(uint32_t *dS, uint32_t *dD, const uint32_t *asrc, bool a_ones,
+                                          const uint32_t (&b)[K], uint32_t cin, uint32_t &cS, uint32_t &bD) {
+  constexpr int GW = K >= 8 ? 8 : 4;
+  uint32_t c = cin, d = cin;
+#pragma unroll
+  for (int g0 = 0; g0 < K; g0 += GW) {
+    uint32_t a[GW], o[GW];
+    load_group<GW>(a, asrc + g0, a_ones);
+    chain_group<GW, true, K>(o, a, b, g0, d);
+    store_group<GW>(dD + g0, o);
+    chain_group<GW, false, K>(o, a, b, g0, c);
+    store_group<GW>(dS + g0, o);
   }
-  asm volatile("addc.u32 %0, 0, 0;" : "=r"(cout));
-  return cout;
+  cS = c;
+  bD = d & 1u;
 }
 
 // Rest of settle_smem once some carry has survived the first word of a chunk: c (-1, 0 or +1)
@@ -347,27 +404,104 @@ __device__ __forceinline__ int settle_smem(uint32_t *chunk, int cout, int v0, co
 }
 
 // ------------------------------------------------------------------ shared-memory cells
-// word w of a cell sits at w + w/32 (one pad word per 32 keeps lane chunks on distinct banks)
-__device__ __forceinline__ int phys(int w) { return w + (w >> 5); }
+// Rings of K >= 4 words per lane: word w of a cell sits at w + 4 (w / 32) (rows of 32 words
+// padded to 36), so every lane chunk and every aligned group of 4 words starts on a 16-byte
+// boundary, and the 8 lanes of a quarter warp that touch one 16-byte vector each in 8
+// consecutive rows hit 8 distinct groups of banks: all cell accesses are 16-byte vectors.
+// Rings of K <= 2 words per lane: w + w / 32 (one pad word per 32 keeps the scalar accesses of
+// a warp on 32 distinct banks).
+template <int K>
+__device__ __forceinline__ int phys(int w) {
+  return K >= 4 ? w + ((w >> 5) << 2) : w + (w >> 5);
+}
 
 template <int K>
 __device__ __forceinline__ void smem_store_plain(uint32_t *cell, const uint32_t (&r)[K], const Geo &g) {
   if (g.lane < g.G) {
-    int b = phys(K * g.lane);
+    const int b = phys<K>(K * g.lane);
+    if constexpr (K >= 4) {
+      uint4 *p = reinterpret_cast<uint4 *>(cell + b);
 #pragma unroll
-    for (int s = 0; s < K; s++) cell[b + s] = r[s];
+      for (int v = 0; v < K / 4; v++) p[v] = make_uint4(r[4 * v], r[4 * v + 1], r[4 * v + 2], r[4 * v + 3]);
+    } else {
+#pragma unroll
+      for (int s = 0; s < K; s++) cell[b + s] = r[s];
+    }
   }
 }
 
 template <int K>
 __device__ __forceinline__ void smem_load_plain(uint32_t (&r)[K], const uint32_t *cell, const Geo &g) {
   if (g.lane < g.G) {
-    int b = phys(K * g.lane);
+    const int b = phys<K>(K * g.lane);
+    if constexpr (K >= 4) {
+      const uint4 *p = reinterpret_cast<const uint4 *>(cell + b);
 #pragma unroll
-    for (int s = 0; s < K; s++) r[s] = cell[b + s];
+      for (int v = 0; v < K / 4; v++) {
+        const uint4 q = p[v];
+        r[4 * v] = q.x;
+        r[4 * v + 1] = q.y;
+        r[4 * v + 2] = q.z;
+        r[4 * v + 3] = q.w;
+      }
+    } else {
+#pragma unroll
+      for (int s = 0; s < K; s++) r[s] = cell[b + s];
+    }
   } else {
 #pragma unroll
     for (int s = 0; s < K; s++) r[s] = 0u;
+  }
+}
+
+// The rotated window of this lane for rotc(m, E') (K >= 4, E' = Ep + flip N with Ep in [0, N)):
+// output word s (word K lane + s of the result) is the funnel shift of window words s and
+// s + 1, where window word 0 has logical index lam0 = K lane - q - 1 (q = Ep / 32; a negative
+// index wrapped past 2^N = -1 and is complemented, and for flip all the others are instead).
+// The window starts u = lam0 mod 4 words into an aligned 16-byte vector; u is the same in
+// every lane (K and NW are multiples of 4), so the window is read as K/4 + 1 aligned vectors
+// and u picks one of four unrolled copies of the shift loop. The vectors lie in at most two
+// 32-word rows, tA of them in the first; the wrap point (logical index 0) falls on a vector
+// boundary, so each vector has a single complement mask. emit(s, word) receives the output
+// words in order s = 0 .. K-1.
+template <int K, int U, class Emit>
+__device__ __forceinline__ void rot_window_u(const uint32_t *cell, int baseA, int baseB, int tA, int lamA,
+                                             uint32_t flip, int sh, Emit &emit) {
+  constexpr int V = K / 4 + 1;
+  uint32_t w[4 * V];
+#pragma unroll
+  for (int t = 0; t < V; t++) {
+    const uint4 v = *reinterpret_cast<const uint4 *>(cell + (t < tA ? baseA : baseB) + 4 * t);
+    const uint32_t m = (lamA + 4 * t < 0 ? TFT_FULL : 0u) ^ flip;
+    w[4 * t] = v.x ^ m;
+    w[4 * t + 1] = v.y ^ m;
+    w[4 * t + 2] = v.z ^ m;
+    w[4 * t + 3] = v.w ^ m;
+    // the outputs whose upper source word is in this vector
+#pragma unroll
+    for (int s = 0; s < K; s++)
+      if (U + s + 1 >= 4 * t && U + s + 1 < 4 * t + 4) emit(s, __funnelshift_l(w[U + s], w[U + s + 1], sh));
+  }
+}
+
+template <int K, class Emit>
+__device__ __forceinline__ void rot_window(const uint32_t *cell, int E, const Geo &g, Emit &emit) {
+  const bool low_wrapped = E < g.N;  // complement the wrapped bits (else the others)
+  const int Ep = low_wrapped ? E : E - g.N;
+  const int q = Ep >> 5, sh = Ep & 31;
+  const int lam0 = K * g.lane - q - 1;
+  const int u = lam0 & 3;
+  const int a = (lam0 < 0 ? lam0 + g.NW : lam0) - u;  // aligned start, in [0, NW)
+  const int r0 = a >> 5, c0 = a & 31, rows = g.NW >> 5;
+  const int r1 = (r0 + 1 == rows) ? 0 : r0 + 1;
+  const int tA = (32 - c0) >> 2;
+  const int baseA = 36 * r0 + c0, baseB = 36 * r1 - 4 * tA;
+  const uint32_t flip = low_wrapped ? 0u : TFT_FULL;
+  switch (u) {
+    case 0: rot_window_u<K, 0>(cell, baseA, baseB, tA, lam0, flip, sh, emit); break;
+    case 1: rot_window_u<K, 1>(cell, baseA, baseB, tA, lam0 - 1, flip, sh, emit); break;
+    case 2: rot_window_u<K, 2>(cell, baseA, baseB, tA, lam0 - 2, flip, sh, emit); break;
+    default: rot_window_u<K, 3>(cell, baseA, baseB, tA, lam0 - 3, flip, sh, emit); break;
   }
 }
 
@@ -376,9 +510,10 @@ __device__ __forceinline__ void smem_load_plain(uint32_t (&r)[K], const uint32_t
 //
 // Output word j of lane l (j = K l + s) is the funnel shift of source words j - q - 1 and
 // j - q (q = E' / 32 words, sh = E' mod 32 bits), each complemented when its logical index
-// is negative (it wrapped past 2^N = -1). A lane's K + 1 source words form one window that
-// crosses at most one 32-word row of the padded cell (or the end of the cell), so the window
-// is two runs of consecutive addresses, each with a lane-uniform complement mask.
+// is negative (it wrapped past 2^N = -1). K >= 4: the window is read as 16-byte vectors
+// (rot_window). K <= 2: a lane's K + 1 source words cross at most one 32-word row of the padded
+// cell (or the end of the cell), so the window is two runs of consecutive addresses, each with
+// a lane-uniform complement mask.
 template <int K>
 __device__ __forceinline__ int smem_read_raw(uint32_t (&r)[K], const uint32_t *cell, uint32_t meta,
                                              int Ereq, const Geo &g);
@@ -409,46 +544,42 @@ __device__ __forceinline__ int smem_read_raw(uint32_t (&r)[K], const uint32_t *c
     for (int s = 0; s < K; s++) r[s] = 0u;
     return 0;
   }
-  const bool low_wrapped = E < g.N;  // complement the wrapped bits (else the others)
-  const int Ep = low_wrapped ? E : E - g.N;
-  const int q = Ep >> 5, sh = Ep & 31;
-  const int lam0 = K * g.lane - q - 1;  // logical index of window word 0 (negative: wrapped)
-  const int i0 = lam0 < 0 ? lam0 + g.NW : lam0;
-  int tb, baseA, baseB;
-  if (g.NW >= 32) {
-    const int c0 = i0 & 31, r0 = i0 >> 5, rows = g.NW >> 5;
-    const int r1 = (r0 + 1 == rows) ? 0 : r0 + 1;
-    tb = 31 - c0;
-    baseA = 33 * r0 + c0;
-    baseB = 33 * r1 + c0 - 32;
+  if constexpr (K >= 4) {
+    auto put = [&](int s, uint32_t w) { r[s] = w; };
+    rot_window<K>(cell, E, g, put);
+    return 0;
   } else {
-    tb = g.NW - 1 - i0;
-    baseA = i0;
-    baseB = i0 - g.NW;
-  }
-  const uint32_t flip = low_wrapped ? 0u : TFT_FULL;
-  const uint32_t mA = (lam0 < 0 ? TFT_FULL : 0u) ^ flip;
-  const uint32_t mB = (lam0 + tb + 1 < 0 ? TFT_FULL : 0u) ^ flip;
-  if (sh == 0) {
-    // word-aligned rotation: output word j is source word j - q, no funnel shift
+    const bool low_wrapped = E < g.N;  // complement the wrapped bits (else the others)
+    const int Ep = low_wrapped ? E : E - g.N;
+    const int q = Ep >> 5, sh = Ep & 31;
+    const int lam0 = K * g.lane - q - 1;  // logical index of window word 0 (negative: wrapped)
+    const int i0 = lam0 < 0 ? lam0 + g.NW : lam0;
+    int tb, baseA, baseB;
+    if (g.NW >= 32) {
+      const int c0 = i0 & 31, r0 = i0 >> 5, rows = g.NW >> 5;
+      const int r1 = (r0 + 1 == rows) ? 0 : r0 + 1;
+      tb = 31 - c0;
+      baseA = 33 * r0 + c0;
+      baseB = 33 * r1 + c0 - 32;
+    } else {
+      tb = g.NW - 1 - i0;
+      baseA = i0;
+      baseB = i0 - g.NW;
+    }
+    const uint32_t flip = low_wrapped ? 0u : TFT_FULL;
+    const uint32_t mA = (lam0 < 0 ? TFT_FULL : 0u) ^ flip;
+    const uint32_t mB = (lam0 + tb + 1 < 0 ? TFT_FULL : 0u) ^ flip;
+    uint32_t prev = cell[0 <= tb ? baseA : baseB] ^ (0 <= tb ? mA : mB);
 #pragma unroll
     for (int s = 0; s < K; s++) {
       const int t = s + 1;
       const bool inA = t <= tb;
-      r[s] = cell[(inA ? baseA : baseB) + t] ^ (inA ? mA : mB);
+      const uint32_t cur = cell[(inA ? baseA : baseB) + t] ^ (inA ? mA : mB);
+      r[s] = __funnelshift_l(prev, cur, sh);  // (cur:prev) << sh, high word (cur for sh = 0)
+      prev = cur;
     }
     return 0;
   }
-  uint32_t prev = cell[0 <= tb ? baseA : baseB] ^ (0 <= tb ? mA : mB);
-#pragma unroll
-  for (int s = 0; s < K; s++) {
-    const int t = s + 1;
-    const bool inA = t <= tb;
-    uint32_t cur = cell[(inA ? baseA : baseB) + t] ^ (inA ? mA : mB);
-    r[s] = __funnelshift_l(prev, cur, sh);  // (cur:prev) << sh, high word
-    prev = cur;
-  }
-  return 0;
 }
 
 // r = r - rotc(m, E) - bin over this lane's chunk, as one borrow chain (E in [0, 2N), m the
@@ -461,10 +592,13 @@ __device__ __forceinline__ uint32_t smem_sub_rotated(uint32_t (&r)[K], const uin
   if (g.lane >= g.G) return 0u;
   uint32_t d, bout;
   asm volatile("sub.cc.u32 %0, 0, %1;" : "=r"(d) : "r"(bin));
+  auto sub = [&](int s, uint32_t w) { asm volatile("subc.cc.u32 %0, %0, %1;" : "+r"(r[s]) : "r"(w)); };
   if (E == 0) {
-    const int b = phys(K * g.lane);
+    const int b = phys<K>(K * g.lane);
 #pragma unroll
-    for (int s = 0; s < K; s++) asm volatile("subc.cc.u32 %0, %0, %1;" : "+r"(r[s]) : "r"(cell[b + s]));
+    for (int s = 0; s < K; s++) sub(s, cell[b + s]);
+  } else if constexpr (K >= 4) {
+    rot_window<K>(cell, E, g, sub);
   } else {
     const bool low_wrapped = E < g.N;
     const int Ep = low_wrapped ? E : E - g.N;
@@ -492,8 +626,7 @@ __device__ __forceinline__ uint32_t smem_sub_rotated(uint32_t (&r)[K], const uin
       const int t = s + 1;
       const bool inA = t <= tb;
       const uint32_t cur = cell[(inA ? baseA : baseB) + t] ^ (inA ? mA : mB);
-      const uint32_t w = sh ? __funnelshift_l(prev, cur, sh) : cur;
-      asm volatile("subc.cc.u32 %0, %0, %1;" : "+r"(r[s]) : "r"(w));
+      sub(s, __funnelshift_l(prev, cur, sh));
       prev = cur;
     }
   }

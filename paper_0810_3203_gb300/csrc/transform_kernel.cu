@@ -46,8 +46,9 @@ __device__ __forceinline__ void write_cell(uint32_t *cell, uint32_t *meta, const
 }
 
 // chunk of this lane inside a shared-memory cell
-__device__ __forceinline__ uint32_t *lane_chunk(uint32_t *cell, int K, const Geo &g) {
-  return cell + phys(K * (g.lane < g.G ? g.lane : 0));
+template <int K>
+__device__ __forceinline__ uint32_t *lane_chunk(uint32_t *cell, const Geo &g) {
+  return cell + phys<K>(K * (g.lane < g.G ? g.lane : 0));
 }
 
 template <int K>
@@ -60,9 +61,9 @@ __device__ __forceinline__ void set_meta(uint32_t *meta, int zflag, int tag, con
 template <int K>
 __device__ __forceinline__ int sum_to(uint32_t *dst, const uint32_t *acell, const uint32_t (&B)[K], int za,
                                       int zb, const Geo &g) {
-  uint32_t *ch = lane_chunk(dst, K, g);
+  uint32_t *ch = lane_chunk<K>(dst, g);
   uint32_t c = 0;
-  if (g.lane < g.G) c = chain_stream<K, false>(ch, lane_chunk(const_cast<uint32_t *>(acell), K, g), za != 0, B,
+  if (g.lane < g.G) c = chain_stream<K, false>(ch, lane_chunk<K>(const_cast<uint32_t *>(acell), g), za != 0, B,
                                                  g.lane == 0 ? 1u : 0u);
   return settle_smem<K>(ch, int(c), za + zb, g);
 }
@@ -71,11 +72,24 @@ __device__ __forceinline__ int sum_to(uint32_t *dst, const uint32_t *acell, cons
 template <int K>
 __device__ __forceinline__ int diff_to(uint32_t *dst, const uint32_t *acell, const uint32_t (&B)[K], int za,
                                        int zb, const Geo &g) {
-  uint32_t *ch = lane_chunk(dst, K, g);
+  uint32_t *ch = lane_chunk<K>(dst, g);
   uint32_t bo = 0;
-  if (g.lane < g.G) bo = chain_stream<K, true>(ch, lane_chunk(const_cast<uint32_t *>(acell), K, g), za != 0, B,
+  if (g.lane < g.G) bo = chain_stream<K, true>(ch, lane_chunk<K>(const_cast<uint32_t *>(acell), g), za != 0, B,
                                                  g.lane == 0 ? 1u : 0u);
   return settle_smem<K>(ch, -int(bo), za - zb, g);
+}
+
+// S (to dS) and D (to dD) of one butterfly from one pass over the cell `acell` (K >= 4); dS or
+// dD may be acell. Sets the zero flags of both outputs.
+template <int K>
+__device__ __forceinline__ void sum_diff_to(uint32_t *dS, uint32_t *dD, const uint32_t *acell, const uint32_t (&B)[K],
+                                            int za, int zb, const Geo &g, int &zs, int &zd) {
+  uint32_t *chS = lane_chunk<K>(dS, g), *chD = lane_chunk<K>(dD, g);
+  uint32_t c = 0, bo = 0;
+  if (g.lane < g.G)
+    bf_stream<K>(chS, chD, lane_chunk<K>(const_cast<uint32_t *>(acell), g), za != 0, B, g.lane == 0 ? 1u : 0u, c, bo);
+  zd = settle_smem<K>(chD, -int(bo), za - zb, g);
+  zs = settle_smem<K>(chS, int(c), za + zb, g);
 }
 
 template <int K, bool SQ>
@@ -121,6 +135,16 @@ __device__ __forceinline__ void exec_op(const OpDesc &op, uint32_t *cells, uint3
     // so that x_i is still intact for the sum, which then rewrites cell i word by word
     const bool wantS = op.flags & OPF_S, wantD = op.flags & OPF_D;
     const bool toj = op.flags & OPF_S_TO_J, toi = op.flags & OPF_D_TO_I;
+    if constexpr (K >= 4) {
+      if (wantS && wantD && toj == toi) {
+        // S and D from one pass over x_i (S to i and D to j, or S to j and D to i)
+        int zs, zd;
+        sum_diff_to<K>(toj ? cj : ci, toi ? ci : cj, ci, B, za, zb, g, zs, zd);
+        set_meta<K>(meta + (toi ? op.i : op.j), zd, pend(op.p1), g);
+        set_meta<K>(meta + (toj ? op.j : op.i), zs, pend(op.p0), g);
+        return;
+      }
+    }
     if (wantD && !toi) {
       const int zd = diff_to<K>(cj, ci, B, za, zb, g);
       set_meta<K>(meta + op.j, zd, pend(op.p1), g);
@@ -149,7 +173,9 @@ __device__ __forceinline__ void exec_op(const OpDesc &op, uint32_t *cells, uint3
 
 // Copy the N-bit part of a cell between global memory (16-byte aligned when vec16) and a
 // shared-memory cell, with consecutive lanes on consecutive addresses (coalesced); returns the
-// top limb's low word on loads.
+// top limb's low word on loads. Groups of 4 words never straddle a 32-word row, so for K >= 4
+// both sides move 16-byte vectors.
+template <int K>
 __device__ __forceinline__ uint32_t gmem_to_smem_cell(uint32_t *scell, const uint64_t *gcell, bool vec16,
                                                       const Geo &g) {
   const uint32_t *w32 = reinterpret_cast<const uint32_t *>(gcell);
@@ -157,17 +183,21 @@ __device__ __forceinline__ uint32_t gmem_to_smem_cell(uint32_t *scell, const uin
     const uint4 *src = reinterpret_cast<const uint4 *>(w32);
     for (int q = g.lane; q < g.NW / 4; q += 32) {
       const uint4 v = __ldg(src + q);
-      const int pw = phys(4 * q);  // 4 words in one 32-word row
-      scell[pw] = v.x;
-      scell[pw + 1] = v.y;
-      scell[pw + 2] = v.z;
-      scell[pw + 3] = v.w;
+      const int pw = phys<K>(4 * q);
+      if constexpr (K >= 4) {
+        *reinterpret_cast<uint4 *>(scell + pw) = v;
+      } else {
+        scell[pw] = v.x;
+        scell[pw + 1] = v.y;
+        scell[pw + 2] = v.z;
+        scell[pw + 3] = v.w;
+      }
     }
   } else {
     const uint2 *src = reinterpret_cast<const uint2 *>(w32);
     for (int q = g.lane; q < g.NW / 2; q += 32) {
       const uint2 v = __ldg(src + q);
-      const int pw = phys(2 * q);
+      const int pw = phys<K>(2 * q);
       scell[pw] = v.x;
       scell[pw + 1] = v.y;
     }
@@ -175,19 +205,23 @@ __device__ __forceinline__ uint32_t gmem_to_smem_cell(uint32_t *scell, const uin
   return __ldg(w32 + g.NW);
 }
 
+template <int K>
 __device__ __forceinline__ void smem_to_gmem_cell(uint64_t *gcell, const uint32_t *scell, uint32_t top, bool vec16,
                                                   const Geo &g) {
   uint32_t *w32 = reinterpret_cast<uint32_t *>(gcell);
   if (vec16 && (g.NW & 3) == 0) {
     uint4 *dst = reinterpret_cast<uint4 *>(w32);
     for (int q = g.lane; q < g.NW / 4; q += 32) {
-      const int pw = phys(4 * q);
-      dst[q] = make_uint4(scell[pw], scell[pw + 1], scell[pw + 2], scell[pw + 3]);
+      const int pw = phys<K>(4 * q);
+      if constexpr (K >= 4)
+        dst[q] = *reinterpret_cast<const uint4 *>(scell + pw);
+      else
+        dst[q] = make_uint4(scell[pw], scell[pw + 1], scell[pw + 2], scell[pw + 3]);
     }
   } else {
     uint2 *dst = reinterpret_cast<uint2 *>(w32);
     for (int q = g.lane; q < g.NW / 2; q += 32) {
-      const int pw = phys(2 * q);
+      const int pw = phys<K>(2 * q);
       dst[q] = make_uint2(scell[pw], scell[pw + 1]);
     }
   }
@@ -315,13 +349,15 @@ __global__ void __launch_bounds__(MINB == 3 ? 256 : 512, MINB) job_kernel(uint64
     jd.cell0 += sg.cell_off;
   }
   KGeo kg;
+  // a FULL ring has N = 1024 K: its geometry is compile-time
+  if (FULL) N = 1024 * K;
   kg.g.N = N;
   kg.g.NW = N / 32;
   kg.g.G = FULL ? 32 : kg.g.NW / K;
   kg.g.lane = threadIdx.x & 31;
   kg.g.twoN = 2 * N;
   kg.ord = SQ ? 4 * N : 2 * N;
-  kg.mask = mask;
+  kg.mask = FULL ? uint32_t(kg.ord - 1) : mask;
   const Geo &g = kg.g;
   const int nslots = 1 << ((jd.pad > 0 ? jd.pad : ls) - lc);
   const int L2 = nslots, b = nslots / C;
@@ -345,9 +381,9 @@ __global__ void __launch_bounds__(MINB == 3 ? 256 : 512, MINB) job_kernel(uint64
     const int m = job_cell(load_layout, rank, s, C, L2, b);
     if (m >= jd.nload) continue;
     const uint64_t *gc = x + (jd.cell0 + int64_t(m) * jd.mstride) * stride_limbs;
-    const uint32_t T = gmem_to_smem_cell(cells + s * P, gc, vec16, g);
+    const uint32_t T = gmem_to_smem_cell<K>(cells + s * P, gc, vec16, g);
     __syncwarp();
-    const int z = settle_smem<K>(lane_chunk(cells + s * P, K, g), 0, -1 - int(T), g);
+    const int z = settle_smem<K>(lane_chunk<K>(cells + s * P, g), 0, -1 - int(T), g);
     set_meta<K>(meta + s, z, 0, g);
   }
   __syncthreads();
@@ -396,7 +432,7 @@ __global__ void __launch_bounds__(MINB == 3 ? 256 : 512, MINB) job_kernel(uint64
     smem_store_plain<K>(cells + s * P, r, g);
     __syncwarp();
     uint64_t *gc = x + (jd.cell0 + int64_t(m) * jd.mstride) * stride_limbs;
-    smem_to_gmem_cell(gc, cells + s * P, top, vec16, g);
+    smem_to_gmem_cell<K>(gc, cells + s * P, top, vec16, g);
   }
 }
 
@@ -435,14 +471,20 @@ template <int K, bool SQ>
 cudaError_t launch_k(const Launch &L, uint64_t *x, int64_t stride_limbs, const Ring &r, cudaStream_t s) {
   const int nslots = 1 << (L.ls - L.lc);
   const size_t base_words = (size_t(nslots) * size_t(r.pitch) + size_t(nslots) + 1) & ~size_t(1);
+  const uint32_t ord = uint32_t((SQ ? 4 : 2) * r.N);
+  const uint32_t mask = (ord & (ord - 1)) == 0 ? ord - 1 : 0u;
+  // three CTAs per SM when the cells fit in 75 KB; the program is staged in shared memory only
+  // if it fits beside them (else its ops are read through the read-only path)
+  const size_t small_words = (75 * 1024) / 4;
+  if (L.nwarps <= 8 && base_words <= small_words) {
+    const int cap = size_t(L.prog_words) <= small_words - base_words ? L.prog_words : 0;
+    const size_t smem = (base_words + size_t(cap)) * 4;
+    return r.G == 32 ? launch_km<K, 3, true, SQ>(L, x, stride_limbs, r, s, smem, cap, mask)
+                     : launch_km<K, 3, false, SQ>(L, x, stride_limbs, r, s, smem, cap, mask);
+  }
   const size_t max_words = (227 * 1024) / 4;
   const int prog_cap = int(std::min<size_t>(size_t(L.prog_words), max_words > base_words ? max_words - base_words : 0));
   const size_t smem = (base_words + size_t(prog_cap)) * 4;
-  const uint32_t ord = uint32_t((SQ ? 4 : 2) * r.N);
-  const uint32_t mask = (ord & (ord - 1)) == 0 ? ord - 1 : 0u;
-  if (L.nwarps <= 8 && smem <= 75 * 1024)
-    return r.G == 32 ? launch_km<K, 3, true, SQ>(L, x, stride_limbs, r, s, smem, prog_cap, mask)
-                     : launch_km<K, 3, false, SQ>(L, x, stride_limbs, r, s, smem, prog_cap, mask);
   return r.G == 32 ? launch_km<K, 1, true, SQ>(L, x, stride_limbs, r, s, smem, prog_cap, mask)
                    : launch_km<K, 1, false, SQ>(L, x, stride_limbs, r, s, smem, prog_cap, mask);
 }
