@@ -403,6 +403,7 @@ def run_gpu(args):
                           "passes_padded": tg.transform_plan(1, l, n_pad, n_pad, N)["passes"]}
 
     sn = sn_leg(tg, device, stream, 10)
+    pointwise = pointwise_leg(tg, device, stream)
     ok &= sn["bit_exact_roundtrip"]
     batch = None if args.no_batch else batch_leg(tg, device, stream, 2, 3, not args.no_tune)
     ok &= batch is None or batch["bit_exact_vs_plain"]
@@ -439,6 +440,7 @@ def run_gpu(args):
     }
     line["zero_padded_itft"] = padded
     line["sn"] = sn
+    line["pointwise"] = pointwise
     if tuned is not None:
         line["tuned_config"] = tuned
     if batch is not None:
@@ -639,6 +641,41 @@ def sn_leg(tg, device, stream, steps):
     return {"workload": f"S[y]/(y^{H}+1) over Z/mZ, m = 2^40 + 15, L = 2^{l}, n = {n}, pieces of {M // 4} "
                         "coefficients, seed 7", "ms_per_round_trip": round(sec * 1e3, 3),
             "gbs_algorithmic": round(gbs, 2), "bit_exact_roundtrip": ok}
+
+
+def pointwise_leg(tg, device, stream):
+    """Pointwise products mod 2^N + 1 by both methods (schoolbook warp kernel; a second
+    Schoenhage-Strassen level on the transform kernels): ms per batch of uniform residues,
+    resident in HBM, and whether the two agree bit for bit."""
+    import numpy as np
+    import torch
+
+    out = {}
+    for N, n in ((8192, 20000), (32768, 10000)):
+        W = N // 64 + 1
+        s = W + (W & 1)
+        a = torch.from_numpy(workloads.residues(21, n, N, stride=s).view(np.int64)).to(device)
+        b = torch.from_numpy(workloads.residues(22, n, N, stride=s).view(np.int64)).to(device)
+        ms, res = {}, {}
+        for m in (1, 2):
+            x = a.clone()
+            tg.pointwise(x, b, n, N, s, m, stream=stream)
+            res[m] = x.clone()
+            for _ in range(2):
+                tg.pointwise(x, b, n, N, s, m, stream=stream)
+            torch.cuda.synchronize(device)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(5):
+                tg.pointwise(x, b, n, N, s, m, stream=stream)
+            e1.record(stream)
+            torch.cuda.synchronize(device)
+            ms[m] = e0.elapsed_time(e1) / 5
+        plan = tg.pointwise_plan(N, 2)
+        out[str(N)] = {"products": n, "ms_schoolbook": round(ms[1], 4), "ms_recursive": round(ms[2], 4),
+                       "recursive_k": plan["k"], "inner_N": plan["N_inner"],
+                       "auto_method": tg.pointwise_plan(N)["method"], "bit_exact": bool(torch.equal(res[1], res[2]))}
+    return out
 
 
 def run_batch(args):

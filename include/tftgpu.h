@@ -280,6 +280,35 @@ typedef struct {
 int zx_transform_plan(int kind, int l, int64_t z, int64_t n, int f, int64_t N, zx_transform_info *out);
 
 /*
+ * Pointwise products in Z/(2^N+1) (the step between the forward and inverse transforms of a
+ * product, Sec. 5.1): a_i <- a_i * b_i mod 2^N + 1 for i < n, over canonical cells (N/64 + 1
+ * limbs, little-endian, value in [0, 2^N]) spaced stride_limbs apart in device memory; a and b
+ * are caller-owned and must not overlap (a may equal b only for squaring, a == b exactly).
+ * method 1: one warp per product, schoolbook product scanning with a negacyclic fold.
+ * method 2: a second Schoenhage-Strassen level on the transform kernels: 2^k pieces of
+ *   M = N / 2^k bits, weighted by theta^t (theta = 2^{N'/2^k}, theta^{2^k} = -1) in the inner
+ *   ring Z/(2^{N'}+1) with N' >= 2M + k + 1, a TFT and ITFT of length 2^k, the inner products
+ *   by method 1, and the negacyclic recombination. Device scratch comes from the stream's
+ *   memory pool, in chunks of at most 256 MB.
+ * method 0: whichever zx_pointwise_plan reports for N.
+ * Both methods give the same canonical residues. Returns ZX_EINVAL on bad arguments,
+ * ZX_EUNSUPPORTED when N has no recursive plan (method 2), ZX_ENOMEM, ZX_ECUDA. Asynchronous
+ * on `stream`.
+ */
+typedef struct {
+    int32_t method;       /* 1 (schoolbook) or 2 (recursive): the resolved method */
+    int32_t k;            /* log2 of the pieces per product (method 2; else 0) */
+    int64_t N_inner;      /* N' of the inner ring (method 2; else 0) */
+    int64_t stride_inner; /* limbs per inner cell in the scratch (method 2; else 0) */
+    double cost_recursive;  /* estimated word operations per product, method 2 (0: no plan) */
+    double cost_schoolbook; /* estimated word operations per product, method 1 */
+} zx_pointwise_info;
+
+int zx_pointwise_plan(int64_t N, int method, zx_pointwise_info *out);
+int zx_pointwise(uint64_t *a, const uint64_t *b, int64_t n, int64_t N, int64_t stride_limbs, int method,
+                 void *stream);
+
+/*
  * The on-chip schedule of one job (host only): a sub-transform of 2^ls cells (TFT: kind 0,
  * ITFT: kind 1) with the given z, n, f, spread over 2^lc CTAs of a cluster, over
  * Z/(2^N+1) with omega = 2 (mode 0), S[y]/(y^N+1) with omega = y (mode 1: rotations mod 2N,

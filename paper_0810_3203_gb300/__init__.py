@@ -25,7 +25,8 @@ ZX_HOST, ZX_DEVICE = 0, 1
 EXPORTS = ("tft", "tft_ex", "itft", "itft_ex", "zx_plan", "zx_mul", "zx_mul_batch",
            "zx_transform_plan", "zx_mul_noalloc", "zx_job_program", "zx_strerror", "zx_last_error",
            "zx_version", "zx_server_create", "zx_server_submit", "zx_server_poll", "zx_server_drain",
-           "zx_server_stats", "zx_server_destroy", "zx_tune", "zx_config_get", "zx_config_set", "sn_tft", "sn_itft", "tft_sqrt2", "itft_sqrt2")
+           "zx_server_stats", "zx_server_destroy", "zx_tune", "zx_config_get", "zx_config_set", "sn_tft", "sn_itft", "tft_sqrt2", "itft_sqrt2",
+           "zx_pointwise", "zx_pointwise_plan")
 
 _lib = None
 
@@ -60,6 +61,11 @@ class ZxServerInfo(C.Structure):
                 ("waves", C.c_int64), ("max_wave_products", C.c_int64), ("slots", C.c_int32),
                 ("max_waves_in_flight", C.c_int32), ("arena_bytes", C.c_int64),
                 ("arena_peak_bytes", C.c_int64)]
+
+
+class ZxPointwiseInfo(C.Structure):
+    _fields_ = [("method", C.c_int32), ("k", C.c_int32), ("N_inner", C.c_int64), ("stride_inner", C.c_int64),
+                ("cost_recursive", C.c_double), ("cost_schoolbook", C.c_double)]
 
 
 class ZxTransformInfo(C.Structure):
@@ -109,6 +115,8 @@ def load(build_if_missing=True):
     L.itft_sqrt2.argtypes = [vp, i32, i64, i64, i32, i64, i64, i64, i32, vp]
     L.sn_tft.argtypes = [vp, i32, i64, i64, i64, C.c_uint64, i64, i64, vp]
     L.sn_itft.argtypes = [vp, i32, i64, i64, i32, i64, C.c_uint64, i64, i64, i32, vp]
+    L.zx_pointwise.argtypes = [vp, vp, i64, i64, i64, i32, vp]
+    L.zx_pointwise_plan.argtypes = [i64, i32, C.POINTER(ZxPointwiseInfo)]
     L.zx_strerror.argtypes = [i32]
     L.zx_strerror.restype = C.c_char_p
     L.zx_last_error.argtypes = []
@@ -117,7 +125,8 @@ def load(build_if_missing=True):
     for name in ("tft", "tft_ex", "itft", "itft_ex", "zx_plan", "zx_mul", "zx_mul_batch",
                  "zx_transform_plan", "zx_mul_noalloc", "zx_job_program", "zx_server_create",
                  "zx_server_submit", "zx_server_poll", "zx_server_drain", "zx_server_stats",
-                 "zx_server_destroy", "zx_tune", "zx_config_get", "zx_config_set", "sn_tft", "sn_itft", "tft_sqrt2", "itft_sqrt2"):
+                 "zx_server_destroy", "zx_tune", "zx_config_get", "zx_config_set", "sn_tft", "sn_itft", "tft_sqrt2", "itft_sqrt2",
+                 "zx_pointwise", "zx_pointwise_plan"):
         getattr(L, name).restype = i32
     _lib = L
     return L
@@ -183,6 +192,19 @@ def transform_plan(kind, l, z, n, N, f=0):
     info = ZxTransformInfo()
     _check(load().zx_transform_plan(kind, l, z, n, f, N, C.byref(info)), "zx_transform_plan")
     return {k: getattr(info, k) for k, _ in ZxTransformInfo._fields_}
+
+
+def pointwise_plan(N, method=0):
+    """Pointwise method for ring N (zx_pointwise_plan): method 1 schoolbook, 2 recursive, with
+    the inner ring of the recursion and both cost estimates."""
+    info = ZxPointwiseInfo()
+    _check(load().zx_pointwise_plan(N, method, C.byref(info)), "zx_pointwise_plan")
+    return {k: getattr(info, k) for k, _ in ZxPointwiseInfo._fields_}
+
+
+def pointwise(a, b, n, N, stride_limbs, method=0, stream=None):
+    """a_i <- a_i b_i mod 2^N + 1 for i < n (zx_pointwise) on device tensors of canonical cells."""
+    _check(load().zx_pointwise(_dev_ptr(a), _dev_ptr(b), n, N, stride_limbs, method, _stream(stream)), "zx_pointwise")
 
 
 def job_program(kind, ls, lc, z, n, N, f=0, mode=0):

@@ -137,6 +137,24 @@ cudaError_t run_sn_transform(const TransformPlan &p, uint64_t *x, int64_t stride
 // Enqueue a plan on a stream.
 cudaError_t run_transform(const TransformPlan &p, uint64_t *x, int64_t stride_limbs,
                           cudaStream_t s);
+// The same plan applied to `reps` buffers of rep_cells cells each, back to back from x: every
+// launch covers all of them (replica r shifts each job by r * rep_cells cells).
+cudaError_t run_transform_reps(const TransformPlan &p, uint64_t *x, int64_t stride_limbs, int64_t reps,
+                               int64_t rep_cells, cudaStream_t s);
+
+// Pointwise products by a second Schoenhage-Strassen level (rec_pointwise.cu): 2^k pieces of
+// M = N / 2^k bits, inner ring Z/(2^Ni + 1) with Ni >= 2M + k + 1 and 2^k | Ni.
+struct RecPlan {
+  int64_t N = 0, M = 0, Ni = 0, stride_i = 0;
+  int k = 0;
+  int nwp = 0;        // 32-bit words of a recovered piece c_t + 2^{k+2M}
+  double cost = 0.0;  // word operations per outer product (estimate)
+};
+bool rec_plan_for(int64_t N, int k, RecPlan *out);
+bool rec_plan_auto(int64_t N, RecPlan *out);
+// a_i <- a_i b_i mod 2^N + 1 for i < n (canonical cells of stride limbs); *err gets a ZX_ code
+cudaError_t run_rec_pointwise(uint64_t *a, const uint64_t *b, int64_t n, int64_t stride, const Ring &ro,
+                              const RecPlan &rp, cudaStream_t s, int *err);
 
 // Kernels of the Z[x] path (zx_kernels.cu).
 cudaError_t launch_pack(const uint64_t *coef, int64_t len, int64_t limbs, int is_signed,

@@ -328,13 +328,23 @@ template <int K, int MINB, bool FULL, bool SQ>
 __global__ void __launch_bounds__(MINB == 3 ? 256 : 512, MINB) job_kernel(uint64_t *__restrict__ x, int64_t stride_limbs,
                                                   const JobDesc *__restrict__ jobs, int N, int ls, int lc,
                                                   uint32_t mask, int prog_cap,
-                                                  const Segment *__restrict__ segs, int nsegs) {
+                                                  const Segment *__restrict__ segs, int nsegs, int64_t rep_cells,
+                                                  int rep_ctas) {
   extern __shared__ uint32_t smem[];
   const int C = 1 << lc;
   const int rank = int(blockIdx.x) & (C - 1);
   JobDesc jd;
   if (nsegs == 0) {
-    jd = jobs[blockIdx.x >> lc];
+    // replicated launch: rep_ctas CTAs per replica, replica r shifted by r * rep_cells cells
+    int b = int(blockIdx.x);
+    int64_t shift = 0;
+    if (rep_ctas > 0) {
+      const int r = b / rep_ctas;
+      b -= r * rep_ctas;
+      shift = int64_t(r) * rep_cells;
+    }
+    jd = jobs[b >> lc];
+    jd.cell0 += shift;
   } else {
     // merged launch: the last segment that starts at or before this CTA (segments hold whole
     // clusters, so the CTAs of one cluster agree)
@@ -440,7 +450,7 @@ namespace {
 
 template <int K, int MINB, bool FULL, bool SQ>
 cudaError_t launch_km(const Launch &L, uint64_t *x, int64_t stride_limbs, const Ring &r, cudaStream_t s,
-                      size_t smem, int prog_cap, uint32_t mask) {
+                      size_t smem, int prog_cap, uint32_t mask, int64_t reps, int64_t rep_cells) {
   static thread_local int configured[8] = {0, 0, 0, 0, 0, 0, 0, 0};
   int dev = 0;
   cudaGetDevice(&dev);
@@ -452,7 +462,9 @@ cudaError_t launch_km(const Launch &L, uint64_t *x, int64_t stride_limbs, const 
     if (dev < 8) configured[dev] = 1;
   }
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(unsigned(L.njobs) << L.lc);
+  const int64_t per_rep = int64_t(L.njobs) << L.lc;
+  if (per_rep * reps > int64_t(0x7fffffff)) return cudaErrorInvalidConfiguration;
+  cfg.gridDim = dim3(unsigned(per_rep * reps));
   cfg.blockDim = dim3(unsigned(L.nwarps * 32));
   cfg.dynamicSmemBytes = smem;
   cfg.stream = s;
@@ -464,11 +476,12 @@ cudaError_t launch_km(const Launch &L, uint64_t *x, int64_t stride_limbs, const 
   cfg.attrs = attr;
   cfg.numAttrs = L.lc > 0 ? 1 : 0;
   return cudaLaunchKernelEx(&cfg, job_kernel<K, MINB, FULL, SQ>, x, stride_limbs, (const JobDesc *)L.d_jobs, int(r.N), L.ls,
-                            L.lc, mask, prog_cap, L.d_segs, L.nsegs);
+                            L.lc, mask, prog_cap, L.d_segs, L.nsegs, rep_cells, reps > 1 ? int(per_rep) : 0);
 }
 
 template <int K, bool SQ>
-cudaError_t launch_k(const Launch &L, uint64_t *x, int64_t stride_limbs, const Ring &r, cudaStream_t s) {
+cudaError_t launch_k(const Launch &L, uint64_t *x, int64_t stride_limbs, const Ring &r, cudaStream_t s,
+                     int64_t reps, int64_t rep_cells) {
   const int nslots = 1 << (L.ls - L.lc);
   const size_t base_words = (size_t(nslots) * size_t(r.pitch) + size_t(nslots) + 1) & ~size_t(1);
   const uint32_t ord = uint32_t((SQ ? 4 : 2) * r.N);
@@ -479,34 +492,44 @@ cudaError_t launch_k(const Launch &L, uint64_t *x, int64_t stride_limbs, const R
   if (L.nwarps <= 8 && base_words <= small_words) {
     const int cap = size_t(L.prog_words) <= small_words - base_words ? L.prog_words : 0;
     const size_t smem = (base_words + size_t(cap)) * 4;
-    return r.G == 32 ? launch_km<K, 3, true, SQ>(L, x, stride_limbs, r, s, smem, cap, mask)
-                     : launch_km<K, 3, false, SQ>(L, x, stride_limbs, r, s, smem, cap, mask);
+    return r.G == 32 ? launch_km<K, 3, true, SQ>(L, x, stride_limbs, r, s, smem, cap, mask, reps, rep_cells)
+                     : launch_km<K, 3, false, SQ>(L, x, stride_limbs, r, s, smem, cap, mask, reps, rep_cells);
   }
   const size_t max_words = (227 * 1024) / 4;
   const int prog_cap = int(std::min<size_t>(size_t(L.prog_words), max_words > base_words ? max_words - base_words : 0));
   const size_t smem = (base_words + size_t(prog_cap)) * 4;
-  return r.G == 32 ? launch_km<K, 1, true, SQ>(L, x, stride_limbs, r, s, smem, prog_cap, mask)
-                   : launch_km<K, 1, false, SQ>(L, x, stride_limbs, r, s, smem, prog_cap, mask);
+  return r.G == 32 ? launch_km<K, 1, true, SQ>(L, x, stride_limbs, r, s, smem, prog_cap, mask, reps, rep_cells)
+                   : launch_km<K, 1, false, SQ>(L, x, stride_limbs, r, s, smem, prog_cap, mask, reps, rep_cells);
 }
 
 }  // namespace
 
-cudaError_t run_transform(const TransformPlan &p, uint64_t *x, int64_t stride_limbs, cudaStream_t s) {
+cudaError_t run_transform_reps(const TransformPlan &p, uint64_t *x, int64_t stride_limbs, int64_t reps,
+                               int64_t rep_cells, cudaStream_t s) {
+  if (reps < 1) return cudaSuccess;
   const bool sq = p.mode == RING_SQRT2;
   for (const Launch &L : p.launches) {
+    if (reps > 1 && L.nsegs != 0) return cudaErrorInvalidValue;
     cudaError_t e;
+#define TFT_LK(KK) (sq ? launch_k<KK, true>(L, x, stride_limbs, p.ring, s, reps, rep_cells) \
+                       : launch_k<KK, false>(L, x, stride_limbs, p.ring, s, reps, rep_cells))
     switch (p.ring.K) {
-      case 1: e = sq ? launch_k<1, true>(L, x, stride_limbs, p.ring, s) : launch_k<1, false>(L, x, stride_limbs, p.ring, s); break;
-      case 2: e = sq ? launch_k<2, true>(L, x, stride_limbs, p.ring, s) : launch_k<2, false>(L, x, stride_limbs, p.ring, s); break;
-      case 4: e = sq ? launch_k<4, true>(L, x, stride_limbs, p.ring, s) : launch_k<4, false>(L, x, stride_limbs, p.ring, s); break;
-      case 8: e = sq ? launch_k<8, true>(L, x, stride_limbs, p.ring, s) : launch_k<8, false>(L, x, stride_limbs, p.ring, s); break;
-      case 16: e = sq ? launch_k<16, true>(L, x, stride_limbs, p.ring, s) : launch_k<16, false>(L, x, stride_limbs, p.ring, s); break;
-      case 32: e = sq ? launch_k<32, true>(L, x, stride_limbs, p.ring, s) : launch_k<32, false>(L, x, stride_limbs, p.ring, s); break;
+      case 1: e = TFT_LK(1); break;
+      case 2: e = TFT_LK(2); break;
+      case 4: e = TFT_LK(4); break;
+      case 8: e = TFT_LK(8); break;
+      case 16: e = TFT_LK(16); break;
+      case 32: e = TFT_LK(32); break;
       default: return cudaErrorInvalidValue;
     }
+#undef TFT_LK
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
+}
+
+cudaError_t run_transform(const TransformPlan &p, uint64_t *x, int64_t stride_limbs, cudaStream_t s) {
+  return run_transform_reps(p, x, stride_limbs, 1, 0, s);
 }
 
 }  // namespace tftgpu

@@ -125,3 +125,31 @@ def test_launch_configuration_get_set_without_a_device():
         tg.config_set(N)
     assert tg.config_get(N) == default
     assert tg.transform_plan(0, 16, 40000, 40000, N) == shape
+
+
+def test_recursive_pointwise_plans_follow_the_ring_rules(lib):
+    """The inner ring of the recursive pointwise products: 2^k pieces of M = N / 2^k bits (whole
+    32-bit words), N' >= 2M + k + 1 so that every c_t (|c_t| < 2^k 2^{2M}) is determined by its
+    residue, 2^k | N' (theta = 2^{N'/2^k} has theta^{2^k} = -1), N' a supported ring."""
+    import paper_0810_3203_gb300 as tg
+    for N in (2048, 3072, 4096, 8192, 12288, 16384, 20480, 32768):
+        p = tg.pointwise_plan(N, 2)
+        k, Ni = p["k"], p["N_inner"]
+        M = N >> k
+        assert p["method"] == 2 and k >= 2 and M % 32 == 0 and M << k == N, (N, p)
+        assert Ni >= 2 * M + k + 1 and Ni % (1 << k) == 0, (N, p)
+        assert (Ni <= 1024 and Ni % 64 == 0) or (Ni % 1024 == 0 and Ni <= 32768), (N, p)
+        assert p["stride_inner"] >= Ni // 64 + 1 and p["stride_inner"] % 2 == 0
+        assert 0 < p["cost_recursive"] and p["cost_schoolbook"] == (N // 32) ** 2
+        assert tg.pointwise_plan(N, 1)["method"] == 1 and tg.pointwise_plan(N, 1)["k"] == 0
+        assert tg.pointwise_plan(N)["method"] in (1, 2)
+    # the schoolbook kernel is the faster one on every supported ring (measured), so auto keeps it
+    for N in (1024, 4096, 32768):
+        assert tg.pointwise_plan(N)["method"] == 1
+    with pytest.raises(tg.TftError) as ei:
+        tg.pointwise_plan(64, 2)  # four pieces of 16 bits: not whole 32-bit words
+    assert ei.value.code == tg.ZX_EUNSUPPORTED
+    with pytest.raises(tg.TftError) as ei:
+        tg.pointwise_plan(4096, 5)
+    assert ei.value.code == tg.ZX_EINVAL
+    assert lib.zx_pointwise(None, None, 1, 4096, 65, 1, None) == tg.ZX_EINVAL
