@@ -101,9 +101,18 @@ struct JobDesc {
   int32_t nstore;
   int32_t nscale;
   int32_t escale;
-  int32_t pad;  // log2 of the job's cells (0: the launch's ls); single-CTA launches mix sizes
+  int32_t pad;  // bits 0-7: log2 of the job's cells (0: the launch's ls; single-CTA launches
+                // mix sizes); JOB_RAW_STORE: the job's stored cells stay in internal form
 };
 static_assert(sizeof(JobDesc) == 48, "JobDesc layout");
+
+// A later pass of the same transform stores every cell this job stores, so the job may write
+// them in the kernel's internal form: the N-bit storage word m = x - 1 (unrotated) and, in the
+// top limb, bit 63 set with the cell's metadata word (pending rotation << 1 | zero flag) below.
+// A canonical top limb is 0 or 1, so loads tell the two forms apart.
+constexpr int32_t JOB_RAW_STORE = 1 << 8;
+constexpr uint64_t kRawTopMark = uint64_t(1) << 63;
+TFT_HD inline int job_ls(int32_t pad, int ls) { return (pad & 0xff) > 0 ? (pad & 0xff) : ls; }
 
 // One segment of a merged launch: the jobs of one cached plan launch, applied to a buffer that
 // starts `cell_off` cells after the launch's base pointer. Segment s covers the CTAs

@@ -286,6 +286,27 @@ bool launch_order(const JobRec &a, const JobRec &b) {
 
 }  // namespace
 
+// Flag the jobs whose every stored cell is stored again by a later pass (JOB_RAW_STORE): they
+// may leave their cells in internal form, which a later load recognises by the top limb. The
+// last store of every cell stays canonical. Passes are the unit: jobs of one pass touch
+// disjoint cells, and merged launches keep the pass order.
+static void mark_raw_stores(std::vector<JobRec> &jobs, int l) {
+  if (l > 22 || jobs.empty()) return;
+  const int64_t L = int64_t(1) << l;
+  std::vector<int> last(size_t(L), -1);
+  for (const JobRec &j : jobs)
+    for (int64_t m = 0; m < j.d.nstore; m++) {
+      const int64_t c = j.d.cell0 + m * j.d.mstride;
+      if (c < 0 || c >= L) return;  // not a plan over [0, L): leave every store canonical
+      last[size_t(c)] = std::max(last[size_t(c)], j.pass);
+    }
+  for (JobRec &j : jobs) {
+    bool raw = j.d.nstore > 0;
+    for (int64_t m = 0; m < j.d.nstore && raw; m++) raw = last[size_t(j.d.cell0 + m * j.d.mstride)] > j.pass;
+    if (raw) j.d.pad |= JOB_RAW_STORE;
+  }
+}
+
 int64_t zero_padded_outputs(int l, int64_t n, int64_t N) {
   Planner P(N);
   const int64_t L = int64_t(1) << l;
@@ -352,6 +373,7 @@ void build_host_plan(int kind, int l, int64_t z, int64_t n, int f, int64_t N, in
   out->npasses = kind == KIND_TFT ? P.tft(0, 0, 1, l, e, z, n)
                                   : P.itft(0, 0, 1, l, e, z, n, f, scale ? inv_l_exponent(l, twoN, mode) : -1);
   std::map<std::tuple<int, int, int, int64_t, int64_t, int>, int> index;
+  mark_raw_stores(P.jobs, l);
   std::stable_sort(P.jobs.begin(), P.jobs.end(), launch_order);
   for (size_t i = 0; i < P.jobs.size();) {
     size_t k = i;
@@ -414,6 +436,7 @@ const TransformPlan *get_transform_plan(int kind, int l, int64_t z, int64_t n, i
     j.d.image = image_cache().get(j.kind, j.ls, j.lc, j.z, j.n, j.f, N, err, mode);
     if (!j.d.image) return nullptr;
   }
+  mark_raw_stores(P.jobs, l);
   std::stable_sort(P.jobs.begin(), P.jobs.end(), launch_order);
   std::vector<JobDesc> flat;
   std::vector<std::pair<size_t, Launch>> groups;

@@ -156,7 +156,7 @@ __global__ void __launch_bounds__(256, 2)
   g.M = 2 * H;
   g.lane = threadIdx.x & 31;
   g.m = m;
-  const int nslots = 1 << (jd.pad > 0 ? jd.pad : ls);
+  const int nslots = 1 << job_ls(jd.pad, ls);
   uint64_t *cells = sn_smem;
   uint32_t *meta = reinterpret_cast<uint32_t *>(cells + size_t(nslots) * H);
   uint32_t *pstage = meta + ((nslots + 1) & ~1);  // 8-byte aligned

@@ -173,10 +173,10 @@ __device__ __forceinline__ void exec_op(const OpDesc &op, uint32_t *cells, uint3
 
 // Copy the N-bit part of a cell between global memory (16-byte aligned when vec16) and a
 // shared-memory cell, with consecutive lanes on consecutive addresses (coalesced); returns the
-// top limb's low word on loads. Groups of 4 words never straddle a 32-word row, so for K >= 4
-// both sides move 16-byte vectors.
+// top limb on loads. Groups of 4 words never straddle a 32-word row, so for K >= 4 both sides
+// move 16-byte vectors.
 template <int K>
-__device__ __forceinline__ uint32_t gmem_to_smem_cell(uint32_t *scell, const uint64_t *gcell, bool vec16,
+__device__ __forceinline__ uint64_t gmem_to_smem_cell(uint32_t *scell, const uint64_t *gcell, bool vec16,
                                                       const Geo &g) {
   const uint32_t *w32 = reinterpret_cast<const uint32_t *>(gcell);
   if (vec16 && (g.NW & 3) == 0) {
@@ -202,11 +202,11 @@ __device__ __forceinline__ uint32_t gmem_to_smem_cell(uint32_t *scell, const uin
       scell[pw + 1] = v.y;
     }
   }
-  return __ldg(w32 + g.NW);
+  return __ldg(gcell + g.NW / 2);
 }
 
 template <int K>
-__device__ __forceinline__ void smem_to_gmem_cell(uint64_t *gcell, const uint32_t *scell, uint32_t top, bool vec16,
+__device__ __forceinline__ void smem_to_gmem_cell(uint64_t *gcell, const uint32_t *scell, uint64_t top, bool vec16,
                                                   const Geo &g) {
   uint32_t *w32 = reinterpret_cast<uint32_t *>(gcell);
   if (vec16 && (g.NW & 3) == 0) {
@@ -225,7 +225,7 @@ __device__ __forceinline__ void smem_to_gmem_cell(uint64_t *gcell, const uint32_
       dst[q] = make_uint2(scell[pw], scell[pw + 1]);
     }
   }
-  if (g.lane == 0) gcell[g.NW / 2] = uint64_t(top);
+  if (g.lane == 0) gcell[g.NW / 2] = top;
 }
 
 // cell index of the job held at `slot` of CTA `rank` in the given layout
@@ -369,7 +369,7 @@ __global__ void __launch_bounds__(MINB == 3 ? 256 : 512, MINB) job_kernel(uint64
   kg.ord = SQ ? 4 * N : 2 * N;
   kg.mask = FULL ? uint32_t(kg.ord - 1) : mask;
   const Geo &g = kg.g;
-  const int nslots = 1 << ((jd.pad > 0 ? jd.pad : ls) - lc);
+  const int nslots = 1 << (job_ls(jd.pad, ls) - lc);
   const int L2 = nslots, b = nslots / C;
   const int P = cell_pitch_words(g.NW);
   uint32_t *cells = smem;
@@ -391,10 +391,15 @@ __global__ void __launch_bounds__(MINB == 3 ? 256 : 512, MINB) job_kernel(uint64
     const int m = job_cell(load_layout, rank, s, C, L2, b);
     if (m >= jd.nload) continue;
     const uint64_t *gc = x + (jd.cell0 + int64_t(m) * jd.mstride) * stride_limbs;
-    const uint32_t T = gmem_to_smem_cell<K>(cells + s * P, gc, vec16, g);
-    __syncwarp();
-    const int z = settle_smem<K>(lane_chunk<K>(cells + s * P, g), 0, -1 - int(T), g);
-    set_meta<K>(meta + s, z, 0, g);
+    const uint64_t T = gmem_to_smem_cell<K>(cells + s * P, gc, vec16, g);
+    if (T & kRawTopMark) {
+      // written by an earlier pass in internal form: the words are m, the top limb the metadata
+      if (g.lane == 0) meta[s] = uint32_t(T);
+    } else {
+      __syncwarp();
+      const int z = settle_smem<K>(lane_chunk<K>(cells + s * P, g), 0, -1 - int(T & 1u), g);
+      set_meta<K>(meta + s, z, 0, g);
+    }
   }
   __syncthreads();
 
@@ -422,13 +427,20 @@ __global__ void __launch_bounds__(MINB == 3 ? 256 : 512, MINB) job_kernel(uint64
     }
   }
 
-  // store: x = rotc(m, t) + 1, with the final scaling where requested
+  // store: x = rotc(m, t) + 1, with the final scaling where requested; or, when a later pass
+  // stores these cells again, m as it is with the rotation and zero flag in the top limb
+  const bool raw = (jd.pad & JOB_RAW_STORE) != 0;
   for (int s = warp; s < nslots; s += nw) {
     const int m = job_cell(store_layout, rank, s, C, L2, b);
     if (m >= jd.nstore) continue;
     uint32_t r[K];
     int E = int(meta[s] >> 1) + (m < jd.nscale ? jd.escale : 0);
     if (E >= kg.ord) E -= kg.ord;
+    uint64_t *gc = x + (jd.cell0 + int64_t(m) * jd.mstride) * stride_limbs;
+    if (raw) {
+      smem_to_gmem_cell<K>(gc, cells + s * P, kRawTopMark | (uint64_t(E) << 1) | (meta[s] & 1u), vec16, g);
+      continue;
+    }
     const int z = read_omega_pow<K, SQ>(r, cells + s * P, int(meta[s] & 1u), E, g);
     uint32_t top = 0;
     if (z) {
@@ -441,7 +453,6 @@ __global__ void __launch_bounds__(MINB == 3 ? 256 : 512, MINB) job_kernel(uint64
     __syncwarp();
     smem_store_plain<K>(cells + s * P, r, g);
     __syncwarp();
-    uint64_t *gc = x + (jd.cell0 + int64_t(m) * jd.mstride) * stride_limbs;
     smem_to_gmem_cell<K>(gc, cells + s * P, top, vec16, g);
   }
 }
