@@ -404,6 +404,7 @@ def run_gpu(args):
 
     sn = sn_leg(tg, device, stream, 10)
     pointwise = pointwise_leg(tg, device, stream)
+    e1 = None if args.no_e1 else e1_leg(tg, device, stream)
     ok &= sn["bit_exact_roundtrip"]
     batch = None if args.no_batch else batch_leg(tg, device, stream, 2, 3, not args.no_tune)
     ok &= batch is None or batch["bit_exact_vs_plain"]
@@ -441,6 +442,7 @@ def run_gpu(args):
     line["zero_padded_itft"] = padded
     line["sn"] = sn
     line["pointwise"] = pointwise
+    line["e1_sweep"] = e1
     if tuned is not None:
         line["tuned_config"] = tuned
     if batch is not None:
@@ -643,6 +645,68 @@ def sn_leg(tg, device, stream, steps):
             "gbs_algorithmic": round(gbs, 2), "bit_exact_roundtrip": ok}
 
 
+def e1_leg(tg, device, stream, reps=3):
+    """Products shaped like the Sec. 5.1 measurements: f and g of equal length (512 .. 16384 in
+    5 % steps), 8000-bit unsigned coefficients (ring N = 16384, as the paper's "about 16000
+    bits"). Per length: the zx_mul device time (operands and result resident), and on the
+    product's own ring the time of its three transforms truncated (z = length, n = the padded
+    output count) against full length (n = L, a plain power-of-two transform)."""
+    import numpy as np
+    import torch
+
+    w = workloads.SMOOTHNESS_SWEEP
+    lengths, v = [], float(w["len_lo"])
+    while int(round(v)) <= w["len_hi"]:
+        if not lengths or int(round(v)) != lengths[-1]:
+            lengths.append(int(round(v)))
+        v *= w["step"]
+    if lengths[-1] != w["len_hi"]:
+        lengths.append(w["len_hi"])
+    bits = w["bits"]
+    m = (bits + 63) // 64
+
+    def timed(fn):
+        fn()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize(device)
+        return a.elapsed_time(b) / reps
+
+    rows = []
+    for k, n in enumerate(lengths):
+        plan = tg.zx_plan(n, bits, n, bits)
+        F = torch.from_numpy(workloads.coefficients(w["seed"] + 2 * k, n, bits, m).view(np.int64)).to(device)
+        G = torch.from_numpy(workloads.coefficients(w["seed"] + 2 * k + 1, n, bits, m).view(np.int64)).to(device)
+        mh = plan["limbs_h"]
+        H = torch.empty((2 * n - 1) * mh, dtype=torch.int64, device=device)
+        t_mul = timed(lambda: tg.zx_mul(F, n, m, G, n, m, H, mh, False, bits, bits, stream=stream))
+        l, N, st, nf = plan["l"], plan["N"], plan["stride_limbs"], plan["n_fft"]
+        L = 1 << l
+        X = torch.from_numpy(workloads.residues(w["seed"] + 1000 + k, L, N, stride=st).view(np.int64)).to(device)
+        tf, itf = (tg.tft_sqrt2, tg.itft_sqrt2) if plan["sqrt2"] else (tg.tft_ex, tg.itft_ex)
+
+        def three(nn):
+            tf(X, l, n, nn, N, 0, st, stream=stream)
+            tf(X, l, n, nn, N, 0, st, stream=stream)
+            itf(X, l, nn, nn, 0, N, 0, st, scale=1, stream=stream)
+
+        t_trunc = timed(lambda: three(nf))
+        t_full = timed(lambda: three(L))
+        rows.append([n, l, round(t_mul, 4), round(t_trunc, 4), round(t_full, 4)])
+        del F, G, H, X
+    mul = [r[2] for r in rows]
+    steps = [mul[i + 1] / mul[i] for i in range(len(mul) - 1)]
+    return {"workload": f"{len(lengths)} products, equal lengths {lengths[0]} .. {lengths[-1]} in 5 % steps, "
+                        f"{bits}-bit unsigned coefficients, ring N = 16384, seed {w['seed']}",
+            "columns": ["length", "l", "ms_zx_mul", "ms_3_transforms_truncated", "ms_3_transforms_full_L"],
+            "rows": rows,
+            "max_step_ratio": round(max(steps), 3),
+            "truncated_over_full": round(sum(r[3] for r in rows) / sum(r[4] for r in rows), 4)}
+
+
 def pointwise_leg(tg, device, stream):
     """Pointwise products mod 2^N + 1 by both methods (schoolbook warp kernel; a second
     Schoenhage-Strassen level on the transform kernels): ms per batch of uniform residues,
@@ -745,6 +809,7 @@ def main():
     ap.add_argument("--no-batch", action="store_true", help="skip the 512-product batch leg")
     ap.add_argument("--no-tune", action="store_true", help="keep the default launch configurations")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving leg")
+    ap.add_argument("--no-e1", action="store_true", help="skip the Sec. 5.1-shaped product sweep")
     ap.add_argument("--serve-requests", type=int, default=1000)
     ap.add_argument("--serve-only", action="store_true", help="time only the serving leg")
     ap.add_argument("--batch-only", action="store_true",
