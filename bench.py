@@ -366,17 +366,36 @@ def run_gpu(args):
                             for n in ns)
     traffic = recorded_traffic()
 
-    # end to end through the C ABI with host buffers: H2D inputs, TFT, ITFT, D2H results
-    pinned = {n: torch.from_numpy(host[n].view(np.int64)).pin_memory() for n in ns}
+    # end to end through the C ABI with host buffers: per n, H2D of its n input cells from
+    # pinned memory, TFT, ITFT, D2H of its n result cells (the other L - n cells of a buffer are
+    # the transforms' scratch and stay on the device). The copies run on their own streams, so
+    # the copies of one n overlap the transforms of the others; a buffer is refilled only after
+    # its previous results have left.
+    span = {n: n * stride for n in ns}  # limbs of the n cells
+    pinned = {n: torch.from_numpy(host[n].view(np.int64)[:span[n]].copy()).pin_memory() for n in ns}
     outp = {n: torch.empty_like(pinned[n]).pin_memory() for n in ns}
     h2d = sum(pinned[n].numel() * 8 for n in ns)
+    s_in, s_comp, s_out = torch.cuda.Stream(device), torch.cuda.Stream(device), torch.cuda.Stream(device)
+    drained = {}
 
     def e2e_step():
         for n in ns:
-            dev[n].copy_(pinned[n], non_blocking=True)
-            tg.tft_ex(dev[n], l, n, n, N, 0, stride, stream=stream)
-            tg.itft_ex(dev[n], l, n, n, 0, N, 0, stride, 1, stream=stream)
-            outp[n].copy_(dev[n], non_blocking=True)
+            if n in drained:
+                s_in.wait_event(drained[n])
+            with torch.cuda.stream(s_in):
+                dev[n][:span[n]].copy_(pinned[n], non_blocking=True)
+            arrived = torch.cuda.Event()
+            arrived.record(s_in)
+            s_comp.wait_event(arrived)
+            tg.tft_ex(dev[n], l, n, n, N, 0, stride, stream=s_comp)
+            tg.itft_ex(dev[n], l, n, n, 0, N, 0, stride, 1, stream=s_comp)
+            done = torch.cuda.Event()
+            done.record(s_comp)
+            s_out.wait_event(done)
+            with torch.cuda.stream(s_out):
+                outp[n].copy_(dev[n][:span[n]], non_blocking=True)
+            drained[n] = torch.cuda.Event()
+            drained[n].record(s_out)
 
     e2e_secs = timed_steps(e2e_step, max(1, args.steps // 2), 1, sync, device)
     e2e_value = sb * max(1, args.steps // 2) * ws / e2e_secs / 1e9
