@@ -505,6 +505,42 @@ __device__ __forceinline__ void rot_window(const uint32_t *cell, int E, const Ge
   }
 }
 
+// The same window for K <= 2 (rows of 33 words, scalar reads): a lane's K + 1 source words
+// cross at most one 32-word row of the padded cell (or the end of the cell), so the window is
+// two runs of consecutive addresses, each with a lane-uniform complement mask.
+template <int K, class Emit>
+__device__ __forceinline__ void rot_window_scalar(const uint32_t *cell, int E, const Geo &g, Emit &emit) {
+  const bool low_wrapped = E < g.N;  // complement the wrapped bits (else the others)
+  const int Ep = low_wrapped ? E : E - g.N;
+  const int q = Ep >> 5, sh = Ep & 31;
+  const int lam0 = K * g.lane - q - 1;  // logical index of window word 0 (negative: wrapped)
+  const int i0 = lam0 < 0 ? lam0 + g.NW : lam0;
+  int tb, baseA, baseB;
+  if (g.NW >= 32) {
+    const int c0 = i0 & 31, r0 = i0 >> 5, rows = g.NW >> 5;
+    const int r1 = (r0 + 1 == rows) ? 0 : r0 + 1;
+    tb = 31 - c0;
+    baseA = 33 * r0 + c0;
+    baseB = 33 * r1 + c0 - 32;
+  } else {
+    tb = g.NW - 1 - i0;
+    baseA = i0;
+    baseB = i0 - g.NW;
+  }
+  const uint32_t flip = low_wrapped ? 0u : TFT_FULL;
+  const uint32_t mA = (lam0 < 0 ? TFT_FULL : 0u) ^ flip;
+  const uint32_t mB = (lam0 + tb + 1 < 0 ? TFT_FULL : 0u) ^ flip;
+  uint32_t prev = cell[0 <= tb ? baseA : baseB] ^ (0 <= tb ? mA : mB);
+#pragma unroll
+  for (int s = 0; s < K; s++) {
+    const int t = s + 1;
+    const bool inA = t <= tb;
+    const uint32_t cur = cell[(inA ? baseA : baseB) + t] ^ (inA ? mA : mB);
+    emit(s, __funnelshift_l(prev, cur, sh));  // (cur:prev) << sh, high word (cur for sh = 0)
+    prev = cur;
+  }
+}
+
 // raw = rotc(m, E) for the cell (see the file comment); E in [0, 2N). The zero cell reads as
 // all ones with the returned flag set (then x 2^E = raw + 1 - 2^N = 0).
 //
@@ -544,42 +580,12 @@ __device__ __forceinline__ int smem_read_raw(uint32_t (&r)[K], const uint32_t *c
     for (int s = 0; s < K; s++) r[s] = 0u;
     return 0;
   }
-  if constexpr (K >= 4) {
-    auto put = [&](int s, uint32_t w) { r[s] = w; };
+  auto put = [&](int s, uint32_t w) { r[s] = w; };
+  if constexpr (K >= 4)
     rot_window<K>(cell, E, g, put);
-    return 0;
-  } else {
-    const bool low_wrapped = E < g.N;  // complement the wrapped bits (else the others)
-    const int Ep = low_wrapped ? E : E - g.N;
-    const int q = Ep >> 5, sh = Ep & 31;
-    const int lam0 = K * g.lane - q - 1;  // logical index of window word 0 (negative: wrapped)
-    const int i0 = lam0 < 0 ? lam0 + g.NW : lam0;
-    int tb, baseA, baseB;
-    if (g.NW >= 32) {
-      const int c0 = i0 & 31, r0 = i0 >> 5, rows = g.NW >> 5;
-      const int r1 = (r0 + 1 == rows) ? 0 : r0 + 1;
-      tb = 31 - c0;
-      baseA = 33 * r0 + c0;
-      baseB = 33 * r1 + c0 - 32;
-    } else {
-      tb = g.NW - 1 - i0;
-      baseA = i0;
-      baseB = i0 - g.NW;
-    }
-    const uint32_t flip = low_wrapped ? 0u : TFT_FULL;
-    const uint32_t mA = (lam0 < 0 ? TFT_FULL : 0u) ^ flip;
-    const uint32_t mB = (lam0 + tb + 1 < 0 ? TFT_FULL : 0u) ^ flip;
-    uint32_t prev = cell[0 <= tb ? baseA : baseB] ^ (0 <= tb ? mA : mB);
-#pragma unroll
-    for (int s = 0; s < K; s++) {
-      const int t = s + 1;
-      const bool inA = t <= tb;
-      const uint32_t cur = cell[(inA ? baseA : baseB) + t] ^ (inA ? mA : mB);
-      r[s] = __funnelshift_l(prev, cur, sh);  // (cur:prev) << sh, high word (cur for sh = 0)
-      prev = cur;
-    }
-    return 0;
-  }
+  else
+    rot_window_scalar<K>(cell, E, g, put);
+  return 0;
 }
 
 // r = r - rotc(m, E) - bin over this lane's chunk, as one borrow chain (E in [0, 2N), m the
@@ -600,35 +606,7 @@ __device__ __forceinline__ uint32_t smem_sub_rotated(uint32_t (&r)[K], const uin
   } else if constexpr (K >= 4) {
     rot_window<K>(cell, E, g, sub);
   } else {
-    const bool low_wrapped = E < g.N;
-    const int Ep = low_wrapped ? E : E - g.N;
-    const int q = Ep >> 5, sh = Ep & 31;
-    const int lam0 = K * g.lane - q - 1;
-    const int i0 = lam0 < 0 ? lam0 + g.NW : lam0;
-    int tb, baseA, baseB;
-    if (g.NW >= 32) {
-      const int c0 = i0 & 31, r0 = i0 >> 5, rows = g.NW >> 5;
-      const int r1 = (r0 + 1 == rows) ? 0 : r0 + 1;
-      tb = 31 - c0;
-      baseA = 33 * r0 + c0;
-      baseB = 33 * r1 + c0 - 32;
-    } else {
-      tb = g.NW - 1 - i0;
-      baseA = i0;
-      baseB = i0 - g.NW;
-    }
-    const uint32_t flip = low_wrapped ? 0u : TFT_FULL;
-    const uint32_t mA = (lam0 < 0 ? TFT_FULL : 0u) ^ flip;
-    const uint32_t mB = (lam0 + tb + 1 < 0 ? TFT_FULL : 0u) ^ flip;
-    uint32_t prev = cell[0 <= tb ? baseA : baseB] ^ (0 <= tb ? mA : mB);
-#pragma unroll
-    for (int s = 0; s < K; s++) {
-      const int t = s + 1;
-      const bool inA = t <= tb;
-      const uint32_t cur = cell[(inA ? baseA : baseB) + t] ^ (inA ? mA : mB);
-      sub(s, __funnelshift_l(prev, cur, sh));
-      prev = cur;
-    }
+    rot_window_scalar<K>(cell, E, g, sub);
   }
   asm volatile("subc.u32 %0, 0, 0;" : "=r"(bout));
   return bout & 1u;
