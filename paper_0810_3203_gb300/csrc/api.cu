@@ -167,6 +167,31 @@ int device_product(const zx_poly *f, const zx_poly *g, zx_poly *h, BatchProduct 
   return ZX_OK;
 }
 
+// A non-blocking stream of the calling thread on the current device, with two events, for
+// work that forks from a caller's stream and joins it again (events order it both ways, so a
+// helper shared by successive calls is always correct).
+cudaError_t helper_stream(cudaStream_t *s, cudaEvent_t *fork, cudaEvent_t *join) {
+  struct Helper {
+    cudaStream_t s = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
+  };
+  static thread_local Helper per_dev[16];
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 16) return cudaErrorInvalidDevice;
+  Helper &h = per_dev[dev];
+  if (!h.s) {
+    if ((e = cudaStreamCreateWithFlags(&h.s, cudaStreamNonBlocking)) != cudaSuccess) return e;
+    if ((e = cudaEventCreateWithFlags(&h.fork, cudaEventDisableTiming)) != cudaSuccess) return e;
+    if ((e = cudaEventCreateWithFlags(&h.join, cudaEventDisableTiming)) != cudaSuccess) return e;
+  }
+  *s = h.s;
+  *fork = h.fork;
+  *join = h.join;
+  return cudaSuccess;
+}
+
 // Pointwise method for ring N: 1 (schoolbook) or 2 (recursive, with *rp filled). Auto picks the
 // recursion when its estimated word operations fall below kRecAutoRatio of the schoolbook's
 // NW^2 word products. Measured on GB300 (10^4 products at N = 32768: 9.27 ms recursive, 1.38 ms
@@ -383,13 +408,19 @@ int zx_mul(const zx_poly *f, const zx_poly *g, zx_poly *h, void *stream) {
     cleanup();
     return fail(err ? err : ZX_ECUDA, "planning failed");
   }
-  if ((ce = launch_pack(df, f->len, f->limbs, f->is_signed, F, zp.stride, zp.ring, s)) != cudaSuccess ||
-      (ce = launch_pack(dg, g->len, g->limbs, g->is_signed, Gb, zp.stride, zp.ring, s)) != cudaSuccess ||
-      (ce = run_transform(*pf, F, zp.stride, s)) != cudaSuccess ||
-      (ce = run_transform(*pg, Gb, zp.stride, s)) != cudaSuccess ||
+  // the two forward transforms are independent: g's runs on a helper stream forked from s
+  cudaStream_t s2 = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr;
+  if ((ce = helper_stream(&s2, &fork, &join)) != cudaSuccess || (ce = cudaEventRecord(fork, s)) != cudaSuccess ||
+      (ce = cudaStreamWaitEvent(s2, fork, 0)) != cudaSuccess ||
+      (ce = launch_pack(dg, g->len, g->limbs, g->is_signed, Gb, zp.stride, zp.ring, s2)) != cudaSuccess ||
+      (ce = run_transform(*pg, Gb, zp.stride, s2)) != cudaSuccess || (ce = cudaEventRecord(join, s2)) != cudaSuccess ||
+      (ce = launch_pack(df, f->len, f->limbs, f->is_signed, F, zp.stride, zp.ring, s)) != cudaSuccess ||
+      (ce = run_transform(*pf, F, zp.stride, s)) != cudaSuccess || (ce = cudaStreamWaitEvent(s, join, 0)) != cudaSuccess ||
       (ce = pointwise_products(F, Gb, zp.nf, zp.stride, zp.ring, s, &err)) != cudaSuccess ||
       (ce = run_transform(*pi, F, zp.stride, s)) != cudaSuccess ||
       (ce = launch_lift(F, zp.n, zp.stride, sgn, hd, h->limbs, zp.ring, s)) != cudaSuccess) {
+    if (s2 && join && cudaEventRecord(join, s2) == cudaSuccess) cudaStreamWaitEvent(s, join, 0);  // before the frees
     cleanup();
     return cuda_fail(ce, "zx_mul launch");
   }

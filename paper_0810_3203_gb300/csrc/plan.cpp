@@ -184,9 +184,14 @@ struct Planner {
   // every CTA row of the job's split holds at least one cell per CTA (2 lc <= l)
   int cluster_log2(int l) const { return l <= ls_max ? 0 : l - ls_c; }
   bool leaf(int l) const {
+    // a whole transform of more than 64 cells takes the two-pass split: as one job it would run
+    // on a single CTA (one SM) for l levels, as two passes its jobs spread over the SMs
+    if (depth == 0 && l > kTopSingleJobMax) return false;
     const int lc = cluster_log2(l);
     return lc == 0 || (lc <= kMaxClusterLog2 && 2 * lc <= l);
   }
+  static constexpr int kTopSingleJobMax = 6;
+  int depth = 0;  // recursion depth of the current tft / itft call (0: the whole transform)
 
   void job(int pass, int kind, int64_t cell0, int64_t ms, int l, int64_t e, int64_t z, int64_t n,
            int f, int64_t nscale, int64_t escale) {
@@ -221,10 +226,12 @@ struct Planner {
     int64_t n2 = n % L2, n1 = n / L2, n1p = (n + L2 - 1) / L2;
     int64_t z2 = z % L2, z1 = z / L2, z2p = z1 > 0 ? L2 : z2;
     int dc = 0, dr = 0;
+    depth++;
     for (int64_t u = 0; u < z2p; u++)
       dc = std::max(dc, tft(pass, cell0 + u * ms, ms * L2, l1, e + u * w, u < z2 ? z1 + 1 : z1, n1p));
     for (int64_t u = 0; u < n1p; u++)
       dr = std::max(dr, tft(pass + dc, cell0 + u * L2 * ms, ms, l2, e * L1, z2p, u < n1 ? L2 : n2));
+    depth--;
     return dc + dr;
   }
 
@@ -243,6 +250,7 @@ struct Planner {
     int64_t z2p = z1 > 0 ? L2 : z2;
     int64_t m = std::min(n2, z2), mp = std::max(n2, z2);
     int p = pass, d = 0;
+    depth++;
     for (int64_t u = 0; u < n1; u++) d = std::max(d, itft(p, cell0 + u * L2 * ms, ms, l2, e * L1, L2, L2, 0, -1));
     p += d;
     d = 0;
@@ -254,6 +262,7 @@ struct Planner {
     for (int64_t u = 0; u < n2; u++)
       d = std::max(d, itft(p, cell0 + u * ms, ms * L2, l1, e + u * w, u < m ? z1 + 1 : z1, n1 + 1, 0, escale));
     p += d;
+    depth--;
     return p - pass;
   }
 };
@@ -326,6 +335,7 @@ int64_t zero_padded_outputs(int l, int64_t n, int64_t N) {
     g <<= (ll - l1);
     grains.push_back(g);
     ll = l1;
+    P.depth = 1;  // below the whole transform
   }
   if (grains.empty()) return n;
   // the top level's whole rows always (they remove a pass); finer ones while they add at most n/32
