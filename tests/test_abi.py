@@ -153,3 +153,20 @@ def test_recursive_pointwise_plans_follow_the_ring_rules(lib):
         tg.pointwise_plan(4096, 5)
     assert ei.value.code == tg.ZX_EINVAL
     assert lib.zx_pointwise(None, None, 1, 4096, 65, 1, None) == tg.ZX_EINVAL
+
+
+def test_whole_transforms_above_64_cells_take_two_passes(lib):
+    """A whole transform of more than 64 cells is never a single job (that job would run all l
+    levels on one CTA while the other SMs idle): it takes the Bailey split, whose jobs spread
+    over the SMs; up to 64 cells it stays one job."""
+    import paper_0810_3203_gb300 as tg
+    for N in (128, 1024, 4096):
+        for l in range(1, 12):
+            if (2 * N) % (1 << l):
+                continue
+            L = 1 << l
+            shape = tg.transform_plan(0, l, L, L, N)
+            if l <= 6:
+                assert shape["passes"] == 1 and shape["jobs"] == 1, (N, l, shape)
+            else:
+                assert shape["passes"] >= 2 and shape["jobs"] > 1, (N, l, shape)
