@@ -102,3 +102,28 @@ def test_large_sqrt2_product_eval_mod(tg, orc):
         t = rng.randrange(P)
         lhs = orc.poly_eval_mod(f, lf, m, False, t, P) * orc.poly_eval_mod(g, lg, m, False, t, P) % P
         assert lhs == orc.poly_eval_mod(h, lf + lg - 1, mh, False, t, P)
+
+
+def test_largest_transform_the_library_takes(tg, orc):
+    """The largest transform: omega = sqrt2 over Z/(2^32768+1) at L = 4N = 2^17 (537 MB of
+    cells), z = n = 100000 with the stride padded to 16 bytes. Every TFT output against the
+    oracle's Algorithm 1, every ITFT output (with f = 1) against the oracle's Algorithm 2, and
+    the scaled round trip restoring the input."""
+    N, l, n = 32768, 17, 100000
+    W = N // 64 + 1
+    st = W + (W & 1)
+    x = workloads.residues(41, n, N, stride=st, cells=1 << l)
+    cols = lambda a, k: a.reshape(-1, st)[:k, :W]
+    ref = x.copy()
+    orc.sqrt2_tft(ref, l, n, n, 5, N, stride=st)
+    got = run(tg.tft_sqrt2, x, l, n, n, N, 5, st)
+    assert np.array_equal(cols(got, n), cols(ref, n)), "TFT"
+    ref = x.copy()
+    orc.sqrt2_itft(ref, l, n, n - 1, 1, 5, N, stride=st)
+    got = run(tg.itft_sqrt2, x, l, n, n - 1, 1, N, 5, st)
+    assert np.array_equal(cols(got, n), cols(ref, n)), "ITFT"
+    d = torch.from_numpy(x.view(np.int64)).cuda()
+    tg.tft_sqrt2(d, l, n, n, N, 0, st)
+    tg.itft_sqrt2(d, l, n, n, 0, N, 0, st, scale=1)
+    torch.cuda.synchronize()
+    assert np.array_equal(cols(d.cpu().numpy().view(np.uint64), n), cols(x, n)), "round trip"
