@@ -147,7 +147,11 @@ int zx_plan(int64_t len_f, int64_t bits_f, int64_t len_g, int64_t bits_g, int is
  *   stream-ordered memory pool on `stream` and returned to it before the call's work ends.
  *   Host operands are copied with cudaMemcpyAsync on `stream` (pinned host memory makes those
  *   copies asynchronous); when any operand is on the host the call synchronises `stream`
- *   before returning, otherwise it is asynchronous.
+ *   before returning, otherwise it is asynchronous. g's packing and TFT run on an internal
+ *   stream of the calling thread, forked from `stream` and joined back into it with events,
+ *   so all of the call's work is ordered after the work already on `stream` and before
+ *   anything enqueued on `stream` later. When the pointwise method for N is the recursive one
+ *   (zx_pointwise_plan), its scratch also comes from the pool on `stream`.
  */
 int zx_mul(const zx_poly *f, const zx_poly *g, zx_poly *h, void *stream);
 
