@@ -89,10 +89,12 @@ struct TransformPlan {
 };
 
 // Cached plan of TFT (kind = KIND_TFT) or ITFT for the given parameters; nullptr with *err set
-// on failure. escale < 0 means no final scaling.
+// on failure. escale < 0 means no final scaling. `replicated`: the plan runs on many sequences
+// at once (run_transform_reps), so a transform that fits one job stays one job (alone, one
+// that has more than 64 cells takes two passes to spread over the SMs).
 const TransformPlan *get_transform_plan(int kind, int l, int64_t z, int64_t n, int f, int64_t N,
                                         int64_t e, int64_t stride_limbs, int scale, int *err,
-                                        int mode = RING_FERMAT);
+                                        int mode = RING_FERMAT, bool replicated = false);
 
 // Outputs a product's transforms compute when the product length n is padded with known zero
 // coefficients up to a whole number of rows of the top-level split (Sec. 6): the ITFT then has

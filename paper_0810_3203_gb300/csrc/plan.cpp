@@ -189,11 +189,12 @@ struct Planner {
   bool leaf(int l) const {
     // a whole transform of more than 64 cells takes the two-pass split: as one job it would run
     // on a single CTA (one SM) for l levels, as two passes its jobs spread over the SMs
-    if (depth == 0 && l > kTopSingleJobMax) return false;
+    if (whole_split && depth == 0 && l > kTopSingleJobMax) return false;
     const int lc = cluster_log2(l);
     return lc == 0 || (lc <= kMaxClusterLog2 && 2 * lc <= l);
   }
   static constexpr int kTopSingleJobMax = 6;
+  bool whole_split = true;  // false for plans that run on many sequences at once
   int depth = 0;  // recursion depth of the current tft / itft call (0: the whole transform)
 
   void job(int pass, int kind, int64_t cell0, int64_t ms, int l, int64_t e, int64_t z, int64_t n,
@@ -418,13 +419,15 @@ void build_host_plan(int kind, int l, int64_t z, int64_t n, int f, int64_t N, in
 }
 
 const TransformPlan *get_transform_plan(int kind, int l, int64_t z, int64_t n, int f, int64_t N,
-                                        int64_t e, int64_t stride_limbs, int scale, int *err, int mode) {
+                                        int64_t e, int64_t stride_limbs, int scale, int *err, int mode,
+                                        bool replicated) {
   int dev = 0;
   cudaGetDevice(&dev);
   const int64_t twoN = omega_order(N, mode);
   e = md(e, twoN);
   const PlanConfig cfg = plan_config(N);
-  const int cfg_key = cfg.ls_max | (cfg.ls_c << 5) | (cfg.max_warps << 10) | (cfg.split << 16) | (mode << 20);
+  const int cfg_key = cfg.ls_max | (cfg.ls_c << 5) | (cfg.max_warps << 10) | (cfg.split << 16) | (mode << 20) |
+                      (replicated ? 1 << 23 : 0);
   auto key = std::make_tuple(dev, kind, l, z, n, f, N, e, scale, cfg_key);
   PlanCache &pc = plan_cache();
   {
@@ -433,6 +436,7 @@ const TransformPlan *get_transform_plan(int kind, int l, int64_t z, int64_t n, i
     if (it != pc.plans.end()) return it->second.get();
   }
   Planner P(N, &cfg, mode);
+  P.whole_split = !replicated;
   int npass;
   if (kind == KIND_TFT)
     npass = P.tft(0, 0, 1, l, e, z, n);

@@ -348,8 +348,9 @@ cudaError_t run_rec_pointwise(uint64_t *a, const uint64_t *b, int64_t n, int64_t
   if (n <= 0) return cudaSuccess;
   const Ring ri = make_ring(rp.Ni);
   const int64_t Ki = int64_t(1) << rp.k;
-  const TransformPlan *pt = get_transform_plan(KIND_TFT, rp.k, Ki, Ki, 0, rp.Ni, 0, rp.stride_i, 0, err);
-  const TransformPlan *pi = pt ? get_transform_plan(KIND_ITFT, rp.k, Ki, Ki, 0, rp.Ni, 0, rp.stride_i, 1, err) : nullptr;
+  const TransformPlan *pt = get_transform_plan(KIND_TFT, rp.k, Ki, Ki, 0, rp.Ni, 0, rp.stride_i, 0, err, RING_FERMAT, true);
+  const TransformPlan *pi =
+      pt ? get_transform_plan(KIND_ITFT, rp.k, Ki, Ki, 0, rp.Ni, 0, rp.stride_i, 1, err, RING_FERMAT, true) : nullptr;
   if (!pi) {
     if (*err == ZX_OK) *err = ZX_ECUDA;
     return cudaErrorInvalidValue;
