@@ -54,17 +54,16 @@ int cluster_cta_ls(const Ring &r) {
 }
 
 // Default: the largest single-CTA job the shared memory allows, eight cells per CTA of a cluster
-// job, eight warps per CTA (sixteen when the largest job fills an SM's shared memory), the
-// paper's split. Measured on GB300 (zx_tune): small
+// job, up to sixteen warps per CTA, the paper's split. Measured on GB300 (zx_tune): small
 // clusters and CTAs that three or more share an SM beat fewer, larger jobs with fewer passes,
 // because a job's time is set by the latency of its dependency levels.
 PlanConfig default_config(const Ring &r) {
   PlanConfig c;
   c.ls_max = max_onchip_ls(r);
   c.ls_c = std::min(3, cluster_cta_ls(r));
-  // 16 warps when the largest job holds a whole SM's shared memory anyway (one CTA per SM):
-  // then nothing else hides its latency. Jobs that three CTAs per SM can hold keep 8 warps.
-  c.max_warps = (size_t(1) << c.ls_max) * (size_t(r.pitch) + 1) * 4 > size_t(75) * 1024 ? 16 : 8;
+  // up to 16 warps per CTA; a launch with enough CTAs to fill the SMs three deep runs jobs
+  // that fit three to an SM with 8 (launch_k)
+  c.max_warps = 16;
   c.split = 0;
   return c;
 }
@@ -101,6 +100,8 @@ int warps_for_job(int ls, int lc, int max_warps) {
   const int nslots = 1 << (ls - lc);
   return std::max(1, std::min(max_warps, nslots / 2));
 }
+
+
 
 namespace {
 

@@ -490,6 +490,18 @@ cudaError_t launch_km(const Launch &L, uint64_t *x, int64_t stride_limbs, const 
                             L.lc, mask, prog_cap, L.d_segs, L.nsegs, rep_cells, reps > 1 ? int(per_rep) : 0);
 }
 
+// SMs of the current device (cached per host thread and device)
+int sm_count() {
+  static thread_local int dev_cached = -1, count = 0;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 152;
+  if (dev != dev_cached) {
+    if (cudaDeviceGetAttribute(&count, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || count <= 0) count = 152;
+    dev_cached = dev;
+  }
+  return count;
+}
+
 template <int K, bool SQ>
 cudaError_t launch_k(const Launch &L, uint64_t *x, int64_t stride_limbs, const Ring &r, cudaStream_t s,
                      int64_t reps, int64_t rep_cells) {
@@ -497,14 +509,19 @@ cudaError_t launch_k(const Launch &L, uint64_t *x, int64_t stride_limbs, const R
   const size_t base_words = (size_t(nslots) * size_t(r.pitch) + size_t(nslots) + 1) & ~size_t(1);
   const uint32_t ord = uint32_t((SQ ? 4 : 2) * r.N);
   const uint32_t mask = (ord & (ord - 1)) == 0 ? ord - 1 : 0u;
-  // three CTAs per SM when the cells fit in 75 KB; the program is staged in shared memory only
-  // if it fits beside them (else its ops are read through the read-only path)
+  // three CTAs per SM of at most 8 warps when the cells fit in 75 KB and the launch has the
+  // CTAs to fill the SMs three deep (a smaller launch gives each CTA all of its warps instead);
+  // the program is staged in shared memory only if it fits beside the cells (else its ops are
+  // read through the read-only path)
   const size_t small_words = (75 * 1024) / 4;
-  if (L.nwarps <= 8 && base_words <= small_words) {
+  const int64_t ctas = (int64_t(L.njobs) << L.lc) * reps;
+  if (base_words <= small_words && (L.nwarps <= 8 || ctas >= 3 * int64_t(sm_count()))) {
+    Launch L8 = L;
+    L8.nwarps = std::min(L.nwarps, 8);
     const int cap = size_t(L.prog_words) <= small_words - base_words ? L.prog_words : 0;
     const size_t smem = (base_words + size_t(cap)) * 4;
-    return r.G == 32 ? launch_km<K, 3, true, SQ>(L, x, stride_limbs, r, s, smem, cap, mask, reps, rep_cells)
-                     : launch_km<K, 3, false, SQ>(L, x, stride_limbs, r, s, smem, cap, mask, reps, rep_cells);
+    return r.G == 32 ? launch_km<K, 3, true, SQ>(L8, x, stride_limbs, r, s, smem, cap, mask, reps, rep_cells)
+                     : launch_km<K, 3, false, SQ>(L8, x, stride_limbs, r, s, smem, cap, mask, reps, rep_cells);
   }
   const size_t max_words = (227 * 1024) / 4;
   const int prog_cap = int(std::min<size_t>(size_t(L.prog_words), max_words > base_words ? max_words - base_words : 0));
