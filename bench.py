@@ -463,6 +463,8 @@ def run_gpu(args):
     sn = sn_leg(tg, device, stream, 10)
     pointwise = pointwise_leg(tg, device, stream)
     e1 = None if args.no_e1 else e1_leg(tg, device, stream)
+    small = small_legs(tg, device, stream)
+    ok &= small["small_round_trip"]["bit_exact_roundtrip"]
     ok &= sn["bit_exact_roundtrip"]
     batch = None if args.no_batch else batch_leg(tg, device, stream, 2, 3, not args.no_tune)
     ok &= batch is None or batch["bit_exact_vs_plain"]
@@ -503,6 +505,7 @@ def run_gpu(args):
     line["sn"] = sn
     line["pointwise"] = pointwise
     line["e1_sweep"] = e1
+    line.update(small)
     if tuned is not None:
         line["tuned_config"] = tuned
     if batch is not None:
@@ -703,6 +706,54 @@ def sn_leg(tg, device, stream, steps):
     return {"workload": f"S[y]/(y^{H}+1) over Z/mZ, m = 2^40 + 15, L = 2^{l}, n = {n}, pieces of {M // 4} "
                         "coefficients, seed 7", "ms_per_round_trip": round(sec * 1e3, 3),
             "gbs_algorithmic": round(gbs, 2), "bit_exact_roundtrip": ok}
+
+
+def small_legs(tg, device, stream, reps=50):
+    """The small round trip (TFT then ITFT over Z/(2^1024+1), L = 2^8, n = z = 200) timed call
+    by call, its bound being latency; and the medium product (3000 x 2500 coefficients of 2000
+    bits, ring N = 4096) through zx_mul. Operands resident; medians of CUDA-event times."""
+    import numpy as np
+    import torch
+
+    def median_ms(fn):
+        for _ in range(5):
+            fn()
+        torch.cuda.synchronize(device)
+        times = []
+        for _ in range(reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            b.synchronize()
+            times.append(a.elapsed_time(b))
+        return statistics.median(times)
+
+    w = workloads.ROUNDTRIP_SMALL
+    N, l, n = w["N"], w["l"], w["n"]
+    W = N // 64 + 1
+    x = workloads.residues(w["seed"], n, N, cells=1 << l)
+    d = torch.from_numpy(x.view(np.int64)).to(device)
+    t_tft = median_ms(lambda: tg.tft(d, l, n, N, stream=stream))
+    t_itft = median_ms(lambda: tg.itft(d, l, n, N, stream=stream))
+    t_rt = median_ms(lambda: (tg.tft(d, l, n, N, stream=stream), tg.itft(d, l, n, N, stream=stream)))
+    # as many ITFTs as TFTs, each ITFT inverting a TFT: the buffer is back to x
+    ok = bool(np.array_equal(d.cpu().numpy().view(np.uint64)[:n * W], x[:n * W]))
+    p = workloads.PRODUCT_MEDIUM
+    bits, lf, lg = p["bits"], p["len_f"], p["len_g"]
+    m = (bits + 63) // 64
+    F = torch.from_numpy(workloads.coefficients(p["seed"], lf, bits, m).view(np.int64)).to(device)
+    G = torch.from_numpy(workloads.coefficients(p["seed"] + 1, lg, bits, m).view(np.int64)).to(device)
+    plan = tg.zx_plan(lf, bits, lg, bits)
+    mh = plan["limbs_h"]
+    H = torch.zeros((lf + lg - 1) * mh, dtype=torch.int64, device=device)
+    t_mul = median_ms(lambda: tg.zx_mul(F, lf, m, G, lg, m, H, mh, False, bits, bits, stream=stream))
+    return {"small_round_trip": {"workload": f"Z/(2^{N}+1), L = 2^{l}, n = z = {n}, seed {w['seed']}",
+                                 "us_tft": round(t_tft * 1e3, 1), "us_itft": round(t_itft * 1e3, 1),
+                                 "us_round_trip": round(t_rt * 1e3, 1), "bit_exact_roundtrip": ok},
+            "medium_product": {"workload": f"{lf} x {lg} coefficients of {bits} bits, unsigned, seed {p['seed']}; "
+                                           f"ring N = {plan['N']}, L = 2^{plan['l']}",
+                               "ms_zx_mul": round(t_mul, 4)}}
 
 
 def e1_leg(tg, device, stream, reps=3):
