@@ -115,37 +115,53 @@ def recorded_traffic():
 
 
 class ClockSampler:
-    """nvidia-smi samples (every 200 ms) while the timed region runs."""
+    """nvidia-smi samples every 50 ms, each stamped on arrival. Started before the warm-up (the
+    tool takes a moment to start); only the samples stamped inside the timed region
+    [mark_start(), mark_stop() + one interval] count. If none lands there (a region shorter than
+    the interval), the first sample after the region's start is used and flagged."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    INTERVAL_S = 0.05
 
     def __init__(self, gpu_index):
         self.gpu = gpu_index
         self.proc = None
         self.lines = []
         self.thread = None
+        self.t0 = self.t1 = None
 
     def start(self):
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", str(int(self.INTERVAL_S * 1000))],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except Exception:
             self.proc = None
             return
         self.thread = threading.Thread(target=self._read, daemon=True)
         self.thread.start()
+        deadline = time.perf_counter() + 3.0
+        while not self.lines and time.perf_counter() < deadline:
+            time.sleep(0.01)
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.perf_counter(), line.strip()))
+
+    def mark_start(self):
+        self.t0 = time.perf_counter()
+
+    def mark_stop(self):
+        self.t1 = time.perf_counter()
 
     def stop(self):
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        # one more interval, so that a sample taken inside the region has arrived
+        time.sleep(self.INTERVAL_S * 1.5)
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)
@@ -153,9 +169,17 @@ class ClockSampler:
             self.proc.kill()
         if self.thread:
             self.thread.join(timeout=2)
+        t0 = self.t0 if self.t0 is not None else float("-inf")
+        t1 = (self.t1 if self.t1 is not None else float("inf")) + self.INTERVAL_S
+        inside = [ln for t, ln in self.lines if t0 <= t <= t1]
+        note = None
+        if not inside:
+            after = [ln for t, ln in self.lines if t >= t0]
+            inside = after[:1]
+            note = "no sample inside the timed region; the first one after its start"
         sm, smax, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        for ln in inside:
             parts = [p.strip() for p in ln.split(",")]
             if len(parts) < 9:
                 continue
@@ -167,9 +191,12 @@ class ClockSampler:
             for name, val in zip(names, parts[5:9]):
                 if val.lower().startswith("active"):
                     reasons.add(name)
-        return {"sm_mhz": statistics.median(sm) if sm else None,
-                "sm_max_mhz": max(smax) if smax else None,
-                "reasons": sorted(reasons), "samples": len(sm)}
+        out = {"sm_mhz": statistics.median(sm) if sm else None,
+               "sm_max_mhz": max(smax) if smax else None,
+               "reasons": sorted(reasons), "samples": len(sm), "interval_ms": int(self.INTERVAL_S * 1000)}
+        if note:
+            out["note"] = note
+        return out
 
 
 # ---------------------------------------------------------------- distributed helpers
@@ -350,20 +377,22 @@ def run_gpu(args):
         torch.cuda.synchronize(device)
 
     clocks = ClockSampler(local)
+    clocks.start()
     # warm-up, then exactly K timed steps between barriers and device syncs
     for _ in range(args.warmup):
         step()
     sync()
     barrier(device)
     sync()
-    clocks.start()
     start, stop = mk(), mk()
     t0 = time.perf_counter()
+    clocks.mark_start()
     start.record(stream)
     for k in range(args.steps):
         step()
     stop.record(stream)
     sync()
+    clocks.mark_stop()
     barrier(device)
     sync()
     wall = time.perf_counter() - t0
