@@ -26,6 +26,7 @@ namespace tftgpu {
 namespace {
 
 constexpr int kForkStreams = 4;
+constexpr size_t kGroupProducts = 96;  // products per group at most
 
 struct DeviceStreams {
   bool ready = false;
@@ -115,23 +116,35 @@ int layout_batch(const std::vector<BatchProduct> &items, const std::vector<int> 
   out->groups.clear();
   int64_t cell_off = 0;  // in cells of the current group's stride, from the pool's start
   size_t byte_off = 0;
+  // the products of one ring, dealt round-robin into groups of at most kGroupProducts, so that
+  // a ring with many products runs as several groups on the forked streams (one group's
+  // pointwise products then overlap another's transforms)
+  std::vector<std::vector<int>> subs;
   for (size_t a = 0; a < idx.size();) {
     size_t b = a;
     while (b < idx.size() && items[idx[b]].N == items[idx[a]].N && items[idx[b]].mode == items[idx[a]].mode) b++;
+    const size_t ng = (b - a + kGroupProducts - 1) / kGroupProducts;
+    for (size_t g = 0; g < ng; g++) {
+      subs.emplace_back();
+      for (size_t t = a + g; t < b; t += ng) subs.back().push_back(idx[t]);
+    }
+    a = b;
+  }
+  for (const std::vector<int> &sub : subs) {
     BatchGroup gd;
-    const BatchProduct &p0 = items[idx[a]];
+    const BatchProduct &p0 = items[sub[0]];
     gd.ring = make_ring(p0.N);
     gd.mode = p0.mode;
     gd.stride = p0.stride;
-    gd.count = int(b - a);
+    gd.count = int(sub.size());
     std::vector<PackItem> pk;
     std::vector<PointwiseItem> pw;
     std::vector<LiftItem> lf;
     MergedSegs mt, mi;
     const size_t cell_bytes = size_t(gd.stride) * 8;
     cell_off = int64_t((byte_off + cell_bytes - 1) / cell_bytes);  // first whole cell after the last group
-    for (size_t t = a; t < b; t++) {
-      const BatchProduct &p = items[idx[t]];
+    for (size_t t = 0; t < sub.size(); t++) {
+      const BatchProduct &p = items[sub[t]];
       const int64_t L = int64_t(1) << p.l;
       const int64_t cf = cell_off, cg = cell_off + L;
       cell_off += 2 * L;
@@ -146,7 +159,7 @@ int layout_batch(const std::vector<BatchProduct> &items, const std::vector<int> 
       if ((rc = mt.add(KIND_TFT, p.l, p.len_f, p.nf, p.N, p.stride, cf, 0, p.mode)) ||
           (rc = mt.add(KIND_TFT, p.l, p.len_g, p.nf, p.N, p.stride, cg, 0, p.mode)) ||
           (rc = mi.add(KIND_ITFT, p.l, p.nf, p.nf, p.N, p.stride, cf, 1, p.mode))) {
-        *msg = "planning failed for product " + std::to_string(idx[t]);
+        *msg = "planning failed for product " + std::to_string(sub[t]);
         img.bytes.swap(*desc);
         return rc;
       }
@@ -158,7 +171,6 @@ int layout_batch(const std::vector<BatchProduct> &items, const std::vector<int> 
     to_launches(mt, &img, &gd.tft);
     to_launches(mi, &img, &gd.itft);
     out->groups.push_back(std::move(gd));
-    a = b;
   }
   out->pool_bytes = byte_off;
   img.bytes.swap(*desc);
