@@ -67,3 +67,33 @@ def test_two_rank_replicas_take_the_slowest_rank():
     # both ranks report the same (slowest) time, at least rank 1's 3 x 0.1 s
     assert abs(res[0][2] - res[1][2]) < 1e-9
     assert res[0][2] >= 0.3
+
+
+def test_clock_samples_count_only_inside_the_timed_region(monkeypatch):
+    """The sampler keeps the samples stamped between the region's start and its end plus one
+    interval, and reports a throttle reason only if one of those samples shows it."""
+    monkeypatch.setattr(bench.time, "sleep", lambda s: None)
+
+    def line(mhz, hw="Not Active", pcap="Not Active"):
+        return f"0, {mhz}, 2070, 900.0, 0x0, {hw}, Not Active, Not Active, {pcap}"
+
+    class FakeProc:
+        def terminate(self):
+            pass
+
+        def wait(self, timeout=None):
+            return 0
+
+    c = bench.ClockSampler(0)
+    c.proc = FakeProc()
+    c.lines = [(0.0, line(1500, hw="Active")), (1.00, line(2070)), (1.04, line(2055, pcap="Active")),
+               (1.20, line(900))]
+    c.t0, c.t1 = 0.99, 1.05
+    out = c.stop()
+    assert out["samples"] == 2 and out["sm_mhz"] == (2070 + 2055) / 2
+    assert out["reasons"] == ["sw_power_cap"] and "note" not in out
+    # a region shorter than the interval: the first sample after its start, flagged
+    c.lines = [(0.0, line(1500)), (2.5, line(2070))]
+    c.t0, c.t1 = 2.0, 2.01
+    out = c.stop()
+    assert out["samples"] == 1 and out["sm_mhz"] == 2070 and "note" in out

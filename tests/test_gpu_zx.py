@@ -106,3 +106,48 @@ def test_buffer_too_small_reports_needed_limbs(tg):
     with pytest.raises(tg.TftError) as ei:
         tg.zx_mul(f, lf, 8, g, lg, 8, h, 2, False, bits, bits)
     assert ei.value.code == tg.ZX_EBUFSIZE
+
+
+def test_concurrent_calls_from_two_threads(tg):
+    """Two host threads call zx_mul at the same time, each on its own stream: every call forks
+    its g transform onto its thread's helper stream and joins it back with events, so the
+    results are the same as those of the calls made one after another."""
+    import threading
+
+    shapes = [(700, 900, 300), (2500, 1800, 500), (64, 3000, 128), (4000, 4000, 700), (1, 1, 64), (300, 5, 1000)]
+    jobs = []
+    for k, (lf, lg, bits) in enumerate(shapes * 2):
+        m = (bits + 63) // 64
+        F = torch.from_numpy(workloads.coefficients(500 + 2 * k, lf, bits, m).view(np.int64)).cuda()
+        G = torch.from_numpy(workloads.coefficients(501 + 2 * k, lg, bits, m).view(np.int64)).cuda()
+        mh = tg.zx_plan(lf, bits, lg, bits)["limbs_h"]
+        jobs.append((F, lf, m, G, lg, mh, bits))
+    ref = []
+    for F, lf, m, G, lg, mh, bits in jobs:
+        H = torch.zeros((lf + lg - 1) * mh, dtype=torch.int64, device="cuda")
+        tg.zx_mul(F, lf, m, G, lg, m, H, mh, False, bits, bits)
+        ref.append(H)
+    torch.cuda.synchronize()
+    outs = [torch.full_like(r, -1) for r in ref]
+    errors = []
+
+    def worker(part):
+        try:
+            s = torch.cuda.Stream()
+            for _ in range(3):
+                for i in part:
+                    F, lf, m, G, lg, mh, bits = jobs[i]
+                    tg.zx_mul(F, lf, m, G, lg, m, outs[i], mh, False, bits, bits, stream=s)
+            s.synchronize()
+        except Exception as exc:  # reported below, on the main thread
+            errors.append(exc)
+
+    threads = [threading.Thread(target=worker, args=(list(range(t, len(jobs), 2)),)) for t in range(2)]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join(120)
+    assert not errors, errors
+    torch.cuda.synchronize()
+    for i, (r, o) in enumerate(zip(ref, outs)):
+        assert torch.equal(r, o), i
