@@ -228,3 +228,23 @@ def test_invalid_arguments(tg):
     with pytest.raises(tg.TftError) as ei:
         tg.tft_ex(x, 2, 1, 1, 1088, 0, 18)  # N > 1024 not a multiple of 1024
     assert ei.value.code == tg.ZX_EUNSUPPORTED
+
+
+@pytest.mark.parametrize("n,f,e", [(40000, 0, 0), (52000, 1, 12345)])
+def test_large_itft_vs_oracle(tg, orc, n, f, e):
+    """Z/(2^32768+1), l = 16, 16-byte aligned cells as the benchmark lays them out: every output of
+    the exact ITFT (Algorithm 2 with its partial rows, z = n + f) against the oracle's, with the
+    weight zeta = 2^e and without the final division by L."""
+    w = workloads.TRANSFORM_LARGE
+    N, l = w["N"], w["l"]
+    W = limbs(N)
+    st = W + (W & 1)
+    z = n + f
+    x = workloads.residues(w["seed"] + 7, z, N, stride=st, cells=1 << l)
+    d = to_dev(x)
+    tg.itft_ex(d, l, z, n, f, N, e, st, scale=0)
+    got = from_dev(d)
+    ref = x.copy()
+    orc.itft(ref, l, z, n, f, e, N, stride=st)
+    bad = cells_eq(got, ref, n + f, st, W)
+    assert bad.size == 0, f"{bad.size} cells differ, first {bad[:5]}"
