@@ -38,7 +38,7 @@ extern "C" {
 #define ZX_EINVAL 1       /* a size, index or flag violates the stated preconditions */
 #define ZX_ENOMEM 2       /* device or pinned-host allocation failed */
 #define ZX_ECUDA 3        /* a CUDA runtime call or kernel launch failed */
-#define ZX_ETIMEOUT 4     /* a bounded device-side wait gave up (batched path) */
+#define ZX_ETIMEOUT 4     /* a bounded wait gave up (server drain; device waits, zx_wait_status) */
 #define ZX_EBUFSIZE 5     /* an output buffer is too small; the needed size is reported */
 #define ZX_EUNSUPPORTED 6 /* valid for the paper, but outside this library's supported sizes */
 
@@ -326,6 +326,24 @@ int zx_pointwise(uint64_t *a, const uint64_t *b, int64_t n, int64_t N, int64_t s
  */
 int zx_job_program(int kind, int ls, int lc, int64_t z, int64_t n, int f, int64_t N, int mode, uint32_t *buf,
                    int64_t cap_words, int64_t *size_words);
+
+/*
+ * Bounded device-side waits. The transform kernel stages the cells of single-CTA jobs in
+ * shared memory with bulk (TMA) copies and waits for their completion on an mbarrier with a
+ * time limit of one second. A wait that runs out waits once more (also bounded) for the copies
+ * still in flight, then stops that CTA and sets a status word of the device; the outputs of
+ * the call it belonged to are then unspecified. Launches do not synchronise, so the status is
+ * read on request:
+ *   zx_wait_status  synchronises `stream`, then reads and clears the status word of the current
+ *                   device (atomically). ZX_OK when no wait gave up since the last read,
+ *                   ZX_ETIMEOUT when one did, ZX_ECUDA on a CUDA error.
+ *   zx_wait_probe   enqueues one warp that waits on an mbarrier that nothing completes until
+ *                   limit_us microseconds (1 .. 10^6, else ZX_EINVAL) have passed, and reports
+ *                   it as the transform kernel does: the error path, taken without a fault.
+ *                   Asynchronous; for tests.
+ */
+int zx_wait_status(void *stream);
+int zx_wait_probe(int64_t limit_us, void *stream);
 
 /* Human-readable name of a status code (static storage). */
 const char *zx_strerror(int code);

@@ -26,7 +26,7 @@ EXPORTS = ("tft", "tft_ex", "itft", "itft_ex", "zx_plan", "zx_mul", "zx_mul_batc
            "zx_transform_plan", "zx_mul_noalloc", "zx_job_program", "zx_strerror", "zx_last_error",
            "zx_version", "zx_server_create", "zx_server_submit", "zx_server_poll", "zx_server_drain",
            "zx_server_stats", "zx_server_destroy", "zx_tune", "zx_config_get", "zx_config_set", "sn_tft", "sn_itft", "tft_sqrt2", "itft_sqrt2",
-           "zx_pointwise", "zx_pointwise_plan")
+           "zx_pointwise", "zx_pointwise_plan", "zx_wait_status", "zx_wait_probe")
 
 _lib = None
 
@@ -117,6 +117,8 @@ def load(build_if_missing=True):
     L.sn_itft.argtypes = [vp, i32, i64, i64, i32, i64, C.c_uint64, i64, i64, i32, vp]
     L.zx_pointwise.argtypes = [vp, vp, i64, i64, i64, i32, vp]
     L.zx_pointwise_plan.argtypes = [i64, i32, C.POINTER(ZxPointwiseInfo)]
+    L.zx_wait_status.argtypes = [vp]
+    L.zx_wait_probe.argtypes = [i64, vp]
     L.zx_strerror.argtypes = [i32]
     L.zx_strerror.restype = C.c_char_p
     L.zx_last_error.argtypes = []
@@ -358,6 +360,18 @@ class Server:
 
     def __exit__(self, *exc):
         self.close()
+
+
+def wait_status(stream=None):
+    """Synchronise the stream, then read and clear the device's bounded-wait status: the
+    status code, ZX_OK or ZX_ETIMEOUT (a transform kernel's bulk-load wait gave up)."""
+    return load().zx_wait_status(_stream(stream))
+
+
+def wait_probe(limit_us, stream=None):
+    """Enqueue one warp that waits limit_us microseconds on a barrier nothing completes and
+    reports it as a transform's wait that gave up (the error path, taken without a fault)."""
+    _check(load().zx_wait_probe(limit_us, _stream(stream)), "zx_wait_probe")
 
 
 def version():

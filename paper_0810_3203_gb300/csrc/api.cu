@@ -604,6 +604,21 @@ const char *zx_strerror(int code) {
 
 const char *zx_last_error(void) { return g_last_error.c_str(); }
 
+int zx_wait_status(void *stream) {
+  uint32_t fault = 0;
+  const cudaError_t ce = read_wait_status(&fault, cudaStream_t(stream));
+  if (ce != cudaSuccess) return cuda_fail(ce, "reading the wait status");
+  if (fault) return fail(ZX_ETIMEOUT, "a bounded device-side wait gave up (outputs of that call are unspecified)");
+  return ZX_OK;
+}
+
+int zx_wait_probe(int64_t limit_us, void *stream) {
+  if (limit_us < 1 || limit_us > 1000000) return fail(ZX_EINVAL, "limit_us must be in [1, 10^6]");
+  const cudaError_t ce = run_wait_probe(uint64_t(limit_us) * 1000u, cudaStream_t(stream));
+  if (ce != cudaSuccess) return cuda_fail(ce, "wait probe launch");
+  return ZX_OK;
+}
+
 const char *zx_version(void) { return "tftgpu 0.1 sm_103a"; }
 
 }  // extern "C"

@@ -144,6 +144,13 @@ cudaError_t run_transform(const TransformPlan &p, uint64_t *x, int64_t stride_li
 cudaError_t run_transform_reps(const TransformPlan &p, uint64_t *x, int64_t stride_limbs, int64_t reps,
                                int64_t rep_cells, cudaStream_t s);
 
+// Bounded device waits (transform_kernel.cu). A job kernel whose bulk load did not land within
+// its limit stops and sets a per-device status word; read_wait_status synchronises s, then
+// returns that word in *fault and clears it (atomically on the device). run_wait_probe enqueues
+// one warp that waits limit_ns on a barrier nothing completes and reports it the same way.
+cudaError_t read_wait_status(uint32_t *fault, cudaStream_t s);
+cudaError_t run_wait_probe(uint64_t limit_ns, cudaStream_t s);
+
 // Pointwise products by a second Schoenhage-Strassen level (rec_pointwise.cu): 2^k pieces of
 // M = N / 2^k bits, inner ring Z/(2^Ni + 1) with Ni >= 2M + k + 1 and 2^k | Ni.
 struct RecPlan {

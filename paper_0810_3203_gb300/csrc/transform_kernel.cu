@@ -228,6 +228,57 @@ __device__ __forceinline__ void smem_to_gmem_cell(uint64_t *gcell, const uint32_
   if (g.lane == 0) gcell[g.NW / 2] = top;
 }
 
+// Set (never cleared on the device) when a bounded wait of a kernel gave up; read and cleared
+// by the host through read_wait_status.
+__device__ uint32_t g_wait_fault;
+
+// Wait limit of a bulk-copy completion (the copies of one job land within microseconds).
+constexpr uint64_t kBulkWaitNs = 1000000000ull;
+
+__device__ __forceinline__ uint64_t globaltimer_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Wait for the given phase parity of an mbarrier; false when limit_ns passed first.
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t mb, uint32_t parity, uint64_t limit_ns) {
+  const uint64_t t0 = globaltimer_ns();
+  for (;;) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(mb), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if (globaltimer_ns() - t0 > limit_ns) return false;
+  }
+}
+
+// Bulk (TMA) load of the N-bit parts of a job's first nl cells, one 128-byte row per lane and
+// cell, into the padded shared-memory rows; completion is counted on the mbarrier mb (one
+// arrival, by thread 0, announcing all the bytes). Needs 16-byte aligned cells and NW a
+// multiple of 32 (rows of 32 words); cell s is read from gcell(s).
+template <typename CellAddr>
+__device__ __forceinline__ void bulk_load_cells(uint32_t *cells, int P, int nl, uint32_t mb, int NW, int warp, int nw,
+                                                int lane, CellAddr gcell) {
+  if (threadIdx.x == 0) {
+    const uint32_t bytes = uint32_t(nl) * uint32_t(NW) * 4u;
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mb), "r"(bytes) : "memory");
+  }
+  const int rows = NW >> 5;
+  if (lane >= rows) return;
+  for (int s = warp; s < nl; s += nw) {
+    const uint32_t dst = uint32_t(__cvta_generic_to_shared(cells + s * P + 36 * lane));
+    uint64_t src;
+    asm volatile("cvta.to.global.u64 %0, %1;" : "=l"(src) : "l"(reinterpret_cast<const char *>(gcell(s)) + 128 * lane));
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], 128, [%2];" ::"r"(dst),
+                 "l"(src), "r"(mb)
+                 : "memory");
+  }
+}
+
 // cell index of the job held at `slot` of CTA `rank` in the given layout
 __device__ __forceinline__ int job_cell(uint32_t layout, int rank, int slot, int C, int L2, int b) {
   if (C == 1) return slot;
@@ -374,8 +425,10 @@ __global__ void __launch_bounds__(MINB == 3 ? 256 : 512, MINB) job_kernel(uint64
   const int P = cell_pitch_words(g.NW);
   uint32_t *cells = smem;
   uint32_t *meta = smem + nslots * P;
-  // program staging area, 8-byte aligned, after the cells and their metadata
-  uint32_t *pstage = smem + ((nslots * P + nslots + 1) & ~1);
+  // after the cells and their metadata: the load's mbarrier (8-byte aligned, 4 words), then
+  // the program staging area
+  uint32_t *mbar = smem + ((nslots * P + nslots + 1) & ~1);
+  uint32_t *pstage = mbar + 4;
   const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const uint32_t *img = jd.image;
   const int nstages = int(img[0]);
@@ -385,20 +438,57 @@ __global__ void __launch_bounds__(MINB == 3 ? 256 : 512, MINB) job_kernel(uint64
   for (int s = threadIdx.x; s < nslots; s += blockDim.x)
     if (job_cell(load_layout, rank, s, C, L2, b) >= jd.nload) meta[s] = 1u;
 
-  // load (coalesced) into shared memory, then the storage form m = x - 1
+  // load into shared memory, then the storage form m = x - 1
   const bool vec16 = ((reinterpret_cast<uintptr_t>(x) & 15) == 0) && ((stride_limbs & 1) == 0);
-  for (int s = warp; s < nslots; s += nw) {
-    const int m = job_cell(load_layout, rank, s, C, L2, b);
-    if (m >= jd.nload) continue;
-    const uint64_t *gc = x + (jd.cell0 + int64_t(m) * jd.mstride) * stride_limbs;
-    const uint64_t T = gmem_to_smem_cell<K>(cells + s * P, gc, vec16, g);
-    if (T & kRawTopMark) {
-      // written by an earlier pass in internal form: the words are m, the top limb the metadata
-      if (g.lane == 0) meta[s] = uint32_t(T);
-    } else {
-      __syncwarp();
-      const int z = settle_smem<K>(lane_chunk<K>(cells + s * P, g), 0, -1 - int(T & 1u), g);
-      set_meta<K>(meta + s, z, 0, g);
+  if (K >= 4 && vec16 && C == 1 && (g.NW & 31) == 0) {
+    // single-CTA job (slot s holds cell s): bulk copies of whole rows, then each cell's top limb
+    const int nl = jd.nload < nslots ? jd.nload : nslots;
+    const uint32_t mb = uint32_t(__cvta_generic_to_shared(mbar));
+    if (threadIdx.x == 0) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb) : "memory");
+      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    __syncthreads();
+    const uint64_t *x0 = x + jd.cell0 * stride_limbs;
+    const int64_t cstep = jd.mstride * stride_limbs;
+    bulk_load_cells(cells, P, nl, mb, g.NW, warp, nw, g.lane,
+                    [&](int s) { return x0 + int64_t(s) * cstep; });
+    const bool landed = mbar_wait_bounded(mb, 0, kBulkWaitNs);
+    if (__syncthreads_or(!landed)) {
+      // the copies did not all land in time: wait once more for those in flight, report, stop
+      if (!landed) mbar_wait_bounded(mb, 0, kBulkWaitNs);
+      __syncthreads();
+      if (threadIdx.x == 0) atomicOr(&g_wait_fault, 1u);
+      return;
+    }
+    for (int s = warp; s < nl; s += nw) {
+      const uint64_t T = __ldg(x0 + int64_t(s) * cstep + g.NW / 2);
+      if (T & kRawTopMark) {
+        // written by an earlier pass in internal form: the words are m, the top limb the metadata
+        if (g.lane == 0) meta[s] = uint32_t(T);
+      } else {
+        const int z = settle_smem<K>(lane_chunk<K>(cells + s * P, g), 0, -1 - int(T & 1u), g);
+        set_meta<K>(meta + s, z, 0, g);
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(mb) : "memory");
+  } else {
+    // coalesced plain loads
+    for (int s = warp; s < nslots; s += nw) {
+      const int m = job_cell(load_layout, rank, s, C, L2, b);
+      if (m >= jd.nload) continue;
+      const uint64_t *gc = x + (jd.cell0 + int64_t(m) * jd.mstride) * stride_limbs;
+      const uint64_t T = gmem_to_smem_cell<K>(cells + s * P, gc, vec16, g);
+      if (T & kRawTopMark) {
+        // written by an earlier pass in internal form: the words are m, the top limb the metadata
+        if (g.lane == 0) meta[s] = uint32_t(T);
+      } else {
+        __syncwarp();
+        const int z = settle_smem<K>(lane_chunk<K>(cells + s * P, g), 0, -1 - int(T & 1u), g);
+        set_meta<K>(meta + s, z, 0, g);
+      }
     }
   }
   __syncthreads();
@@ -506,7 +596,8 @@ template <int K, bool SQ>
 cudaError_t launch_k(const Launch &L, uint64_t *x, int64_t stride_limbs, const Ring &r, cudaStream_t s,
                      int64_t reps, int64_t rep_cells) {
   const int nslots = 1 << (L.ls - L.lc);
-  const size_t base_words = (size_t(nslots) * size_t(r.pitch) + size_t(nslots) + 1) & ~size_t(1);
+  // cells, their metadata and the load's mbarrier (4 words)
+  const size_t base_words = ((size_t(nslots) * size_t(r.pitch) + size_t(nslots) + 1) & ~size_t(1)) + 4;
   const uint32_t ord = uint32_t((SQ ? 4 : 2) * r.N);
   const uint32_t mask = (ord & (ord - 1)) == 0 ? ord - 1 : 0u;
   // three CTAs per SM of at most 8 warps when the cells fit in 75 KB and the launch has the
@@ -558,6 +649,44 @@ cudaError_t run_transform_reps(const TransformPlan &p, uint64_t *x, int64_t stri
 
 cudaError_t run_transform(const TransformPlan &p, uint64_t *x, int64_t stride_limbs, cudaStream_t s) {
   return run_transform_reps(p, x, stride_limbs, 1, 0, s);
+}
+
+namespace {
+
+// One warp waits on an mbarrier that nothing completes until limit_ns passes, and reports it
+// as the job kernel reports a bulk load that did not land.
+__global__ void wait_probe_kernel(uint64_t limit_ns) {
+  __shared__ alignas(8) uint64_t bar;
+  const uint32_t mb = uint32_t(__cvta_generic_to_shared(&bar));
+  if (threadIdx.x == 0) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb) : "memory");
+  __syncthreads();
+  const bool landed = mbar_wait_bounded(mb, 0, limit_ns);
+  if (__syncthreads_or(!landed) && threadIdx.x == 0) atomicOr(&g_wait_fault, 1u);
+  __syncthreads();
+  if (threadIdx.x == 0) asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(mb) : "memory");
+}
+
+__global__ void take_wait_fault_kernel(uint32_t *out) { *out = atomicExch(&g_wait_fault, 0u); }
+
+}  // namespace
+
+cudaError_t run_wait_probe(uint64_t limit_ns, cudaStream_t s) {
+  wait_probe_kernel<<<1, 32, 0, s>>>(limit_ns);
+  return cudaGetLastError();
+}
+
+cudaError_t read_wait_status(uint32_t *fault, cudaStream_t s) {
+  uint32_t *d = nullptr, v = 0;
+  cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&d), sizeof(uint32_t), s);
+  if (e != cudaSuccess) return e;
+  take_wait_fault_kernel<<<1, 1, 0, s>>>(d);
+  e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&v, d, sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
+  const cudaError_t ef = cudaFreeAsync(d, s);
+  if (e == cudaSuccess) e = ef;
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e == cudaSuccess) *fault = v;
+  return e;
 }
 
 }  // namespace tftgpu
