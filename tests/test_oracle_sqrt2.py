@@ -1,5 +1,5 @@
 """Pins of the oracle's transforms over Z/(2^N+1) with omega = sqrt2 (the sqrt2 trick; not in
-the paper, SURVEY's f4). sqrt2 = 2^{3N/4} - 2^{N/4} squares to 2, so it is a principal 4N-th
+the paper). sqrt2 = 2^{3N/4} - 2^{N/4} squares to 2, so it is a principal 4N-th
 root of unity and transforms of length L | 4N exist: rings half the size the paper's L | 2N
 rule allows. Pins independent of the oracle's recursion:
 
