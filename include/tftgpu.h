@@ -328,6 +328,26 @@ int zx_job_program(int kind, int ls, int lc, int64_t z, int64_t n, int f, int64_
                    int64_t cap_words, int64_t *size_words);
 
 /*
+ * The whole plan of one transform (host only, no device needed): the launches tft_ex / itft_ex
+ * make for these arguments under the ring's current launch configuration, in stream order,
+ * with every job's descriptor and the job images they run (mode 0: omega = 2, mode 2:
+ * omega = sqrt2). For inspection and tests.
+ *   jobs (int64 words): [passes, launches, jobs, images], then per launch
+ *     [ls, lc, warps, program_words, count] followed by `count` jobs of 9 words
+ *     [cell0, mstride, e, nload, nstore, nscale, escale, pad, image]: the job reads its cells
+ *     m < nload at cell0 + m mstride (the others are zero), runs image `image` with weight
+ *     exponent e, stores its cells m < nstore there, those with m < nscale times omega^escale;
+ *     pad bits 0-7 hold the job's log2 size when it differs from the launch's ls, bit 8 that
+ *     its stores stay in the kernel's internal form (a later launch stores them again).
+ *   images (uint32 words): images + 1 offsets, then the images (zx_job_program's format)
+ *     back to back, image k at words [offset k, offset k+1) after the offsets.
+ * The lengths go to *jobs_words and *images_words; ZX_EBUFSIZE when either buffer is too small.
+ */
+int zx_transform_jobs(int kind, int l, int64_t z, int64_t n, int f, int64_t N, int64_t e, int scale, int mode,
+                      int64_t *jobs, int64_t cap_jobs, int64_t *jobs_words, uint32_t *images, int64_t cap_images,
+                      int64_t *images_words);
+
+/*
  * Bounded device-side waits. The transform kernel stages the cells of single-CTA jobs in
  * shared memory with bulk (TMA) copies and waits for their completion on an mbarrier with a
  * time limit of one second. A wait that runs out waits once more (also bounded) for the copies

@@ -26,7 +26,7 @@ EXPORTS = ("tft", "tft_ex", "itft", "itft_ex", "zx_plan", "zx_mul", "zx_mul_batc
            "zx_transform_plan", "zx_mul_noalloc", "zx_job_program", "zx_strerror", "zx_last_error",
            "zx_version", "zx_server_create", "zx_server_submit", "zx_server_poll", "zx_server_drain",
            "zx_server_stats", "zx_server_destroy", "zx_tune", "zx_config_get", "zx_config_set", "sn_tft", "sn_itft", "tft_sqrt2", "itft_sqrt2",
-           "zx_pointwise", "zx_pointwise_plan", "zx_wait_status", "zx_wait_probe")
+           "zx_pointwise", "zx_pointwise_plan", "zx_wait_status", "zx_wait_probe", "zx_transform_jobs")
 
 _lib = None
 
@@ -117,6 +117,8 @@ def load(build_if_missing=True):
     L.sn_itft.argtypes = [vp, i32, i64, i64, i32, i64, C.c_uint64, i64, i64, i32, vp]
     L.zx_pointwise.argtypes = [vp, vp, i64, i64, i64, i32, vp]
     L.zx_pointwise_plan.argtypes = [i64, i32, C.POINTER(ZxPointwiseInfo)]
+    L.zx_transform_jobs.argtypes = [i32, i32, i64, i64, i32, i64, i64, i32, i32, C.POINTER(C.c_int64), i64,
+                                    C.POINTER(C.c_int64), C.POINTER(C.c_uint32), i64, C.POINTER(C.c_int64)]
     L.zx_wait_status.argtypes = [vp]
     L.zx_wait_probe.argtypes = [i64, vp]
     L.zx_strerror.argtypes = [i32]
@@ -360,6 +362,31 @@ class Server:
 
     def __exit__(self, *exc):
         self.close()
+
+
+def transform_jobs(kind, l, z, n, N, f=0, e=0, scale=0, mode=0):
+    """The launches of one transform's plan (see zx_transform_jobs in include/tftgpu.h): a dict
+    with 'passes' and 'launches', each launch a dict of ls, lc, warps, program_words and its
+    'jobs' (dicts of the 9 descriptor fields), and 'images' (numpy uint32 job images)."""
+    nj, ni = C.c_int64(0), C.c_int64(0)
+    load().zx_transform_jobs(kind, l, z, n, f, N, e, scale, mode, None, 0, C.byref(nj), None, 0, C.byref(ni))
+    J = np.zeros(max(1, nj.value), np.int64)
+    I = np.zeros(max(1, ni.value), np.uint32)
+    _check(load().zx_transform_jobs(kind, l, z, n, f, N, e, scale, mode, J.ctypes.data_as(C.POINTER(C.c_int64)),
+                                    J.size, C.byref(nj), I.ctypes.data_as(C.POINTER(C.c_uint32)), I.size,
+                                    C.byref(ni)), "zx_transform_jobs")
+    passes, nlaunch, _, nimg = (int(v) for v in J[:4])
+    fields = ("cell0", "mstride", "e", "nload", "nstore", "nscale", "escale", "pad", "image")
+    launches, k = [], 4
+    for _ in range(nlaunch):
+        ls, lc, warps, pw, count = (int(v) for v in J[k:k + 5])
+        k += 5
+        jobs = [dict(zip(fields, (int(v) for v in J[k + 9 * t:k + 9 * t + 9]))) for t in range(count)]
+        k += 9 * count
+        launches.append(dict(ls=ls, lc=lc, warps=warps, program_words=pw, jobs=jobs))
+    off = [int(v) for v in I[:nimg + 1]]
+    images = [I[nimg + 1 + off[t]:nimg + 1 + off[t + 1]].copy() for t in range(nimg)]
+    return dict(passes=passes, launches=launches, images=images)
 
 
 def wait_status(stream=None):

@@ -604,6 +604,40 @@ const char *zx_strerror(int code) {
 
 const char *zx_last_error(void) { return g_last_error.c_str(); }
 
+int zx_transform_jobs(int kind, int l, int64_t z, int64_t n, int f, int64_t N, int64_t e, int scale, int mode,
+                      int64_t *jobs, int64_t cap_jobs, int64_t *jobs_words, uint32_t *images, int64_t cap_images,
+                      int64_t *images_words) {
+  if (!jobs_words || !images_words) return fail(ZX_EINVAL, "jobs_words or images_words is NULL");
+  if (kind != KIND_TFT && kind != KIND_ITFT) return fail(ZX_EINVAL, "kind must be 0 (TFT) or 1 (ITFT)");
+  if (mode != RING_FERMAT && mode != RING_SQRT2) return fail(ZX_EINVAL, "mode must be 0 or 2");
+  int rc = check_ring(l, N, mode);
+  if (rc) return rc;
+  if ((rc = check_sizes(kind, l, z, n, f))) return rc;
+  HostPlan hp;
+  build_host_plan(kind, l, z, n, f, N, e, scale, &hp, mode);
+  std::vector<int64_t> J = {hp.npasses, int64_t(hp.groups.size()), 0, int64_t(hp.programs.size())};
+  for (const HostPlan::Group &g : hp.groups) {
+    J.insert(J.end(), {g.ls, g.lc, g.nwarps, g.prog_words, int64_t(g.jobs.size())});
+    for (size_t i = 0; i < g.jobs.size(); i++) {
+      const JobDesc &d = g.jobs[i];
+      J.insert(J.end(), {d.cell0, d.mstride, d.e, d.nload, d.nstore, d.nscale, d.escale, d.pad, g.prog_index[i]});
+    }
+    J[2] += int64_t(g.jobs.size());
+  }
+  std::vector<uint32_t> I(hp.programs.size() + 1, 0u);
+  for (size_t k = 0; k < hp.programs.size(); k++) {
+    I[k + 1] = I[k] + uint32_t(hp.programs[k].size());
+  }
+  for (const auto &img : hp.programs) I.insert(I.end(), img.begin(), img.end());
+  *jobs_words = int64_t(J.size());
+  *images_words = int64_t(I.size());
+  if (!jobs || !images || cap_jobs < int64_t(J.size()) || cap_images < int64_t(I.size()))
+    return fail(ZX_EBUFSIZE, "buffers too small for the plan");
+  std::memcpy(jobs, J.data(), J.size() * sizeof(int64_t));
+  std::memcpy(images, I.data(), I.size() * sizeof(uint32_t));
+  return ZX_OK;
+}
+
 int zx_wait_status(void *stream) {
   uint32_t fault = 0;
   const cudaError_t ce = read_wait_status(&fault, cudaStream_t(stream));

@@ -1,0 +1,181 @@
+"""CPU check of whole transform plans: every launch of a TFT / ITFT plan, run job by job on
+Python values, against the oracle.
+
+zx_transform_jobs returns the launches tft_ex / itft_ex make (in stream order), each job's
+descriptor and the job images. A launch's jobs run concurrently on the GPU, so here each
+launch reads the buffer as the previous launch left it and its stores land together. Besides
+the values, the plans must be safe to run as launches of independent CTAs:
+
+  * every cell a job reads or writes lies in [0, L);
+  * within one launch, no two jobs store the same cell and no job reads a cell another job
+    stores;
+  * a job that stores the kernel's internal form (pad bit 8) only stores cells that a later
+    launch stores again, so every output leaves in canonical form.
+
+The arithmetic is Python integers, so this checks the planner's passes, strides, weights,
+scaling and bookkeeping (Algorithms 1 and 2 split into passes, Secs. 3-4), not the limb
+arithmetic of the kernel.
+"""
+import random
+
+import pytest
+
+from jobsim import Fermat, run_image
+
+JOB_RAW_STORE = 1 << 8
+
+
+@pytest.fixture(scope="module")
+def tg():
+    import paper_0810_3203_gb300 as m
+    m.build.build()
+    m.load(build_if_missing=False)
+    return m
+
+
+def job_cells(jd, count):
+    return [jd["cell0"] + m * jd["mstride"] for m in range(count)]
+
+
+def check_plan_safety(plan, L, outputs):
+    """The launch-level properties of the module docstring; returns nothing, asserts."""
+    launches = plan["launches"]
+    stored_by = []  # per launch: the set of cells it stores
+    for k, launch in enumerate(launches):
+        stores, loads = {}, {}
+        for t, jd in enumerate(launch["jobs"]):
+            for c in job_cells(jd, max(jd["nload"], jd["nstore"])):
+                assert 0 <= c < L, (k, t, c)
+            for c in job_cells(jd, jd["nstore"]):
+                assert c not in stores, f"launch {k}: cell {c} stored by jobs {stores[c]} and {t}"
+                stores[c] = t
+            for c in job_cells(jd, jd["nload"]):
+                loads.setdefault(c, set()).add(t)
+        for c, t in stores.items():
+            assert loads.get(c, {t}) <= {t}, f"launch {k}: cell {c} stored by job {t}, read by {loads[c]}"
+        stored_by.append(set(stores))
+    later = set()
+    for k in range(len(launches) - 1, -1, -1):
+        for t, jd in enumerate(launches[k]["jobs"]):
+            if jd["pad"] & JOB_RAW_STORE:
+                cells = set(job_cells(jd, jd["nstore"]))
+                assert cells <= later, f"launch {k} job {t}: internal form stored but never rewritten"
+        later |= stored_by[k]
+    assert set(outputs) <= later, "an output cell is never stored"
+
+
+def run_plan(plan, N, vals, L, mode=0):
+    """The buffer after every launch of the plan, from inputs `vals` (zeros beyond them)."""
+    R = Fermat(N, mode)
+    x = list(vals) + [0] * (L - len(vals))
+    for launch in plan["launches"]:
+        out = {}
+        for jd in launch["jobs"]:
+            ls = (jd["pad"] & 0xFF) or launch["ls"]
+            cells = job_cells(jd, max(jd["nload"], jd["nstore"]))
+            inputs = [x[c] for c in cells[:jd["nload"]]]
+            got = run_image(plan["images"][jd["image"]], ls, N, jd["e"], inputs, jd["nload"], jd["nstore"],
+                            jd["nscale"], jd["escale"], ring=R)
+            for m, v in got.items():
+                out[cells[m]] = v
+        for c, v in out.items():
+            x[c] = v
+    return x
+
+
+def oracle_transform(orc, kind, vals, l, z, n, f, e, N, mode):
+    x = orc.cells_from_ints(vals, N, count=1 << l)
+    if kind == 0:
+        (orc.sqrt2_tft if mode == 2 else orc.tft)(x, l, z, n, e, N)
+        return orc.cells_to_ints(x, N, n)
+    (orc.sqrt2_itft if mode == 2 else orc.itft)(x, l, z, n, f, e, N)
+    return orc.cells_to_ints(x, N, n + f)
+
+
+def check_case(tg, orc, kind, l, z, n, f, e, N, scale=0, mode=0, seed=0):
+    L = 1 << l
+    p = (1 << N) + 1
+    rng = random.Random(seed)
+    vals = [rng.randrange(p) for _ in range(z)]
+    # structured cells too: 0, -1 = 2^N and 1
+    for i, v in zip(range(0, z, max(1, z // 3)), (0, p - 1, 1)):
+        vals[i] = v
+    plan = tg.transform_jobs(kind, l, z, n, N, f=f, e=e, scale=scale, mode=mode)
+    outs = n if kind == 0 else n + f
+    check_plan_safety(plan, L, range(outs))
+    got = run_plan(plan, N, vals, L, mode)[:outs]
+    want = oracle_transform(orc, kind, vals, l, z, n, f, e, N, mode)
+    if kind == 1 and scale:
+        inv = pow(2, -l, p)
+        want = [v * inv % p for v in want[:n]] + want[n:]
+    assert got == want, (kind, l, z, n, f, e, N, scale, mode)
+    return plan
+
+
+# (kind, l, z, n, f, e, N, scale): single launches, two-pass plans (more than 64 cells) and
+# ragged lengths on both sides of the row boundaries
+DEFAULT_CASES = [
+    (0, 6, 40, 37, 0, 5, 256, 0),
+    (1, 6, 40, 37, 1, 5, 256, 0),
+    (0, 9, 300, 300, 0, 0, 1024, 0),
+    (1, 9, 300, 300, 0, 0, 1024, 1),
+    (0, 10, 1024, 1024, 0, 17, 1024, 0),
+    (1, 10, 1024, 1000, 1, 17, 1024, 0),
+    (0, 11, 1500, 1999, 0, 3, 1024, 0),
+    (1, 11, 1999, 1500, 1, 3, 1024, 1),
+    (1, 11, 1025, 1025, 0, 0, 1024, 1),
+    (0, 12, 2049, 2049, 0, 1, 2048, 0),
+]
+
+
+@pytest.mark.parametrize("case", DEFAULT_CASES)
+def test_default_plans_match_the_oracle(tg, orc, case):
+    kind, l, z, n, f, e, N, scale = case
+    check_case(tg, orc, kind, l, z, n, f, e, N, scale, seed=l * 7 + kind)
+
+
+# pinned launch configurations: 8-cell single-CTA jobs with 64-cell jobs on 8-CTA clusters,
+# 4-cell jobs with 16-cell jobs on 4-CTA clusters, the ceil(l/2) top split
+PINNED = [
+    dict(ls_max=3, ls_c=3, max_warps=8, split=0),
+    dict(ls_max=2, ls_c=2, max_warps=16, split=1),
+    dict(ls_max=4, ls_c=2, max_warps=8, split=1),
+]
+
+
+@pytest.mark.parametrize("cfg", PINNED, ids=lambda c: f"ls{c['ls_max']}c{c['ls_c']}s{c['split']}")
+def test_pinned_configurations_match_the_oracle(tg, orc, cfg):
+    N = 2048
+    before = tg.config_get(N)
+    tg.config_set(N, cfg)
+    try:
+        rng = random.Random(cfg["ls_max"] * 31 + cfg["split"])
+        passes = set()
+        for kind, l, z, n, f in ((0, 12, 4096, 4096, 0), (1, 12, 4096, 4096, 0), (0, 11, 1333, 1700, 0),
+                                 (1, 11, 1700, 1333, 1), (1, 12, 3001, 2999, 1), (0, 9, 200, 511, 0)):
+            e = rng.randrange(2 * N)
+            plan = check_case(tg, orc, kind, l, z, n, f, e, N, scale=kind, seed=l + 3 * kind + n)
+            passes.add(plan["passes"])
+            assert any(L["lc"] > 0 for L in plan["launches"]) or cfg["ls_c"] < 3 or l < 12
+        assert max(passes) >= 3  # these configurations split the transforms into several passes
+    finally:
+        tg.config_set(N, before)
+
+
+@pytest.mark.parametrize("kind,l,z,n,f", [(0, 10, 700, 1024, 0), (1, 10, 1024, 900, 1), (0, 11, 2048, 1500, 0)])
+def test_sqrt2_plans_match_the_oracle(tg, orc, kind, l, z, n, f):
+    """omega = sqrt2 (L | 4N): rotation amounts mod 4N, the odd powers of sqrt2 included."""
+    N = 512
+    check_case(tg, orc, kind, l, z, n, f, 11, N, scale=kind, mode=2, seed=l + kind)
+
+
+def test_the_benchmark_plan_is_safe(tg):
+    """The l = 16, N = 32768 plans of the benchmark's n (too large to run in Python): every
+    launch-level property, and the internal form on all but the last pass."""
+    L = 1 << 16
+    for n in (32769, 40000, 45000, 52000, 65536):
+        for kind in (0, 1):
+            plan = tg.transform_jobs(kind, 16, n, n, 32768, scale=kind)
+            check_plan_safety(plan, L, range(n))
+            raw = [any(jd["pad"] & JOB_RAW_STORE for jd in launch["jobs"]) for launch in plan["launches"]]
+            assert not raw[-1] and (kind == 1 or all(raw[:-1])), (kind, n, raw)
