@@ -77,6 +77,16 @@ def cell_bytes(N):
     return 8 * (N // 64 + 1)
 
 
+def cell_stride(W, requested):
+    """Limbs between consecutive cells: W rounded up to even (16-byte aligned cells) unless a
+    stride is requested, which must hold a cell (>= W) and keep 16-byte alignment (even)."""
+    if not requested:
+        return W + (W & 1)
+    if requested < W or requested % 2:
+        raise SystemExit(f"--stride must be an even number of limbs >= {W}")
+    return requested
+
+
 def step_bytes(N, l, ns):
     return sum((alg_cells_tft(l, n, n) + alg_cells_itft(l, n, n)) * cell_bytes(N) for n in ns)
 
@@ -340,7 +350,7 @@ def run_gpu(args):
     tg.load()
     N, l, ns = WORKLOAD["N"], WORKLOAD["l"], list(WORKLOAD["ns"])
     W = N // 64 + 1
-    stride = W + (W & 1)  # 16-byte aligned cells
+    stride = cell_stride(W, args.stride)
     L = 1 << l
     stream = torch.cuda.current_stream(device)
     host = {n: workloads.residues(WORKLOAD["seed"], n, N, stride=stride, cells=L) for n in ns}
@@ -432,7 +442,8 @@ def run_gpu(args):
     peak, peak_kind = measured_peak()
     launches_per_step = sum(tg.transform_plan(0, l, n, n, N)["launches"] + tg.transform_plan(1, l, n, n, N)["launches"]
                             for n in ns)
-    traffic = recorded_traffic()
+    # the record was taken on the default layout
+    traffic = recorded_traffic() if stride == cell_stride(W, 0) else None
 
     # end to end through the C ABI with host buffers: per n, H2D of its n input cells from
     # pinned memory, TFT, ITFT, D2H of its n result cells (the other L - n cells of a buffer are
@@ -921,7 +932,7 @@ def run_profile_case(args):
         ls_max, ls_c, mw, sp = (int(v) for v in args.config.split(","))
         tg.config_set(N, {"ls_max": ls_max, "ls_c": ls_c, "max_warps": mw, "split": sp})
     W = N // 64 + 1
-    stride = W + (W & 1)
+    stride = cell_stride(W, args.stride)
     x = workloads.residues(WORKLOAD["seed"], n, N, stride=stride, cells=1 << l)
     d = torch.from_numpy(x.view(np.int64)).cuda()
     for _ in range(args.profile_reps):
@@ -946,6 +957,8 @@ def main():
     ap.add_argument("--profile-reps", type=int, default=1)
     ap.add_argument("--config", default="",
                     help="ls_max,ls_c,max_warps,split: launch configuration for --profile-case")
+    ap.add_argument("--stride", type=int, default=0,
+                    help="limbs between cells of the large transforms (default: W rounded up to even)")
     ap.add_argument("--no-batch", action="store_true", help="skip the 512-product batch leg")
     ap.add_argument("--no-tune", action="store_true", help="keep the default launch configurations")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving leg")

@@ -97,3 +97,12 @@ def test_clock_samples_count_only_inside_the_timed_region(monkeypatch):
     c.t0, c.t1 = 2.0, 2.01
     out = c.stop()
     assert out["samples"] == 1 and out["sm_mhz"] == 2070 and "note" in out
+
+
+def test_cell_stride_defaults_to_aligned_cells_and_checks_requests():
+    assert bench.cell_stride(513, 0) == 514  # W = 513 at N = 32768: 16-byte aligned cells
+    assert bench.cell_stride(17, 0) == 18
+    assert bench.cell_stride(513, 528) == 528  # 128-byte aligned cells
+    for bad in (512, 515):
+        with pytest.raises(SystemExit):
+            bench.cell_stride(513, bad)
