@@ -170,3 +170,34 @@ def test_whole_transforms_above_64_cells_take_two_passes(lib):
                 assert shape["passes"] == 1 and shape["jobs"] == 1, (N, l, shape)
             else:
                 assert shape["passes"] >= 2 and shape["jobs"] > 1, (N, l, shape)
+
+
+def test_transform_jobs_reports_sizes_and_rejects_bad_arguments(lib):
+    import numpy as np
+    import paper_0810_3203_gb300 as tg
+    i64, u32 = C.c_int64, C.c_uint32
+    nj, ni = i64(0), i64(0)
+    # sizes first (no buffers): ZX_EBUFSIZE with both lengths written
+    rc = lib.zx_transform_jobs(0, 10, 700, 900, 0, 1024, 0, 0, 0, None, 0, C.byref(nj), None, 0, C.byref(ni))
+    assert rc == tg.ZX_EBUFSIZE and nj.value > 4 and ni.value > 1
+    J, I = np.zeros(nj.value, np.int64), np.zeros(ni.value, np.uint32)
+    ok = lib.zx_transform_jobs(0, 10, 700, 900, 0, 1024, 0, 0, 0, J.ctypes.data_as(C.POINTER(i64)), J.size,
+                               C.byref(nj), I.ctypes.data_as(C.POINTER(u32)), I.size, C.byref(ni))
+    assert ok == tg.ZX_OK
+    # header: passes, launches, jobs (the launches' counts add up), images
+    plan = tg.transform_jobs(0, 10, 700, 900, 1024)
+    assert int(J[0]) == plan["passes"] and int(J[1]) == len(plan["launches"])
+    assert int(J[2]) == sum(len(L["jobs"]) for L in plan["launches"]) and int(J[3]) == len(plan["images"])
+    # one word short on either buffer
+    rc = lib.zx_transform_jobs(0, 10, 700, 900, 0, 1024, 0, 0, 0, J.ctypes.data_as(C.POINTER(i64)), J.size - 1,
+                               C.byref(nj), I.ctypes.data_as(C.POINTER(u32)), I.size, C.byref(ni))
+    assert rc == tg.ZX_EBUFSIZE
+    bad = [(2, 10, 700, 900, 0, 1024, 0),   # kind
+           (0, 12, 700, 900, 0, 1024, 0),   # L does not divide 2N
+           (0, 10, 700, 1025, 0, 1024, 0),  # n > L
+           (1, 10, 700, 701, 0, 1024, 0),   # ITFT with z < n
+           (0, 10, 700, 900, 0, 1000, 0),   # N not a multiple of 64
+           (0, 10, 700, 900, 0, 1024, 1)]   # mode 1 (S[y] rings have their own planner)
+    for kind, l, z, n, f, N, mode in bad:
+        rc = lib.zx_transform_jobs(kind, l, z, n, f, N, 0, 0, mode, None, 0, C.byref(nj), None, 0, C.byref(ni))
+        assert rc in (tg.ZX_EINVAL, tg.ZX_EUNSUPPORTED), (kind, l, z, n, f, N, mode, rc)
