@@ -77,6 +77,17 @@ def cell_bytes(N):
     return 8 * (N // 64 + 1)
 
 
+def plan_bytes(tg, kind, l, n, N):
+    """Bytes of the cells every job of the plan of one transform call reads (nload) and writes
+    (nstore), each cell 8 W bytes (the N + 1 bits, no padding)."""
+    try:
+        plan = tg.transform_jobs(kind, l, n, n, N, scale=kind)
+    except tg.TftError:
+        return None
+    cells = sum(j["nload"] + j["nstore"] for launch in plan["launches"] for j in launch["jobs"])
+    return cells * cell_bytes(N)
+
+
 def cell_stride(W, requested):
     """Limbs between consecutive cells: W rounded up to even (16-byte aligned cells) unless a
     stride is requested, which must hold a cell (>= W) and keep 16-byte alignment (even)."""
@@ -530,6 +541,10 @@ def run_gpu(args):
                      "traffic": traffic.get("dram_bytes_per_tft") if traffic else None,
                      "traffic_unit": "DRAM bytes of one TFT call at n = 40000 (ncu), against "
                                      f"{traffic.get('alg_bytes_per_tft') if traffic else None} algorithmic",
+                     "plan_bytes": plan_bytes(tg, 0, l, 40000, N),
+                     "plan_bytes_unit": "bytes the plan's jobs read and write in one TFT call at n = 40000 "
+                                        "(from zx_transform_jobs; stores still dirty in L2 when a launch ends "
+                                        "escape the kernel's ncu counters)",
                      "kernel": "job_kernel<32> (every launch of the TFT and ITFT calls; the only kernel of "
                                "the timed region, its time the region's device time)"},
         "per_n_ms": {str(n): [round(a, 3), round(b, 3)] for n, (a, b) in per_n.items()},

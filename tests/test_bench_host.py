@@ -106,3 +106,16 @@ def test_cell_stride_defaults_to_aligned_cells_and_checks_requests():
     for bad in (512, 515):
         with pytest.raises(SystemExit):
             bench.cell_stride(513, bad)
+
+
+def test_plan_bytes_of_the_benchmark_tft():
+    """The l = 16, n = 40000 TFT's jobs read and write 2.0x the algorithmic bytes of the
+    paper's two-pass schedule: four passes of 16-cell jobs, each cell read and written once a
+    pass (the first pass reads the n inputs, the others about n cells)."""
+    import paper_0810_3203_gb300 as tg
+    tg.load()
+    b = bench.plan_bytes(tg, 0, 16, 40000, 32768)
+    alg = bench.alg_cells_tft(16, 40000, 40000) * bench.cell_bytes(32768)
+    # reads 40000 + 40960 + 40192 + 40000 cells, writes 40960 + 40192 + 40000 + 40000
+    assert b == 2 * 161152 * bench.cell_bytes(32768)
+    assert 1.95 < b / alg < 2.05
