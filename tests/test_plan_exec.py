@@ -179,3 +179,15 @@ def test_the_benchmark_plan_is_safe(tg):
             check_plan_safety(plan, L, range(n))
             raw = [any(jd["pad"] & JOB_RAW_STORE for jd in launch["jobs"]) for launch in plan["launches"]]
             assert not raw[-1] and (kind == 1 or all(raw[:-1])), (kind, n, raw)
+
+
+def test_the_profiled_plan_shape(tg):
+    """The TFT at n = 40000, l = 16, N = 32768 under its default configuration is the plan the
+    ncu summaries describe: four passes of 16-cell single-CTA jobs, 4096, 2560, 2512 and 2500
+    jobs (one CTA each), the first three storing the internal form."""
+    plan = tg.transform_jobs(0, 16, 40000, 40000, 32768)
+    assert plan["passes"] == 4
+    assert [len(L["jobs"]) for L in plan["launches"]] == [4096, 2560, 2512, 2500]
+    assert all(L["lc"] == 0 and L["ls"] == 4 for L in plan["launches"])
+    raw = [all(jd["pad"] & JOB_RAW_STORE for jd in L["jobs"]) for L in plan["launches"]]
+    assert raw == [True, True, True, False]
