@@ -184,10 +184,17 @@ def test_the_benchmark_plan_is_safe(tg):
 def test_the_profiled_plan_shape(tg):
     """The TFT at n = 40000, l = 16, N = 32768 under its default configuration is the plan the
     ncu summaries describe: four passes of 16-cell single-CTA jobs, 4096, 2560, 2512 and 2500
-    jobs (one CTA each), the first three storing the internal form."""
+    jobs (one CTA each), all but the last storing the internal form where they may. A job
+    stores canonical cells when one of its cells is never stored again:
+
+      * pass 1: top column u's 256-cell TFT (height 157) splits 16 x 16, and its inner column c
+        stores inner rows 0..9 (rows 16 r + c). Pass 2 stores rows below 157 only, so inner
+        columns 13, 14, 15 of every top column stay canonical: 3 x 256 = 768 jobs.
+      * pass 2: inner row 9 of top column u stores row 156. The last row's TFT outputs only
+        columns below n2 = 64, so the 256 - 64 = 192 columns from 64 on stay canonical."""
     plan = tg.transform_jobs(0, 16, 40000, 40000, 32768)
     assert plan["passes"] == 4
     assert [len(L["jobs"]) for L in plan["launches"]] == [4096, 2560, 2512, 2500]
     assert all(L["lc"] == 0 and L["ls"] == 4 for L in plan["launches"])
-    raw = [all(jd["pad"] & JOB_RAW_STORE for jd in L["jobs"]) for L in plan["launches"]]
-    assert raw == [True, True, True, False]
+    canonical = [sum(not jd["pad"] & JOB_RAW_STORE for jd in L["jobs"]) for L in plan["launches"]]
+    assert canonical == [768, 192, 0, 2500], canonical
