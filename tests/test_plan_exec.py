@@ -198,3 +198,26 @@ def test_the_profiled_plan_shape(tg):
     assert all(L["lc"] == 0 and L["ls"] == 4 for L in plan["launches"])
     canonical = [sum(not jd["pad"] & JOB_RAW_STORE for jd in L["jobs"]) for L in plan["launches"]]
     assert canonical == [768, 192, 0, 2500], canonical
+
+
+def test_plan_safety_sweep(tg):
+    """The launch-level rules (no execution) over ring sizes, lengths and both transforms:
+    every cell in bounds, no cell written by two CTAs of one launch or read by one while
+    another writes it, internal-form stores always rewritten. Includes the padded lengths the
+    products' zero-padded ITFT uses at the benchmark's size."""
+    rng = random.Random(2024)
+    cases = []
+    for N, lmax in ((64, 7), (1024, 11), (4096, 13), (32768, 16)):
+        for l in range(1, lmax + 1):
+            L = 1 << l
+            for _ in range(3 if l < lmax else 6):
+                n = rng.randint(1, L)
+                cases.append((0, l, rng.randint(1, L), n, 0, N))
+                f = rng.randint(0, 1) if n < L else 0
+                cases.append((1, l, rng.randint(n, L), n, f, N))
+    for n in (33024, 40192, 45056, 52224):
+        cases.append((1, 16, n, n, 0, 32768))
+        cases.append((0, 16, n, n, 0, 32768))
+    for kind, l, z, n, f, N in cases:
+        plan = tg.transform_jobs(kind, l, z, n, N, f=f, e=rng.randrange(2 * N), scale=kind)
+        check_plan_safety(plan, 1 << l, range(n if kind == 0 else n + f))
