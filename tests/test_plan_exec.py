@@ -218,6 +218,14 @@ def test_plan_safety_sweep(tg):
     for n in (33024, 40192, 45056, 52224):
         cases.append((1, 16, n, n, 0, 32768))
         cases.append((0, 16, n, n, 0, 32768))
-    for kind, l, z, n, f, N in cases:
-        plan = tg.transform_jobs(kind, l, z, n, N, f=f, e=rng.randrange(2 * N), scale=kind)
+    cases = [c + (0,) for c in cases]
+    # omega = sqrt2: L | 4N, one level more per ring
+    for N, lmax in ((64, 8), (1024, 12), (8192, 15)):
+        for l in range(lmax - 3, lmax + 1):
+            L = 1 << l
+            n = rng.randint(1, L)
+            cases.append((0, l, rng.randint(1, L), n, 0, N, 2))
+            cases.append((1, l, rng.randint(n, L), n, 1 if n < L else 0, N, 2))
+    for kind, l, z, n, f, N, mode in cases:
+        plan = tg.transform_jobs(kind, l, z, n, N, f=f, e=rng.randrange(2 * N), scale=kind, mode=mode)
         check_plan_safety(plan, 1 << l, range(n if kind == 0 else n + f))
