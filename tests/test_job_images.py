@@ -33,7 +33,7 @@ def oracle_itft(orc, vals, l, z, n, f, e, N):
     return orc.cells_to_ints(x, N, n + f)
 
 
-@pytest.mark.parametrize("ls,lc", [(2, 1), (3, 0), (4, 2), (5, 2), (6, 3), (7, 2), (8, 3), (8, 4)])
+@pytest.mark.parametrize("ls,lc", [(2, 1), (3, 0), (4, 2), (5, 1), (5, 2), (6, 2), (6, 3), (7, 2), (8, 3), (8, 4)])
 def test_tft_images(tg, orc, ls, lc):
     N = 256 if ls <= 8 else 1024
     L, p = 1 << ls, (1 << N) + 1
@@ -46,7 +46,7 @@ def test_tft_images(tg, orc, ls, lc):
         assert [got[m] for m in range(n)] == oracle_tft(orc, vals, ls, z, n, e, N), (ls, lc, z, n, e)
 
 
-@pytest.mark.parametrize("ls,lc", [(2, 1), (3, 0), (4, 2), (5, 2), (6, 3), (7, 2), (8, 3), (8, 4)])
+@pytest.mark.parametrize("ls,lc", [(2, 1), (3, 0), (4, 2), (5, 1), (5, 2), (6, 2), (6, 3), (7, 2), (8, 3), (8, 4)])
 def test_itft_images(tg, orc, ls, lc):
     N = 256
     L, p = 1 << ls, (1 << N) + 1
