@@ -1,6 +1,6 @@
 // The host planner and job-image builder under AddressSanitizer and UBSan: transform plans over
 // a sweep of rings, lengths, weights and both omega modes, and job images of every single-CTA
-// and cluster shape. Built and run by tests/test_planner_sanitized.py; any report fails it.
+// and cluster shape. Built and run by tests/test_sanitizers.py; any report fails it.
 #include <cstdio>
 #include <random>
 #include <vector>
