@@ -283,6 +283,13 @@ def oracle_roundtrip_seconds(n, N, l):
     return time.perf_counter() - t0
 
 
+def reference_sample_n(steps, warmup):
+    """n of one step of the reference arm: 40000 (the CPU baseline's n) while steps + warmup
+    <= 25, else scaled down so the whole run stays near 25 round trips at n = 40000 of oracle
+    work (about 1.5 min on 3.4 s round trips), and never below 2048."""
+    return max(2048, min(40000, (40000 * 25) // max(1, steps + warmup)))
+
+
 def _oracle_roundtrip_task(args):
     return oracle_roundtrip_seconds(*args)
 
@@ -316,7 +323,7 @@ def run_reference(args):
     if rank != 0:
         return 0
     N, l = WORKLOAD["N"], WORKLOAD["l"]
-    n = 40000
+    n = reference_sample_n(args.steps, args.warmup)
     secs = []
 
     def step():
@@ -325,10 +332,10 @@ def run_reference(args):
     for _ in range(args.warmup):
         step()
     secs.clear()
-    t0 = time.perf_counter()
     for _ in range(args.steps):
         step()
-    elapsed = time.perf_counter() - t0
+    # the oracle's own time (the seeded inputs are generated outside it)
+    elapsed = sum(secs)
     b = (alg_cells_tft(l, n, n) + alg_cells_itft(l, n, n)) * cell_bytes(N)
     value = b * args.steps / elapsed / 1e9
     line = {
@@ -336,7 +343,7 @@ def run_reference(args):
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": round(elapsed / args.steps * 1e3, 3), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-        "config": {"workload": "TFT+ITFT round trip over Z/(2^32768+1), L = 2^16, n = 40000 "
+        "config": {"workload": f"TFT+ITFT round trip over Z/(2^32768+1), L = 2^16, n = {n} "
                                "(bounded sample of the n sweep)", "N": N, "l": l, "ns": [n],
                    "seed": WORKLOAD["seed"]},
         "cpu_baseline": {"value": round(value, 4), "unit": "GB/s", "cores": 1, "kind": "oracle",

@@ -119,3 +119,14 @@ def test_plan_bytes_of_the_benchmark_tft():
     # reads 40000 + 40960 + 40192 + 40000 cells, writes 40960 + 40192 + 40000 + 40000
     assert b == 2 * 161152 * bench.cell_bytes(32768)
     assert 1.95 < b / alg < 2.05
+
+
+def test_reference_steps_stay_bounded():
+    """The reference arm's oracle work stays near 25 round trips at n = 40000 for any step
+    count, and keeps n = 40000 for short runs."""
+    assert bench.reference_sample_n(1, 3) == 40000
+    assert bench.reference_sample_n(22, 3) == 40000
+    for steps in (30, 100, 400):
+        n = bench.reference_sample_n(steps, 3)
+        assert 2048 <= n < 40000 and (steps + 3) * n <= 25 * 40000
+    assert bench.reference_sample_n(1000, 3) == 2048  # the floor
