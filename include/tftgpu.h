@@ -235,14 +235,15 @@ typedef struct {
     int32_t candidates; /* configurations timed */
     float best_ms;      /* round-trip time of the chosen configuration */
     float default_ms;   /* round-trip time of the default configuration */
-    int32_t pad;
+    int32_t fused;      /* 1: a plan whose jobs all run on single CTAs is one persistent launch
+                           (zx_transform_schedule); 0: one launch per global-memory pass */
 } zx_tune_info;
 
 int zx_tune(uint64_t *x, int l, int64_t n, int64_t N, int64_t stride_limbs, int reps, void *stream,
             zx_tune_info *out);
 
-/* The launch configuration used for ring N (ls_max, ls_c, max_warps, split; the other fields are
- * zero), and pinning one, e.g. a result of zx_tune saved from an earlier process. zx_config_set
+/* The launch configuration used for ring N (ls_max, ls_c, max_warps, split, fused; the other
+ * fields are zero), and pinning one, e.g. a result of zx_tune saved from an earlier process. zx_config_set
  * returns ZX_EINVAL for a configuration the ring cannot run (shared memory, warps, split); with
  * cfg == NULL it restores the default. Host only. */
 int zx_config_get(int64_t N, zx_tune_info *out);
@@ -348,11 +349,31 @@ int zx_transform_jobs(int kind, int l, int64_t z, int64_t n, int f, int64_t N, i
                       int64_t *images_words);
 
 /*
+ * The persistent form of the same plan (host only, no device needed; no counterpart in the
+ * paper, which runs the passes one after the other). When every job of the plan runs on a
+ * single CTA, tft_ex / itft_ex enqueue one launch whose CTAs claim the jobs in a fixed order from
+ * a counter; a claimed job first waits (bounded) until the jobs it depends on have finished: the
+ * last job that stored a cell it reads or stores, and every job that read a cell it stores since
+ * that cell was last stored. Every dependency comes earlier in the claim order, so the earliest
+ * unfinished job can always run. The order is a list schedule over `slots` concurrent CTAs
+ * (0: 456, three per SM of a GB300) that takes the deepest ready pass first, so that a pass
+ * re-reads the cells the previous pass has just written from L2.
+ *   out (int64 words): [count], then per claim position k: [job, ndeps, deps...] where job is the
+ *   position of the job in zx_transform_jobs' list (launches in order, their jobs in order) and
+ *   deps are claim positions below k. count = 0 when the plan runs as one launch per pass.
+ * The length goes to *words; ZX_EBUFSIZE when out is too small (the length is still written).
+ */
+int zx_transform_schedule(int kind, int l, int64_t z, int64_t n, int f, int64_t N, int64_t e, int scale, int mode,
+                          int slots, int64_t *out, int64_t cap, int64_t *words);
+
+/*
  * Bounded device-side waits. The transform kernel stages the cells of single-CTA jobs in
  * shared memory with bulk (TMA) copies and waits for their completion on an mbarrier with a
  * time limit of one second. A wait that runs out waits once more (also bounded) for the copies
  * still in flight, then stops that CTA and sets a status word of the device; the outputs of
- * the call it belonged to are then unspecified. Launches do not synchronise, so the status is
+ * the call it belonged to are then unspecified. In a persistent launch (zx_transform_schedule)
+ * a job's wait for the jobs it depends on is bounded too (two seconds); one that runs out sets
+ * the same status word, and later waits of any launch on the device then return at once. Launches do not synchronise, so the status is
  * read on request:
  *   zx_wait_status  synchronises `stream`, then reads and clears the status word of the current
  *                   device (atomically). ZX_OK when no wait gave up since the last read,

@@ -26,7 +26,8 @@ EXPORTS = ("tft", "tft_ex", "itft", "itft_ex", "zx_plan", "zx_mul", "zx_mul_batc
            "zx_transform_plan", "zx_mul_noalloc", "zx_job_program", "zx_strerror", "zx_last_error",
            "zx_version", "zx_server_create", "zx_server_submit", "zx_server_poll", "zx_server_drain",
            "zx_server_stats", "zx_server_destroy", "zx_tune", "zx_config_get", "zx_config_set", "sn_tft", "sn_itft", "tft_sqrt2", "itft_sqrt2",
-           "zx_pointwise", "zx_pointwise_plan", "zx_wait_status", "zx_wait_probe", "zx_transform_jobs")
+           "zx_pointwise", "zx_pointwise_plan", "zx_wait_status", "zx_wait_probe", "zx_transform_jobs",
+           "zx_transform_schedule")
 
 _lib = None
 
@@ -53,7 +54,7 @@ class ZxPlanInfo(C.Structure):
 
 class ZxTuneInfo(C.Structure):
     _fields_ = [("ls_max", C.c_int32), ("ls_c", C.c_int32), ("max_warps", C.c_int32), ("split", C.c_int32),
-                ("candidates", C.c_int32), ("best_ms", C.c_float), ("default_ms", C.c_float), ("pad", C.c_int32)]
+                ("candidates", C.c_int32), ("best_ms", C.c_float), ("default_ms", C.c_float), ("fused", C.c_int32)]
 
 
 class ZxServerInfo(C.Structure):
@@ -111,6 +112,8 @@ def load(build_if_missing=True):
     L.zx_tune.argtypes = [vp, i32, i64, i64, i64, i32, vp, C.POINTER(ZxTuneInfo)]
     L.zx_config_get.argtypes = [i64, C.POINTER(ZxTuneInfo)]
     L.zx_config_set.argtypes = [i64, C.POINTER(ZxTuneInfo)]
+    L.zx_transform_schedule.argtypes = [i32, i32, i64, i64, i32, i64, i64, i32, i32, i32, C.POINTER(C.c_int64), i64,
+                                        C.POINTER(C.c_int64)]
     L.tft_sqrt2.argtypes = [vp, i32, i64, i64, i64, i64, i64, vp]
     L.itft_sqrt2.argtypes = [vp, i32, i64, i64, i32, i64, i64, i64, i32, vp]
     L.sn_tft.argtypes = [vp, i32, i64, i64, i64, C.c_uint64, i64, i64, vp]
@@ -269,7 +272,7 @@ def tune(x, l, n, N, stride_limbs=None, reps=2, stream=None):
     info = ZxTuneInfo()
     s = stride_limbs or limbs(N)
     _check(load().zx_tune(_dev_ptr(x), l, n, N, s, reps, _stream(stream), C.byref(info)), "zx_tune")
-    return {k: getattr(info, k) for k, _ in ZxTuneInfo._fields_ if k != "pad"}
+    return {k: getattr(info, k) for k, _ in ZxTuneInfo._fields_}
 
 
 def tft_sqrt2(x, l, z, n, N, e=0, stride_limbs=None, stream=None):
@@ -295,10 +298,10 @@ def sn_itft(x, l, z, n, f, M, m, e=0, stride=None, scale=0, stream=None):
 
 
 def config_get(N):
-    """Launch configuration used for ring N: ls_max, ls_c, max_warps, split."""
+    """Launch configuration used for ring N: ls_max, ls_c, max_warps, split, fused."""
     info = ZxTuneInfo()
     _check(load().zx_config_get(N, C.byref(info)), "zx_config_get")
-    return {k: getattr(info, k) for k in ("ls_max", "ls_c", "max_warps", "split")}
+    return {k: getattr(info, k) for k in ("ls_max", "ls_c", "max_warps", "split", "fused")}
 
 
 def config_set(N, cfg=None):
@@ -306,7 +309,7 @@ def config_set(N, cfg=None):
     if cfg is None:
         _check(load().zx_config_set(N, None), "zx_config_set")
         return
-    info = ZxTuneInfo(cfg["ls_max"], cfg["ls_c"], cfg["max_warps"], cfg["split"], 0, 0.0, 0.0, 0)
+    info = ZxTuneInfo(cfg["ls_max"], cfg["ls_c"], cfg["max_warps"], cfg["split"], 0, 0.0, 0.0, cfg.get("fused", 1))
     _check(load().zx_config_set(N, C.byref(info)), "zx_config_set")
 
 
@@ -387,6 +390,24 @@ def transform_jobs(kind, l, z, n, N, f=0, e=0, scale=0, mode=0):
     off = [int(v) for v in I[:nimg + 1]]
     images = [I[nimg + 1 + off[t]:nimg + 1 + off[t + 1]].copy() for t in range(nimg)]
     return dict(passes=passes, launches=launches, images=images)
+
+
+def transform_schedule(kind, l, z, n, N, f=0, e=0, scale=0, mode=0, slots=0):
+    """The persistent form of a transform's plan (zx_transform_schedule in include/tftgpu.h): a
+    list of (job, deps) in claim order, job indexing transform_jobs' jobs launch by launch and
+    deps the claim positions it waits for; empty when the plan runs as one launch per pass."""
+    w = C.c_int64(0)
+    load().zx_transform_schedule(kind, l, z, n, f, N, e, scale, mode, slots, None, 0, C.byref(w))
+    W = np.zeros(max(1, w.value), np.int64)
+    _check(load().zx_transform_schedule(kind, l, z, n, f, N, e, scale, mode, slots,
+                                        W.ctypes.data_as(C.POINTER(C.c_int64)), W.size, C.byref(w)),
+           "zx_transform_schedule")
+    out, k = [], 1
+    for _ in range(int(W[0])):
+        job, nd = int(W[k]), int(W[k + 1])
+        out.append((job, [int(v) for v in W[k + 2:k + 2 + nd]]))
+        k += 2 + nd
+    return out
 
 
 def wait_status(stream=None):

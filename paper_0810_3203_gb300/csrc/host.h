@@ -47,8 +47,10 @@ Ring make_ring(int64_t N);
 // the cells per CTA of a cluster job (ls_c, both log2), the warps per CTA (8 or 16) and the
 // top-level split (0: L1 = 2^floor(l/2) as in the paper, 1: L1 = 2^ceil(l/2)). Every choice
 // computes the same outputs; they differ in speed. zx_tune measures the candidates.
+// fused: a plan whose jobs all run on single CTAs is one persistent launch that claims the jobs
+// in dependency order (FusedSchedule) instead of one launch per pass (zx_tune compares both).
 struct PlanConfig {
-  int ls_max = 0, ls_c = 0, max_warps = 16, split = 0;
+  int ls_max = 0, ls_c = 0, max_warps = 16, split = 0, fused = 0;
 };
 PlanConfig default_config(const Ring &r);
 bool config_valid(const Ring &r, const PlanConfig &c);
@@ -80,12 +82,34 @@ struct Launch {
   int nsegs = 0;
 };
 
+// One persistent launch over every job of a plan whose jobs are all single-CTA jobs. Jobs are
+// claimed in `order` (positions in the plan's pass-ordered job list); claimed job k waits for
+// the jobs at claim positions deps[dep_off[k] .. dep_off[k + 1]): the last job that stored a
+// cell k reads or stores, and every job that read a cell k stores since it was last stored.
+// The order is a list schedule over `slots` concurrent CTAs that prefers the deepest pass among
+// the jobs whose dependencies are done, so a pass re-reads what the previous one just wrote
+// while it is still in L2.
+struct FusedSchedule {
+  std::vector<int32_t> order;
+  std::vector<int32_t> dep_off;
+  std::vector<int32_t> deps;
+};
+// jobs in pass order with their pass numbers; L cells; false (and an empty schedule) when the
+// plan does not qualify (a job outside [0, L), or L above 2^22)
+bool build_fused_schedule(const std::vector<JobDesc> &jobs, const std::vector<int> &pass, int64_t L, int slots,
+                          FusedSchedule *out);
+
 struct TransformPlan {
   Ring ring;
   int mode = RING_FERMAT;  // RingMode of the rotation amounts
   std::vector<Launch> launches;  // in stream order
   int npasses = 0;
   int64_t njobs = 0;
+  // the fused form (used when f_njobs > 0 and the caller allows it): one launch of f_ls-sized
+  // single-CTA jobs in claim order with their dependency lists, all in device memory
+  int f_njobs = 0, f_ls = 0, f_nwarps = 0, f_prog_words = 0;
+  const JobDesc *f_jobs = nullptr;
+  const int32_t *f_dep_off = nullptr, *f_deps = nullptr;
 };
 
 // Cached plan of TFT (kind = KIND_TFT) or ITFT for the given parameters; nullptr with *err set
@@ -124,6 +148,10 @@ struct HostPlan {
 };
 void build_host_plan(int kind, int l, int64_t z, int64_t n, int f, int64_t N, int64_t e, int scale,
                      HostPlan *out, int mode = RING_FERMAT);
+// The fused schedule of the same plan (empty when it has none), with `order` given as positions
+// in HostPlan's launch-major job list.
+void build_host_schedule(int kind, int l, int64_t z, int64_t n, int f, int64_t N, int64_t e, int scale,
+                         FusedSchedule *out, int mode = RING_FERMAT, int slots = 0);
 
 // Plans over S[y]/(y^{M/2}+1), H = M/2 coefficients per element (single-CTA jobs; the ITFT's
 // final division by L is escale = l halvings). nullptr with *err set on failure.
@@ -136,9 +164,11 @@ void sn_plan_shape(int kind, int l, int64_t z, int64_t n, int f, int64_t H, int 
 cudaError_t run_sn_transform(const TransformPlan &p, uint64_t *x, int64_t stride, int64_t H, uint64_t m,
                              cudaStream_t s);
 
-// Enqueue a plan on a stream.
+// Enqueue a plan on a stream. A plan with a fused form runs as one persistent launch, whose
+// claim counter and done flags come from the stream-ordered allocator; allow_fused = false
+// keeps one launch per pass and allocates nothing.
 cudaError_t run_transform(const TransformPlan &p, uint64_t *x, int64_t stride_limbs,
-                          cudaStream_t s);
+                          cudaStream_t s, bool allow_fused = true);
 // The same plan applied to `reps` buffers of rep_cells cells each, back to back from x: every
 // launch covers all of them (replica r shifts each job by r * rep_cells cells).
 cudaError_t run_transform_reps(const TransformPlan &p, uint64_t *x, int64_t stride_limbs, int64_t reps,

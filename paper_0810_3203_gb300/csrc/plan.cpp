@@ -14,6 +14,7 @@
 #include <map>
 #include <memory>
 #include <mutex>
+#include <queue>
 #include <tuple>
 #include <vector>
 
@@ -72,7 +73,7 @@ bool config_valid(const Ring &r, const PlanConfig &c) {
   auto fits = [&](int ls) { return ls >= 1 && ls <= 16 && size_t(1) << ls <= 65536 &&
                                    (size_t(1) << ls) * (size_t(r.pitch) + 1) * 4 <= kSmemBudget; };
   return fits(c.ls_max) && fits(c.ls_c) && c.ls_c <= c.ls_max + 1 && (c.max_warps == 8 || c.max_warps == 16) &&
-         (c.split == 0 || c.split == 1);
+         (c.split == 0 || c.split == 1) && (c.fused == 0 || c.fused == 1);
 }
 
 namespace {
@@ -321,6 +322,92 @@ static void mark_raw_stores(std::vector<JobRec> &jobs, int l) {
   }
 }
 
+bool build_fused_schedule(const std::vector<JobDesc> &jobs, const std::vector<int> &pass, int64_t L, int slots,
+                          FusedSchedule *out) {
+  *out = FusedSchedule();
+  const int nj = int(jobs.size());
+  if (nj == 0 || L > (int64_t(1) << 22) || slots < 1) return false;
+  // dependencies, taking the jobs in pass order (jobs of one pass touch disjoint cells)
+  const size_t ncells = size_t(L);
+  std::vector<int32_t> last_store(ncells, -1);
+  std::vector<std::vector<int32_t>> readers(ncells);
+  std::vector<std::vector<int32_t>> deps(nj);
+  for (int j = 0; j < nj; j++) {
+    const JobDesc &d = jobs[j];
+    const int64_t span = std::max(d.nload, d.nstore);
+    for (int64_t m = 0; m < span; m++) {
+      const int64_t c = d.cell0 + m * d.mstride;
+      if (c < 0 || c >= L) return false;
+    }
+    std::vector<int32_t> &dj = deps[j];
+    for (int64_t m = 0; m < span; m++) {
+      const size_t c = size_t(d.cell0 + m * d.mstride);
+      if (last_store[c] >= 0) dj.push_back(last_store[c]);
+      if (m < d.nstore) dj.insert(dj.end(), readers[c].begin(), readers[c].end());
+    }
+    std::sort(dj.begin(), dj.end());
+    dj.erase(std::unique(dj.begin(), dj.end()), dj.end());
+    for (int64_t m = 0; m < span; m++) {
+      const size_t c = size_t(d.cell0 + m * d.mstride);
+      if (m < d.nstore) {
+        last_store[c] = j;
+        readers[c].clear();
+      } else if (m < d.nload) {
+        readers[c].push_back(j);
+      }
+    }
+  }
+  // list schedule: rounds of `slots` jobs; a job is ready once every job it depends on ran in an
+  // earlier round; among ready jobs the deepest pass goes first, then the plan order
+  std::vector<std::vector<int32_t>> users(nj);
+  std::vector<int32_t> pending(nj);
+  for (int j = 0; j < nj; j++) {
+    pending[j] = int32_t(deps[j].size());
+    for (int32_t d : deps[j]) users[d].push_back(j);
+  }
+  auto later = [&](int32_t a, int32_t b) { return pass[a] != pass[b] ? pass[a] < pass[b] : a > b; };
+  std::priority_queue<int32_t, std::vector<int32_t>, decltype(later)> ready(later);
+  for (int j = 0; j < nj; j++)
+    if (!pending[j]) ready.push(j);
+  std::vector<int32_t> pos(nj, -1), round;
+  out->order.reserve(nj);
+  while (!ready.empty()) {
+    round.clear();
+    while (!ready.empty() && int(round.size()) < slots) {
+      const int32_t j = ready.top();
+      ready.pop();
+      pos[j] = int32_t(out->order.size());
+      out->order.push_back(j);
+      round.push_back(j);
+    }
+    for (int32_t j : round)
+      for (int32_t u : users[j])
+        if (--pending[u] == 0) ready.push(u);
+  }
+  if (int(out->order.size()) != nj) {  // a cycle cannot occur; keep the per-pass launches if it did
+    *out = FusedSchedule();
+    return false;
+  }
+  out->dep_off.push_back(0);
+  for (int k = 0; k < nj; k++) {
+    for (int32_t d : deps[out->order[k]]) out->deps.push_back(pos[d]);
+    out->dep_off.push_back(int32_t(out->deps.size()));
+  }
+  return true;
+}
+
+// Concurrent CTAs of a fused launch, for the list schedule (the launch uses the occupancy of its
+// kernel; this only shapes the order): three single-CTA jobs per SM.
+static int schedule_slots() {
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) {
+    cudaGetLastError();
+    sms = 152;
+  }
+  return 3 * sms;
+}
+
 int64_t zero_padded_outputs(int l, int64_t n, int64_t N) {
   Planner P(N);
   const int64_t L = int64_t(1) << l;
@@ -419,6 +506,34 @@ void build_host_plan(int kind, int l, int64_t z, int64_t n, int f, int64_t N, in
   }
 }
 
+void build_host_schedule(int kind, int l, int64_t z, int64_t n, int f, int64_t N, int64_t e, int scale,
+                         FusedSchedule *out, int mode, int slots) {
+  *out = FusedSchedule();
+  const int64_t twoN = omega_order(N, mode);
+  e = md(e, twoN);
+  Planner P(N, nullptr, mode);
+  if (kind == KIND_TFT)
+    P.tft(0, 0, 1, l, e, z, n);
+  else
+    P.itft(0, 0, 1, l, e, z, n, f, scale ? inv_l_exponent(l, twoN, mode) : -1);
+  mark_raw_stores(P.jobs, l);
+  std::stable_sort(P.jobs.begin(), P.jobs.end(), launch_order);
+  int nl = 0;
+  bool single = true;
+  for (size_t i = 0; i < P.jobs.size(); i++) {
+    if (i == 0 || !same_launch(P.jobs[i], P.jobs[i - 1])) nl++;
+    single = single && P.jobs[i].lc == 0;
+  }
+  if (!P.cfg.fused || !single || nl < 2) return;
+  std::vector<JobDesc> flat;
+  std::vector<int> passes;
+  for (const JobRec &j : P.jobs) {
+    flat.push_back(j.d);
+    passes.push_back(j.pass);
+  }
+  build_fused_schedule(flat, passes, int64_t(1) << l, slots > 0 ? slots : 456, out);
+}
+
 const TransformPlan *get_transform_plan(int kind, int l, int64_t z, int64_t n, int f, int64_t N,
                                         int64_t e, int64_t stride_limbs, int scale, int *err, int mode,
                                         bool replicated) {
@@ -428,7 +543,7 @@ const TransformPlan *get_transform_plan(int kind, int l, int64_t z, int64_t n, i
   e = md(e, twoN);
   const PlanConfig cfg = plan_config(N);
   const int cfg_key = cfg.ls_max | (cfg.ls_c << 5) | (cfg.max_warps << 10) | (cfg.split << 16) | (mode << 20) |
-                      (replicated ? 1 << 23 : 0);
+                      (replicated ? 1 << 23 : 0) | (cfg.fused << 24);
   auto key = std::make_tuple(dev, kind, l, z, n, f, N, e, scale, cfg_key);
   PlanCache &pc = plan_cache();
   {
@@ -487,6 +602,41 @@ const TransformPlan *get_transform_plan(int kind, int l, int64_t z, int64_t n, i
     plan->launches.push_back(g.second);
   }
   (void)stride_limbs;
+  // the fused form: every job single-CTA, more than one launch, not replicated
+  bool fusable = cfg.fused && !replicated && plan->launches.size() > 1;
+  for (const Launch &L : plan->launches) fusable = fusable && L.lc == 0;
+  FusedSchedule fs;
+  std::vector<int> passes;
+  for (const JobRec &j : P.jobs) passes.push_back(j.pass);
+  if (fusable && build_fused_schedule(flat, passes, int64_t(1) << l, schedule_slots(), &fs)) {
+    const size_t nj = fs.order.size();
+    const size_t bytes = nj * sizeof(JobDesc) + (fs.dep_off.size() + fs.deps.size()) * sizeof(int32_t);
+    std::vector<unsigned char> blob(bytes);
+    JobDesc *hj = reinterpret_cast<JobDesc *>(blob.data());
+    for (size_t k = 0; k < nj; k++) hj[k] = flat[size_t(fs.order[k])];
+    int32_t *ho = reinterpret_cast<int32_t *>(hj + nj);
+    std::memcpy(ho, fs.dep_off.data(), fs.dep_off.size() * sizeof(int32_t));
+    std::memcpy(ho + fs.dep_off.size(), fs.deps.data(), fs.deps.size() * sizeof(int32_t));
+    unsigned char *dblob = nullptr;
+    if (cudaMalloc(&dblob, bytes) != cudaSuccess) {
+      *err = ZX_ENOMEM;
+      return nullptr;
+    }
+    if (cudaMemcpy(dblob, blob.data(), bytes, cudaMemcpyHostToDevice) != cudaSuccess) {
+      cudaFree(dblob);
+      *err = ZX_ECUDA;
+      return nullptr;
+    }
+    plan->f_njobs = int(nj);
+    plan->f_jobs = reinterpret_cast<const JobDesc *>(dblob);
+    plan->f_dep_off = reinterpret_cast<const int32_t *>(dblob + nj * sizeof(JobDesc));
+    plan->f_deps = plan->f_dep_off + fs.dep_off.size();
+    for (const Launch &L : plan->launches) {
+      plan->f_ls = std::max(plan->f_ls, L.ls);
+      plan->f_prog_words = std::max(plan->f_prog_words, L.prog_words);
+    }
+    plan->f_nwarps = warps_for_job(plan->f_ls, 0, P.cfg.max_warps);
+  }
   std::lock_guard<std::mutex> lk(pc.mu);
   auto &slot = pc.plans[key];
   if (!slot) slot = std::move(plan);

@@ -173,7 +173,8 @@ __device__ __forceinline__ void exec_op(const OpDesc &op, uint32_t *cells, uint3
 
 // Copy the N-bit part of a cell between global memory (16-byte aligned when vec16) and a
 // shared-memory cell, with consecutive lanes on consecutive addresses (coalesced); returns the
-// top limb on loads. Groups of 4 words never straddle a 32-word row, so for K >= 4 both sides
+// top limb on loads. Cell loads go through L2 only (ld.global.cg): in a persistent launch
+// another CTA of the same kernel may have written the cell. Groups of 4 words never straddle a 32-word row, so for K >= 4 both sides
 // move 16-byte vectors.
 template <int K>
 __device__ __forceinline__ uint64_t gmem_to_smem_cell(uint32_t *scell, const uint64_t *gcell, bool vec16,
@@ -182,7 +183,7 @@ __device__ __forceinline__ uint64_t gmem_to_smem_cell(uint32_t *scell, const uin
   if (vec16 && (g.NW & 3) == 0) {
     const uint4 *src = reinterpret_cast<const uint4 *>(w32);
     for (int q = g.lane; q < g.NW / 4; q += 32) {
-      const uint4 v = __ldg(src + q);
+      const uint4 v = __ldcg(src + q);
       const int pw = phys<K>(4 * q);
       if constexpr (K >= 4) {
         *reinterpret_cast<uint4 *>(scell + pw) = v;
@@ -196,13 +197,13 @@ __device__ __forceinline__ uint64_t gmem_to_smem_cell(uint32_t *scell, const uin
   } else {
     const uint2 *src = reinterpret_cast<const uint2 *>(w32);
     for (int q = g.lane; q < g.NW / 2; q += 32) {
-      const uint2 v = __ldg(src + q);
+      const uint2 v = __ldcg(src + q);
       const int pw = phys<K>(2 * q);
       scell[pw] = v.x;
       scell[pw + 1] = v.y;
     }
   }
-  return __ldg(gcell + g.NW / 2);
+  return __ldcg(gcell + g.NW / 2);
 }
 
 template <int K>
@@ -372,53 +373,67 @@ __device__ __forceinline__ void exchange(uint32_t *cells, uint32_t *meta, int P,
   __syncthreads();
 }
 
-// MINB = 3: jobs of at most 8 warps and 75 KB of shared memory, three CTAs per SM (registers
-// capped at 85 per thread); MINB = 1: up to 16 warps, one CTA per SM. FULL: all 32 lanes hold
-// words (NW = 32 K), which lets the compiler drop the idle-lane cases.
-template <int K, int MINB, bool FULL, bool SQ>
-__global__ void __launch_bounds__(MINB == 3 ? 256 : 512, MINB) job_kernel(uint64_t *__restrict__ x, int64_t stride_limbs,
-                                                  const JobDesc *__restrict__ jobs, int N, int ls, int lc,
-                                                  uint32_t mask, int prog_cap,
-                                                  const Segment *__restrict__ segs, int nsegs, int64_t rep_cells,
-                                                  int rep_ctas) {
+// Arguments of a persistent launch that runs every job of a plan (njobs > 0): the CTAs claim
+// jobs in the order of `jobs` from a counter, wait until the jobs listed for a claimed job have
+// finished (their done flags), run it and set its own flag. Every job a job waits for comes
+// earlier in the claim order and was claimed by a CTA that is running, so the earliest
+// unfinished job can always proceed; the waits are bounded all the same.
+struct FusedArgs {
+  const JobDesc *jobs;     // in claim order
+  const int32_t *dep_off;  // job k waits for deps[dep_off[k] .. dep_off[k + 1])
+  const int32_t *deps;     // claim positions, all below k
+  uint32_t *sync;          // [0] claim counter, [1 + k] done flag of job k (zero on entry)
+  int njobs;               // 0: one job per CTA (plain or merged launch)
+};
+
+// Wait limit of a dependency (a job finishes within microseconds; a whole plan within
+// milliseconds).
+constexpr uint64_t kDepWaitNs = 2000000000ull;
+
+// Dynamic shared memory a job kernel may take: the 227 KB of a block less the kernel's static
+// claim word (with room for its alignment).
+constexpr size_t kJobDynSmem = 227 * 1024 - 64;
+
+__device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t *p) {
+  uint32_t v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void st_release_u32(uint32_t *p, uint32_t v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// One warp waits until every job job k depends on has set its done flag, polling with a short
+// sleep. It gives up when the limit passes (bit 2 of the status word) or when an earlier wait
+// has given up, so that no CTA waits twice on a plan that already failed.
+__device__ __forceinline__ void wait_deps(const FusedArgs &fa, int k, int lane) {
+  const int a = fa.dep_off[k], b = fa.dep_off[k + 1];
+  const uint64_t t0 = globaltimer_ns();
+  for (int base = a; base < b; base += 32) {
+    const int d = base + lane < b ? fa.deps[base + lane] : -1;
+    for (;;) {
+      const uint32_t done = d >= 0 ? ld_acquire_u32(fa.sync + 1 + d) : 1u;
+      if (__all_sync(TFT_FULL, done != 0)) break;
+      if (*reinterpret_cast<volatile uint32_t *>(&g_wait_fault) & 2u) return;
+      if (globaltimer_ns() - t0 > kDepWaitNs) {
+        if (lane == 0) atomicOr(&g_wait_fault, 2u);
+        return;
+      }
+      __nanosleep(256);
+    }
+  }
+}
+
+// One job (see the file comment): load its cells into shared memory, run the stages of its
+// image, store. Returns false when its bulk load did not land in time (the status word of the
+// device is set; its outputs are then unspecified).
+template <int K, bool SQ>
+__device__ __forceinline__ bool run_job(const JobDesc &jd, uint64_t *__restrict__ x, int64_t stride_limbs, int ls,
+                                        int lc, const KGeo &kg, int prog_cap) {
   extern __shared__ uint32_t smem[];
   const int C = 1 << lc;
   const int rank = int(blockIdx.x) & (C - 1);
-  JobDesc jd;
-  if (nsegs == 0) {
-    // replicated launch: rep_ctas CTAs per replica, replica r shifted by r * rep_cells cells
-    int b = int(blockIdx.x);
-    int64_t shift = 0;
-    if (rep_ctas > 0) {
-      const int r = b / rep_ctas;
-      b -= r * rep_ctas;
-      shift = int64_t(r) * rep_cells;
-    }
-    jd = jobs[b >> lc];
-    jd.cell0 += shift;
-  } else {
-    // merged launch: the last segment that starts at or before this CTA (segments hold whole
-    // clusters, so the CTAs of one cluster agree)
-    int lo = 0, hi = nsegs - 1;
-    while (lo < hi) {
-      const int mid = (lo + hi + 1) >> 1;
-      if (segs[mid].first_cta <= int(blockIdx.x)) lo = mid;
-      else hi = mid - 1;
-    }
-    const Segment sg = segs[lo];
-    jd = sg.jobs[(int(blockIdx.x) - sg.first_cta) >> lc];
-    jd.cell0 += sg.cell_off;
-  }
-  KGeo kg;
-  // a FULL ring has N = 1024 K: its geometry is compile-time
-  if (FULL) N = 1024 * K;
-  kg.g.N = N;
-  kg.g.NW = N / 32;
-  kg.g.G = FULL ? 32 : kg.g.NW / K;
-  kg.g.lane = threadIdx.x & 31;
-  kg.g.twoN = 2 * N;
-  kg.ord = SQ ? 4 * N : 2 * N;
-  kg.mask = FULL ? uint32_t(kg.ord - 1) : mask;
   const Geo &g = kg.g;
   const int nslots = 1 << (job_ls(jd.pad, ls) - lc);
   const int L2 = nslots, b = nslots / C;
@@ -460,10 +475,10 @@ __global__ void __launch_bounds__(MINB == 3 ? 256 : 512, MINB) job_kernel(uint64
       if (!landed) mbar_wait_bounded(mb, 0, kBulkWaitNs);
       __syncthreads();
       if (threadIdx.x == 0) atomicOr(&g_wait_fault, 1u);
-      return;
+      return false;
     }
     for (int s = warp; s < nl; s += nw) {
-      const uint64_t T = __ldg(x0 + int64_t(s) * cstep + g.NW / 2);
+      const uint64_t T = __ldcg(x0 + int64_t(s) * cstep + g.NW / 2);
       if (T & kRawTopMark) {
         // written by an earlier pass in internal form: the words are m, the top limb the metadata
         if (g.lane == 0) meta[s] = uint32_t(T);
@@ -545,18 +560,89 @@ __global__ void __launch_bounds__(MINB == 3 ? 256 : 512, MINB) job_kernel(uint64
     __syncwarp();
     smem_to_gmem_cell<K>(gc, cells + s * P, top, vec16, g);
   }
+  return true;
+}
+
+// MINB = 3: jobs of at most 8 warps and 75 KB of shared memory, three CTAs per SM (registers
+// capped at 85 per thread); MINB = 1: up to 16 warps, one CTA per SM. FULL: all 32 lanes hold
+// words (NW = 32 K), which lets the compiler drop the idle-lane cases.
+template <int K, int MINB, bool FULL, bool SQ>
+__global__ void __launch_bounds__(MINB == 3 ? 256 : 512, MINB) job_kernel(uint64_t *__restrict__ x, int64_t stride_limbs,
+                                                  const JobDesc *__restrict__ jobs, int N, int ls, int lc,
+                                                  uint32_t mask, int prog_cap,
+                                                  const Segment *__restrict__ segs, int nsegs, int64_t rep_cells,
+                                                  int rep_ctas, FusedArgs fa) {
+  KGeo kg;
+  // a FULL ring has N = 1024 K: its geometry is compile-time
+  if (FULL) N = 1024 * K;
+  kg.g.N = N;
+  kg.g.NW = N / 32;
+  kg.g.G = FULL ? 32 : kg.g.NW / K;
+  kg.g.lane = threadIdx.x & 31;
+  kg.g.twoN = 2 * N;
+  kg.ord = SQ ? 4 * N : 2 * N;
+  kg.mask = FULL ? uint32_t(kg.ord - 1) : mask;
+  __shared__ int s_claim;
+  const bool fused = fa.njobs > 0;
+  for (;;) {
+    JobDesc jd;
+    int k = 0;
+    if (fused) {
+      __syncthreads();  // the previous job is done with shared memory and with s_claim
+      if (threadIdx.x == 0) s_claim = int(atomicAdd(fa.sync, 1u));
+      __syncthreads();
+      k = s_claim;
+      if (k >= fa.njobs) return;
+      if (threadIdx.x < 32) wait_deps(fa, k, kg.g.lane);
+      __syncthreads();
+      // the cells written by the jobs waited for are read by bulk copies (async proxy) below
+      asm volatile("fence.proxy.async.global;" ::: "memory");
+      jd = fa.jobs[k];
+      lc = 0;
+    } else if (nsegs == 0) {
+      // replicated launch: rep_ctas CTAs per replica, replica r shifted by r * rep_cells cells
+      int b = int(blockIdx.x);
+      int64_t shift = 0;
+      if (rep_ctas > 0) {
+        const int r = b / rep_ctas;
+        b -= r * rep_ctas;
+        shift = int64_t(r) * rep_cells;
+      }
+      jd = jobs[b >> lc];
+      jd.cell0 += shift;
+    } else {
+      // merged launch: the last segment that starts at or before this CTA (segments hold whole
+      // clusters, so the CTAs of one cluster agree)
+      int lo = 0, hi = nsegs - 1;
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (segs[mid].first_cta <= int(blockIdx.x)) lo = mid;
+        else hi = mid - 1;
+      }
+      const Segment sg = segs[lo];
+      jd = sg.jobs[(int(blockIdx.x) - sg.first_cta) >> lc];
+      jd.cell0 += sg.cell_off;
+    }
+    run_job<K, SQ>(jd, x, stride_limbs, ls, lc, kg, prog_cap);
+    if (!fused) return;
+    __syncthreads();  // every store of the job has been issued
+    if (threadIdx.x == 0) {
+      __threadfence();
+      st_release_u32(fa.sync + 1 + k, 1u);
+    }
+  }
 }
 
 namespace {
 
 template <int K, int MINB, bool FULL, bool SQ>
 cudaError_t launch_km(const Launch &L, uint64_t *x, int64_t stride_limbs, const Ring &r, cudaStream_t s,
-                      size_t smem, int prog_cap, uint32_t mask, int64_t reps, int64_t rep_cells) {
+                      size_t smem, int prog_cap, uint32_t mask, int64_t reps, int64_t rep_cells, const FusedArgs &fa) {
   static thread_local int configured[8] = {0, 0, 0, 0, 0, 0, 0, 0};
   int dev = 0;
   cudaGetDevice(&dev);
   if (dev >= 8 || !configured[dev]) {
-    cudaError_t e = cudaFuncSetAttribute(job_kernel<K, MINB, FULL, SQ>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    cudaError_t e = cudaFuncSetAttribute(job_kernel<K, MINB, FULL, SQ>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kJobDynSmem));
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(job_kernel<K, MINB, FULL, SQ>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     if (e != cudaSuccess) return e;
@@ -566,6 +652,16 @@ cudaError_t launch_km(const Launch &L, uint64_t *x, int64_t stride_limbs, const 
   const int64_t per_rep = int64_t(L.njobs) << L.lc;
   if (per_rep * reps > int64_t(0x7fffffff)) return cudaErrorInvalidConfiguration;
   cfg.gridDim = dim3(unsigned(per_rep * reps));
+  if (fa.njobs > 0) {
+    // persistent: as many CTAs as the SMs hold at once, at most one per job
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, job_kernel<K, MINB, FULL, SQ>,
+                                                                 L.nwarps * 32, smem);
+    if (e != cudaSuccess) return e;
+    int sms = 0;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    cfg.gridDim = dim3(unsigned(std::max(1, std::min(fa.njobs, std::max(1, per_sm) * sms))));
+  }
   cfg.blockDim = dim3(unsigned(L.nwarps * 32));
   cfg.dynamicSmemBytes = smem;
   cfg.stream = s;
@@ -577,7 +673,7 @@ cudaError_t launch_km(const Launch &L, uint64_t *x, int64_t stride_limbs, const 
   cfg.attrs = attr;
   cfg.numAttrs = L.lc > 0 ? 1 : 0;
   return cudaLaunchKernelEx(&cfg, job_kernel<K, MINB, FULL, SQ>, x, stride_limbs, (const JobDesc *)L.d_jobs, int(r.N), L.ls,
-                            L.lc, mask, prog_cap, L.d_segs, L.nsegs, rep_cells, reps > 1 ? int(per_rep) : 0);
+                            L.lc, mask, prog_cap, L.d_segs, L.nsegs, rep_cells, reps > 1 ? int(per_rep) : 0, fa);
 }
 
 // SMs of the current device (cached per host thread and device)
@@ -594,7 +690,7 @@ int sm_count() {
 
 template <int K, bool SQ>
 cudaError_t launch_k(const Launch &L, uint64_t *x, int64_t stride_limbs, const Ring &r, cudaStream_t s,
-                     int64_t reps, int64_t rep_cells) {
+                     int64_t reps, int64_t rep_cells, const FusedArgs &fa) {
   const int nslots = 1 << (L.ls - L.lc);
   // cells, their metadata and the load's mbarrier (4 words)
   const size_t base_words = ((size_t(nslots) * size_t(r.pitch) + size_t(nslots) + 1) & ~size_t(1)) + 4;
@@ -604,51 +700,77 @@ cudaError_t launch_k(const Launch &L, uint64_t *x, int64_t stride_limbs, const R
   // CTAs to fill the SMs three deep (a smaller launch gives each CTA all of its warps instead);
   // the program is staged in shared memory only if it fits beside the cells (else its ops are
   // read through the read-only path)
-  const size_t small_words = (75 * 1024) / 4;
+  const size_t small_words = (75 * 1024 - 64) / 4;  // three per SM beside the static claim word
   const int64_t ctas = (int64_t(L.njobs) << L.lc) * reps;
   if (base_words <= small_words && (L.nwarps <= 8 || ctas >= 3 * int64_t(sm_count()))) {
     Launch L8 = L;
     L8.nwarps = std::min(L.nwarps, 8);
     const int cap = size_t(L.prog_words) <= small_words - base_words ? L.prog_words : 0;
     const size_t smem = (base_words + size_t(cap)) * 4;
-    return r.G == 32 ? launch_km<K, 3, true, SQ>(L8, x, stride_limbs, r, s, smem, cap, mask, reps, rep_cells)
-                     : launch_km<K, 3, false, SQ>(L8, x, stride_limbs, r, s, smem, cap, mask, reps, rep_cells);
+    return r.G == 32 ? launch_km<K, 3, true, SQ>(L8, x, stride_limbs, r, s, smem, cap, mask, reps, rep_cells, fa)
+                     : launch_km<K, 3, false, SQ>(L8, x, stride_limbs, r, s, smem, cap, mask, reps, rep_cells, fa);
   }
-  const size_t max_words = (227 * 1024) / 4;
+  const size_t max_words = kJobDynSmem / 4;
   const int prog_cap = int(std::min<size_t>(size_t(L.prog_words), max_words > base_words ? max_words - base_words : 0));
   const size_t smem = (base_words + size_t(prog_cap)) * 4;
-  return r.G == 32 ? launch_km<K, 1, true, SQ>(L, x, stride_limbs, r, s, smem, prog_cap, mask, reps, rep_cells)
-                   : launch_km<K, 1, false, SQ>(L, x, stride_limbs, r, s, smem, prog_cap, mask, reps, rep_cells);
+  return r.G == 32 ? launch_km<K, 1, true, SQ>(L, x, stride_limbs, r, s, smem, prog_cap, mask, reps, rep_cells, fa)
+                   : launch_km<K, 1, false, SQ>(L, x, stride_limbs, r, s, smem, prog_cap, mask, reps, rep_cells, fa);
 }
 
 }  // namespace
 
+// launch one Launch (or the fused form when fa.njobs > 0) for the ring's words per lane
+static cudaError_t launch_any(const TransformPlan &p, const Launch &L, uint64_t *x, int64_t stride_limbs,
+                              cudaStream_t s, int64_t reps, int64_t rep_cells, const FusedArgs &fa) {
+  const bool sq = p.mode == RING_SQRT2;
+#define TFT_LK(KK) (sq ? launch_k<KK, true>(L, x, stride_limbs, p.ring, s, reps, rep_cells, fa) \
+                       : launch_k<KK, false>(L, x, stride_limbs, p.ring, s, reps, rep_cells, fa))
+  switch (p.ring.K) {
+    case 1: return TFT_LK(1);
+    case 2: return TFT_LK(2);
+    case 4: return TFT_LK(4);
+    case 8: return TFT_LK(8);
+    case 16: return TFT_LK(16);
+    case 32: return TFT_LK(32);
+    default: return cudaErrorInvalidValue;
+  }
+#undef TFT_LK
+}
+
 cudaError_t run_transform_reps(const TransformPlan &p, uint64_t *x, int64_t stride_limbs, int64_t reps,
                                int64_t rep_cells, cudaStream_t s) {
   if (reps < 1) return cudaSuccess;
-  const bool sq = p.mode == RING_SQRT2;
+  const FusedArgs none = {nullptr, nullptr, nullptr, nullptr, 0};
   for (const Launch &L : p.launches) {
     if (reps > 1 && L.nsegs != 0) return cudaErrorInvalidValue;
-    cudaError_t e;
-#define TFT_LK(KK) (sq ? launch_k<KK, true>(L, x, stride_limbs, p.ring, s, reps, rep_cells) \
-                       : launch_k<KK, false>(L, x, stride_limbs, p.ring, s, reps, rep_cells))
-    switch (p.ring.K) {
-      case 1: e = TFT_LK(1); break;
-      case 2: e = TFT_LK(2); break;
-      case 4: e = TFT_LK(4); break;
-      case 8: e = TFT_LK(8); break;
-      case 16: e = TFT_LK(16); break;
-      case 32: e = TFT_LK(32); break;
-      default: return cudaErrorInvalidValue;
-    }
-#undef TFT_LK
+    const cudaError_t e = launch_any(p, L, x, stride_limbs, s, reps, rep_cells, none);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
 }
 
-cudaError_t run_transform(const TransformPlan &p, uint64_t *x, int64_t stride_limbs, cudaStream_t s) {
-  return run_transform_reps(p, x, stride_limbs, 1, 0, s);
+cudaError_t run_transform(const TransformPlan &p, uint64_t *x, int64_t stride_limbs, cudaStream_t s,
+                          bool allow_fused) {
+  if (!allow_fused || p.f_njobs == 0) return run_transform_reps(p, x, stride_limbs, 1, 0, s);
+  // claim counter and done flags, zeroed, for this call only (two calls of one plan may overlap
+  // on different streams)
+  uint32_t *sync = nullptr;
+  const size_t bytes = (size_t(p.f_njobs) + 1) * sizeof(uint32_t);
+  cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&sync), bytes, s);
+  if (e != cudaSuccess) return e;
+  e = cudaMemsetAsync(sync, 0, bytes, s);
+  if (e == cudaSuccess) {
+    Launch L;
+    L.ls = p.f_ls;
+    L.lc = 0;
+    L.nwarps = p.f_nwarps;
+    L.njobs = p.f_njobs;
+    L.prog_words = p.f_prog_words;
+    const FusedArgs fa = {p.f_jobs, p.f_dep_off, p.f_deps, sync, p.f_njobs};
+    e = launch_any(p, L, x, stride_limbs, s, 1, 0, fa);
+  }
+  const cudaError_t ef = cudaFreeAsync(sync, s);
+  return e != cudaSuccess ? e : ef;
 }
 
 namespace {

@@ -171,10 +171,10 @@ extern "C" int zx_mul_noalloc(const zx_poly *f, const zx_poly *g, zx_poly *h, vo
   cudaError_t ce;
   if ((ce = launch_pack(f->data, f->len, f->limbs, f->is_signed, F, info.stride_limbs, r, s)) != cudaSuccess ||
       (ce = launch_pack(g->data, g->len, g->limbs, g->is_signed, G, info.stride_limbs, r, s)) != cudaSuccess ||
-      (ce = run_transform(*pf, F, info.stride_limbs, s)) != cudaSuccess ||
-      (ce = run_transform(*pg, G, info.stride_limbs, s)) != cudaSuccess ||
+      (ce = run_transform(*pf, F, info.stride_limbs, s, false)) != cudaSuccess ||
+      (ce = run_transform(*pg, G, info.stride_limbs, s, false)) != cudaSuccess ||
       (ce = launch_pointwise(F, G, info.n_fft, info.stride_limbs, r, s)) != cudaSuccess ||
-      (ce = run_transform(*pi, F, info.stride_limbs, s)) != cudaSuccess ||
+      (ce = run_transform(*pi, F, info.stride_limbs, s, false)) != cudaSuccess ||
       (ce = launch_lift(F, info.n, info.stride_limbs, sgn, h->data, h->limbs, r, s)) != cudaSuccess)
     return na_fail(ZX_ECUDA, std::string("zx_mul_noalloc launch: ") + cudaGetErrorString(ce));
   return ZX_OK;
