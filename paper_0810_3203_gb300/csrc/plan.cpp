@@ -524,7 +524,7 @@ void build_host_schedule(int kind, int l, int64_t z, int64_t n, int f, int64_t N
     if (i == 0 || !same_launch(P.jobs[i], P.jobs[i - 1])) nl++;
     single = single && P.jobs[i].lc == 0;
   }
-  if (!P.cfg.fused || !single || nl < 2) return;
+  if (!P.cfg.fused || !single || nl < 2 || P.ring.K < 4) return;
   std::vector<JobDesc> flat;
   std::vector<int> passes;
   for (const JobRec &j : P.jobs) {
@@ -603,7 +603,8 @@ const TransformPlan *get_transform_plan(int kind, int l, int64_t z, int64_t n, i
   }
   (void)stride_limbs;
   // the fused form: every job single-CTA, more than one launch, not replicated
-  bool fusable = cfg.fused && !replicated && plan->launches.size() > 1;
+  // (the persistent kernel is built for rings of four or more words per lane)
+  bool fusable = cfg.fused && !replicated && plan->launches.size() > 1 && P.ring.K >= 4;
   for (const Launch &L : plan->launches) fusable = fusable && L.lc == 0;
   FusedSchedule fs;
   std::vector<int> passes;

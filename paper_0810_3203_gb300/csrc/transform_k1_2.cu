@@ -1,0 +1,9 @@
+// Per-pass launches of the sub-transform kernel (job_kernel.cuh) for rings of one or two 32-bit words per lane (N <= 2048).
+#include "job_kernel.cuh"
+
+namespace tftgpu {
+
+TFT_DEFINE_PLAIN(1)
+TFT_DEFINE_PLAIN(2)
+
+}  // namespace tftgpu

@@ -1,0 +1,9 @@
+// Per-pass launches of the sub-transform kernel (job_kernel.cuh) for rings of four or eight words per lane (N = 4096 .. 8192).
+#include "job_kernel.cuh"
+
+namespace tftgpu {
+
+TFT_DEFINE_PLAIN(4)
+TFT_DEFINE_PLAIN(8)
+
+}  // namespace tftgpu

@@ -1,749 +1,46 @@
-// The sub-transform kernel. One job (a TFT or ITFT of Ls = 2^ls cells) runs on a cluster of
-// C = 2^lc CTAs; every CTA keeps Ls / C cells in shared memory for the whole job, so global
-// memory is read once and written once per cell. Inside a CTA the base-case butterflies of
-// Algorithm 1 or 2 run as a program of dependency levels (program.cpp), one warp per
-// butterfly. When C > 1 the cells move between the column layout and the row layout of the
-// job's own C x (Ls / C) split through distributed shared memory (STAGE_XCHG / STAGE_SWAP).
-#include <cooperative_groups.h>
-#include <cuda_runtime.h>
-
-#include <algorithm>
-#include <cstdio>
-
-#include "common.h"
-#include "host.h"
-#include "ring_warp.cuh"
-
-namespace cg = cooperative_groups;
+// Per-pass launches of the sub-transform kernel (job_kernel.cuh) and the host entry points that
+// enqueue a plan: one launch per pass, or the plan's persistent form (transform_fused.cu).
+#include "job_kernel.cuh"
 
 namespace tftgpu {
 
-struct KGeo {
-  Geo g;
-  int ord;        // order of omega: 2N (omega = 2) or 4N (omega = sqrt2); exponents are mod ord
-  uint32_t mask;  // ord - 1 when ord is a power of two, else 0
-};
-
-__device__ __forceinline__ int rot_amount(RotA a, int e, const KGeo &k) {
-  if (k.mask) return int((uint32_t(a.mul) * uint32_t(e) + uint32_t(a.add)) & k.mask);
-  long long v = ((long long)a.mul * e + a.add) % k.ord;
-  return int(v);
-}
-
-// raw form of x omega^E (E in [0, ord)): a rotation for omega = 2, a power of sqrt2 otherwise
-template <int K, bool SQ>
-__device__ __forceinline__ int read_omega_pow(uint32_t (&r)[K], const uint32_t *cell, int zflag, int E,
-                                              const Geo &g) {
-  if (SQ) return smem_read_pow<K>(r, cell, zflag, E, g);
-  return smem_read_abs<K>(r, cell, zflag, E, g);
-}
-
-template <int K>
-__device__ __forceinline__ void write_cell(uint32_t *cell, uint32_t *meta, const uint32_t (&r)[K],
-                                           int zflag, int tag, const Geo &g) {
-  if (!zflag) smem_store_plain<K>(cell, r, g);
-  if (g.lane == 0) *meta = (uint32_t(tag) << 1) | uint32_t(zflag);
-}
-
-// chunk of this lane inside a shared-memory cell
-template <int K>
-__device__ __forceinline__ uint32_t *lane_chunk(uint32_t *cell, const Geo &g) {
-  return cell + phys<K>(K * (g.lane < g.G ? g.lane : 0));
-}
-
-template <int K>
-__device__ __forceinline__ void set_meta(uint32_t *meta, int zflag, int tag, const Geo &g) {
-  if (g.lane == 0) *meta = (uint32_t(tag) << 1) | uint32_t(zflag);
-}
-
-// S - 1 = rawA + rawB + 1 - (za + zb) 2^N, written to `dst` in storage form; rawA is the
-// unrotated cell `acell` (all ones when za), rawB is in registers
-template <int K>
-__device__ __forceinline__ int sum_to(uint32_t *dst, const uint32_t *acell, const uint32_t (&B)[K], int za,
-                                      int zb, const Geo &g) {
-  uint32_t *ch = lane_chunk<K>(dst, g);
-  uint32_t c = 0;
-  if (g.lane < g.G) c = chain_stream<K, false>(ch, lane_chunk<K>(const_cast<uint32_t *>(acell), g), za != 0, B,
-                                                 g.lane == 0 ? 1u : 0u);
-  return settle_smem<K>(ch, int(c), za + zb, g);
-}
-
-// D - 1 = rawA - rawB - 1 - (za - zb) 2^N, written to `dst` in storage form
-template <int K>
-__device__ __forceinline__ int diff_to(uint32_t *dst, const uint32_t *acell, const uint32_t (&B)[K], int za,
-                                       int zb, const Geo &g) {
-  uint32_t *ch = lane_chunk<K>(dst, g);
-  uint32_t bo = 0;
-  if (g.lane < g.G) bo = chain_stream<K, true>(ch, lane_chunk<K>(const_cast<uint32_t *>(acell), g), za != 0, B,
-                                                 g.lane == 0 ? 1u : 0u);
-  return settle_smem<K>(ch, -int(bo), za - zb, g);
-}
-
-// S (to dS) and D (to dD) of one butterfly from one pass over the cell `acell` (K >= 4); dS or
-// dD may be acell. Sets the zero flags of both outputs.
-template <int K>
-__device__ __forceinline__ void sum_diff_to(uint32_t *dS, uint32_t *dD, const uint32_t *acell, const uint32_t (&B)[K],
-                                            int za, int zb, const Geo &g, int &zs, int &zd) {
-  uint32_t *chS = lane_chunk<K>(dS, g), *chD = lane_chunk<K>(dD, g);
-  uint32_t c = 0, bo = 0;
-  if (g.lane < g.G)
-    bf_stream<K>(chS, chD, lane_chunk<K>(const_cast<uint32_t *>(acell), g), za != 0, B, g.lane == 0 ? 1u : 0u, c, bo);
-  zd = settle_smem<K>(chD, -int(bo), za - zb, g);
-  zs = settle_smem<K>(chS, int(c), za + zb, g);
-}
-
-template <int K, bool SQ>
-__device__ __forceinline__ void exec_op(const OpDesc &op, uint32_t *cells, uint32_t *meta, int P, int e,
-                                        const KGeo &kg) {
-  const Geo &g = kg.g;
-  uint32_t *ci = cells + op.i * P, *cj = cells + op.j * P;
-  const uint32_t mi = meta[op.i], mj = meta[op.j];
-  if (op.kind == OP_TAG) {
-    const int ti = int(mi >> 1);
-    if (op.flags & OPF_COPY) {
-      uint32_t v[K];
-      smem_load_plain<K>(v, ci, g);
-      int tj = ti + rot_amount(op.rb, e, kg);
-      if (tj >= kg.ord) tj -= kg.ord;
-      __syncwarp();
-      write_cell<K>(cj, meta + op.j, v, int(mi & 1u), tj, g);
-    }
-    int tn = ti + rot_amount(op.ra, e, kg);
-    if (tn >= kg.ord) tn -= kg.ord;
-    __syncwarp();
-    if (g.lane == 0) meta[op.i] = (uint32_t(tn) << 1) | (mi & 1u);
-    return;
-  }
-  // x_i 2^Ei (+-) x_j 2^Ej = 2^Ei (x_i (+-) x_j 2^(Ej - Ei)): read x_i without rotation and
-  // x_j with the difference, and give the outputs Ei more pending rotation
-  int Ei = int(mi >> 1) + rot_amount(op.ra, e, kg);
-  if (Ei >= kg.ord) Ei -= kg.ord;
-  int Ej = int(mj >> 1) + rot_amount(op.rb, e, kg);
-  if (Ej >= kg.ord) Ej -= kg.ord;
-  int Er = Ej - Ei;
-  if (Er < 0) Er += kg.ord;
-  const int za = int(mi & 1u), zb = int(mj & 1u);
-  uint32_t B[K];
-  read_omega_pow<K, SQ>(B, cj, zb, Er, g);
-  __syncwarp();
-  auto pend = [&](RotA p) {
-    int t = rot_amount(p, e, kg) + Ei;
-    return t >= kg.ord ? t - kg.ord : t;
-  };
-  if (op.kind == OP_BF) {
-    // x_i is streamed from its cell: the difference goes first when it is written to cell j,
-    // so that x_i is still intact for the sum, which then rewrites cell i word by word
-    const bool wantS = op.flags & OPF_S, wantD = op.flags & OPF_D;
-    const bool toj = op.flags & OPF_S_TO_J, toi = op.flags & OPF_D_TO_I;
-    if constexpr (K >= 4) {
-      if (wantS && wantD && toj == toi) {
-        // S and D from one pass over x_i (S to i and D to j, or S to j and D to i)
-        int zs, zd;
-        sum_diff_to<K>(toj ? cj : ci, toi ? ci : cj, ci, B, za, zb, g, zs, zd);
-        set_meta<K>(meta + (toi ? op.i : op.j), zd, pend(op.p1), g);
-        set_meta<K>(meta + (toj ? op.j : op.i), zs, pend(op.p0), g);
-        return;
-      }
-    }
-    if (wantD && !toi) {
-      const int zd = diff_to<K>(cj, ci, B, za, zb, g);
-      set_meta<K>(meta + op.j, zd, pend(op.p1), g);
-    }
-    if (wantS) {
-      const int zs = sum_to<K>(toj ? cj : ci, ci, B, za, zb, g);
-      set_meta<K>(meta + (toj ? op.j : op.i), zs, pend(op.p0), g);
-    }
-    if (wantD && toi) {
-      const int zd = diff_to<K>(ci, ci, B, za, zb, g);
-      set_meta<K>(meta + op.i, zd, pend(op.p1), g);
-    }
-    return;
-  }
-  // OP_CROSS: D = x_i - x_j -> x_j (pending p1); then x_i <- x_i + D
-  const int zd = diff_to<K>(cj, ci, B, za, zb, g);
-  set_meta<K>(meta + op.j, zd, pend(op.p1), g);
-  __syncwarp();
-  if (zd)
-    set_ones<K>(B, g);
-  else
-    smem_load_plain<K>(B, cj, g);
-  const int zs = sum_to<K>(ci, ci, B, za, zd, g);
-  set_meta<K>(meta + op.i, zs, Ei, g);
-}
-
-// Copy the N-bit part of a cell between global memory (16-byte aligned when vec16) and a
-// shared-memory cell, with consecutive lanes on consecutive addresses (coalesced); returns the
-// top limb on loads. Cell loads go through L2 only (ld.global.cg): in a persistent launch
-// another CTA of the same kernel may have written the cell. Groups of 4 words never straddle a 32-word row, so for K >= 4 both sides
-// move 16-byte vectors.
-template <int K>
-__device__ __forceinline__ uint64_t gmem_to_smem_cell(uint32_t *scell, const uint64_t *gcell, bool vec16,
-                                                      const Geo &g) {
-  const uint32_t *w32 = reinterpret_cast<const uint32_t *>(gcell);
-  if (vec16 && (g.NW & 3) == 0) {
-    const uint4 *src = reinterpret_cast<const uint4 *>(w32);
-    for (int q = g.lane; q < g.NW / 4; q += 32) {
-      const uint4 v = __ldcg(src + q);
-      const int pw = phys<K>(4 * q);
-      if constexpr (K >= 4) {
-        *reinterpret_cast<uint4 *>(scell + pw) = v;
-      } else {
-        scell[pw] = v.x;
-        scell[pw + 1] = v.y;
-        scell[pw + 2] = v.z;
-        scell[pw + 3] = v.w;
-      }
-    }
-  } else {
-    const uint2 *src = reinterpret_cast<const uint2 *>(w32);
-    for (int q = g.lane; q < g.NW / 2; q += 32) {
-      const uint2 v = __ldcg(src + q);
-      const int pw = phys<K>(2 * q);
-      scell[pw] = v.x;
-      scell[pw + 1] = v.y;
-    }
-  }
-  return __ldcg(gcell + g.NW / 2);
-}
-
-template <int K>
-__device__ __forceinline__ void smem_to_gmem_cell(uint64_t *gcell, const uint32_t *scell, uint64_t top, bool vec16,
-                                                  const Geo &g) {
-  uint32_t *w32 = reinterpret_cast<uint32_t *>(gcell);
-  if (vec16 && (g.NW & 3) == 0) {
-    uint4 *dst = reinterpret_cast<uint4 *>(w32);
-    for (int q = g.lane; q < g.NW / 4; q += 32) {
-      const int pw = phys<K>(4 * q);
-      if constexpr (K >= 4)
-        dst[q] = *reinterpret_cast<const uint4 *>(scell + pw);
-      else
-        dst[q] = make_uint4(scell[pw], scell[pw + 1], scell[pw + 2], scell[pw + 3]);
-    }
-  } else {
-    uint2 *dst = reinterpret_cast<uint2 *>(w32);
-    for (int q = g.lane; q < g.NW / 2; q += 32) {
-      const int pw = phys<K>(2 * q);
-      dst[q] = make_uint2(scell[pw], scell[pw + 1]);
-    }
-  }
-  if (g.lane == 0) gcell[g.NW / 2] = top;
-}
-
-// Set (never cleared on the device) when a bounded wait of a kernel gave up; read and cleared
-// by the host through read_wait_status.
+// The status word of the bounded waits on each device (see job_kernel.cuh).
 __device__ uint32_t g_wait_fault;
 
-// Wait limit of a bulk-copy completion (the copies of one job land within microseconds).
-constexpr uint64_t kBulkWaitNs = 1000000000ull;
-
-__device__ __forceinline__ uint64_t globaltimer_ns() {
-  uint64_t t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-
-// Wait for the given phase parity of an mbarrier; false when limit_ns passed first.
-__device__ __forceinline__ bool mbar_wait_bounded(uint32_t mb, uint32_t parity, uint64_t limit_ns) {
-  const uint64_t t0 = globaltimer_ns();
-  for (;;) {
-    uint32_t done;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(done)
-        : "r"(mb), "r"(parity)
-        : "memory");
-    if (done) return true;
-    if (globaltimer_ns() - t0 > limit_ns) return false;
-  }
-}
-
-// Bulk (TMA) load of the N-bit parts of a job's first nl cells, one 128-byte row per lane and
-// cell, into the padded shared-memory rows; completion is counted on the mbarrier mb (one
-// arrival, by thread 0, announcing all the bytes). Needs 16-byte aligned cells and NW a
-// multiple of 32 (rows of 32 words); cell s is read from gcell(s).
-template <typename CellAddr>
-__device__ __forceinline__ void bulk_load_cells(uint32_t *cells, int P, int nl, uint32_t mb, int NW, int warp, int nw,
-                                                int lane, CellAddr gcell) {
-  if (threadIdx.x == 0) {
-    const uint32_t bytes = uint32_t(nl) * uint32_t(NW) * 4u;
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mb), "r"(bytes) : "memory");
-  }
-  const int rows = NW >> 5;
-  if (lane >= rows) return;
-  for (int s = warp; s < nl; s += nw) {
-    const uint32_t dst = uint32_t(__cvta_generic_to_shared(cells + s * P + 36 * lane));
-    uint64_t src;
-    asm volatile("cvta.to.global.u64 %0, %1;" : "=l"(src) : "l"(reinterpret_cast<const char *>(gcell(s)) + 128 * lane));
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], 128, [%2];" ::"r"(dst),
-                 "l"(src), "r"(mb)
-                 : "memory");
-  }
-}
-
-// cell index of the job held at `slot` of CTA `rank` in the given layout
-__device__ __forceinline__ int job_cell(uint32_t layout, int rank, int slot, int C, int L2, int b) {
-  if (C == 1) return slot;
-  if (layout == LAYOUT_ROW) return rank * L2 + slot;
-  return (slot / b) * L2 + rank * b + (slot % b);
-}
-
-// one op descriptor from shared memory (8-byte aligned) or, when the program did not fit
-// there, from global memory through the read-only path
-__device__ __forceinline__ OpDesc load_op_shared(const uint32_t *p) {
-  const uint2 *q = reinterpret_cast<const uint2 *>(p);
-  uint2 w0 = q[0], w1 = q[1], w2 = q[2], w3 = q[3], w4 = q[4];
-  OpDesc o;
-  uint2 *d = reinterpret_cast<uint2 *>(&o);
-  d[0] = w0;
-  d[1] = w1;
-  d[2] = w2;
-  d[3] = w3;
-  d[4] = w4;
-  return o;
-}
-
-__device__ __forceinline__ OpDesc load_op_global(const uint32_t *p) {
-  const uint2 *q = reinterpret_cast<const uint2 *>(p);
-  OpDesc o;
-  uint2 *d = reinterpret_cast<uint2 *>(&o);
-#pragma unroll
-  for (int k = 0; k < 5; k++) d[k] = __ldg(q + k);
-  return o;
-}
-
-template <int K, bool STAGED, bool SQ>
-__device__ __forceinline__ void run_program(const uint32_t *pg, uint32_t *cells, uint32_t *meta, int P, int e,
-                                            const KGeo &kg, int warp, int nw) {
-  const int nlev = int(pg[0]);
-  const uint32_t *ops = pg + prog_ops_offset_words(nlev);
-  const int ow = int(sizeof(OpDesc) / 4);
-  for (int v = 0; v < nlev; v++) {
-    const int a = int(pg[2 + v]), b = int(pg[3 + v]);
-    for (int o = a + warp; o < b; o += nw) {
-      const OpDesc op = STAGED ? load_op_shared(ops + o * ow) : load_op_global(ops + o * ow);
-      exec_op<K, SQ>(op, cells, meta, P, e, kg);
-    }
-    __syncthreads();
-  }
-}
-
-// Cells of CTA `rank` that arrive from partner `y` in a layout exchange: local slots
-// [y b, y b + b) take the partner's slots [rank b, rank b + b). A cell is one block of P words
-// in either CTA, copied whole with 16-byte loads from the partner's shared memory (consecutive
-// lanes on consecutive addresses). The (partner distance r, block offset i) items go in chunks
-// of one cell per warp: read into registers, cluster barrier, write locally. Pairs are
-// symmetric (y = rank ^ r), so when a chunk's barrier is passed every block it touches has
-// been read by its partner, and later chunks touch other blocks. All CTAs run the same number
-// of chunks and barriers.
-constexpr int kXchgVec = 9;  // 16-byte vectors per lane: cells of up to 9 * 32 * 4 = 1152 words
-
-template <int K>
-__device__ __forceinline__ void exchange(uint32_t *cells, uint32_t *meta, int P, int rank, int C, int b, int only,
-                                         const Geo &g, int warp, int nw) {
-  cg::cluster_group cluster = cg::this_cluster();
-  const int items = (C - 1) * b;
-  const int nvec = P / 4;
-  cluster.sync();  // partners finished writing the cells we are about to read
-  for (int base = 0; base < items; base += nw) {
-    const int t = base + warp;
-    const int r = 1 + t / b, i = t % b, y = rank ^ r;
-    const bool mine = t < items && y < C && (only < 0 || rank == only || y == only);
-    uint4 buf[kXchgVec];
-    uint32_t m = 0;
-    if (mine) {
-      const uint4 *src = reinterpret_cast<const uint4 *>(cluster.map_shared_rank(cells, y) + (rank * b + i) * P);
-#pragma unroll
-      for (int k = 0; k < kXchgVec; k++) {
-        const int v = g.lane + 32 * k;
-        if (v < nvec) buf[k] = src[v];
-      }
-      m = *(cluster.map_shared_rank(meta, y) + (rank * b + i));
-    }
-    cluster.sync();
-    if (mine) {
-      uint4 *dst = reinterpret_cast<uint4 *>(cells + (y * b + i) * P);
-#pragma unroll
-      for (int k = 0; k < kXchgVec; k++) {
-        const int v = g.lane + 32 * k;
-        if (v < nvec) dst[v] = buf[k];
-      }
-      if (g.lane == 0) meta[y * b + i] = m;
-    }
-  }
-  __syncthreads();
-}
-
-// Arguments of a persistent launch that runs every job of a plan (njobs > 0): the CTAs claim
-// jobs in the order of `jobs` from a counter, wait until the jobs listed for a claimed job have
-// finished (their done flags), run it and set its own flag. Every job a job waits for comes
-// earlier in the claim order and was claimed by a CTA that is running, so the earliest
-// unfinished job can always proceed; the waits are bounded all the same.
-struct FusedArgs {
-  const JobDesc *jobs;     // in claim order
-  const int32_t *dep_off;  // job k waits for deps[dep_off[k] .. dep_off[k + 1])
-  const int32_t *deps;     // claim positions, all below k
-  uint32_t *sync;          // [0] claim counter, [1 + k] done flag of job k (zero on entry)
-  int njobs;               // 0: one job per CTA (plain or merged launch)
-};
-
-// Wait limit of a dependency (a job finishes within microseconds; a whole plan within
-// milliseconds).
-constexpr uint64_t kDepWaitNs = 2000000000ull;
-
-// Dynamic shared memory a job kernel may take: the 227 KB of a block less the kernel's static
-// claim word (with room for its alignment).
-constexpr size_t kJobDynSmem = 227 * 1024 - 64;
-
-__device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t *p) {
-  uint32_t v;
-  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-
-__device__ __forceinline__ void st_release_u32(uint32_t *p, uint32_t v) {
-  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-
-// One warp waits until every job job k depends on has set its done flag, polling with a short
-// sleep. It gives up when the limit passes (bit 2 of the status word) or when an earlier wait
-// has given up, so that no CTA waits twice on a plan that already failed.
-__device__ __forceinline__ void wait_deps(const FusedArgs &fa, int k, int lane) {
-  const int a = fa.dep_off[k], b = fa.dep_off[k + 1];
-  const uint64_t t0 = globaltimer_ns();
-  for (int base = a; base < b; base += 32) {
-    const int d = base + lane < b ? fa.deps[base + lane] : -1;
-    for (;;) {
-      const uint32_t done = d >= 0 ? ld_acquire_u32(fa.sync + 1 + d) : 1u;
-      if (__all_sync(TFT_FULL, done != 0)) break;
-      if (*reinterpret_cast<volatile uint32_t *>(&g_wait_fault) & 2u) return;
-      if (globaltimer_ns() - t0 > kDepWaitNs) {
-        if (lane == 0) atomicOr(&g_wait_fault, 2u);
-        return;
-      }
-      __nanosleep(256);
-    }
-  }
-}
-
-// One job (see the file comment): load its cells into shared memory, run the stages of its
-// image, store. Returns false when its bulk load did not land in time (the status word of the
-// device is set; its outputs are then unspecified).
-template <int K, bool SQ>
-__device__ __forceinline__ bool run_job(const JobDesc &jd, uint64_t *__restrict__ x, int64_t stride_limbs, int ls,
-                                        int lc, const KGeo &kg, int prog_cap) {
-  extern __shared__ uint32_t smem[];
-  const int C = 1 << lc;
-  const int rank = int(blockIdx.x) & (C - 1);
-  const Geo &g = kg.g;
-  const int nslots = 1 << (job_ls(jd.pad, ls) - lc);
-  const int L2 = nslots, b = nslots / C;
-  const int P = cell_pitch_words(g.NW);
-  uint32_t *cells = smem;
-  uint32_t *meta = smem + nslots * P;
-  // after the cells and their metadata: the load's mbarrier (8-byte aligned, 4 words), then
-  // the program staging area
-  uint32_t *mbar = smem + ((nslots * P + nslots + 1) & ~1);
-  uint32_t *pstage = mbar + 4;
-  const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  const uint32_t *img = jd.image;
-  const int nstages = int(img[0]);
-  const uint32_t load_layout = img[2], store_layout = img[3];
-
-  // slots whose cells are not inputs read as the implicit zeros
-  for (int s = threadIdx.x; s < nslots; s += blockDim.x)
-    if (job_cell(load_layout, rank, s, C, L2, b) >= jd.nload) meta[s] = 1u;
-
-  // load into shared memory, then the storage form m = x - 1
-  const bool vec16 = ((reinterpret_cast<uintptr_t>(x) & 15) == 0) && ((stride_limbs & 1) == 0);
-  if (K >= 4 && vec16 && C == 1 && (g.NW & 31) == 0) {
-    // single-CTA job (slot s holds cell s): bulk copies of whole rows, then each cell's top limb
-    const int nl = jd.nload < nslots ? jd.nload : nslots;
-    const uint32_t mb = uint32_t(__cvta_generic_to_shared(mbar));
-    if (threadIdx.x == 0) {
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb) : "memory");
-      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    }
-    __syncthreads();
-    const uint64_t *x0 = x + jd.cell0 * stride_limbs;
-    const int64_t cstep = jd.mstride * stride_limbs;
-    bulk_load_cells(cells, P, nl, mb, g.NW, warp, nw, g.lane,
-                    [&](int s) { return x0 + int64_t(s) * cstep; });
-    const bool landed = mbar_wait_bounded(mb, 0, kBulkWaitNs);
-    if (__syncthreads_or(!landed)) {
-      // the copies did not all land in time: wait once more for those in flight, report, stop
-      if (!landed) mbar_wait_bounded(mb, 0, kBulkWaitNs);
-      __syncthreads();
-      if (threadIdx.x == 0) atomicOr(&g_wait_fault, 1u);
-      return false;
-    }
-    for (int s = warp; s < nl; s += nw) {
-      const uint64_t T = __ldcg(x0 + int64_t(s) * cstep + g.NW / 2);
-      if (T & kRawTopMark) {
-        // written by an earlier pass in internal form: the words are m, the top limb the metadata
-        if (g.lane == 0) meta[s] = uint32_t(T);
-      } else {
-        const int z = settle_smem<K>(lane_chunk<K>(cells + s * P, g), 0, -1 - int(T & 1u), g);
-        set_meta<K>(meta + s, z, 0, g);
-      }
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(mb) : "memory");
-  } else {
-    // coalesced plain loads
-    for (int s = warp; s < nslots; s += nw) {
-      const int m = job_cell(load_layout, rank, s, C, L2, b);
-      if (m >= jd.nload) continue;
-      const uint64_t *gc = x + (jd.cell0 + int64_t(m) * jd.mstride) * stride_limbs;
-      const uint64_t T = gmem_to_smem_cell<K>(cells + s * P, gc, vec16, g);
-      if (T & kRawTopMark) {
-        // written by an earlier pass in internal form: the words are m, the top limb the metadata
-        if (g.lane == 0) meta[s] = uint32_t(T);
-      } else {
-        __syncwarp();
-        const int z = settle_smem<K>(lane_chunk<K>(cells + s * P, g), 0, -1 - int(T & 1u), g);
-        set_meta<K>(meta + s, z, 0, g);
-      }
-    }
-  }
-  __syncthreads();
-
-  for (int st = 0; st < nstages; st++) {
-    const uint32_t *ent = img + job_header_words() + st * job_stage_words(C);
-    const uint32_t type = ent[0];
-    if (type == STAGE_PROG) {
-      const uint32_t off = ent[2 + rank];
-      if (off) {
-        // copy this CTA's program into shared memory when it fits (ops are then read from there)
-        const uint32_t *pg = img + off;
-        const int words = prog_ops_offset_words(int(pg[0])) + int(pg[1]) * int(sizeof(OpDesc) / 4);
-        if (words <= prog_cap) {
-          const uint2 *src = reinterpret_cast<const uint2 *>(pg);
-          uint2 *dst = reinterpret_cast<uint2 *>(pstage);
-          for (int w = threadIdx.x; w < (words + 1) / 2; w += blockDim.x) dst[w] = __ldg(src + w);
-          __syncthreads();
-          run_program<K, true, SQ>(pstage, cells, meta, P, jd.e, kg, warp, nw);
-        } else {
-          run_program<K, false, SQ>(pg, cells, meta, P, jd.e, kg, warp, nw);
-        }
-      }
-    } else {
-      exchange<K>(cells, meta, P, rank, C, b, type == STAGE_SWAP ? int(ent[1]) : -1, g, warp, nw);
-    }
-  }
-
-  // store: x = rotc(m, t) + 1, with the final scaling where requested; or, when a later pass
-  // stores these cells again, m as it is with the rotation and zero flag in the top limb
-  const bool raw = (jd.pad & JOB_RAW_STORE) != 0;
-  for (int s = warp; s < nslots; s += nw) {
-    const int m = job_cell(store_layout, rank, s, C, L2, b);
-    if (m >= jd.nstore) continue;
-    uint32_t r[K];
-    int E = int(meta[s] >> 1) + (m < jd.nscale ? jd.escale : 0);
-    if (E >= kg.ord) E -= kg.ord;
-    uint64_t *gc = x + (jd.cell0 + int64_t(m) * jd.mstride) * stride_limbs;
-    if (raw) {
-      smem_to_gmem_cell<K>(gc, cells + s * P, kRawTopMark | (uint64_t(E) << 1) | (meta[s] & 1u), vec16, g);
-      continue;
-    }
-    const int z = read_omega_pow<K, SQ>(r, cells + s * P, int(meta[s] & 1u), E, g);
-    uint32_t top = 0;
-    if (z) {
-#pragma unroll
-      for (int q = 0; q < K; q++) r[q] = 0u;
-    } else {
-      top = add_small<K>(r, 1u, g);
-    }
-    // through the cell's own slot (no longer needed) so the global writes are coalesced
-    __syncwarp();
-    smem_store_plain<K>(cells + s * P, r, g);
-    __syncwarp();
-    smem_to_gmem_cell<K>(gc, cells + s * P, top, vec16, g);
-  }
-  return true;
-}
-
-// MINB = 3: jobs of at most 8 warps and 75 KB of shared memory, three CTAs per SM (registers
-// capped at 85 per thread); MINB = 1: up to 16 warps, one CTA per SM. FULL: all 32 lanes hold
-// words (NW = 32 K), which lets the compiler drop the idle-lane cases.
-template <int K, int MINB, bool FULL, bool SQ>
-__global__ void __launch_bounds__(MINB == 3 ? 256 : 512, MINB) job_kernel(uint64_t *__restrict__ x, int64_t stride_limbs,
-                                                  const JobDesc *__restrict__ jobs, int N, int ls, int lc,
-                                                  uint32_t mask, int prog_cap,
-                                                  const Segment *__restrict__ segs, int nsegs, int64_t rep_cells,
-                                                  int rep_ctas, FusedArgs fa) {
-  KGeo kg;
-  // a FULL ring has N = 1024 K: its geometry is compile-time
-  if (FULL) N = 1024 * K;
-  kg.g.N = N;
-  kg.g.NW = N / 32;
-  kg.g.G = FULL ? 32 : kg.g.NW / K;
-  kg.g.lane = threadIdx.x & 31;
-  kg.g.twoN = 2 * N;
-  kg.ord = SQ ? 4 * N : 2 * N;
-  kg.mask = FULL ? uint32_t(kg.ord - 1) : mask;
-  __shared__ int s_claim;
-  const bool fused = fa.njobs > 0;
-  for (;;) {
-    JobDesc jd;
-    int k = 0;
-    if (fused) {
-      __syncthreads();  // the previous job is done with shared memory and with s_claim
-      if (threadIdx.x == 0) s_claim = int(atomicAdd(fa.sync, 1u));
-      __syncthreads();
-      k = s_claim;
-      if (k >= fa.njobs) return;
-      if (threadIdx.x < 32) wait_deps(fa, k, kg.g.lane);
-      __syncthreads();
-      // the cells written by the jobs waited for are read by bulk copies (async proxy) below
-      asm volatile("fence.proxy.async.global;" ::: "memory");
-      jd = fa.jobs[k];
-      lc = 0;
-    } else if (nsegs == 0) {
-      // replicated launch: rep_ctas CTAs per replica, replica r shifted by r * rep_cells cells
-      int b = int(blockIdx.x);
-      int64_t shift = 0;
-      if (rep_ctas > 0) {
-        const int r = b / rep_ctas;
-        b -= r * rep_ctas;
-        shift = int64_t(r) * rep_cells;
-      }
-      jd = jobs[b >> lc];
-      jd.cell0 += shift;
-    } else {
-      // merged launch: the last segment that starts at or before this CTA (segments hold whole
-      // clusters, so the CTAs of one cluster agree)
-      int lo = 0, hi = nsegs - 1;
-      while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (segs[mid].first_cta <= int(blockIdx.x)) lo = mid;
-        else hi = mid - 1;
-      }
-      const Segment sg = segs[lo];
-      jd = sg.jobs[(int(blockIdx.x) - sg.first_cta) >> lc];
-      jd.cell0 += sg.cell_off;
-    }
-    run_job<K, SQ>(jd, x, stride_limbs, ls, lc, kg, prog_cap);
-    if (!fused) return;
-    __syncthreads();  // every store of the job has been issued
-    if (threadIdx.x == 0) {
-      __threadfence();
-      st_release_u32(fa.sync + 1 + k, 1u);
-    }
-  }
-}
-
-namespace {
-
-template <int K, int MINB, bool FULL, bool SQ>
-cudaError_t launch_km(const Launch &L, uint64_t *x, int64_t stride_limbs, const Ring &r, cudaStream_t s,
-                      size_t smem, int prog_cap, uint32_t mask, int64_t reps, int64_t rep_cells, const FusedArgs &fa) {
-  static thread_local int configured[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+// Its device address on the current device (looked up once per device and host thread).
+static uint32_t *fault_word() {
+  static thread_local uint32_t *addr[8] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   int dev = 0;
-  cudaGetDevice(&dev);
-  if (dev >= 8 || !configured[dev]) {
-    cudaError_t e = cudaFuncSetAttribute(job_kernel<K, MINB, FULL, SQ>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kJobDynSmem));
-    if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(job_kernel<K, MINB, FULL, SQ>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-    if (e != cudaSuccess) return e;
-    if (dev < 8) configured[dev] = 1;
-  }
-  cudaLaunchConfig_t cfg = {};
-  const int64_t per_rep = int64_t(L.njobs) << L.lc;
-  if (per_rep * reps > int64_t(0x7fffffff)) return cudaErrorInvalidConfiguration;
-  cfg.gridDim = dim3(unsigned(per_rep * reps));
-  if (fa.njobs > 0) {
-    // persistent: as many CTAs as the SMs hold at once, at most one per job
-    int per_sm = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, job_kernel<K, MINB, FULL, SQ>,
-                                                                 L.nwarps * 32, smem);
-    if (e != cudaSuccess) return e;
-    int sms = 0;
-    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-    cfg.gridDim = dim3(unsigned(std::max(1, std::min(fa.njobs, std::max(1, per_sm) * sms))));
-  }
-  cfg.blockDim = dim3(unsigned(L.nwarps * 32));
-  cfg.dynamicSmemBytes = smem;
-  cfg.stream = s;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = 1u << L.lc;
-  attr[0].val.clusterDim.y = 1;
-  attr[0].val.clusterDim.z = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = L.lc > 0 ? 1 : 0;
-  return cudaLaunchKernelEx(&cfg, job_kernel<K, MINB, FULL, SQ>, x, stride_limbs, (const JobDesc *)L.d_jobs, int(r.N), L.ls,
-                            L.lc, mask, prog_cap, L.d_segs, L.nsegs, rep_cells, reps > 1 ? int(per_rep) : 0, fa);
+  if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
+  if (dev < 8 && addr[dev]) return addr[dev];
+  void *p = nullptr;
+  if (cudaGetSymbolAddress(&p, g_wait_fault) != cudaSuccess) return nullptr;
+  if (dev < 8) addr[dev] = static_cast<uint32_t *>(p);
+  return static_cast<uint32_t *>(p);
 }
 
-// SMs of the current device (cached per host thread and device)
-int sm_count() {
-  static thread_local int dev_cached = -1, count = 0;
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess) return 152;
-  if (dev != dev_cached) {
-    if (cudaDeviceGetAttribute(&count, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || count <= 0) count = 152;
-    dev_cached = dev;
-  }
-  return count;
-}
-
-template <int K, bool SQ>
-cudaError_t launch_k(const Launch &L, uint64_t *x, int64_t stride_limbs, const Ring &r, cudaStream_t s,
-                     int64_t reps, int64_t rep_cells, const FusedArgs &fa) {
-  const int nslots = 1 << (L.ls - L.lc);
-  // cells, their metadata and the load's mbarrier (4 words)
-  const size_t base_words = ((size_t(nslots) * size_t(r.pitch) + size_t(nslots) + 1) & ~size_t(1)) + 4;
-  const uint32_t ord = uint32_t((SQ ? 4 : 2) * r.N);
-  const uint32_t mask = (ord & (ord - 1)) == 0 ? ord - 1 : 0u;
-  // three CTAs per SM of at most 8 warps when the cells fit in 75 KB and the launch has the
-  // CTAs to fill the SMs three deep (a smaller launch gives each CTA all of its warps instead);
-  // the program is staged in shared memory only if it fits beside the cells (else its ops are
-  // read through the read-only path)
-  const size_t small_words = (75 * 1024 - 64) / 4;  // three per SM beside the static claim word
-  const int64_t ctas = (int64_t(L.njobs) << L.lc) * reps;
-  if (base_words <= small_words && (L.nwarps <= 8 || ctas >= 3 * int64_t(sm_count()))) {
-    Launch L8 = L;
-    L8.nwarps = std::min(L.nwarps, 8);
-    const int cap = size_t(L.prog_words) <= small_words - base_words ? L.prog_words : 0;
-    const size_t smem = (base_words + size_t(cap)) * 4;
-    return r.G == 32 ? launch_km<K, 3, true, SQ>(L8, x, stride_limbs, r, s, smem, cap, mask, reps, rep_cells, fa)
-                     : launch_km<K, 3, false, SQ>(L8, x, stride_limbs, r, s, smem, cap, mask, reps, rep_cells, fa);
-  }
-  const size_t max_words = kJobDynSmem / 4;
-  const int prog_cap = int(std::min<size_t>(size_t(L.prog_words), max_words > base_words ? max_words - base_words : 0));
-  const size_t smem = (base_words + size_t(prog_cap)) * 4;
-  return r.G == 32 ? launch_km<K, 1, true, SQ>(L, x, stride_limbs, r, s, smem, prog_cap, mask, reps, rep_cells, fa)
-                   : launch_km<K, 1, false, SQ>(L, x, stride_limbs, r, s, smem, prog_cap, mask, reps, rep_cells, fa);
-}
-
-}  // namespace
-
-// launch one Launch (or the fused form when fa.njobs > 0) for the ring's words per lane
+// one launch of a plan's per-pass form, by the ring's words per lane
 static cudaError_t launch_any(const TransformPlan &p, const Launch &L, uint64_t *x, int64_t stride_limbs,
-                              cudaStream_t s, int64_t reps, int64_t rep_cells, const FusedArgs &fa) {
-  const bool sq = p.mode == RING_SQRT2;
-#define TFT_LK(KK) (sq ? launch_k<KK, true>(L, x, stride_limbs, p.ring, s, reps, rep_cells, fa) \
-                       : launch_k<KK, false>(L, x, stride_limbs, p.ring, s, reps, rep_cells, fa))
+                              cudaStream_t s, int64_t reps, int64_t rep_cells, uint32_t *fault) {
   switch (p.ring.K) {
-    case 1: return TFT_LK(1);
-    case 2: return TFT_LK(2);
-    case 4: return TFT_LK(4);
-    case 8: return TFT_LK(8);
-    case 16: return TFT_LK(16);
-    case 32: return TFT_LK(32);
+    case 1: return launch_plain_k1(p, L, x, stride_limbs, s, reps, rep_cells, fault);
+    case 2: return launch_plain_k2(p, L, x, stride_limbs, s, reps, rep_cells, fault);
+    case 4: return launch_plain_k4(p, L, x, stride_limbs, s, reps, rep_cells, fault);
+    case 8: return launch_plain_k8(p, L, x, stride_limbs, s, reps, rep_cells, fault);
+    case 16: return launch_plain_k16(p, L, x, stride_limbs, s, reps, rep_cells, fault);
+    case 32: return launch_plain_k32(p, L, x, stride_limbs, s, reps, rep_cells, fault);
     default: return cudaErrorInvalidValue;
   }
-#undef TFT_LK
 }
 
 cudaError_t run_transform_reps(const TransformPlan &p, uint64_t *x, int64_t stride_limbs, int64_t reps,
                                int64_t rep_cells, cudaStream_t s) {
   if (reps < 1) return cudaSuccess;
-  const FusedArgs none = {nullptr, nullptr, nullptr, nullptr, 0};
+  uint32_t *fault = fault_word();
+  if (!fault) return cudaErrorInvalidSymbol;
   for (const Launch &L : p.launches) {
     if (reps > 1 && L.nsegs != 0) return cudaErrorInvalidValue;
-    const cudaError_t e = launch_any(p, L, x, stride_limbs, s, reps, rep_cells, none);
+    const cudaError_t e = launch_any(p, L, x, stride_limbs, s, reps, rep_cells, fault);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
@@ -751,7 +48,9 @@ cudaError_t run_transform_reps(const TransformPlan &p, uint64_t *x, int64_t stri
 
 cudaError_t run_transform(const TransformPlan &p, uint64_t *x, int64_t stride_limbs, cudaStream_t s,
                           bool allow_fused) {
-  if (!allow_fused || p.f_njobs == 0) return run_transform_reps(p, x, stride_limbs, 1, 0, s);
+  if (!allow_fused || p.f_njobs == 0 || p.ring.K < 4) return run_transform_reps(p, x, stride_limbs, 1, 0, s);
+  uint32_t *fault = fault_word();
+  if (!fault) return cudaErrorInvalidSymbol;
   // claim counter and done flags, zeroed, for this call only (two calls of one plan may overlap
   // on different streams)
   uint32_t *sync = nullptr;
@@ -760,14 +59,9 @@ cudaError_t run_transform(const TransformPlan &p, uint64_t *x, int64_t stride_li
   if (e != cudaSuccess) return e;
   e = cudaMemsetAsync(sync, 0, bytes, s);
   if (e == cudaSuccess) {
-    Launch L;
-    L.ls = p.f_ls;
-    L.lc = 0;
-    L.nwarps = p.f_nwarps;
-    L.njobs = p.f_njobs;
-    L.prog_words = p.f_prog_words;
     const FusedArgs fa = {p.f_jobs, p.f_dep_off, p.f_deps, sync, p.f_njobs};
-    e = launch_any(p, L, x, stride_limbs, s, 1, 0, fa);
+    e = p.ring.K == 32 ? launch_fused_k32(p, x, stride_limbs, s, fa, fault)
+                       : launch_fused_small(p, x, stride_limbs, s, fa, fault);
   }
   const cudaError_t ef = cudaFreeAsync(sync, s);
   return e != cudaSuccess ? e : ef;

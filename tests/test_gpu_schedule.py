@@ -13,7 +13,7 @@ pytestmark = pytest.mark.gpu
 
 torch = pytest.importorskip("torch")
 
-RINGS = (1024, 4096, 32768)
+RINGS = (4096, 8192, 32768)
 
 
 @pytest.fixture(scope="module")
@@ -76,7 +76,7 @@ def test_benchmark_itft_on_the_bulk_layout(tg, orc):
     assert tg.wait_status() == tg.ZX_OK
 
 
-@pytest.mark.parametrize("N,l", [(1024, 10), (1024, 11), (4096, 12), (4096, 13)])
+@pytest.mark.parametrize("N,l", [(4096, 10), (4096, 11), (4096, 12), (8192, 13)])
 def test_smaller_rings(tg, orc, N, l):
     rng = random.Random(N + l)
     W = N // 64 + 1

@@ -24,7 +24,7 @@ def tg():
     m.load(build_if_missing=False)
     # the persistent form is a configuration choice (zx_tune compares it): pin it on the rings
     # used here, restore the defaults afterwards
-    rings = (1024, 2048, 32768)
+    rings = (4096, 8192, 32768)
     before = {N: m.config_get(N) for N in rings}
     for N in rings:
         m.config_set(N, dict(before[N], fused=1))
@@ -98,17 +98,19 @@ def replay(plan, sched, jobs, N, vals, L, order_seed, mode=0):
     return x
 
 
-# (kind, l, z, n, f, e, N, scale): plans of two or more passes of single-CTA jobs
+# (kind, l, z, n, f, e, N, scale): plans of two or more passes of single-CTA jobs (the persistent
+# form exists for rings of four or more 32-bit words per lane, N >= 4096)
 CASES = [
-    (0, 10, 1024, 1024, 0, 17, 1024, 0),
-    (1, 10, 1024, 1000, 1, 17, 1024, 0),
-    (0, 11, 1500, 1999, 0, 3, 1024, 0),
-    (1, 11, 1999, 1500, 1, 3, 1024, 1),
-    (1, 11, 1025, 1025, 0, 0, 1024, 1),
-    (0, 12, 2049, 2049, 0, 1, 2048, 0),
-    (1, 12, 3001, 2999, 1, 5, 2048, 1),
-    (0, 9, 300, 300, 0, 0, 1024, 0),
-    (1, 9, 300, 300, 0, 0, 1024, 1),
+    (0, 10, 1024, 1024, 0, 17, 4096, 0),
+    (1, 10, 1024, 1000, 1, 17, 4096, 0),
+    (0, 11, 1500, 1999, 0, 3, 4096, 0),
+    (1, 11, 1999, 1500, 1, 3, 4096, 1),
+    (1, 11, 1025, 1025, 0, 0, 4096, 1),
+    (0, 12, 2049, 2049, 0, 1, 4096, 0),
+    (1, 12, 3001, 2999, 1, 5, 4096, 1),
+    (0, 9, 300, 300, 0, 0, 4096, 0),
+    (1, 9, 300, 300, 0, 0, 4096, 1),
+    (0, 13, 5000, 6001, 0, 7, 8192, 0),
 ]
 
 
@@ -162,10 +164,12 @@ def test_the_schedule_interleaves_the_passes(tg):
     assert first_pass2 < 1000 < last_pass1, (first_pass2, last_pass1)
 
 
-def test_cluster_and_single_launch_plans_have_no_persistent_form(tg):
-    # one launch (a transform that one job holds) and plans with cluster jobs keep their launches
-    assert tg.transform_schedule(0, 6, 40, 37, 256) == []
-    N = 2048
+def test_cluster_small_ring_and_single_launch_plans_have_no_persistent_form(tg):
+    # one launch (a transform that one job holds), rings of fewer than four words per lane, and
+    # plans with cluster jobs keep their launches
+    assert tg.transform_schedule(0, 6, 40, 37, 4096) == []
+    assert tg.transform_schedule(0, 11, 2048, 2048, 1024) == []
+    N = 4096
     before = tg.config_get(N)
     tg.config_set(N, dict(ls_max=3, ls_c=3, max_warps=8, split=0, fused=1))
     try:
