@@ -12,8 +12,9 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libtftgpu.so")
-SOURCES = ["api.cu", "transform_kernel.cu", "transform_k1_2.cu", "transform_k4_8.cu", "transform_k16.cu",
-           "transform_k32.cu", "transform_fused.cu", "transform_fused_k32.cu", "zx_kernels.cu", "zx_noalloc.cu", "zx_batch.cu", "zx_server.cu", "sn_kernel.cu", "rec_pointwise.cu", "plan.cpp", "program.cpp"]
+SOURCES = ["api.cu", "transform_kernel.cu", "transform_small.cu", "transform_k4_8.cu", "transform_k16.cu",
+           "transform_k16_sq.cu", "transform_k32.cu", "transform_k32_sq.cu", "transform_fused.cu",
+           "transform_fused_k32.cu", "zx_kernels.cu", "zx_noalloc.cu", "zx_batch.cu", "zx_server.cu", "sn_kernel.cu", "rec_pointwise.cu", "plan.cpp", "program.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

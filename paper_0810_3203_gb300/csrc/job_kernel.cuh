@@ -249,7 +249,9 @@ __device__ __forceinline__ uint64_t globaltimer_ns() {
 }
 
 // Wait for the given phase parity of an mbarrier; false when limit_ns passed first.
-__device__ __forceinline__ bool mbar_wait_bounded(uint32_t mb, uint32_t parity, uint64_t limit_ns) {
+// sleep_ns > 0: the thread sleeps that long between polls (for a single waiting thread).
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t mb, uint32_t parity, uint64_t limit_ns,
+                                                  unsigned sleep_ns = 0) {
   const uint64_t t0 = globaltimer_ns();
   for (;;) {
     uint32_t done;
@@ -260,6 +262,7 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint32_t mb, uint32_t parity, 
         : "memory");
     if (done) return true;
     if (globaltimer_ns() - t0 > limit_ns) return false;
+    if (sleep_ns) __nanosleep(sleep_ns);
   }
 }
 
@@ -448,10 +451,14 @@ TFT_HD inline int job_stage_word(int nslots, int pitch) { return job_tops_word(n
 // One job (see the file comment): load its cells into shared memory, run the stages of its
 // image, store. Returns false when its bulk load did not land in time (the status word of the
 // device is set; its outputs are then unspecified).
-template <int K, bool SQ>
+//
+// SINGLE: the launch runs single-CTA jobs only (lc = 0 at compile time), which drops the cluster
+// exchange and its registers from the kernel.
+template <int K, bool SQ, bool SINGLE>
 __device__ __forceinline__ bool run_job(const JobDesc &jd, uint64_t *__restrict__ x, int64_t stride_limbs, int ls,
                                         int lc, const KGeo &kg, int prog_cap, uint32_t *fault) {
   extern __shared__ uint32_t smem[];
+  if (SINGLE) lc = 0;
   const int C = 1 << lc;
   const int rank = int(blockIdx.x) & (C - 1);
   const Geo &g = kg.g;
@@ -506,10 +513,15 @@ __device__ __forceinline__ bool run_job(const JobDesc &jd, uint64_t *__restrict_
     bulk_load_cells(cells, tops, P, nl, mb, g.NW, warp, nw, g.lane,
                     [&](int s) { return x0 + int64_t(s) * cstep; });
     stage_first_program();
-    const bool landed = mbar_wait_bounded(mb, 0, kBulkWaitNs);
+    // One thread waits for the copies, sleeping between polls; the others wait at the barrier,
+    // which takes no issue slots from the butterflies of the other CTAs on the SM. The barrier
+    // orders every thread's reads of the copied cells after that thread's observation of the
+    // completed phase.
+    bool landed = true;
+    if (threadIdx.x == 0) landed = mbar_wait_bounded(mb, 0, kBulkWaitNs, 64);
     if (__syncthreads_or(!landed)) {
       // the copies did not all land in time: wait once more for those in flight, report, stop
-      if (!landed) mbar_wait_bounded(mb, 0, kBulkWaitNs);
+      if (!landed) mbar_wait_bounded(mb, 0, kBulkWaitNs, 64);
       __syncthreads();
       if (threadIdx.x == 0) atomicOr(fault, 1u);
       return false;
@@ -568,7 +580,7 @@ __device__ __forceinline__ bool run_job(const JobDesc &jd, uint64_t *__restrict_
         }
       }
     } else {
-      exchange<K>(cells, meta, P, rank, C, b, type == STAGE_SWAP ? int(ent[1]) : -1, g, warp, nw);
+      if (!SINGLE) exchange<K>(cells, meta, P, rank, C, b, type == STAGE_SWAP ? int(ent[1]) : -1, g, warp, nw);
     }
   }
 
@@ -622,7 +634,7 @@ __device__ __forceinline__ KGeo make_kgeo(int N, uint32_t mask) {
 }
 
 // One job per CTA (per cluster): a plain launch, a replicated one or a merged one.
-template <int K, int MINB, bool FULL, bool SQ>
+template <int K, int MINB, bool FULL, bool SQ, bool SINGLE>
 __global__ void __launch_bounds__(MINB == 3 ? 256 : 512, MINB) job_kernel(uint64_t *__restrict__ x, int64_t stride_limbs,
                                                   const JobDesc *__restrict__ jobs, int N, int ls, int lc,
                                                   uint32_t mask, int prog_cap,
@@ -654,7 +666,7 @@ __global__ void __launch_bounds__(MINB == 3 ? 256 : 512, MINB) job_kernel(uint64
     jd = sg.jobs[(int(blockIdx.x) - sg.first_cta) >> lc];
     jd.cell0 += sg.cell_off;
   }
-  run_job<K, SQ>(jd, x, stride_limbs, ls, lc, kg, prog_cap, fault);
+  run_job<K, SQ, SINGLE>(jd, x, stride_limbs, ls, lc, kg, prog_cap, fault);
 }
 
 // The persistent form (FusedArgs): single-CTA jobs claimed in order until none is left.
@@ -663,9 +675,19 @@ __global__ void __launch_bounds__(MINB == 3 ? 256 : 512, MINB) job_kernel_fused(
                                                   int64_t stride_limbs, int N, int ls, uint32_t mask, int prog_cap,
                                                   FusedArgs fa, uint32_t *fault) {
   const KGeo kg = make_kgeo<K, FULL, SQ>(N, mask);
+  // A job's done flag is set at the top of the CTA's next iteration by one thread of warp 1 (all
+  // of the job's stores were issued before the barrier there), while thread 0 claims the next job
+  // and warp 0 checks its dependencies: the fence overlaps the claim and the check, and no flag
+  // waits on a check.
   __shared__ int s_claim;
+  const int publisher = blockDim.x > 32 ? 32 : 0;
+  uint32_t *done = nullptr;  // done flag of this CTA's previous job, not yet set
   for (;;) {
     __syncthreads();  // the previous job is done with shared memory and with s_claim
+    if (int(threadIdx.x) == publisher && done) {
+      __threadfence();
+      st_release_u32(done, 1u);
+    }
     if (threadIdx.x == 0) s_claim = int(atomicAdd(fa.sync, 1u));
     __syncthreads();
     const int k = s_claim;
@@ -674,12 +696,8 @@ __global__ void __launch_bounds__(MINB == 3 ? 256 : 512, MINB) job_kernel_fused(
     __syncthreads();
     // the cells written by the jobs waited for are read by bulk copies (async proxy) below
     asm volatile("fence.proxy.async.global;" ::: "memory");
-    run_job<K, SQ>(fa.jobs[k], x, stride_limbs, ls, 0, kg, prog_cap, fault);
-    __syncthreads();  // every store of the job has been issued
-    if (threadIdx.x == 0) {
-      __threadfence();
-      st_release_u32(fa.sync + 1 + k, 1u);
-    }
+    run_job<K, SQ, true>(fa.jobs[k], x, stride_limbs, ls, 0, kg, prog_cap, fault);
+    done = fa.sync + 1 + k;
   }
 }
 
@@ -697,9 +715,13 @@ static cudaError_t launch_km(const Launch &L, uint64_t *x, int64_t stride_limbs,
       e = cudaFuncSetAttribute(job_kernel_fused<K, MINB, FULL, SQ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                int(kJobDynSmem));
     } else {
-      e = cudaFuncSetAttribute(job_kernel<K, MINB, FULL, SQ>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kJobDynSmem));
+      e = cudaFuncSetAttribute(job_kernel<K, MINB, FULL, SQ, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               int(kJobDynSmem));
       if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(job_kernel<K, MINB, FULL, SQ>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        e = cudaFuncSetAttribute(job_kernel<K, MINB, FULL, SQ, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 int(kJobDynSmem));
+      if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(job_kernel<K, MINB, FULL, SQ, false>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     }
     if (e != cudaSuccess) return e;
     if (dev < 8) configured[dev] = 1;
@@ -733,7 +755,11 @@ static cudaError_t launch_km(const Launch &L, uint64_t *x, int64_t stride_limbs,
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = L.lc > 0 ? 1 : 0;
-  return cudaLaunchKernelEx(&cfg, job_kernel<K, MINB, FULL, SQ>, x, stride_limbs, (const JobDesc *)L.d_jobs, int(r.N), L.ls,
+  if (L.lc == 0)
+    return cudaLaunchKernelEx(&cfg, job_kernel<K, MINB, FULL, SQ, true>, x, stride_limbs, (const JobDesc *)L.d_jobs,
+                              int(r.N), L.ls, 0, mask, prog_cap, L.d_segs, L.nsegs, rep_cells,
+                              reps > 1 ? int(per_rep) : 0, fault);
+  return cudaLaunchKernelEx(&cfg, job_kernel<K, MINB, FULL, SQ, false>, x, stride_limbs, (const JobDesc *)L.d_jobs, int(r.N), L.ls,
                             L.lc, mask, prog_cap, L.d_segs, L.nsegs, rep_cells, reps > 1 ? int(per_rep) : 0, fault);
 }
 
@@ -783,15 +809,21 @@ static cudaError_t launch_k(const Launch &L, uint64_t *x, int64_t stride_limbs, 
 // parallel (transform_k*.cu: one launch of a plan's per-pass form; transform_fused*.cu: the
 // persistent form, rings of four or more words per lane). fault is the device address of the
 // status word of the bounded waits.
-#define TFT_DECLARE_LAUNCHES(KK)                                                                          \
-  cudaError_t launch_plain_k##KK(const TransformPlan &p, const Launch &L, uint64_t *x, int64_t stride_limbs, \
-                                 cudaStream_t s, int64_t reps, int64_t rep_cells, uint32_t *fault)
-TFT_DECLARE_LAUNCHES(1);
-TFT_DECLARE_LAUNCHES(2);
-TFT_DECLARE_LAUNCHES(4);
-TFT_DECLARE_LAUNCHES(8);
-TFT_DECLARE_LAUNCHES(16);
-TFT_DECLARE_LAUNCHES(32);
+#define TFT_DECLARE_LAUNCHES(KK, SQN)                                                                       \
+  cudaError_t launch_plain_k##KK##_##SQN(const TransformPlan &p, const Launch &L, uint64_t *x, int64_t stride_limbs, \
+                                        cudaStream_t s, int64_t reps, int64_t rep_cells, uint32_t *fault)
+TFT_DECLARE_LAUNCHES(1, w2);
+TFT_DECLARE_LAUNCHES(1, sq);
+TFT_DECLARE_LAUNCHES(2, w2);
+TFT_DECLARE_LAUNCHES(2, sq);
+TFT_DECLARE_LAUNCHES(4, w2);
+TFT_DECLARE_LAUNCHES(4, sq);
+TFT_DECLARE_LAUNCHES(8, w2);
+TFT_DECLARE_LAUNCHES(8, sq);
+TFT_DECLARE_LAUNCHES(16, w2);
+TFT_DECLARE_LAUNCHES(16, sq);
+TFT_DECLARE_LAUNCHES(32, w2);
+TFT_DECLARE_LAUNCHES(32, sq);
 #undef TFT_DECLARE_LAUNCHES
 cudaError_t launch_fused_small(const TransformPlan &p, uint64_t *x, int64_t stride_limbs, cudaStream_t s,
                                const FusedArgs &fa, uint32_t *fault);  // K = 4, 8, 16
@@ -799,12 +831,12 @@ cudaError_t launch_fused_k32(const TransformPlan &p, uint64_t *x, int64_t stride
                              const FusedArgs &fa, uint32_t *fault);
 
 // Definitions for the translation units above.
-#define TFT_DEFINE_PLAIN(KK)                                                                                 \
-  cudaError_t launch_plain_k##KK(const TransformPlan &p, const Launch &L, uint64_t *x, int64_t stride_limbs,    \
-                                 cudaStream_t s, int64_t reps, int64_t rep_cells, uint32_t *fault) {          \
+// SQN: w2 for omega = 2, sq for omega = sqrt2 (SQ = false / true)
+#define TFT_DEFINE_PLAIN(KK, SQN, SQB)                                                                      \
+  cudaError_t launch_plain_k##KK##_##SQN(const TransformPlan &p, const Launch &L, uint64_t *x, int64_t stride_limbs, \
+                                        cudaStream_t s, int64_t reps, int64_t rep_cells, uint32_t *fault) {  \
     const FusedArgs none = {nullptr, nullptr, nullptr, nullptr, 0};                                           \
-    return p.mode == RING_SQRT2 ? launch_k<KK, true, false>(L, x, stride_limbs, p.ring, s, reps, rep_cells, none, fault) \
-                                : launch_k<KK, false, false>(L, x, stride_limbs, p.ring, s, reps, rep_cells, none, fault); \
+    return launch_k<KK, SQB, false>(L, x, stride_limbs, p.ring, s, reps, rep_cells, none, fault);             \
   }
 
 template <int K>

@@ -3,7 +3,9 @@
 
 namespace tftgpu {
 
-TFT_DEFINE_PLAIN(4)
-TFT_DEFINE_PLAIN(8)
+TFT_DEFINE_PLAIN(4, w2, false)
+TFT_DEFINE_PLAIN(4, sq, true)
+TFT_DEFINE_PLAIN(8, w2, false)
+TFT_DEFINE_PLAIN(8, sq, true)
 
 }  // namespace tftgpu

@@ -22,15 +22,19 @@ static uint32_t *fault_word() {
 // one launch of a plan's per-pass form, by the ring's words per lane
 static cudaError_t launch_any(const TransformPlan &p, const Launch &L, uint64_t *x, int64_t stride_limbs,
                               cudaStream_t s, int64_t reps, int64_t rep_cells, uint32_t *fault) {
+  const bool sq = p.mode == RING_SQRT2;
+#define TFT_PL(KK) (sq ? launch_plain_k##KK##_sq(p, L, x, stride_limbs, s, reps, rep_cells, fault) \
+                       : launch_plain_k##KK##_w2(p, L, x, stride_limbs, s, reps, rep_cells, fault))
   switch (p.ring.K) {
-    case 1: return launch_plain_k1(p, L, x, stride_limbs, s, reps, rep_cells, fault);
-    case 2: return launch_plain_k2(p, L, x, stride_limbs, s, reps, rep_cells, fault);
-    case 4: return launch_plain_k4(p, L, x, stride_limbs, s, reps, rep_cells, fault);
-    case 8: return launch_plain_k8(p, L, x, stride_limbs, s, reps, rep_cells, fault);
-    case 16: return launch_plain_k16(p, L, x, stride_limbs, s, reps, rep_cells, fault);
-    case 32: return launch_plain_k32(p, L, x, stride_limbs, s, reps, rep_cells, fault);
+    case 1: return TFT_PL(1);
+    case 2: return TFT_PL(2);
+    case 4: return TFT_PL(4);
+    case 8: return TFT_PL(8);
+    case 16: return TFT_PL(16);
+    case 32: return TFT_PL(32);
     default: return cudaErrorInvalidValue;
   }
+#undef TFT_PL
 }
 
 cudaError_t run_transform_reps(const TransformPlan &p, uint64_t *x, int64_t stride_limbs, int64_t reps,

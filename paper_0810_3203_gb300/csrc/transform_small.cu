@@ -3,7 +3,9 @@
 
 namespace tftgpu {
 
-TFT_DEFINE_PLAIN(1)
-TFT_DEFINE_PLAIN(2)
+TFT_DEFINE_PLAIN(1, w2, false)
+TFT_DEFINE_PLAIN(1, sq, true)
+TFT_DEFINE_PLAIN(2, w2, false)
+TFT_DEFINE_PLAIN(2, sq, true)
 
 }  // namespace tftgpu
