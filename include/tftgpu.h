@@ -176,6 +176,12 @@ int zx_mul_batch(const zx_poly *fs, const zx_poly *gs, zx_poly *hs, int count, v
  *     exceed 16 MiB is rejected with ZX_EUNSUPPORTED, and ZX_ENOMEM reports a full plan region;
  *   - the first call on a device looks up that array's address (cudaGetSymbolAddress) with the
  *     device current, so make the first call on each device before any stream capture;
+ *   - the first call for each product shape (lengths, bit sizes, signedness) writes that shape's
+ *     launch plans into the array from host memory, which a stream capture cannot record for
+ *     later replays: such a call returns ZX_EINVAL while `stream` is capturing. Make one call
+ *     per shape (and one after changing the ring's launch configuration with zx_config_set or
+ *     zx_tune) before capturing; captured calls of known shapes replay correctly;
+ *   - the pointwise products use the schoolbook kernel (zx_mul's default method);
  *   - all calls share the array: calls whose GPU work overlaps (different streams or threads
  *     without ordering between them) race. Order them on one stream.
  * It calls no cudaMalloc, cudaFree or other allocating routine; the call is asynchronous.
@@ -220,7 +226,9 @@ int zx_server_destroy(zx_server *srv);
  * the split L1 = 2^floor(l/2) for cache reasons; every configuration computes the same
  * outputs). Candidates: cells per CTA of a cluster job (2^3 .. 2^6), the largest job held by one
  * CTA (the shared-memory limit, or the size at which three CTAs share an SM), warps per CTA
- * (8 or 16) and, for odd l, the top-level split floor or ceil(l/2). The round trips use
+ * (8 or 16) and, for odd l, the top-level split floor or ceil(l/2). The setting `fused` is kept as
+ * it is: single round trips cannot show its cost when transforms run on concurrent streams. The
+ * round trips use
  * omega = 2 when L | 2N, else omega = sqrt2 (L | 4N), the transforms products use. For each candidate the call
  * times `reps` TFT + ITFT round trips (Algorithm 1, then Algorithm 2 with the division by L)
  * of length n over the caller's device buffer x (L = 2^l cells of stride_limbs >= N/64 + 1
@@ -235,15 +243,19 @@ typedef struct {
     int32_t candidates; /* configurations timed */
     float best_ms;      /* round-trip time of the chosen configuration */
     float default_ms;   /* round-trip time of the default configuration */
-    int32_t fused;      /* 1: a plan whose jobs all run on single CTAs is one persistent launch
-                           (zx_transform_schedule); 0: one launch per global-memory pass */
+    int32_t fused;      /* when a plan whose jobs all run on single CTAs (rings of N = 2^k >= 4096)
+                           is one persistent launch (zx_transform_schedule) instead of one
+                           launch per global-memory pass: 0 never (the default), 1 for the TFT
+                           and the ITFT, 2 for the ITFT only. A persistent launch holds every
+                           CTA slot of the GPU until it finishes, so transforms on concurrent
+                           streams stop overlapping; it pays for a transform that runs alone */
 } zx_tune_info;
 
 int zx_tune(uint64_t *x, int l, int64_t n, int64_t N, int64_t stride_limbs, int reps, void *stream,
             zx_tune_info *out);
 
 /* The launch configuration used for ring N (ls_max, ls_c, max_warps, split, fused; the other
- * fields are zero), and pinning one, e.g. a result of zx_tune saved from an earlier process. zx_config_set
+ * fields are zero; a tuned configuration is kept as zx_tune chose it), and pinning one, e.g. a result of zx_tune saved from an earlier process. zx_config_set
  * returns ZX_EINVAL for a configuration the ring cannot run (shared memory, warps, split); with
  * cfg == NULL it restores the default. Host only. */
 int zx_config_get(int64_t N, zx_tune_info *out);

@@ -470,7 +470,9 @@ int zx_tune(uint64_t *x, int l, int64_t n, int64_t N, int64_t stride_limbs, int 
   int ls3 = 1;
   while (ls3 < 16 && (size_t(2) << ls3) * (size_t(r.pitch) + 1) * 4 <= size_t(72) * 1024) ls3++;
   std::vector<PlanConfig> cands;
-  cands.push_back(def);
+  PlanConfig def_kept = def;
+  def_kept.fused = before.fused;
+  cands.push_back(def_kept);
   for (int ls_max : {def.ls_max, ls3})
     for (int ls_c = 3; ls_c <= 6; ls_c++)
       for (int mw : {8, 16})
@@ -480,6 +482,7 @@ int zx_tune(uint64_t *x, int l, int64_t n, int64_t N, int64_t stride_limbs, int 
           c.ls_c = ls_c;
           c.max_warps = mw;
           c.split = sp;
+          c.fused = before.fused;  // kept as it is (see PlanConfig)
           if (!config_valid(r, c)) continue;
           bool dup = false;
           for (const PlanConfig &o : cands)
@@ -519,16 +522,6 @@ int zx_tune(uint64_t *x, int l, int64_t n, int64_t N, int64_t stride_limbs, int 
       chosen = c;
     }
   }
-  if (!rc) {
-    // the same configuration with the passes as one persistent launch or one launch each
-    PlanConfig other = chosen;
-    other.fused = chosen.fused ? 0 : 1;
-    float ms = 0.0f;
-    if (!(rc = time_cfg(other, &ms)) && ms < best) {
-      best = ms;
-      chosen = other;
-    }
-  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   set_plan_config(N, rc ? before : chosen);
@@ -539,7 +532,7 @@ int zx_tune(uint64_t *x, int l, int64_t n, int64_t N, int64_t stride_limbs, int 
   out->max_warps = chosen.max_warps;
   out->split = chosen.split;
   out->fused = chosen.fused;
-  out->candidates = int32_t(cands.size()) + 1;
+  out->candidates = int32_t(cands.size());
   out->best_ms = best;
   out->default_ms = def_ms;
   return ZX_OK;

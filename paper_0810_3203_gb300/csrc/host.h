@@ -47,10 +47,18 @@ Ring make_ring(int64_t N);
 // the cells per CTA of a cluster job (ls_c, both log2), the warps per CTA (8 or 16) and the
 // top-level split (0: L1 = 2^floor(l/2) as in the paper, 1: L1 = 2^ceil(l/2)). Every choice
 // computes the same outputs; they differ in speed. zx_tune measures the candidates.
-// fused: a plan whose jobs all run on single CTAs is one persistent launch that claims the jobs
-// in dependency order (FusedSchedule) instead of one launch per pass (zx_tune compares both).
+// fused: whether a plan whose jobs all run on single CTAs is one persistent launch that claims
+// the jobs in dependency order (FusedSchedule) instead of one launch per pass: 0 never (the
+// default), 1 for both transforms, 2 for the ITFT only. Measured on GB300 at l = 16, N = 32768:
+// alone, the persistent ITFT is faster from n = 40000 on (its serial last-row steps overlap with
+// the rest), the TFT slower; with several transforms on concurrent streams, persistent launches
+// hold every CTA slot until they finish and the transforms stop overlapping, so the five-stream
+// benchmark step went from 4.74 to 5.18 ms. zx_tune times single round trips and therefore leaves
+// this setting as it is; zx_config_set chooses it.
+enum { FUSED_NONE = 0, FUSED_ALL = 1, FUSED_ITFT = 2 };
+inline bool fused_for(int fused, int kind) { return fused == FUSED_ALL || (fused == FUSED_ITFT && kind == KIND_ITFT); }
 struct PlanConfig {
-  int ls_max = 0, ls_c = 0, max_warps = 16, split = 0, fused = 0;
+  int ls_max = 0, ls_c = 0, max_warps = 16, split = 0, fused = FUSED_NONE;
 };
 PlanConfig default_config(const Ring &r);
 bool config_valid(const Ring &r, const PlanConfig &c);

@@ -711,7 +711,7 @@ static cudaError_t launch_km(const Launch &L, uint64_t *x, int64_t stride_limbs,
   cudaGetDevice(&dev);
   if (dev >= 8 || !configured[dev]) {
     cudaError_t e;
-    if (FUSED) {
+    if constexpr (FUSED) {
       e = cudaFuncSetAttribute(job_kernel_fused<K, MINB, FULL, SQ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                int(kJobDynSmem));
     } else {
@@ -730,7 +730,10 @@ static cudaError_t launch_km(const Launch &L, uint64_t *x, int64_t stride_limbs,
   const int64_t per_rep = int64_t(L.njobs) << L.lc;
   if (per_rep * reps > int64_t(0x7fffffff)) return cudaErrorInvalidConfiguration;
   cfg.gridDim = dim3(unsigned(per_rep * reps));
-  if (FUSED) {
+  if constexpr (FUSED) {
+    cfg.blockDim = dim3(unsigned(L.nwarps * 32));
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
     // persistent: as many CTAs as the SMs hold at once, at most one per job
     int per_sm = 0;
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, job_kernel_fused<K, MINB, FULL, SQ>,
@@ -739,28 +742,27 @@ static cudaError_t launch_km(const Launch &L, uint64_t *x, int64_t stride_limbs,
     int sms = 0;
     if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
     cfg.gridDim = dim3(unsigned(std::max(1, std::min(fa.njobs, std::max(1, per_sm) * sms))));
+    return cudaLaunchKernelEx(&cfg, job_kernel_fused<K, MINB, FULL, SQ>, x, stride_limbs, int(r.N), L.ls, mask,
+                              prog_cap, fa, fault);
+  } else {
     cfg.blockDim = dim3(unsigned(L.nwarps * 32));
     cfg.dynamicSmemBytes = smem;
     cfg.stream = s;
-    return cudaLaunchKernelEx(&cfg, job_kernel_fused<K, MINB, FULL, SQ>, x, stride_limbs, int(r.N), L.ls, mask,
-                              prog_cap, fa, fault);
-  }
-  cfg.blockDim = dim3(unsigned(L.nwarps * 32));
-  cfg.dynamicSmemBytes = smem;
-  cfg.stream = s;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = 1u << L.lc;
-  attr[0].val.clusterDim.y = 1;
-  attr[0].val.clusterDim.z = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = L.lc > 0 ? 1 : 0;
-  if (L.lc == 0)
-    return cudaLaunchKernelEx(&cfg, job_kernel<K, MINB, FULL, SQ, true>, x, stride_limbs, (const JobDesc *)L.d_jobs,
-                              int(r.N), L.ls, 0, mask, prog_cap, L.d_segs, L.nsegs, rep_cells,
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 1u << L.lc;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = L.lc > 0 ? 1 : 0;
+    if (L.lc == 0)
+      return cudaLaunchKernelEx(&cfg, job_kernel<K, MINB, FULL, SQ, true>, x, stride_limbs, (const JobDesc *)L.d_jobs,
+                                int(r.N), L.ls, 0, mask, prog_cap, L.d_segs, L.nsegs, rep_cells,
+                                reps > 1 ? int(per_rep) : 0, fault);
+    return cudaLaunchKernelEx(&cfg, job_kernel<K, MINB, FULL, SQ, false>, x, stride_limbs, (const JobDesc *)L.d_jobs,
+                              int(r.N), L.ls, L.lc, mask, prog_cap, L.d_segs, L.nsegs, rep_cells,
                               reps > 1 ? int(per_rep) : 0, fault);
-  return cudaLaunchKernelEx(&cfg, job_kernel<K, MINB, FULL, SQ, false>, x, stride_limbs, (const JobDesc *)L.d_jobs, int(r.N), L.ls,
-                            L.lc, mask, prog_cap, L.d_segs, L.nsegs, rep_cells, reps > 1 ? int(per_rep) : 0, fault);
+  }
 }
 
 // SMs of the current device (cached per host thread and device)
@@ -794,15 +796,25 @@ static cudaError_t launch_k(const Launch &L, uint64_t *x, int64_t stride_limbs, 
     L8.nwarps = std::min(L.nwarps, 8);
     const int cap = size_t(L.prog_words) <= small_words - base_words ? L.prog_words : 0;
     const size_t smem = (base_words + size_t(cap)) * 4;
-    // (rings of four or more words per lane fill all 32 lanes: the persistent form is built FULL only)
-    if (FUSED || r.G == 32) return launch_km<K, 3, true, SQ, FUSED>(L8, x, stride_limbs, r, s, smem, cap, mask, reps, rep_cells, fa, fault);
-    return launch_km<K, 3, false, SQ, FUSED>(L8, x, stride_limbs, r, s, smem, cap, mask, reps, rep_cells, fa, fault);
+    // (the persistent form is built for rings that fill all 32 lanes only)
+    if constexpr (FUSED) {
+      if (r.G != 32) return cudaErrorInvalidValue;
+      return launch_km<K, 3, true, SQ, FUSED>(L8, x, stride_limbs, r, s, smem, cap, mask, reps, rep_cells, fa, fault);
+    } else {
+      if (r.G == 32) return launch_km<K, 3, true, SQ, FUSED>(L8, x, stride_limbs, r, s, smem, cap, mask, reps, rep_cells, fa, fault);
+      return launch_km<K, 3, false, SQ, FUSED>(L8, x, stride_limbs, r, s, smem, cap, mask, reps, rep_cells, fa, fault);
+    }
   }
   const size_t max_words = kJobDynSmem / 4;
   const int prog_cap = int(std::min<size_t>(size_t(L.prog_words), max_words > base_words ? max_words - base_words : 0));
   const size_t smem = (base_words + size_t(prog_cap)) * 4;
-  if (FUSED || r.G == 32) return launch_km<K, 1, true, SQ, FUSED>(L, x, stride_limbs, r, s, smem, prog_cap, mask, reps, rep_cells, fa, fault);
-  return launch_km<K, 1, false, SQ, FUSED>(L, x, stride_limbs, r, s, smem, prog_cap, mask, reps, rep_cells, fa, fault);
+  if constexpr (FUSED) {
+    if (r.G != 32) return cudaErrorInvalidValue;
+    return launch_km<K, 1, true, SQ, FUSED>(L, x, stride_limbs, r, s, smem, prog_cap, mask, reps, rep_cells, fa, fault);
+  } else {
+    if (r.G == 32) return launch_km<K, 1, true, SQ, FUSED>(L, x, stride_limbs, r, s, smem, prog_cap, mask, reps, rep_cells, fa, fault);
+    return launch_km<K, 1, false, SQ, FUSED>(L, x, stride_limbs, r, s, smem, prog_cap, mask, reps, rep_cells, fa, fault);
+  }
 }
 
 // Launch entry points, one translation unit per group of rings so that they compile in

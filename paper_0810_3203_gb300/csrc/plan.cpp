@@ -73,7 +73,7 @@ bool config_valid(const Ring &r, const PlanConfig &c) {
   auto fits = [&](int ls) { return ls >= 1 && ls <= 16 && size_t(1) << ls <= 65536 &&
                                    (size_t(1) << ls) * (size_t(r.pitch) + 1) * 4 <= kSmemBudget; };
   return fits(c.ls_max) && fits(c.ls_c) && c.ls_c <= c.ls_max + 1 && (c.max_warps == 8 || c.max_warps == 16) &&
-         (c.split == 0 || c.split == 1) && (c.fused == 0 || c.fused == 1);
+         (c.split == 0 || c.split == 1) && (c.fused >= FUSED_NONE && c.fused <= FUSED_ITFT);
 }
 
 namespace {
@@ -524,7 +524,7 @@ void build_host_schedule(int kind, int l, int64_t z, int64_t n, int f, int64_t N
     if (i == 0 || !same_launch(P.jobs[i], P.jobs[i - 1])) nl++;
     single = single && P.jobs[i].lc == 0;
   }
-  if (!P.cfg.fused || !single || nl < 2 || P.ring.K < 4) return;
+  if (!fused_for(P.cfg.fused, kind) || !single || nl < 2 || P.ring.K < 4 || P.ring.G != 32) return;
   std::vector<JobDesc> flat;
   std::vector<int> passes;
   for (const JobRec &j : P.jobs) {
@@ -603,8 +603,10 @@ const TransformPlan *get_transform_plan(int kind, int l, int64_t z, int64_t n, i
   }
   (void)stride_limbs;
   // the fused form: every job single-CTA, more than one launch, not replicated
-  // (the persistent kernel is built for rings of four or more words per lane)
-  bool fusable = cfg.fused && !replicated && plan->launches.size() > 1 && P.ring.K >= 4;
+  // (the persistent kernel is built for rings whose words fill all 32 lanes, four or more words
+  // per lane: N a power of two from 4096 on)
+  bool fusable = fused_for(cfg.fused, kind) && !replicated && plan->launches.size() > 1 && P.ring.K >= 4 &&
+                 P.ring.G == 32;
   for (const Launch &L : plan->launches) fusable = fusable && L.lc == 0;
   FusedSchedule fs;
   std::vector<int> passes;

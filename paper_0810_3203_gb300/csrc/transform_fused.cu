@@ -1,6 +1,7 @@
 // Persistent launches of the sub-transform kernel (job_kernel.cuh) for rings of four to sixteen
-// words per lane: one launch runs every job of a plan's fused form, claiming jobs in dependency
-// order. Rings of fewer words per lane get no fused form from the planner.
+// words per lane whose words fill all 32 lanes (N = 4096, 8192, 16384): one launch runs every job
+// of a plan's fused form, claiming jobs in dependency order. Other rings get no fused form from
+// the planner.
 #include "job_kernel.cuh"
 
 namespace tftgpu {

@@ -52,7 +52,8 @@ cudaError_t run_transform_reps(const TransformPlan &p, uint64_t *x, int64_t stri
 
 cudaError_t run_transform(const TransformPlan &p, uint64_t *x, int64_t stride_limbs, cudaStream_t s,
                           bool allow_fused) {
-  if (!allow_fused || p.f_njobs == 0 || p.ring.K < 4) return run_transform_reps(p, x, stride_limbs, 1, 0, s);
+  if (!allow_fused || p.f_njobs == 0 || p.ring.K < 4 || p.ring.G != 32)
+    return run_transform_reps(p, x, stride_limbs, 1, 0, s);
   uint32_t *fault = fault_word();
   if (!fault) return cudaErrorInvalidSymbol;
   // claim counter and done flags, zeroed, for this call only (two calls of one plan may overlap

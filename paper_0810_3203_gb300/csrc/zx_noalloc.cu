@@ -12,7 +12,10 @@
 //   the remaining 4 MiB       job lists and butterfly programs of the plans used so far
 // The first call on a device looks up the array's device address with cudaGetSymbolAddress
 // (with that device current); make that first call before any stream capture. Plans are
-// written into the array the first time a product shape is seen and kept for later calls.
+// written into the array the first time a product shape is seen (under the ring's launch
+// configuration at that time) and kept for later calls; that first call for a shape is refused
+// while the stream is capturing, since a capture cannot record the upload of host data for later
+// replays. The pointwise products use the schoolbook kernel (zx_mul's default method).
 // Nothing in the ring buffers needs to start at zero: the transforms read only cells that
 // the pack step of the same call has written. All calls share the array, so calls whose work
 // overlaps on the GPU (different streams or host threads without ordering) race.
@@ -40,10 +43,13 @@ constexpr size_t kScratchLimbs = kRingLimbs + kPlanLimbs;  // 20 MiB in total
 
 static __device__ __align__(256) uint64_t g_noalloc_scratch[kScratchLimbs];
 
+// plans of one device, keyed by the transform and the ring's launch configuration when planned
+using PlanKey = std::tuple<int, int, int64_t, int64_t, int, int64_t, int64_t, int, int, int, int, int, int>;
+
 struct NoAllocDevice {
   uint64_t *base = nullptr;  // device address of g_noalloc_scratch on this device
   size_t plan_used = 0;      // limbs of the plan region in use
-  std::map<std::tuple<int, int, int64_t, int64_t, int, int64_t, int64_t, int>, std::unique_ptr<TransformPlan>> plans;
+  std::map<PlanKey, std::unique_ptr<TransformPlan>> plans;
 };
 
 std::mutex g_mu;
@@ -80,14 +86,26 @@ uint64_t *plan_space(NoAllocDevice &st, size_t bytes) {
   return p;
 }
 
+// The plan of one transform in the plan region: found in the cache, or built and uploaded. The
+// upload copies host memory to the device, which a stream capture cannot record for later
+// replays, so a plan that is not cached yet is refused while `s` is capturing.
 int plan_in_scratch(NoAllocDevice &st, int kind, int l, int64_t z, int64_t n, int f, int64_t N, int scale,
                     int mode, cudaStream_t s, const TransformPlan **out) {
-  auto key = std::make_tuple(kind, l, z, n, f, N, int64_t(mode), scale);
+  const PlanConfig cfg = plan_config(N);
+  const PlanKey key(kind, l, z, n, f, N, int64_t(mode), scale, cfg.ls_max, cfg.ls_c, cfg.max_warps, cfg.split,
+                    cfg.fused);
   auto it = st.plans.find(key);
   if (it != st.plans.end()) {
     *out = it->second.get();
     return ZX_OK;
   }
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  cudaError_t ce = cudaStreamIsCapturing(s, &cap);
+  if (ce != cudaSuccess) return na_fail(ZX_ECUDA, std::string("cudaStreamIsCapturing: ") + cudaGetErrorString(ce));
+  if (cap != cudaStreamCaptureStatusNone)
+    return na_fail(ZX_EINVAL,
+                   "zx_mul_noalloc: the first call for a product shape (or after a change of the ring's launch "
+                   "configuration) uploads its launch plan and cannot be captured; make it once before capturing");
   HostPlan hp;
   build_host_plan(kind, l, z, n, f, N, 0, scale, &hp, mode);
   size_t need = 0;
@@ -95,11 +113,17 @@ int plan_in_scratch(NoAllocDevice &st, int kind, int l, int64_t z, int64_t n, in
   for (const auto &g : hp.groups) need += (g.jobs.size() * sizeof(JobDesc) + 15) / 16 * 16;
   if (st.plan_used * 8 + need > kPlanLimbs * 8)
     return na_fail(ZX_ENOMEM, "zx_mul_noalloc: the 4 MiB plan region is full (too many distinct product shapes)");
+  // on a failed upload the region taken so far is given back
+  const size_t used_before = st.plan_used;
+  auto upload_fail = [&](cudaError_t e) {
+    st.plan_used = used_before;
+    return na_fail(ZX_ECUDA, std::string("plan upload: ") + cudaGetErrorString(e));
+  };
   std::vector<const uint32_t *> dprog;
   for (const auto &img : hp.programs) {
     uint64_t *d = plan_space(st, img.size() * 4);
     cudaError_t e = cudaMemcpyAsync(d, img.data(), img.size() * 4, cudaMemcpyHostToDevice, s);
-    if (e != cudaSuccess) return na_fail(ZX_ECUDA, std::string("plan upload: ") + cudaGetErrorString(e));
+    if (e != cudaSuccess) return upload_fail(e);
     dprog.push_back(reinterpret_cast<const uint32_t *>(d));
   }
   std::unique_ptr<TransformPlan> plan(new TransformPlan());
@@ -110,7 +134,7 @@ int plan_in_scratch(NoAllocDevice &st, int kind, int l, int64_t z, int64_t n, in
     for (size_t i = 0; i < g.jobs.size(); i++) g.jobs[i].image = dprog[g.prog_index[i]];
     uint64_t *d = plan_space(st, g.jobs.size() * sizeof(JobDesc));
     cudaError_t e = cudaMemcpyAsync(d, g.jobs.data(), g.jobs.size() * sizeof(JobDesc), cudaMemcpyHostToDevice, s);
-    if (e != cudaSuccess) return na_fail(ZX_ECUDA, std::string("plan upload: ") + cudaGetErrorString(e));
+    if (e != cudaSuccess) return upload_fail(e);
     Launch L;
     L.ls = g.ls;
     L.lc = g.lc;

@@ -248,3 +248,44 @@ def test_large_itft_vs_oracle(tg, orc, n, f, e):
     orc.itft(ref, l, z, n, f, e, N, stride=st)
     bad = cells_eq(got, ref, n + f, st, W)
     assert bad.size == 0, f"{bad.size} cells differ, first {bad[:5]}"
+
+
+@pytest.mark.parametrize("n", [32769, 65536])
+def test_large_tft_on_the_bulk_layout(tg, orc, n):
+    """Z/(2^32768+1), l = 16, on the benchmark's 16-byte aligned 514-limb cells (bulk loads):
+    every TFT output against the oracle's Algorithm 1, at the sweep's two ends (one cell past
+    L/2, whose top column pass has n2 = 1, and the full length)."""
+    w = workloads.TRANSFORM_LARGE
+    N, l = w["N"], w["l"]
+    W = limbs(N)
+    st = W + 1
+    x = workloads.residues(w["seed"] + n, n, N, stride=st, cells=1 << l)
+    d = to_dev(x)
+    tg.tft_ex(d, l, n, n, N, 0, st)
+    got = from_dev(d)
+    ref = x.copy()
+    orc.tft(ref, l, n, n, 0, N, stride=st)
+    bad = cells_eq(got, ref, n, st, W)
+    assert bad.size == 0, f"{bad.size} cells differ, first {bad[:5]}"
+
+
+@pytest.mark.parametrize("N,l,n", [(4096, 12, 3001), (32768, 13, 7777)])
+def test_structured_residues_on_the_bulk_layout(tg, orc, N, l, n):
+    """Residues with long runs of equal bits (carries and borrows that cross many lanes) on the
+    bulk-load path (even strides, N >= 4096): TFT and exact ITFT against the oracle."""
+    W = limbs(N)
+    st = W + 1
+    x = workloads.structured_residues(5 + l, n, N, stride=st, cells=1 << l)
+    d = to_dev(x)
+    tg.tft_ex(d, l, n, n, N, 0, st)
+    got = from_dev(d)
+    ref = x.copy()
+    orc.tft(ref, l, n, n, 0, N, stride=st)
+    assert cells_eq(got, ref, n, st, W).size == 0
+    nn, f = n - 5, 1
+    d = to_dev(x)
+    tg.itft_ex(d, l, n, nn, f, N, 3, st, scale=0)
+    got = from_dev(d)
+    ref = x.copy()
+    orc.itft(ref, l, n, nn, f, 3, N, stride=st)
+    assert cells_eq(got, ref, nn + f, st, W).size == 0

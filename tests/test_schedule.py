@@ -169,6 +169,15 @@ def test_cluster_small_ring_and_single_launch_plans_have_no_persistent_form(tg):
     # plans with cluster jobs keep their launches
     assert tg.transform_schedule(0, 6, 40, 37, 4096) == []
     assert tg.transform_schedule(0, 11, 2048, 2048, 1024) == []
+    # N = 9216: sixteen words per lane in 18 of the 32 lanes; the persistent kernel is built for
+    # rings that fill every lane only
+    before = tg.config_get(9216)
+    tg.config_set(9216, dict(before, fused=1))
+    try:
+        assert len(tg.transform_jobs(1, 11, 2048, 2000, 9216)["launches"]) >= 2
+        assert tg.transform_schedule(1, 11, 2048, 2000, 9216) == []
+    finally:
+        tg.config_set(9216, before)
     N = 4096
     before = tg.config_get(N)
     tg.config_set(N, dict(ls_max=3, ls_c=3, max_warps=8, split=0, fused=1))

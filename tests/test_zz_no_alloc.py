@@ -67,3 +67,69 @@ def test_noalloc_rejects_oversized_and_host_operands(tg):
     with pytest.raises(tg.TftError) as ei:
         tg.zx_mul_noalloc(f, 4, 1, f, 4, 1, np.zeros(7, np.uint64), 2)
     assert ei.value.code == tg.ZX_EINVAL
+
+
+def test_noalloc_on_the_sqrt2_ring(tg):
+    # 1500 x 1500 coefficients of 500 bits: zx_plan picks omega = sqrt2 (a ring of N = 1024
+    # instead of 2048), whose plans and kernels this entry point shares with zx_mul
+    assert tg.zx_plan(1500, 500, 1500, 500)["sqrt2"] == 1
+    ref, out = both_products(tg, 91, 1500, 1500, 500, False)
+    assert np.array_equal(ref, out)
+
+
+def test_noalloc_allocates_nothing_on_a_side_stream(tg):
+    """A shape seen for the first time (its plans are written into the fixed array) on a stream
+    other than the default one: no device memory is taken from the driver or from PyTorch's
+    allocator, and the result equals zx_mul's. The same ring and transform length ran just
+    before, so no kernel of the call is loaded for the first time during it."""
+    lf, lg, bits = 2400, 1700, 700
+    ref0, out0 = both_products(tg, 31, lf, lg, bits, False)  # warm: kernels of this ring
+    assert np.array_equal(ref0, out0)
+    mf, F, G = operands(32, lg, lf, bits, False)  # swapped lengths: same n, new plans
+    mh = tg.zx_plan(lg, bits, lf, bits)["limbs_h"]
+    lh = lf + lg - 1
+    ref = torch.zeros(lh * mh, dtype=torch.int64, device="cuda")
+    tg.zx_mul(F, lg, mf, G, lf, mf, ref, mh, False, bits, bits)
+    out = torch.full((lh * mh,), -1, dtype=torch.int64, device="cuda")
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    torch.cuda.synchronize()
+    free0, torch0 = torch.cuda.mem_get_info()[0], torch.cuda.memory_allocated()
+    with torch.cuda.stream(side):
+        tg.zx_mul_noalloc(F, lg, mf, G, lf, mf, out, mh, False, bits, bits, stream=side)
+    side.synchronize()
+    free1, torch1 = torch.cuda.mem_get_info()[0], torch.cuda.memory_allocated()
+    assert (free1, torch1) == (free0, torch0)
+    assert torch.equal(out, ref)
+
+
+def test_noalloc_captured_call_replays(tg):
+    """A call of a shape planned before runs inside a captured CUDA graph and replays to the same
+    result; a shape planned for the first time is refused while the stream is capturing."""
+    lf, lg, bits = 1200, 1100, 450
+    mf, F, G = operands(41, lf, lg, bits, False)
+    mh = tg.zx_plan(lf, bits, lg, bits)["limbs_h"]
+    lh = lf + lg - 1
+    ref = torch.zeros(lh * mh, dtype=torch.int64, device="cuda")
+    tg.zx_mul(F, lf, mf, G, lg, mf, ref, mh, False, bits, bits)
+    out = torch.zeros(lh * mh, dtype=torch.int64, device="cuda")
+    tg.zx_mul_noalloc(F, lf, mf, G, lg, mf, out, mh, False, bits, bits)  # plans this shape
+    torch.cuda.synchronize()
+    assert torch.equal(out, ref)
+    side = torch.cuda.Stream()
+    graph = torch.cuda.CUDAGraph()
+    out.fill_(-1)
+    torch.cuda.synchronize()
+    refused = None
+    with torch.cuda.graph(graph, stream=side):
+        tg.zx_mul_noalloc(F, lf, mf, G, lg, mf, out, mh, False, bits, bits, stream=side)
+        try:  # a shape not planned yet
+            tg.zx_mul_noalloc(F, lf - 1, mf, G, lg, mf, out, mh, False, bits, bits, stream=side)
+        except tg.TftError as e:
+            refused = e
+    assert refused is not None and refused.code == tg.ZX_EINVAL
+    for _ in range(2):
+        out.fill_(-1)
+        graph.replay()
+        torch.cuda.synchronize()
+        assert torch.equal(out, ref)
