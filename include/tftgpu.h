@@ -226,7 +226,9 @@ int zx_server_destroy(zx_server *srv);
  * the split L1 = 2^floor(l/2) for cache reasons; every configuration computes the same
  * outputs). Candidates: cells per CTA of a cluster job (2^3 .. 2^6), the largest job held by one
  * CTA (the shared-memory limit, or the size at which three CTAs share an SM), warps per CTA
- * (8 or 16) and, for odd l, the top-level split floor or ceil(l/2). The setting `fused` is kept as
+ * (8 or 16) and, for odd l, the top-level split floor or ceil(l/2); and the split with the fewest
+ * passes with clusters capped at 2 or 4 CTAs (for l = 16 at N = 32768: three passes, columns of 64
+ * cells on 4-CTA clusters, then rows of 32 cells on 2-CTA clusters). The setting `fused` is kept as
  * it is: single round trips cannot show its cost when transforms run on concurrent streams. The
  * round trips use
  * omega = 2 when L | 2N, else omega = sqrt2 (L | 4N), the transforms products use. For each candidate the call
@@ -239,7 +241,8 @@ typedef struct {
     int32_t ls_max;     /* log2 of the largest job one CTA holds */
     int32_t ls_c;       /* log2 of the cells per CTA of a cluster job */
     int32_t max_warps;  /* warps per CTA */
-    int32_t split;      /* 0: L1 = 2^floor(l/2), 1: L1 = 2^ceil(l/2) */
+    int32_t split;      /* 0: L1 = 2^floor(l/2), 1: L1 = 2^ceil(l/2), 2: at every level the
+                           split with the fewest global-memory passes below it */
     int32_t candidates; /* configurations timed */
     float best_ms;      /* round-trip time of the chosen configuration */
     float default_ms;   /* round-trip time of the default configuration */
@@ -249,13 +252,14 @@ typedef struct {
                            and the ITFT, 2 for the ITFT only. A persistent launch holds every
                            CTA slot of the GPU until it finishes, so transforms on concurrent
                            streams stop overlapping; it pays for a transform that runs alone */
+    int32_t max_cluster_log2; /* cluster jobs use at most 2^max_cluster_log2 CTAs (0 .. 4) */
 } zx_tune_info;
 
 int zx_tune(uint64_t *x, int l, int64_t n, int64_t N, int64_t stride_limbs, int reps, void *stream,
             zx_tune_info *out);
 
-/* The launch configuration used for ring N (ls_max, ls_c, max_warps, split, fused; the other
- * fields are zero; a tuned configuration is kept as zx_tune chose it), and pinning one, e.g. a result of zx_tune saved from an earlier process. zx_config_set
+/* The launch configuration used for ring N (ls_max, ls_c, max_warps, split, fused,
+ * max_cluster_log2; the other fields are zero; a tuned configuration is kept as zx_tune chose it), and pinning one, e.g. a result of zx_tune saved from an earlier process. zx_config_set
  * returns ZX_EINVAL for a configuration the ring cannot run (shared memory, warps, split); with
  * cfg == NULL it restores the default. Host only. */
 int zx_config_get(int64_t N, zx_tune_info *out);

@@ -54,7 +54,8 @@ class ZxPlanInfo(C.Structure):
 
 class ZxTuneInfo(C.Structure):
     _fields_ = [("ls_max", C.c_int32), ("ls_c", C.c_int32), ("max_warps", C.c_int32), ("split", C.c_int32),
-                ("candidates", C.c_int32), ("best_ms", C.c_float), ("default_ms", C.c_float), ("fused", C.c_int32)]
+                ("candidates", C.c_int32), ("best_ms", C.c_float), ("default_ms", C.c_float), ("fused", C.c_int32),
+                ("max_cluster_log2", C.c_int32)]
 
 
 class ZxServerInfo(C.Structure):
@@ -298,10 +299,10 @@ def sn_itft(x, l, z, n, f, M, m, e=0, stride=None, scale=0, stream=None):
 
 
 def config_get(N):
-    """Launch configuration used for ring N: ls_max, ls_c, max_warps, split, fused."""
+    """Launch configuration used for ring N: ls_max, ls_c, max_warps, split, fused, max_cluster_log2."""
     info = ZxTuneInfo()
     _check(load().zx_config_get(N, C.byref(info)), "zx_config_get")
-    return {k: getattr(info, k) for k in ("ls_max", "ls_c", "max_warps", "split", "fused")}
+    return {k: getattr(info, k) for k in ("ls_max", "ls_c", "max_warps", "split", "fused", "max_cluster_log2")}
 
 
 def config_set(N, cfg=None):
@@ -309,7 +310,8 @@ def config_set(N, cfg=None):
     if cfg is None:
         _check(load().zx_config_set(N, None), "zx_config_set")
         return
-    info = ZxTuneInfo(cfg["ls_max"], cfg["ls_c"], cfg["max_warps"], cfg["split"], 0, 0.0, 0.0, cfg.get("fused", 1))
+    info = ZxTuneInfo(cfg["ls_max"], cfg["ls_c"], cfg["max_warps"], cfg["split"], 0, 0.0, 0.0, cfg.get("fused", 0),
+                      cfg.get("max_cluster_log2", 4))
     _check(load().zx_config_set(N, C.byref(info)), "zx_config_set")
 
 

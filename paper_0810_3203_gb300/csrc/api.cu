@@ -476,18 +476,24 @@ int zx_tune(uint64_t *x, int l, int64_t n, int64_t N, int64_t stride_limbs, int 
   for (int ls_max : {def.ls_max, ls3})
     for (int ls_c = 3; ls_c <= 6; ls_c++)
       for (int mw : {8, 16})
-        for (int sp = 0; sp <= (l & 1); sp++) {
-          PlanConfig c;
-          c.ls_max = ls_max;
-          c.ls_c = ls_c;
-          c.max_warps = mw;
-          c.split = sp;
-          c.fused = before.fused;  // kept as it is (see PlanConfig)
-          if (!config_valid(r, c)) continue;
-          bool dup = false;
-          for (const PlanConfig &o : cands)
-            dup = dup || (o.ls_max == c.ls_max && o.ls_c == c.ls_c && o.max_warps == c.max_warps && o.split == c.split);
-          if (!dup) cands.push_back(c);
+        for (int sp = 0; sp <= 2; sp++) {
+          if (sp == 1 && !(l & 1)) continue;  // the ceil split differs for odd l only
+          for (int mlc : {1, 2, 4}) {
+            if ((sp == 2) != (mlc < 4)) continue;  // capped clusters go with the fewest-pass split
+            PlanConfig c;
+            c.ls_max = ls_max;
+            c.ls_c = ls_c;
+            c.max_warps = mw;
+            c.split = sp;
+            c.max_lc = mlc;
+            c.fused = before.fused;  // kept as it is (see PlanConfig)
+            if (!config_valid(r, c)) continue;
+            bool dup = false;
+            for (const PlanConfig &o : cands)
+              dup = dup || (o.ls_max == c.ls_max && o.ls_c == c.ls_c && o.max_warps == c.max_warps &&
+                            o.split == c.split && o.max_lc == c.max_lc);
+            if (!dup) cands.push_back(c);
+          }
         }
   cudaStream_t s = cudaStream_t(stream);
   cudaEvent_t e0, e1;
@@ -515,7 +521,8 @@ int zx_tune(uint64_t *x, int l, int64_t n, int64_t N, int64_t stride_limbs, int 
   for (const PlanConfig &c : cands) {
     float ms = 0.0f;
     if ((rc = time_cfg(c, &ms))) break;
-    if (c.ls_max == def.ls_max && c.ls_c == def.ls_c && c.max_warps == def.max_warps && c.split == def.split)
+    if (c.ls_max == def.ls_max && c.ls_c == def.ls_c && c.max_warps == def.max_warps && c.split == def.split &&
+        c.max_lc == def.max_lc)
       def_ms = ms;
     if (ms < best) {
       best = ms;
@@ -532,6 +539,7 @@ int zx_tune(uint64_t *x, int l, int64_t n, int64_t N, int64_t stride_limbs, int 
   out->max_warps = chosen.max_warps;
   out->split = chosen.split;
   out->fused = chosen.fused;
+  out->max_cluster_log2 = chosen.max_lc;
   out->candidates = int32_t(cands.size());
   out->best_ms = best;
   out->default_ms = def_ms;
@@ -577,6 +585,7 @@ int zx_config_get(int64_t N, zx_tune_info *out) {
   out->max_warps = c.max_warps;
   out->split = c.split;
   out->fused = c.fused;
+  out->max_cluster_log2 = c.max_lc;
   return ZX_OK;
 }
 
@@ -593,6 +602,7 @@ int zx_config_set(int64_t N, const zx_tune_info *cfg) {
   c.max_warps = cfg->max_warps;
   c.split = cfg->split;
   c.fused = cfg->fused;
+  c.max_lc = cfg->max_cluster_log2;
   if (!config_valid(r, c)) return fail(ZX_EINVAL, "configuration not valid for this ring");
   set_plan_config(N, c);
   return ZX_OK;

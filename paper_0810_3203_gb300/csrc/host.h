@@ -57,8 +57,10 @@ Ring make_ring(int64_t N);
 // this setting as it is; zx_config_set chooses it.
 enum { FUSED_NONE = 0, FUSED_ALL = 1, FUSED_ITFT = 2 };
 inline bool fused_for(int fused, int kind) { return fused == FUSED_ALL || (fused == FUSED_ITFT && kind == KIND_ITFT); }
+// max_lc caps cluster jobs at 2^max_lc CTAs (at most kMaxClusterLog2). split 2: at every level,
+// the split with the fewest global-memory passes below it (ties: the one nearest to balanced).
 struct PlanConfig {
-  int ls_max = 0, ls_c = 0, max_warps = 16, split = 0, fused = FUSED_NONE;
+  int ls_max = 0, ls_c = 0, max_warps = 16, split = 0, fused = FUSED_NONE, max_lc = 4;
 };
 PlanConfig default_config(const Ring &r);
 bool config_valid(const Ring &r, const PlanConfig &c);

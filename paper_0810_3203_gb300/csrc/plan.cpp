@@ -10,6 +10,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <memory>
@@ -73,7 +74,8 @@ bool config_valid(const Ring &r, const PlanConfig &c) {
   auto fits = [&](int ls) { return ls >= 1 && ls <= 16 && size_t(1) << ls <= 65536 &&
                                    (size_t(1) << ls) * (size_t(r.pitch) + 1) * 4 <= kSmemBudget; };
   return fits(c.ls_max) && fits(c.ls_c) && c.ls_c <= c.ls_max + 1 && (c.max_warps == 8 || c.max_warps == 16) &&
-         (c.split == 0 || c.split == 1) && (c.fused >= FUSED_NONE && c.fused <= FUSED_ITFT);
+         (c.split >= 0 && c.split <= 2) && (c.fused >= FUSED_NONE && c.fused <= FUSED_ITFT) && c.max_lc >= 0 &&
+         c.max_lc <= kMaxClusterLog2;
 }
 
 namespace {
@@ -183,18 +185,47 @@ struct Planner {
     ls_c = cfg.ls_c;
     split = cfg.split;
   }
-  int top_l1(int l) const { return split ? l - l / 2 : l / 2; }
+  int top_l1(int l) const {
+    if (split == 2) return fewest_pass_l1(l);
+    return split ? l - l / 2 : l / 2;
+  }
 
-  // single CTA up to ls_max; a cluster of up to 16 CTAs of 2^ls_c cells above that, as long as
-  // every CTA row of the job's split holds at least one cell per CTA (2 lc <= l)
+  // single CTA up to ls_max; a cluster of up to 2^max_lc CTAs of 2^ls_c cells above that, as
+  // long as every CTA row of the job's split holds at least one cell per CTA (2 lc <= l)
   int cluster_log2(int l) const { return l <= ls_max ? 0 : l - ls_c; }
+  bool leaf_below_top(int l) const {
+    const int lc = cluster_log2(l);
+    return lc == 0 || (lc > 0 && lc <= cfg.max_lc && 2 * lc <= l);
+  }
   bool leaf(int l) const {
     // a whole transform of more than 64 cells takes the two-pass split: as one job it would run
     // on a single CTA (one SM) for l levels, as two passes its jobs spread over the SMs
     if (whole_split && depth == 0 && l > kTopSingleJobMax) return false;
-    const int lc = cluster_log2(l);
-    return lc == 0 || (lc <= kMaxClusterLog2 && 2 * lc <= l);
+    return leaf_below_top(l);
   }
+  // global-memory passes of a sub-transform of 2^l cells below the top under split 2, and the
+  // split that achieves them (memoised; l <= 30)
+  int min_passes(int l) const {
+    if (l <= 1 || leaf_below_top(l)) return 1;
+    if (memo_passes[l]) return memo_passes[l];
+    int best = 1 << 20;
+    for (int l1 = 1; l1 < l; l1++) best = std::min(best, min_passes(l1) + min_passes(l - l1));
+    memo_passes[l] = best;
+    return best;
+  }
+  int fewest_pass_l1(int l) const {
+    int best = -1, bp = 1 << 20;
+    for (int l1 = 1; l1 < l; l1++) {
+      const int p = min_passes(l1) + min_passes(l - l1);
+      // ties: nearest to the balanced split l / 2, then the smaller column length
+      if (p < bp || (p == bp && std::abs(2 * l1 - l) < std::abs(2 * best - l))) {
+        bp = p;
+        best = l1;
+      }
+    }
+    return best;
+  }
+  mutable int memo_passes[32] = {0};
   static constexpr int kTopSingleJobMax = 6;
   bool whole_split = true;  // false for plans that run on many sequences at once
   int depth = 0;  // recursion depth of the current tft / itft call (0: the whole transform)
@@ -542,8 +573,8 @@ const TransformPlan *get_transform_plan(int kind, int l, int64_t z, int64_t n, i
   const int64_t twoN = omega_order(N, mode);
   e = md(e, twoN);
   const PlanConfig cfg = plan_config(N);
-  const int cfg_key = cfg.ls_max | (cfg.ls_c << 5) | (cfg.max_warps << 10) | (cfg.split << 16) | (mode << 20) |
-                      (replicated ? 1 << 23 : 0) | (cfg.fused << 24);
+  const int cfg_key = cfg.ls_max | (cfg.ls_c << 5) | (cfg.max_warps << 10) | (cfg.split << 16) | (mode << 19) |
+                      (replicated ? 1 << 21 : 0) | (cfg.fused << 22) | (cfg.max_lc << 24);
   auto key = std::make_tuple(dev, kind, l, z, n, f, N, e, scale, cfg_key);
   PlanCache &pc = plan_cache();
   {

@@ -84,7 +84,7 @@ def test_tune_restores_buffer_and_keeps_fastest(tg, orc):
         back = d.cpu().numpy().view(np.uint64)
         assert np.array_equal(cells(back, n, W), cells(x, n, W))
         assert info["candidates"] >= 4 and info["best_ms"] > 0
-        assert tg.config_get(N) == {k: info[k] for k in ("ls_max", "ls_c", "max_warps", "split", "fused")}
+        assert tg.config_get(N) == {k: info[k] for k in ("ls_max", "ls_c", "max_warps", "split", "fused", "max_cluster_log2")}
         # the tuned configuration computes the same transform as the oracle
         ref = x.copy()
         orc.tft(ref, l, n, n, 0, N)
@@ -108,3 +108,38 @@ def test_tune_sqrt2_ring(tg):
         assert np.array_equal(cells(d.cpu().numpy().view(np.uint64), n, W), cells(x, n, W))
     finally:
         tg.config_set(N)
+
+
+def test_fewest_pass_configuration_at_the_benchmark_size(tg, orc):
+    """split 2 with clusters of at most 4 CTAs (three passes for the l = 16 TFT: 64-cell column
+    jobs on 4-CTA clusters, then 32-cell rows) on the benchmark's 514-limb layout: every TFT
+    output at n = 40000 and every exact ITFT output at n = 45000, f = 1, against the oracle."""
+    N, l = 32768, 16
+    W = N // 64 + 1
+    st = W + 1
+    before = tg.config_get(N)
+    tg.config_set(N, dict(before, ls_c=4, split=2, max_cluster_log2=2))
+    try:
+        n = 40000
+        x = workloads.residues(61, n, N, stride=st, cells=1 << l)
+        d = torch.from_numpy(x.view(np.int64)).cuda()
+        tg.tft_ex(d, l, n, n, N, 0, st)
+        got = d.cpu().numpy().view(np.uint64)
+        ref = x.copy()
+        orc.tft(ref, l, n, n, 0, N, stride=st)
+        A = got[:n * st].reshape(n, st)[:, :W]
+        B = ref[:n * st].reshape(n, st)[:, :W]
+        assert np.array_equal(A, B)
+        n, f = 45000, 1
+        x = workloads.residues(62, n + f, N, stride=st, cells=1 << l)
+        d = torch.from_numpy(x.view(np.int64)).cuda()
+        tg.itft_ex(d, l, n + f, n, f, N, 77, st, scale=0)
+        got = d.cpu().numpy().view(np.uint64)
+        ref = x.copy()
+        orc.itft(ref, l, n + f, n, f, 77, N, stride=st)
+        A = got[:(n + f) * st].reshape(n + f, st)[:, :W]
+        B = ref[:(n + f) * st].reshape(n + f, st)[:, :W]
+        assert np.array_equal(A, B)
+    finally:
+        tg.config_set(N, before)
+    assert tg.wait_status() == tg.ZX_OK

@@ -140,10 +140,13 @@ PINNED = [
     dict(ls_max=3, ls_c=3, max_warps=8, split=0),
     dict(ls_max=2, ls_c=2, max_warps=16, split=1),
     dict(ls_max=4, ls_c=2, max_warps=8, split=1),
+    # the fewest-pass split with clusters of at most 4 or 2 CTAs
+    dict(ls_max=3, ls_c=3, max_warps=8, split=2, max_cluster_log2=2),
+    dict(ls_max=3, ls_c=4, max_warps=16, split=2, max_cluster_log2=1),
 ]
 
 
-@pytest.mark.parametrize("cfg", PINNED, ids=lambda c: f"ls{c['ls_max']}c{c['ls_c']}s{c['split']}")
+@pytest.mark.parametrize("cfg", PINNED, ids=lambda c: f"ls{c['ls_max']}c{c['ls_c']}s{c['split']}m{c.get('max_cluster_log2', 4)}")
 def test_pinned_configurations_match_the_oracle(tg, orc, cfg):
     N = 2048
     before = tg.config_get(N)
@@ -157,6 +160,7 @@ def test_pinned_configurations_match_the_oracle(tg, orc, cfg):
             plan = check_case(tg, orc, kind, l, z, n, f, e, N, scale=kind, seed=l + 3 * kind + n)
             passes.add(plan["passes"])
             assert any(L["lc"] > 0 for L in plan["launches"]) or cfg["ls_c"] < 3 or l < 12
+            assert all(L["lc"] <= cfg.get("max_cluster_log2", 4) for L in plan["launches"])
         assert max(passes) >= 3  # these configurations split the transforms into several passes
     finally:
         tg.config_set(N, before)
@@ -229,3 +233,24 @@ def test_plan_safety_sweep(tg):
     for kind, l, z, n, f, N, mode in cases:
         plan = tg.transform_jobs(kind, l, z, n, N, f=f, e=rng.randrange(2 * N), scale=kind, mode=mode)
         check_plan_safety(plan, 1 << l, range(n if kind == 0 else n + f))
+
+
+def test_the_fewest_pass_plan_at_the_benchmark_size(tg):
+    """split 2 with clusters of at most 4 CTAs and 16 cells per cluster CTA: the l = 16 TFT at
+    N = 32768 takes three global-memory passes (64-cell column jobs on 4-CTA clusters, then rows
+    of 32 cells) against four for the paper's split, the exact ITFT three to eight (the partial
+    rows of Algorithm 2 add steps) against twelve; the launch rules hold for both."""
+    N = 32768
+    before = tg.config_get(N)
+    tg.config_set(N, dict(before, ls_c=4, split=2, max_cluster_log2=2))
+    try:
+        for n in (32769, 40000, 45000, 65536):
+            tft = tg.transform_jobs(0, 16, n, n, N)
+            itft = tg.transform_jobs(1, 16, n, n, N, scale=1)
+            assert tft["passes"] == 3 and len(tft["launches"]) == 3, n
+            assert tft["launches"][0]["ls"] == 6 and tft["launches"][0]["lc"] == 2
+            assert itft["passes"] <= 8 and len(itft["launches"]) <= 8, n
+            check_plan_safety(tft, 1 << 16, range(n))
+            check_plan_safety(itft, 1 << 16, range(n))
+    finally:
+        tg.config_set(N, before)
