@@ -376,7 +376,10 @@ def run_gpu(args):
     torch.cuda.synchronize(device)
 
     # launch configuration of the ring: the autotuner's pick, on one of the sweep's buffers (the
-    # round trips restore it), outside every timed region
+    # round trips restore it), outside every timed region; --fused pins the launch form first
+    # (the tuner keeps it)
+    if args.fused >= 0:
+        tg.config_set(N, dict(tg.config_get(N), fused=args.fused))
     tuned = None if args.no_tune else tg.tune(dev[40000 if 40000 in dev else ns[0]], l, 40000 if 40000 in dev else ns[0],
                                               N, stride, reps=2, stream=stream)
 
@@ -983,6 +986,9 @@ def main():
                     help="limbs between cells of the large transforms (default: W rounded up to even)")
     ap.add_argument("--no-batch", action="store_true", help="skip the 512-product batch leg")
     ap.add_argument("--no-tune", action="store_true", help="keep the default launch configurations")
+    ap.add_argument("--fused", type=int, default=-1,
+                    help="launch form of the large transforms (zx_tune_info.fused: 0 one launch per pass, 1 and "
+                         "2 persistent, 3 per-pass persistent loops with L2 prefetch); default: the library's")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving leg")
     ap.add_argument("--no-e1", action="store_true", help="skip the Sec. 5.1-shaped product sweep")
     ap.add_argument("--serve-requests", type=int, default=1000)

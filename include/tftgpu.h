@@ -249,7 +249,9 @@ typedef struct {
     int32_t fused;      /* when a plan whose jobs all run on single CTAs (rings of N = 2^k >= 4096)
                            is one persistent launch (zx_transform_schedule) instead of one
                            launch per global-memory pass: 0 never (the default), 1 for the TFT
-                           and the ITFT, 2 for the ITFT only. A persistent launch holds every
+                           and the ITFT, 2 for the ITFT only; 3: one launch per pass, each a
+                           persistent loop over its jobs that prefetches a CTA's next job
+                           into L2 while it computes the current one. A persistent launch holds every
                            CTA slot of the GPU until it finishes, so transforms on concurrent
                            streams stop overlapping; it pays for a transform that runs alone */
     int32_t max_cluster_log2; /* cluster jobs use at most 2^max_cluster_log2 CTAs (0 .. 4) */

@@ -55,7 +55,10 @@ Ring make_ring(int64_t N);
 // hold every CTA slot until they finish and the transforms stop overlapping, so the five-stream
 // benchmark step went from 4.74 to 5.18 ms. zx_tune times single round trips and therefore leaves
 // this setting as it is; zx_config_set chooses it.
-enum { FUSED_NONE = 0, FUSED_ALL = 1, FUSED_ITFT = 2 };
+// 3: one launch per pass, each as a persistent loop over its single-CTA jobs that prefetches a
+// CTA's next job into L2 while it computes the current one (FUSED_STREAM; rings that fill all 32
+// lanes).
+enum { FUSED_NONE = 0, FUSED_ALL = 1, FUSED_ITFT = 2, FUSED_STREAM = 3 };
 inline bool fused_for(int fused, int kind) { return fused == FUSED_ALL || (fused == FUSED_ITFT && kind == KIND_ITFT); }
 // max_lc caps cluster jobs at 2^max_lc CTAs (at most kMaxClusterLog2). split 2: at every level,
 // the split with the fewest global-memory passes below it (ties: the one nearest to balanced).
@@ -120,6 +123,8 @@ struct TransformPlan {
   int f_njobs = 0, f_ls = 0, f_nwarps = 0, f_prog_words = 0;
   const JobDesc *f_jobs = nullptr;
   const int32_t *f_dep_off = nullptr, *f_deps = nullptr;
+  // launches of single-CTA jobs run as persistent loops with L2 prefetch (FUSED_STREAM)
+  bool stream = false;
 };
 
 // Cached plan of TFT (kind = KIND_TFT) or ITFT for the given parameters; nullptr with *err set

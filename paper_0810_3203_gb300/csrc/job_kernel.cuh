@@ -669,6 +669,39 @@ __global__ void __launch_bounds__(MINB == 3 ? 256 : 512, MINB) job_kernel(uint64
   run_job<K, SQ, SINGLE>(jd, x, stride_limbs, ls, lc, kg, prog_cap, fault);
 }
 
+// L2 prefetch of the input cells of a job (bulk prefetch, no shared memory): one cell per lane
+// of the calling warp, 4 NW bytes each, when the cells are 16-byte aligned.
+__device__ __forceinline__ void prefetch_job_l2(const JobDesc &jd, const uint64_t *x, int64_t stride_limbs, int NW,
+                                                int lane) {
+  const uint64_t *x0 = x + jd.cell0 * stride_limbs;
+  for (int m = lane; m < jd.nload; m += 32) {
+    const void *p = x0 + int64_t(m) * jd.mstride * stride_limbs;
+    uint64_t a;
+    asm volatile("cvta.to.global.u64 %0, %1;" : "=l"(a) : "l"(p));
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a), "r"(uint32_t(NW) * 4u) : "memory");
+  }
+}
+
+// A plain launch of independent single-CTA jobs as a persistent loop: CTA b runs jobs b, b + G,
+// b + 2 G, ... (G CTAs) and, while it works on one, prefetches the cells of its next one into L2,
+// so that the next job's loads overlap the current job's butterflies.
+template <int K, int MINB, bool FULL, bool SQ>
+__global__ void __launch_bounds__(MINB == 3 ? 256 : 512, MINB) job_kernel_stream(uint64_t *__restrict__ x,
+                                                  int64_t stride_limbs, const JobDesc *__restrict__ jobs, int njobs,
+                                                  int N, int ls, uint32_t mask, int prog_cap, uint32_t *fault) {
+  const KGeo kg = make_kgeo<K, FULL, SQ>(N, mask);
+  const bool vec16 = ((reinterpret_cast<uintptr_t>(x) & 15) == 0) && ((stride_limbs & 1) == 0);
+  for (int k = int(blockIdx.x); k < njobs; k += int(gridDim.x)) {
+    const int nk = k + int(gridDim.x);
+    if (vec16 && nk < njobs && threadIdx.x < 32) prefetch_job_l2(jobs[nk], x, stride_limbs, kg.g.NW, kg.g.lane);
+    // the descriptor goes to registers first: passed as a reference into global memory, its fields
+    // would be loaded again wherever the job body uses them
+    const JobDesc jd = jobs[k];
+    run_job<K, SQ, true>(jd, x, stride_limbs, ls, 0, kg, prog_cap, fault);
+    __syncthreads();  // the job is done with shared memory
+  }
+}
+
 // The persistent form (FusedArgs): single-CTA jobs claimed in order until none is left.
 template <int K, int MINB, bool FULL, bool SQ>
 __global__ void __launch_bounds__(MINB == 3 ? 256 : 512, MINB) job_kernel_fused(uint64_t *__restrict__ x,
@@ -696,7 +729,8 @@ __global__ void __launch_bounds__(MINB == 3 ? 256 : 512, MINB) job_kernel_fused(
     __syncthreads();
     // the cells written by the jobs waited for are read by bulk copies (async proxy) below
     asm volatile("fence.proxy.async.global;" ::: "memory");
-    run_job<K, SQ, true>(fa.jobs[k], x, stride_limbs, ls, 0, kg, prog_cap, fault);
+    const JobDesc jd = fa.jobs[k];  // in registers (see job_kernel_stream)
+    run_job<K, SQ, true>(jd, x, stride_limbs, ls, 0, kg, prog_cap, fault);
     done = fa.sync + 1 + k;
   }
 }
@@ -714,6 +748,9 @@ static cudaError_t launch_km(const Launch &L, uint64_t *x, int64_t stride_limbs,
     if constexpr (FUSED) {
       e = cudaFuncSetAttribute(job_kernel_fused<K, MINB, FULL, SQ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                int(kJobDynSmem));
+      if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(job_kernel_stream<K, MINB, FULL, SQ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 int(kJobDynSmem));
     } else {
       e = cudaFuncSetAttribute(job_kernel<K, MINB, FULL, SQ, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                int(kJobDynSmem));
@@ -736,12 +773,17 @@ static cudaError_t launch_km(const Launch &L, uint64_t *x, int64_t stride_limbs,
     cfg.stream = s;
     // persistent: as many CTAs as the SMs hold at once, at most one per job
     int per_sm = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, job_kernel_fused<K, MINB, FULL, SQ>,
-                                                                 L.nwarps * 32, smem);
+    cudaError_t e = fa.sync ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, job_kernel_fused<K, MINB, FULL, SQ>,
+                                                                           L.nwarps * 32, smem)
+                            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, job_kernel_stream<K, MINB, FULL, SQ>,
+                                                                           L.nwarps * 32, smem);
     if (e != cudaSuccess) return e;
     int sms = 0;
     if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
     cfg.gridDim = dim3(unsigned(std::max(1, std::min(fa.njobs, std::max(1, per_sm) * sms))));
+    if (!fa.sync)
+      return cudaLaunchKernelEx(&cfg, job_kernel_stream<K, MINB, FULL, SQ>, x, stride_limbs, fa.jobs, fa.njobs,
+                                int(r.N), L.ls, mask, prog_cap, fault);
     return cudaLaunchKernelEx(&cfg, job_kernel_fused<K, MINB, FULL, SQ>, x, stride_limbs, int(r.N), L.ls, mask,
                               prog_cap, fa, fault);
   } else {
@@ -837,10 +879,12 @@ TFT_DECLARE_LAUNCHES(16, sq);
 TFT_DECLARE_LAUNCHES(32, w2);
 TFT_DECLARE_LAUNCHES(32, sq);
 #undef TFT_DECLARE_LAUNCHES
+// fa.sync null: the plain launch *plain (single-CTA jobs, no segments or replicas) in the
+// persistent streaming form (job_kernel_stream)
 cudaError_t launch_fused_small(const TransformPlan &p, uint64_t *x, int64_t stride_limbs, cudaStream_t s,
-                               const FusedArgs &fa, uint32_t *fault);  // K = 4, 8, 16
+                               const FusedArgs &fa, uint32_t *fault, const Launch *plain = nullptr);  // K = 4, 8, 16
 cudaError_t launch_fused_k32(const TransformPlan &p, uint64_t *x, int64_t stride_limbs, cudaStream_t s,
-                             const FusedArgs &fa, uint32_t *fault);
+                             const FusedArgs &fa, uint32_t *fault, const Launch *plain = nullptr);
 
 // Definitions for the translation units above.
 // SQN: w2 for omega = 2, sq for omega = sqrt2 (SQ = false / true)
@@ -853,13 +897,17 @@ cudaError_t launch_fused_k32(const TransformPlan &p, uint64_t *x, int64_t stride
 
 template <int K>
 cudaError_t launch_fused_as(const TransformPlan &p, uint64_t *x, int64_t stride_limbs, cudaStream_t s,
-                            const FusedArgs &fa, uint32_t *fault) {
+                            const FusedArgs &fa, uint32_t *fault, const Launch *plain) {
   Launch L;
-  L.ls = p.f_ls;
-  L.lc = 0;
-  L.nwarps = p.f_nwarps;
-  L.njobs = p.f_njobs;
-  L.prog_words = p.f_prog_words;
+  if (plain) {
+    L = *plain;
+  } else {
+    L.ls = p.f_ls;
+    L.lc = 0;
+    L.nwarps = p.f_nwarps;
+    L.njobs = p.f_njobs;
+    L.prog_words = p.f_prog_words;
+  }
   return p.mode == RING_SQRT2 ? launch_k<K, true, true>(L, x, stride_limbs, p.ring, s, 1, 0, fa, fault)
                               : launch_k<K, false, true>(L, x, stride_limbs, p.ring, s, 1, 0, fa, fault);
 }

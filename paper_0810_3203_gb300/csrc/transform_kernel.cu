@@ -44,7 +44,14 @@ cudaError_t run_transform_reps(const TransformPlan &p, uint64_t *x, int64_t stri
   if (!fault) return cudaErrorInvalidSymbol;
   for (const Launch &L : p.launches) {
     if (reps > 1 && L.nsegs != 0) return cudaErrorInvalidValue;
-    const cudaError_t e = launch_any(p, L, x, stride_limbs, s, reps, rep_cells, fault);
+    cudaError_t e;
+    if (p.stream && reps == 1 && L.nsegs == 0 && L.lc == 0 && p.ring.K >= 4 && p.ring.G == 32) {
+      const FusedArgs plain = {L.d_jobs, nullptr, nullptr, nullptr, L.njobs};
+      e = p.ring.K == 32 ? launch_fused_k32(p, x, stride_limbs, s, plain, fault, &L)
+                         : launch_fused_small(p, x, stride_limbs, s, plain, fault, &L);
+    } else {
+      e = launch_any(p, L, x, stride_limbs, s, reps, rep_cells, fault);
+    }
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;

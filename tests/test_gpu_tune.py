@@ -143,3 +143,32 @@ def test_fewest_pass_configuration_at_the_benchmark_size(tg, orc):
     finally:
         tg.config_set(N, before)
     assert tg.wait_status() == tg.ZX_OK
+
+
+@pytest.mark.parametrize("N,l,n", [(32768, 16, 40000), (4096, 12, 3001)])
+def test_streaming_launch_form(tg, orc, N, l, n):
+    """fused = 3: every per-pass launch of single-CTA jobs runs as a persistent loop that
+    prefetches a CTA's next job into L2: TFT and exact ITFT outputs against the oracle."""
+    W = N // 64 + 1
+    st = W + 1
+    before = tg.config_get(N)
+    tg.config_set(N, dict(before, fused=3))
+    try:
+        x = workloads.residues(63 + l, n, N, stride=st, cells=1 << l)
+        d = torch.from_numpy(x.view(np.int64)).cuda()
+        tg.tft_ex(d, l, n, n, N, 0, st)
+        got = d.cpu().numpy().view(np.uint64)
+        ref = x.copy()
+        orc.tft(ref, l, n, n, 0, N, stride=st)
+        assert np.array_equal(got[:n * st].reshape(n, st)[:, :W], ref[:n * st].reshape(n, st)[:, :W])
+        nn, f = n - 3, 1
+        d = torch.from_numpy(x.view(np.int64)).cuda()
+        tg.itft_ex(d, l, n, nn, f, N, 5, st, scale=0)
+        got = d.cpu().numpy().view(np.uint64)
+        ref = x.copy()
+        orc.itft(ref, l, n, nn, f, 5, N, stride=st)
+        k = nn + f
+        assert np.array_equal(got[:k * st].reshape(k, st)[:, :W], ref[:k * st].reshape(k, st)[:, :W])
+    finally:
+        tg.config_set(N, before)
+    assert tg.wait_status() == tg.ZX_OK
