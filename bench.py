@@ -116,7 +116,8 @@ def kernel_source_hash():
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_0810_3203_gb300", "csrc")
     # the files that decide what the transform kernel does and which launches a plan makes
-    for f in ("common.h", "plan.cpp", "program.cpp", "ring_warp.cuh", "transform_kernel.cu"):
+    for f in ("common.h", "host.h", "plan.cpp", "program.cpp", "ring_warp.cuh", "job_kernel.cuh",
+              "transform_kernel.cu", "transform_k32.cu"):
         h.update(f.encode())
         h.update(open(os.path.join(csrc, f), "rb").read())
     return h.hexdigest()[:16]
@@ -529,7 +530,8 @@ def run_gpu(args):
     ok &= sn["bit_exact_roundtrip"]
     batch = None if args.no_batch else batch_leg(tg, device, stream, 2, 3, not args.no_tune)
     ok &= batch is None or batch["bit_exact_vs_plain"]
-    serve = None if args.no_serve else serve_leg(tg, device, stream, args.serve_requests, not args.no_tune)
+    serve = None if args.no_serve else serve_leg(tg, device, stream, args.serve_requests, not args.no_tune,
+                                                 slots=args.serve_slots)
     ok &= serve is None or serve["bit_exact_vs_plain"]
 
     if rank != 0:
@@ -666,11 +668,14 @@ def batch_leg(tg, device, stream, steps, warmup, tune=True):
             "speedup_vs_plain": round(tp / tb, 3), "bit_exact_vs_plain": bool(same), "tuned": tuned}
 
 
-def serve_leg(tg, device, stream, count, tune=True):
-    """Poisson arrivals (mean 2000 requests/s) of products with lengths log-uniform in
-    [2^8, 2^15] and coefficient bits log-uniform in [64, 4096], operands resident on the
-    device. The serving loop (continuous batching) against the plain path, where each request
-    runs alone with zx_mul once the previous one has finished; latency = completion - arrival."""
+def serve_leg(tg, device, stream, count, tune=True, rates=(2000.0, 500.0), slots=3):
+    """Poisson arrivals of products with lengths log-uniform in [2^8, 2^15] and coefficient bits
+    log-uniform in [64, 4096], operands resident on the device: the serving loop (continuous
+    batching) against the plain path, where each request runs alone with zx_mul once the
+    previous one has finished; latency = completion - arrival. The first rate (2000 requests/s,
+    the workload's) is above what one GB300 serves, so its latencies include queueing; the second
+    (500/s) is below, so its latencies show what batching adds to a request. The same requests
+    (shapes and operands) are offered at both rates."""
     import numpy as np
     import torch
 
@@ -688,54 +693,71 @@ def serve_leg(tg, device, stream, count, tune=True):
         items.append((F, lf, m, G, lg, m, H, mh, False, bits, bits))
         plain_out.append(torch.zeros_like(H))
     torch.cuda.synchronize(device)
-    arrivals = [t for t, _, _, _ in reqs]
+    base_rate = workloads.SERVE_POISSON["rate"]
     tuned = tune_rings(tg, device, stream, [(lf, bits, lg, bits) for _, lf, lg, bits in reqs], tune)
 
     def pct(v, q):
         v = sorted(v)
         return v[min(len(v) - 1, int(q * len(v)))]
 
-    with tg.Server(slots=3) as srv:
-        for it in items[:16]:  # warm the plan caches
-            srv.submit(*it)
-        srv.drain(600.0)
-        srv.poll(4096)
-        lat = {}
-        t_srv = time.perf_counter()
-        ids = {}
-        for k, it in enumerate(items):
-            while time.perf_counter() - t_srv < arrivals[k]:
-                pass
-            ids[srv.submit(*it)] = k
-        srv.drain(600.0)
-        t_end = time.perf_counter()
-        for rid, st, sec in srv.poll(count + 16):
-            if st != 0:
-                raise RuntimeError(f"request {rid} failed with status {st}")
-            lat[ids[rid]] = sec
-        stats = srv.stats()
-    served = [lat[k] for k in range(count)]
-
-    plain_lat = []
-    t0 = time.perf_counter()
-    for k, ((F, lf, m, G, lg, _, _, mh, sg, b, _), Hp) in enumerate(zip(items, plain_out)):
-        while time.perf_counter() - t0 < arrivals[k]:
-            pass
-        tg.zx_mul(F, lf, m, G, lg, m, Hp, mh, sg, b, b, stream=stream)
+    def one_rate(rate):
+        # the generator's arrival times scale as 1 / rate for the same uniform draws
+        arrivals = [t * base_rate / rate for t, _, _, _ in reqs]
+        for H in [it[6] for it in items] + plain_out:
+            H.zero_()
         torch.cuda.synchronize(device)
-        plain_lat.append(time.perf_counter() - t0 - arrivals[k])
-    t_plain = time.perf_counter() - t0
-    same = all(torch.equal(it[6], hp) for it, hp in zip(items, plain_out))
-    return {"workload": f"{count} requests, Poisson arrivals at 2000/s, lengths log-uniform [2^8, 2^15], "
-                        "coefficient bits log-uniform [64, 4096], unsigned, seed 5",
-            "products_per_s": round(count / (t_end - t_srv), 2),
-            "p50_ms": round(pct(served, 0.5) * 1e3, 3), "p99_ms": round(pct(served, 0.99) * 1e3, 3),
-            "plain_products_per_s": round(count / t_plain, 2),
-            "plain_p50_ms": round(pct(plain_lat, 0.5) * 1e3, 3), "plain_p99_ms": round(pct(plain_lat, 0.99) * 1e3, 3),
-            "offered_per_s": round(count / arrivals[-1], 1), "waves": stats["waves"],
-            "max_wave_products": stats["max_wave_products"], "max_waves_in_flight": stats["max_waves_in_flight"],
-            "arena_peak_gb": round(stats["arena_peak_bytes"] / 1e9, 3), "bit_exact_vs_plain": bool(same),
-            "tuned": tuned}
+        with tg.Server(slots=slots) as srv:
+            for it in items[:16]:  # warm the plan caches
+                srv.submit(*it)
+            srv.drain(600.0)
+            srv.poll(4096)
+            lat = {}
+            t_srv = time.perf_counter()
+            ids = {}
+            for k, it in enumerate(items):
+                while time.perf_counter() - t_srv < arrivals[k]:
+                    pass
+                ids[srv.submit(*it)] = k
+            srv.drain(600.0)
+            t_end = time.perf_counter()
+            for rid, st, sec in srv.poll(count + 16):
+                if st != 0:
+                    raise RuntimeError(f"request {rid} failed with status {st}")
+                lat[ids[rid]] = sec
+            stats = srv.stats()
+        served = [lat[k] for k in range(count)]
+        plain_lat = []
+        t0 = time.perf_counter()
+        for k, ((F, lf, m, G, lg, _, _, mh, sg, b, _), Hp) in enumerate(zip(items, plain_out)):
+            while time.perf_counter() - t0 < arrivals[k]:
+                pass
+            tg.zx_mul(F, lf, m, G, lg, m, Hp, mh, sg, b, b, stream=stream)
+            torch.cuda.synchronize(device)
+            plain_lat.append(time.perf_counter() - t0 - arrivals[k])
+        t_plain = time.perf_counter() - t0
+        same = all(torch.equal(it[6], hp) for it, hp in zip(items, plain_out))
+        return {"products_per_s": round(count / (t_end - t_srv), 2),
+                "p50_ms": round(pct(served, 0.5) * 1e3, 3), "p99_ms": round(pct(served, 0.99) * 1e3, 3),
+                "plain_products_per_s": round(count / t_plain, 2),
+                "plain_p50_ms": round(pct(plain_lat, 0.5) * 1e3, 3),
+                "plain_p99_ms": round(pct(plain_lat, 0.99) * 1e3, 3),
+                "offered_per_s": round(count / arrivals[-1], 1), "waves": stats["waves"],
+                "max_wave_products": stats["max_wave_products"], "max_waves_in_flight": stats["max_waves_in_flight"],
+                "arena_peak_gb": round(stats["arena_peak_bytes"] / 1e9, 3),
+                "learned_time_scale": round(stats["time_scale"], 3), "bit_exact_vs_plain": bool(same)}
+
+    res = one_rate(rates[0])
+    out = {"workload": f"{count} requests, Poisson arrivals at {rates[0]:g}/s, lengths log-uniform [2^8, 2^15], "
+                       "coefficient bits log-uniform [64, 4096], unsigned, seed 5"}
+    out.update(res)
+    for r in rates[1:]:
+        sub = one_rate(r)
+        sub["workload"] = f"the same requests at {r:g}/s (below what the GPU serves)"
+        out[f"at_{int(r)}_per_s"] = sub
+        out["bit_exact_vs_plain"] = out["bit_exact_vs_plain"] and sub["bit_exact_vs_plain"]
+    out["slots"] = slots
+    out["tuned"] = tuned
+    return out
 
 
 def sn_leg(tg, device, stream, steps):
@@ -939,9 +961,40 @@ def run_serve(args):
     device = torch.device("cuda", 0)
     torch.cuda.set_device(device)
     tg.load()
-    res = serve_leg(tg, device, torch.cuda.current_stream(device), args.serve_requests, not args.no_tune)
+    res = serve_leg(tg, device, torch.cuda.current_stream(device), args.serve_requests, not args.no_tune,
+                    slots=args.serve_slots)
     print(json.dumps(res), flush=True)
     return 0 if res["bit_exact_vs_plain"] else 1
+
+
+def run_pointwise_case(args):
+    """Schoolbook pointwise products a_i <- a_i b_i mod 2^N + 1 at N = 32768 (the case ncu
+    captures): 1024 products of 514-limb cells, one warm-up call, then `profile_reps` calls, each
+    timed with CUDA events."""
+    import numpy as np
+    import torch
+
+    import paper_0810_3203_gb300 as tg
+
+    tg.load()
+    N, n, s = 32768, 1024, 514
+    a = torch.from_numpy(workloads.residues(21, n, N, stride=s).view(np.int64)).cuda()
+    b = torch.from_numpy(workloads.residues(22, n, N, stride=s).view(np.int64)).cuda()
+    x = a.clone()
+    tg.pointwise(x, b, n, N, s, 1)
+    ms = []
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for _ in range(args.profile_reps):
+        x.copy_(a)
+        e0.record()
+        tg.pointwise(x, b, n, N, s, 1)
+        e1.record()
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    macs = n * (N // 32) ** 2
+    print(json.dumps({"pointwise_case": "1024 products mod 2^32768+1, schoolbook", "ms": [round(v, 4) for v in ms],
+                      "mac32_per_s": round(macs / (min(ms) * 1e-3), 1)}))
+    return 0
 
 
 def run_profile_case(args):
@@ -956,6 +1009,8 @@ def run_profile_case(args):
     if args.config:
         ls_max, ls_c, mw, sp = (int(v) for v in args.config.split(","))
         tg.config_set(N, {"ls_max": ls_max, "ls_c": ls_c, "max_warps": mw, "split": sp})
+    if args.fused >= 0:
+        tg.config_set(N, dict(tg.config_get(N), fused=args.fused))
     W = N // 64 + 1
     stride = cell_stride(W, args.stride)
     x = workloads.residues(WORKLOAD["seed"], n, N, stride=stride, cells=1 << l)
@@ -980,6 +1035,8 @@ def main():
     ap.add_argument("--profile-case", action="store_true",
                     help="run one TFT + ITFT at n = 40000 and exit (the case profiled with ncu)")
     ap.add_argument("--profile-reps", type=int, default=1)
+    ap.add_argument("--pointwise-case", action="store_true",
+                    help="run only 1024 schoolbook pointwise products at N = 32768 (the case ncu captures)")
     ap.add_argument("--config", default="",
                     help="ls_max,ls_c,max_warps,split: launch configuration for --profile-case")
     ap.add_argument("--stride", type=int, default=0,
@@ -992,12 +1049,15 @@ def main():
     ap.add_argument("--no-serve", action="store_true", help="skip the serving leg")
     ap.add_argument("--no-e1", action="store_true", help="skip the Sec. 5.1-shaped product sweep")
     ap.add_argument("--serve-requests", type=int, default=1000)
+    ap.add_argument("--serve-slots", type=int, default=3, help="stream slots of the serving loop (1 .. 8)")
     ap.add_argument("--serve-only", action="store_true", help="time only the serving leg")
     ap.add_argument("--batch-only", action="store_true",
                     help="time only the 512-product batch against one-at-a-time products")
     args = ap.parse_args()
     if args.profile_case:
         return run_profile_case(args)
+    if args.pointwise_case:
+        return run_pointwise_case(args)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":

@@ -195,9 +195,10 @@ int zx_mul_noalloc(const zx_poly *f, const zx_poly *g, zx_poly *h, void *stream)
  * worker thread. zx_server_submit queues h = f * g (every operand in device memory, same rules
  * as zx_mul; h->is_signed is set) and returns at once with a request id; a product whose ring
  * buffers exceed the arena is refused with ZX_ENOMEM. The worker admits the longest prefix of
- * the queue whose ring buffers fit the free arena into a free slot as one batch, so requests
- * that arrive while others run start as soon as a slot and memory are free and overlap with
- * them on the GPU. f, g and h must stay valid until the request is returned by zx_server_poll.
+ * the queue whose ring buffers fit the free arena into a free slot as one batch, up to about
+ * 20 ms of estimated work (a batch completes as a whole, so this bounds the latency it adds).
+ * Requests that arrive while others run start as soon as a slot and memory are free and overlap
+ * with them on the GPU. f, g and h must stay valid until the request is returned by zx_server_poll.
  * zx_server_poll returns up to `max` finished requests (id, status, seconds from submission to
  * completion; status and latency_s may be NULL). zx_server_drain waits until nothing is queued
  * or running (timeout_s < 0: no limit; ZX_ETIMEOUT otherwise). zx_server_destroy finishes the
@@ -212,6 +213,8 @@ typedef struct {
     int32_t slots;
     int32_t max_waves_in_flight;
     int64_t arena_bytes, arena_peak_bytes;
+    double time_scale;         /* running average of measured batch time (enqueue to
+                                  completion) over the cost model's estimate */
 } zx_server_info;
 
 int zx_server_create(int64_t arena_bytes, int slots, zx_server **out);
@@ -234,8 +237,11 @@ int zx_server_destroy(zx_server *srv);
  * omega = 2 when L | 2N, else omega = sqrt2 (L | 4N), the transforms products use. For each candidate the call
  * times `reps` TFT + ITFT round trips (Algorithm 1, then Algorithm 2 with the division by L)
  * of length n over the caller's device buffer x (L = 2^l cells of stride_limbs >= N/64 + 1
- * limbs holding canonical residues; the round trips restore it), keeps the fastest for every
- * later plan over ring N in this process, and reports it. Synchronises `stream`.
+ * limbs holding canonical residues; the round trips restore it), and keeps for every later plan
+ * over ring N in this process the default configuration, or a candidate at least 3 % faster than
+ * the configuration kept before it (configurations that single round trips cannot tell apart
+ * differ in batches and concurrent use, so noise does not decide), and reports it.
+ * Synchronises `stream`.
  */
 typedef struct {
     int32_t ls_max;     /* log2 of the largest job one CTA holds */

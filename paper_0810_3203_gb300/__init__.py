@@ -62,7 +62,7 @@ class ZxServerInfo(C.Structure):
     _fields_ = [("submitted", C.c_int64), ("completed", C.c_int64), ("pending", C.c_int64),
                 ("waves", C.c_int64), ("max_wave_products", C.c_int64), ("slots", C.c_int32),
                 ("max_waves_in_flight", C.c_int32), ("arena_bytes", C.c_int64),
-                ("arena_peak_bytes", C.c_int64)]
+                ("arena_peak_bytes", C.c_int64), ("time_scale", C.c_double)]
 
 
 class ZxPointwiseInfo(C.Structure):

@@ -249,9 +249,7 @@ __device__ __forceinline__ uint64_t globaltimer_ns() {
 }
 
 // Wait for the given phase parity of an mbarrier; false when limit_ns passed first.
-// sleep_ns > 0: the thread sleeps that long between polls (for a single waiting thread).
-__device__ __forceinline__ bool mbar_wait_bounded(uint32_t mb, uint32_t parity, uint64_t limit_ns,
-                                                  unsigned sleep_ns = 0) {
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t mb, uint32_t parity, uint64_t limit_ns) {
   const uint64_t t0 = globaltimer_ns();
   for (;;) {
     uint32_t done;
@@ -262,7 +260,6 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint32_t mb, uint32_t parity, 
         : "memory");
     if (done) return true;
     if (globaltimer_ns() - t0 > limit_ns) return false;
-    if (sleep_ns) __nanosleep(sleep_ns);
   }
 }
 
@@ -513,15 +510,15 @@ __device__ __forceinline__ bool run_job(const JobDesc &jd, uint64_t *__restrict_
     bulk_load_cells(cells, tops, P, nl, mb, g.NW, warp, nw, g.lane,
                     [&](int s) { return x0 + int64_t(s) * cstep; });
     stage_first_program();
-    // One thread waits for the copies, sleeping between polls; the others wait at the barrier,
-    // which takes no issue slots from the butterflies of the other CTAs on the SM. The barrier
-    // orders every thread's reads of the copied cells after that thread's observation of the
-    // completed phase.
+    // One thread waits for the copies; the others wait at the barrier, which takes no issue
+    // slots from the butterflies of the other CTAs on the SM (the waiting thread polls without
+    // sleeping: a sleep's wake-up delay shows on the short loads of small jobs). The barrier
+    // orders every thread's reads of the copied cells after the observed completion.
     bool landed = true;
-    if (threadIdx.x == 0) landed = mbar_wait_bounded(mb, 0, kBulkWaitNs, 64);
+    if (threadIdx.x == 0) landed = mbar_wait_bounded(mb, 0, kBulkWaitNs);
     if (__syncthreads_or(!landed)) {
       // the copies did not all land in time: wait once more for those in flight, report, stop
-      if (!landed) mbar_wait_bounded(mb, 0, kBulkWaitNs, 64);
+      if (!landed) mbar_wait_bounded(mb, 0, kBulkWaitNs);
       __syncthreads();
       if (threadIdx.x == 0) atomicOr(fault, 1u);
       return false;

@@ -2,7 +2,7 @@
 //
 // Requests (products of device operands) enter a FIFO. A worker thread admits the longest
 // prefix of the FIFO whose ring buffers fit the free part of a device arena reserved at
-// creation, lays it out as one batch (the merged launches of zx_batch.cu) and enqueues it on a
+// creation and whose estimated time fits the wave budget, lays it out as one batch (the merged launches of zx_batch.cu) and enqueues it on a
 // free stream slot; a host function enqueued after the batch marks its requests complete and
 // returns their arena block. Requests that arrive while batches run are admitted as soon as a
 // slot and enough arena are free, so their work overlaps with the batches already on the GPU.
@@ -36,8 +36,14 @@ using Clock = std::chrono::steady_clock;
 constexpr size_t kArenaAlign = 256;
 constexpr int kMaxWaveProducts = 512;
 // A batch completes as a whole, so its size bounds the latency of its requests: a wave takes
-// requests until their estimated device time reaches this budget (or one request exceeds it).
+// requests until their estimated time (a fixed cost model) reaches this budget, or one request
+// exceeds it. A wave runs its ring groups one after another on its slot's stream, so larger
+// waves lose concurrency: on GB300, a budget scaled up with the backlog served 0.8x and one
+// scaled down by the measured time 0.9x the products per second of this fixed one. The server
+// keeps the ratio of measured wave time (enqueue to completion) to the model's estimate, a
+// running average, and reports it (zx_server_info.time_scale).
 constexpr double kWaveBudgetUs = 20000.0;
+constexpr double kScaleMin = 0.05, kScaleMax = 20.0, kScaleWeight = 0.25;
 
 // First-fit allocator over the offsets of one device block; adjacent free ranges merge.
 class Arena {
@@ -106,6 +112,8 @@ struct Wave {
   int slot = 0;
   std::vector<Request *> reqs;
   size_t off = 0, bytes = 0;
+  double est_us = 0;             // cost-model estimate of the wave
+  Clock::time_point t_launch;    // when it was enqueued
 };
 
 }  // namespace
@@ -133,6 +141,7 @@ struct zx_server {
   std::thread worker;
   int64_t n_submitted = 0, n_completed = 0, n_waves = 0, max_wave = 0;
   int max_running = 0;
+  double scale = 1.0;  // learned ratio of measured wave time to the cost model's estimate
 };
 
 namespace tftgpu {
@@ -193,6 +202,11 @@ void worker_main(zx_server *S) {
   std::unique_lock<std::mutex> lk(S->mu);
   for (;;) {
     for (Wave *w : S->finished) {
+      if (w->est_us > 0 && !w->reqs.empty() && w->reqs.front()->status == ZX_OK) {
+        const double took = std::chrono::duration<double, std::micro>(w->reqs.front()->t_done - w->t_launch).count();
+        const double ratio = std::min(kScaleMax, std::max(kScaleMin, took / w->est_us));
+        S->scale = (1.0 - kScaleWeight) * S->scale + kScaleWeight * ratio;
+      }
       S->arena.release(w->off, w->bytes);
       S->busy[w->slot] = 0;
       S->running--;
@@ -233,6 +247,8 @@ void worker_main(zx_server *S) {
         w->slot = slot;
         w->off = off;
         w->bytes = need;
+        w->est_us = est;
+        w->t_launch = Clock::now();
         for (size_t k = 0; k < take; k++) {
           w->reqs.push_back(S->pending.front());
           S->pending.pop_front();
@@ -430,6 +446,7 @@ int zx_server_stats(zx_server *S, zx_server_info *out) {
   out->max_waves_in_flight = S->max_running;
   out->arena_bytes = int64_t(S->cap);
   out->arena_peak_bytes = int64_t(S->arena.peak());
+  out->time_scale = S->scale;
   return ZX_OK;
 }
 
