@@ -117,7 +117,7 @@ def kernel_source_hash():
     csrc = os.path.join(ROOT, "paper_0810_3203_gb300", "csrc")
     # the files that decide what the transform kernel does and which launches a plan makes
     for f in ("common.h", "host.h", "plan.cpp", "program.cpp", "ring_warp.cuh", "job_kernel.cuh",
-              "transform_kernel.cu", "transform_k32.cu"):
+              "transform_kernel.cu", "transform_k32.cu", "transform_fused_k32.cu"):
         h.update(f.encode())
         h.update(open(os.path.join(csrc, f), "rb").read())
     return h.hexdigest()[:16]
@@ -557,8 +557,9 @@ def run_gpu(args):
                      "plan_bytes_unit": "bytes the plan's jobs read and write in one TFT call at n = 40000 "
                                         "(from zx_transform_jobs; stores still dirty in L2 when a launch ends "
                                         "escape the kernel's ncu counters)",
-                     "kernel": "job_kernel<32> (every launch of the TFT and ITFT calls; the only kernel of "
-                               "the timed region, its time the region's device time)"},
+                     "kernel": "job_kernel_stream<32> run with one CTA per job (every launch of the TFT and "
+                               "ITFT calls; the only kernel of the timed region, its time the region's device "
+                               "time)"},
         "per_n_ms": {str(n): [round(a, 3), round(b, 3)] for n, (a, b) in per_n.items()},
         "smoothness": {str(n): round((per_n[n][0] + per_n[n][1]) / (per_n[ns[-1]][0] + per_n[ns[-1]][1]), 4)
                        for n in ns},
@@ -1045,7 +1046,8 @@ def main():
     ap.add_argument("--no-tune", action="store_true", help="keep the default launch configurations")
     ap.add_argument("--fused", type=int, default=-1,
                     help="launch form of the large transforms (zx_tune_info.fused: 0 one launch per pass, 1 and "
-                         "2 persistent, 3 per-pass persistent loops with L2 prefetch); default: the library's")
+                         "2 persistent, 3 per-pass persistent loops with L2 prefetch, 4 one launch per pass through "
+                         "the spill-free kernel); default: the library's")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving leg")
     ap.add_argument("--no-e1", action="store_true", help="skip the Sec. 5.1-shaped product sweep")
     ap.add_argument("--serve-requests", type=int, default=1000)

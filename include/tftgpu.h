@@ -252,14 +252,15 @@ typedef struct {
     int32_t candidates; /* configurations timed */
     float best_ms;      /* round-trip time of the chosen configuration */
     float default_ms;   /* round-trip time of the default configuration */
-    int32_t fused;      /* when a plan whose jobs all run on single CTAs (rings of N = 2^k >= 4096)
-                           is one persistent launch (zx_transform_schedule) instead of one
-                           launch per global-memory pass: 0 never (the default), 1 for the TFT
-                           and the ITFT, 2 for the ITFT only; 3: one launch per pass, each a
-                           persistent loop over its jobs that prefetches a CTA's next job
-                           into L2 while it computes the current one. A persistent launch holds every
-                           CTA slot of the GPU until it finishes, so transforms on concurrent
-                           streams stop overlapping; it pays for a transform that runs alone */
+    int32_t fused;      /* launch form of plans whose jobs all run on single CTAs (rings of
+                           N = 2^k >= 4096): 0 one launch per global-memory pass; 1 one
+                           persistent launch per transform (zx_transform_schedule), 2 the same
+                           for the ITFT only; 3 one launch per pass as a persistent loop that
+                           prefetches a CTA's next job into L2; 4 one launch per pass with one
+                           CTA per job through a kernel that needs no register spills (the
+                           default). A persistent launch holds every CTA slot of the GPU until
+                           it finishes, so transforms on concurrent streams stop overlapping;
+                           it pays for a transform that runs alone */
     int32_t max_cluster_log2; /* cluster jobs use at most 2^max_cluster_log2 CTAs (0 .. 4) */
 } zx_tune_info;
 

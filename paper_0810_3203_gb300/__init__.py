@@ -306,12 +306,14 @@ def config_get(N):
 
 
 def config_set(N, cfg=None):
-    """Pin the launch configuration of ring N (a dict like config_get's), or restore the default."""
+    """Pin the launch configuration of ring N (a dict like config_get's; fused and
+    max_cluster_log2 keep their current values when left out), or restore the default."""
     if cfg is None:
         _check(load().zx_config_set(N, None), "zx_config_set")
         return
-    info = ZxTuneInfo(cfg["ls_max"], cfg["ls_c"], cfg["max_warps"], cfg["split"], 0, 0.0, 0.0, cfg.get("fused", 0),
-                      cfg.get("max_cluster_log2", 4))
+    cur = config_get(N)  # fields the dict leaves out keep their current values
+    info = ZxTuneInfo(cfg["ls_max"], cfg["ls_c"], cfg["max_warps"], cfg["split"], 0, 0.0, 0.0,
+                      cfg.get("fused", cur["fused"]), cfg.get("max_cluster_log2", cur["max_cluster_log2"]))
     _check(load().zx_config_set(N, C.byref(info)), "zx_config_set")
 
 

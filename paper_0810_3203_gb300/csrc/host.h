@@ -47,23 +47,28 @@ Ring make_ring(int64_t N);
 // the cells per CTA of a cluster job (ls_c, both log2), the warps per CTA (8 or 16) and the
 // top-level split (0: L1 = 2^floor(l/2) as in the paper, 1: L1 = 2^ceil(l/2)). Every choice
 // computes the same outputs; they differ in speed. zx_tune measures the candidates.
-// fused: whether a plan whose jobs all run on single CTAs is one persistent launch that claims
-// the jobs in dependency order (FusedSchedule) instead of one launch per pass: 0 never (the
-// default), 1 for both transforms, 2 for the ITFT only. Measured on GB300 at l = 16, N = 32768:
-// alone, the persistent ITFT is faster from n = 40000 on (its serial last-row steps overlap with
-// the rest), the TFT slower; with several transforms on concurrent streams, persistent launches
-// hold every CTA slot until they finish and the transforms stop overlapping, so the five-stream
-// benchmark step went from 4.74 to 5.18 ms. zx_tune times single round trips and therefore leaves
-// this setting as it is; zx_config_set chooses it.
-// 3: one launch per pass, each as a persistent loop over its single-CTA jobs that prefetches a
-// CTA's next job into L2 while it computes the current one (FUSED_STREAM; rings that fill all 32
-// lanes).
-enum { FUSED_NONE = 0, FUSED_ALL = 1, FUSED_ITFT = 2, FUSED_STREAM = 3 };
+// fused, the launch form of plans whose jobs all run on single CTAs (rings that fill all 32
+// lanes; other plans always launch job_kernel once per pass):
+//   0 one launch per pass of job_kernel (segment and replica logic included);
+//   1 one persistent launch per transform that claims the jobs in dependency order
+//     (FusedSchedule), 2 the same for the ITFT only;
+//   3 one launch per pass as a persistent loop over its jobs that prefetches a CTA's next job into
+//     L2 while it computes the current one;
+//   4 one launch per pass, one CTA per job, through the persistent kernels' instantiation: the
+//     default. That job body fits the registers of three CTAs per SM without spilling (job_kernel
+//     spills about 170 bytes a thread, which the 30 KB of L1 beside the shared memory cannot hold),
+//     and it ran 4 % faster on GB300.
+// Measured at l = 16, N = 32768: alone, the persistent ITFT is faster from n = 40000 on, the TFT
+// slower; with several transforms on concurrent streams, persistent launches hold every CTA slot
+// until they finish and the transforms stop overlapping (the five-stream benchmark step went from
+// 4.74 to 5.18 ms). zx_tune times single round trips and therefore leaves this setting as it is;
+// zx_config_set chooses it.
+enum { FUSED_NONE = 0, FUSED_ALL = 1, FUSED_ITFT = 2, FUSED_STREAM = 3, FUSED_DIRECT = 4 };
 inline bool fused_for(int fused, int kind) { return fused == FUSED_ALL || (fused == FUSED_ITFT && kind == KIND_ITFT); }
 // max_lc caps cluster jobs at 2^max_lc CTAs (at most kMaxClusterLog2). split 2: at every level,
 // the split with the fewest global-memory passes below it (ties: the one nearest to balanced).
 struct PlanConfig {
-  int ls_max = 0, ls_c = 0, max_warps = 16, split = 0, fused = FUSED_NONE, max_lc = 4;
+  int ls_max = 0, ls_c = 0, max_warps = 16, split = 0, fused = FUSED_DIRECT, max_lc = 4;
 };
 PlanConfig default_config(const Ring &r);
 bool config_valid(const Ring &r, const PlanConfig &c);
@@ -123,8 +128,9 @@ struct TransformPlan {
   int f_njobs = 0, f_ls = 0, f_nwarps = 0, f_prog_words = 0;
   const JobDesc *f_jobs = nullptr;
   const int32_t *f_dep_off = nullptr, *f_deps = nullptr;
-  // launches of single-CTA jobs run as persistent loops with L2 prefetch (FUSED_STREAM)
-  bool stream = false;
+  // launches of single-CTA jobs run as persistent loops with L2 prefetch (FUSED_STREAM), or
+  // through the same kernel with one CTA per job (FUSED_DIRECT)
+  bool stream = false, direct = false;
 };
 
 // Cached plan of TFT (kind = KIND_TFT) or ITFT for the given parameters; nullptr with *err set

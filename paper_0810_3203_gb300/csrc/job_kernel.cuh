@@ -778,6 +778,12 @@ static cudaError_t launch_km(const Launch &L, uint64_t *x, int64_t stride_limbs,
     int sms = 0;
     if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
     cfg.gridDim = dim3(unsigned(std::max(1, std::min(fa.njobs, std::max(1, per_sm) * sms))));
+    if (!fa.sync && fa.njobs < 0) {
+      // one CTA per job: the streaming kernel's loop runs once and prefetches nothing
+      cfg.gridDim = dim3(unsigned(-fa.njobs));
+      return cudaLaunchKernelEx(&cfg, job_kernel_stream<K, MINB, FULL, SQ>, x, stride_limbs, fa.jobs, -fa.njobs,
+                                int(r.N), L.ls, mask, prog_cap, fault);
+    }
     if (!fa.sync)
       return cudaLaunchKernelEx(&cfg, job_kernel_stream<K, MINB, FULL, SQ>, x, stride_limbs, fa.jobs, fa.njobs,
                                 int(r.N), L.ls, mask, prog_cap, fault);

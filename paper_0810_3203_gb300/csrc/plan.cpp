@@ -74,7 +74,7 @@ bool config_valid(const Ring &r, const PlanConfig &c) {
   auto fits = [&](int ls) { return ls >= 1 && ls <= 16 && size_t(1) << ls <= 65536 &&
                                    (size_t(1) << ls) * (size_t(r.pitch) + 1) * 4 <= kSmemBudget; };
   return fits(c.ls_max) && fits(c.ls_c) && c.ls_c <= c.ls_max + 1 && (c.max_warps == 8 || c.max_warps == 16) &&
-         (c.split >= 0 && c.split <= 2) && (c.fused >= FUSED_NONE && c.fused <= FUSED_STREAM) && c.max_lc >= 0 &&
+         (c.split >= 0 && c.split <= 2) && (c.fused >= FUSED_NONE && c.fused <= FUSED_DIRECT) && c.max_lc >= 0 &&
          c.max_lc <= kMaxClusterLog2;
 }
 
@@ -634,7 +634,9 @@ const TransformPlan *get_transform_plan(int kind, int l, int64_t z, int64_t n, i
   }
   (void)stride_limbs;
   // the fused form: every job single-CTA, more than one launch, not replicated
-  plan->stream = cfg.fused == FUSED_STREAM && !replicated && P.ring.K >= 4 && P.ring.G == 32;
+  plan->stream = (cfg.fused == FUSED_STREAM || cfg.fused == FUSED_DIRECT) && !replicated && P.ring.K >= 4 &&
+                 P.ring.G == 32;
+  plan->direct = cfg.fused == FUSED_DIRECT;
   // (the persistent kernel is built for rings whose words fill all 32 lanes, four or more words
   // per lane: N a power of two from 4096 on)
   bool fusable = fused_for(cfg.fused, kind) && !replicated && plan->launches.size() > 1 && P.ring.K >= 4 &&

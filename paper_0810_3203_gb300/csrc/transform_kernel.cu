@@ -46,7 +46,8 @@ cudaError_t run_transform_reps(const TransformPlan &p, uint64_t *x, int64_t stri
     if (reps > 1 && L.nsegs != 0) return cudaErrorInvalidValue;
     cudaError_t e;
     if (p.stream && reps == 1 && L.nsegs == 0 && L.lc == 0 && p.ring.K >= 4 && p.ring.G == 32) {
-      const FusedArgs plain = {L.d_jobs, nullptr, nullptr, nullptr, L.njobs};
+      // direct: sync is null and njobs negative, one CTA per job (see launch_km)
+      const FusedArgs plain = {L.d_jobs, nullptr, nullptr, nullptr, p.direct ? -L.njobs : L.njobs};
       e = p.ring.K == 32 ? launch_fused_k32(p, x, stride_limbs, s, plain, fault, &L)
                          : launch_fused_small(p, x, stride_limbs, s, plain, fault, &L);
     } else {
