@@ -381,6 +381,8 @@ def run_gpu(args):
     # (the tuner keeps it)
     if args.fused >= 0:
         tg.config_set(N, dict(tg.config_get(N), fused=args.fused))
+    if args.tma >= 0:
+        tg.config_set(N, dict(tg.config_get(N), tma=args.tma))
     tuned = None if args.no_tune else tg.tune(dev[40000 if 40000 in dev else ns[0]], l, 40000 if 40000 in dev else ns[0],
                                               N, stride, reps=2, stream=stream)
 
@@ -557,9 +559,9 @@ def run_gpu(args):
                      "plan_bytes_unit": "bytes the plan's jobs read and write in one TFT call at n = 40000 "
                                         "(from zx_transform_jobs; stores still dirty in L2 when a launch ends "
                                         "escape the kernel's ncu counters)",
-                     "kernel": "job_kernel_stream<32> run with one CTA per job (every launch of the TFT and "
-                               "ITFT calls; the only kernel of the timed region, its time the region's device "
-                               "time)"},
+                     "kernel": "job_kernel_stream<32> run with one CTA per job, one tensor copy per cell in "
+                               "and out (every launch of the TFT and ITFT calls; the only kernel of the timed "
+                               "region, its time the region's device time)"},
         "per_n_ms": {str(n): [round(a, 3), round(b, 3)] for n, (a, b) in per_n.items()},
         "smoothness": {str(n): round((per_n[n][0] + per_n[n][1]) / (per_n[ns[-1]][0] + per_n[ns[-1]][1]), 4)
                        for n in ns},
@@ -1012,17 +1014,32 @@ def run_profile_case(args):
         tg.config_set(N, {"ls_max": ls_max, "ls_c": ls_c, "max_warps": mw, "split": sp})
     if args.fused >= 0:
         tg.config_set(N, dict(tg.config_get(N), fused=args.fused))
+    if args.tma >= 0:
+        tg.config_set(N, dict(tg.config_get(N), tma=args.tma))
     W = N // 64 + 1
     stride = cell_stride(W, args.stride)
     x = workloads.residues(WORKLOAD["seed"], n, N, stride=stride, cells=1 << l)
     d = torch.from_numpy(x.view(np.int64)).cuda()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    t_tft, t_itft = [], []
     for _ in range(args.profile_reps):
+        ev[0].record()
         tg.tft_ex(d, l, n, n, N, 0, stride)
+        ev[1].record()
         tg.itft_ex(d, l, n, n, 0, N, 0, stride, 1)
+        ev[2].record()
+        ev[2].synchronize()
+        t_tft.append(ev[0].elapsed_time(ev[1]))
+        t_itft.append(ev[1].elapsed_time(ev[2]))
     torch.cuda.synchronize()
     back = d.view(-1, stride)[:n, :W].cpu().numpy().view(np.uint64)
     ok = bool(np.array_equal(back, x.reshape(-1, stride)[:n, :W]))
-    print(json.dumps({"profile_case": "tft+itft n=40000 l=16 N=32768", "reps": args.profile_reps, "ok": ok}))
+    out = {"profile_case": "tft+itft n=40000 l=16 N=32768", "reps": args.profile_reps, "ok": ok,
+           "config": tg.config_get(N)}
+    if args.profile_reps > 1:  # the first call plans and warms up
+        out["tft_ms_median"] = round(float(np.median(t_tft[1:])), 4)
+        out["itft_ms_median"] = round(float(np.median(t_itft[1:])), 4)
+    print(json.dumps(out))
     return 0 if ok else 1
 
 
@@ -1048,6 +1065,9 @@ def main():
                     help="launch form of the large transforms (zx_tune_info.fused: 0 one launch per pass, 1 and "
                          "2 persistent, 3 per-pass persistent loops with L2 prefetch, 4 one launch per pass through "
                          "the spill-free kernel); default: the library's")
+    ap.add_argument("--tma", type=int, default=-1,
+                    help="cell copies of the large transforms (zx_tune_info.tma: 1 one tensor copy per cell, 0 row "
+                         "copies and 16-byte stores); default: the library's")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving leg")
     ap.add_argument("--no-e1", action="store_true", help="skip the Sec. 5.1-shaped product sweep")
     ap.add_argument("--serve-requests", type=int, default=1000)

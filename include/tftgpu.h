@@ -262,13 +262,18 @@ typedef struct {
                            it finishes, so transforms on concurrent streams stop overlapping;
                            it pays for a transform that runs alone */
     int32_t max_cluster_log2; /* cluster jobs use at most 2^max_cluster_log2 CTAs (0 .. 4) */
+    int32_t tma;        /* 1 (default): launches of the forms 3 and 4 move each cell with one
+                           tensor (TMA) copy for rings of 8 or more words per lane (N = 8192,
+                           16384, 32768) when the buffer is 16-byte aligned with an even
+                           stride_limbs >= W + 1; 0: row copies and 16-byte stores. Kept as it is
+                           by zx_tune */
 } zx_tune_info;
 
 int zx_tune(uint64_t *x, int l, int64_t n, int64_t N, int64_t stride_limbs, int reps, void *stream,
             zx_tune_info *out);
 
 /* The launch configuration used for ring N (ls_max, ls_c, max_warps, split, fused,
- * max_cluster_log2; the other fields are zero; a tuned configuration is kept as zx_tune chose it), and pinning one, e.g. a result of zx_tune saved from an earlier process. zx_config_set
+ * max_cluster_log2, tma; the other fields are zero; a tuned configuration is kept as zx_tune chose it), and pinning one, e.g. a result of zx_tune saved from an earlier process. zx_config_set
  * returns ZX_EINVAL for a configuration the ring cannot run (shared memory, warps, split); with
  * cfg == NULL it restores the default. Host only. */
 int zx_config_get(int64_t N, zx_tune_info *out);

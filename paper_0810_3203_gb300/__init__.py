@@ -55,7 +55,7 @@ class ZxPlanInfo(C.Structure):
 class ZxTuneInfo(C.Structure):
     _fields_ = [("ls_max", C.c_int32), ("ls_c", C.c_int32), ("max_warps", C.c_int32), ("split", C.c_int32),
                 ("candidates", C.c_int32), ("best_ms", C.c_float), ("default_ms", C.c_float), ("fused", C.c_int32),
-                ("max_cluster_log2", C.c_int32)]
+                ("max_cluster_log2", C.c_int32), ("tma", C.c_int32)]
 
 
 class ZxServerInfo(C.Structure):
@@ -299,21 +299,23 @@ def sn_itft(x, l, z, n, f, M, m, e=0, stride=None, scale=0, stream=None):
 
 
 def config_get(N):
-    """Launch configuration used for ring N: ls_max, ls_c, max_warps, split, fused, max_cluster_log2."""
+    """Launch configuration used for ring N: ls_max, ls_c, max_warps, split, fused, max_cluster_log2,
+    tma."""
     info = ZxTuneInfo()
     _check(load().zx_config_get(N, C.byref(info)), "zx_config_get")
-    return {k: getattr(info, k) for k in ("ls_max", "ls_c", "max_warps", "split", "fused", "max_cluster_log2")}
+    return {k: getattr(info, k) for k in ("ls_max", "ls_c", "max_warps", "split", "fused", "max_cluster_log2", "tma")}
 
 
 def config_set(N, cfg=None):
-    """Pin the launch configuration of ring N (a dict like config_get's; fused and
-    max_cluster_log2 keep their current values when left out), or restore the default."""
+    """Pin the launch configuration of ring N (a dict like config_get's; fused, max_cluster_log2
+    and tma keep their current values when left out), or restore the default."""
     if cfg is None:
         _check(load().zx_config_set(N, None), "zx_config_set")
         return
     cur = config_get(N)  # fields the dict leaves out keep their current values
     info = ZxTuneInfo(cfg["ls_max"], cfg["ls_c"], cfg["max_warps"], cfg["split"], 0, 0.0, 0.0,
-                      cfg.get("fused", cur["fused"]), cfg.get("max_cluster_log2", cur["max_cluster_log2"]))
+                      cfg.get("fused", cur["fused"]), cfg.get("max_cluster_log2", cur["max_cluster_log2"]),
+                      cfg.get("tma", cur["tma"]))
     _check(load().zx_config_set(N, C.byref(info)), "zx_config_set")
 
 

@@ -475,6 +475,7 @@ int zx_tune(uint64_t *x, int l, int64_t n, int64_t N, int64_t stride_limbs, int 
   std::vector<PlanConfig> cands;
   PlanConfig def_kept = def;
   def_kept.fused = before.fused;
+  def_kept.tma = before.tma;
   cands.push_back(def_kept);
   for (int ls_max : {def.ls_max, ls3})
     for (int ls_c = 3; ls_c <= 6; ls_c++)
@@ -490,6 +491,7 @@ int zx_tune(uint64_t *x, int l, int64_t n, int64_t N, int64_t stride_limbs, int 
             c.split = sp;
             c.max_lc = mlc;
             c.fused = before.fused;  // kept as it is (see PlanConfig)
+            c.tma = before.tma;
             if (!config_valid(r, c)) continue;
             bool dup = false;
             for (const PlanConfig &o : cands)
@@ -546,6 +548,7 @@ int zx_tune(uint64_t *x, int l, int64_t n, int64_t N, int64_t stride_limbs, int 
   out->split = chosen.split;
   out->fused = chosen.fused;
   out->max_cluster_log2 = chosen.max_lc;
+  out->tma = chosen.tma;
   out->candidates = int32_t(cands.size());
   out->best_ms = best;
   out->default_ms = def_ms;
@@ -592,6 +595,7 @@ int zx_config_get(int64_t N, zx_tune_info *out) {
   out->split = c.split;
   out->fused = c.fused;
   out->max_cluster_log2 = c.max_lc;
+  out->tma = c.tma;
   return ZX_OK;
 }
 
@@ -609,6 +613,7 @@ int zx_config_set(int64_t N, const zx_tune_info *cfg) {
   c.split = cfg->split;
   c.fused = cfg->fused;
   c.max_lc = cfg->max_cluster_log2;
+  c.tma = cfg->tma;
   if (!config_valid(r, c)) return fail(ZX_EINVAL, "configuration not valid for this ring");
   set_plan_config(N, c);
   return ZX_OK;

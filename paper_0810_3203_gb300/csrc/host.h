@@ -67,8 +67,11 @@ enum { FUSED_NONE = 0, FUSED_ALL = 1, FUSED_ITFT = 2, FUSED_STREAM = 3, FUSED_DI
 inline bool fused_for(int fused, int kind) { return fused == FUSED_ALL || (fused == FUSED_ITFT && kind == KIND_ITFT); }
 // max_lc caps cluster jobs at 2^max_lc CTAs (at most kMaxClusterLog2). split 2: at every level,
 // the split with the fewest global-memory passes below it (ties: the one nearest to balanced).
+// tma 1: the per-pass launches of single-CTA jobs (fused 3 and 4) move whole cells with one
+// tensor copy each (CellMaps) where the ring and the buffer allow it; 0: row copies and 16-byte
+// stores everywhere.
 struct PlanConfig {
-  int ls_max = 0, ls_c = 0, max_warps = 16, split = 0, fused = FUSED_DIRECT, max_lc = 4;
+  int ls_max = 0, ls_c = 0, max_warps = 16, split = 0, fused = FUSED_DIRECT, max_lc = 4, tma = 1;
 };
 PlanConfig default_config(const Ring &r);
 bool config_valid(const Ring &r, const PlanConfig &c);
@@ -131,6 +134,10 @@ struct TransformPlan {
   // launches of single-CTA jobs run as persistent loops with L2 prefetch (FUSED_STREAM), or
   // through the same kernel with one CTA per job (FUSED_DIRECT)
   bool stream = false, direct = false;
+  bool tma = false;  // PlanConfig::tma
+  // one more than the largest cell index a job of the plan reads or writes (the extent of the
+  // tensor maps of a call's buffer)
+  int64_t cell_extent = 0;
 };
 
 // Cached plan of TFT (kind = KIND_TFT) or ITFT for the given parameters; nullptr with *err set

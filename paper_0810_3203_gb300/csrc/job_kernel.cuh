@@ -10,6 +10,7 @@
 #pragma once
 
 #include <cooperative_groups.h>
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -292,6 +293,42 @@ __device__ __forceinline__ void bulk_load_cells(uint32_t *cells, uint32_t *tops,
   }
 }
 
+// Tensor (TMA) copies of whole cells, for rings of 8 or more 32-word rows (K >= 8) whose cells
+// are 16-byte aligned with room for the top limb and the limb after it (stride >= W + 1). The
+// maps (CellMaps, built per transform call by make_cell_maps) view the call's buffer as
+// [cell][row][word] with 32-word rows. The load map's rows are 36 words long, so they overlap
+// the next row by 4 words: one copy fills a cell's padded shared-memory rows (36-word pitch)
+// directly, and the pad of its last row receives the top limb and the limb after it. The store
+// map's rows are 32 words long and its box 36: the pad words fall outside the map and are not
+// written, so a copy stores exactly the N-bit part; the top limb is stored separately.
+struct CellMaps {
+  CUtensorMap ld, st;
+  int mode;  // bit 0: load map valid, bit 1: store map valid
+};
+
+// words of a cell's box (rows of 36 words)
+__host__ __device__ __forceinline__ int cell_box_words(int NW) { return (NW >> 5) * 36; }
+
+__device__ __forceinline__ void tensor_load_cell(uint32_t dst_smem, const CUtensorMap *tm, int cell, uint32_t mb) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+      "[%5];" ::"r"(dst_smem),
+      "l"(reinterpret_cast<uint64_t>(tm)), "r"(0), "r"(0), "r"(cell), "r"(mb)
+      : "memory");
+}
+
+// one cell from shared memory to the caller's buffer as its own bulk group
+__device__ __forceinline__ void tensor_store_cell(const CUtensorMap *tm, int cell, uint32_t src_smem) {
+  asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.tile.bulk_group [%0, {%1, %2, %3}], [%4];" ::"l"(
+                   reinterpret_cast<uint64_t>(tm)),
+               "r"(0), "r"(0), "r"(cell), "r"(src_smem)
+               : "memory");
+  asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+
+// orders this thread's generic shared-memory accesses with later bulk (async proxy) copies
+__device__ __forceinline__ void fence_async_shared() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
 // cell index of the job held at `slot` of CTA `rank` in the given layout
 __device__ __forceinline__ int job_cell(uint32_t layout, int rank, int slot, int C, int L2, int b) {
   if (C == 1) return slot;
@@ -402,9 +439,11 @@ struct FusedArgs {
 // milliseconds).
 constexpr uint64_t kDepWaitNs = 2000000000ull;
 
-// Dynamic shared memory a job kernel may take: the 227 KB of a block less the kernel's static
-// claim word (with room for its alignment).
-constexpr size_t kJobDynSmem = 227 * 1024 - 64;
+// Dynamic shared memory a job kernel may take: the 227 KB of a block less the persistent
+// kernel's static claim word, which the 128-byte alignment of the dynamic cells (tensor copies)
+// rounds up to 128 bytes.
+constexpr size_t kJobStaticSmem = 128;
+constexpr size_t kJobDynSmem = 227 * 1024 - kJobStaticSmem;
 
 __device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t *p) {
   uint32_t v;
@@ -451,10 +490,17 @@ TFT_HD inline int job_stage_word(int nslots, int pitch) { return job_tops_word(n
 //
 // SINGLE: the launch runs single-CTA jobs only (lc = 0 at compile time), which drops the cluster
 // exchange and its registers from the kernel.
-template <int K, bool SQ, bool SINGLE>
+// TM = 3: the cells move through the call's tensor maps tm_ld / tm_st (CellMaps, kernel
+// parameters) and nothing else is compiled; the host launches it only where make_cell_maps
+// succeeded, and the shared-memory alignment the copies need is that of the declaration below
+// (a CTA that finds it otherwise sets bit 4 of the status word and runs nothing). TM = 0: row
+// copies and 16-byte stores. The two are separate instantiations: carrying both paths in one
+// body costs the three-CTAs-per-SM job its spill-free register budget.
+template <int K, bool SQ, bool SINGLE, int TM = 0>
 __device__ __forceinline__ bool run_job(const JobDesc &jd, uint64_t *__restrict__ x, int64_t stride_limbs, int ls,
-                                        int lc, const KGeo &kg, int prog_cap, uint32_t *fault) {
-  extern __shared__ uint32_t smem[];
+                                        int lc, const KGeo &kg, int prog_cap, uint32_t *fault,
+                                        const CUtensorMap *tm_ld = nullptr, const CUtensorMap *tm_st = nullptr) {
+  extern __shared__ __align__(128) uint32_t smem[];
   if (SINGLE) lc = 0;
   const int C = 1 << lc;
   const int rank = int(blockIdx.x) & (C - 1);
@@ -495,20 +541,39 @@ __device__ __forceinline__ bool run_job(const JobDesc &jd, uint64_t *__restrict_
 
   // load into shared memory, then the storage form m = x - 1
   const bool vec16 = ((reinterpret_cast<uintptr_t>(x) & 15) == 0) && ((stride_limbs & 1) == 0);
-  if (K >= 4 && vec16 && C == 1 && (g.NW & 31) == 0 && stride_limbs > g.NW / 2 + 1) {
-    // single-CTA job (slot s holds cell s): bulk copies of whole rows, then each cell's top limb
+  if constexpr (TM != 0) {
+    // tensor copies need 128-byte aligned cells: rows of 36 words in multiples of 8 rows
+    if (!(C == 1 && vec16 && ((g.NW >> 5) & 7) == 0 && (uint32_t(__cvta_generic_to_shared(cells)) & 127u) == 0)) {
+      if (threadIdx.x == 0) atomicOr(fault, 4u);
+      return false;
+    }
+  }
+  if (TM != 0 || (K >= 4 && vec16 && C == 1 && (g.NW & 31) == 0 && stride_limbs > g.NW / 2 + 1)) {
+    // single-CTA job (slot s holds cell s): one tensor copy per cell (its top limb lands in the
+    // pad of its last row), or bulk copies of whole rows and of each cell's top limb
     const int nl = jd.nload < nslots ? jd.nload : nslots;
     const uint32_t mb = uint32_t(__cvta_generic_to_shared(mbar));
+    constexpr bool tens = TM != 0;
     if (threadIdx.x == 0) {
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb) : "memory");
       asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
     __syncthreads();
-    const uint64_t *x0 = x + jd.cell0 * stride_limbs;
-    const int64_t cstep = jd.mstride * stride_limbs;
-    bulk_load_cells(cells, tops, P, nl, mb, g.NW, warp, nw, g.lane,
-                    [&](int s) { return x0 + int64_t(s) * cstep; });
+    if constexpr (tens) {
+      if (threadIdx.x == 0) {
+        const uint32_t bytes = uint32_t(nl) * uint32_t(cell_box_words(g.NW)) * 4u;
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mb), "r"(bytes) : "memory");
+        for (int s = 0; s < nl; s++)
+          tensor_load_cell(uint32_t(__cvta_generic_to_shared(cells + s * P)), tm_ld,
+                           int(jd.cell0 + int64_t(s) * jd.mstride), mb);
+      }
+    } else {
+      const uint64_t *x0 = x + jd.cell0 * stride_limbs;
+      const int64_t cstep = jd.mstride * stride_limbs;
+      bulk_load_cells(cells, tops, P, nl, mb, g.NW, warp, nw, g.lane,
+                      [&](int s) { return x0 + int64_t(s) * cstep; });
+    }
     stage_first_program();
     // One thread waits for the copies; the others wait at the barrier, which takes no issue
     // slots from the butterflies of the other CTAs on the SM (the waiting thread polls without
@@ -524,7 +589,7 @@ __device__ __forceinline__ bool run_job(const JobDesc &jd, uint64_t *__restrict_
       return false;
     }
     for (int s = warp; s < nl; s += nw) {
-      const uint64_t T = *reinterpret_cast<const uint64_t *>(tops + 4 * s);
+      const uint64_t T = *reinterpret_cast<const uint64_t *>(tens ? cells + s * P + P - 4 : tops + 4 * s);
       if (T & kRawTopMark) {
         // written by an earlier pass in internal form: the words are m, the top limb the metadata
         if (g.lane == 0) meta[s] = uint32_t(T);
@@ -582,7 +647,10 @@ __device__ __forceinline__ bool run_job(const JobDesc &jd, uint64_t *__restrict_
   }
 
   // store: x = rotc(m, t) + 1, with the final scaling where requested; or, when a later pass
-  // stores these cells again, m as it is with the rotation and zero flag in the top limb
+  // stores these cells again, m as it is with the rotation and zero flag in the top limb.
+  // TM: each warp leaves its cells' final form in their slots and stores their top limbs, then one
+  // thread issues a tensor copy per cell. Else each warp stores its cells with coalesced 16-byte
+  // stores, through the cell's own slot (no longer needed) when the value changes form.
   const bool raw = (jd.pad & JOB_RAW_STORE) != 0;
   for (int s = warp; s < nslots; s += nw) {
     const int m = job_cell(store_layout, rank, s, C, L2, b);
@@ -592,7 +660,12 @@ __device__ __forceinline__ bool run_job(const JobDesc &jd, uint64_t *__restrict_
     if (E >= kg.ord) E -= kg.ord;
     uint64_t *gc = x + (jd.cell0 + int64_t(m) * jd.mstride) * stride_limbs;
     if (raw) {
-      smem_to_gmem_cell<K>(gc, cells + s * P, kRawTopMark | (uint64_t(E) << 1) | (meta[s] & 1u), vec16, g);
+      const uint64_t T = kRawTopMark | (uint64_t(E) << 1) | (meta[s] & 1u);
+      if constexpr (TM != 0) {
+        if (g.lane == 0) gc[g.NW / 2] = T;
+      } else {
+        smem_to_gmem_cell<K>(gc, cells + s * P, T, vec16, g);
+      }
       continue;
     }
     const int z = read_omega_pow<K, SQ>(r, cells + s * P, int(meta[s] & 1u), E, g);
@@ -603,11 +676,26 @@ __device__ __forceinline__ bool run_job(const JobDesc &jd, uint64_t *__restrict_
     } else {
       top = add_small<K>(r, 1u, g);
     }
-    // through the cell's own slot (no longer needed) so the global writes are coalesced
     __syncwarp();
     smem_store_plain<K>(cells + s * P, r, g);
-    __syncwarp();
-    smem_to_gmem_cell<K>(gc, cells + s * P, top, vec16, g);
+    if constexpr (TM != 0) {
+      if (g.lane == 0) gc[g.NW / 2] = top;
+    } else {
+      __syncwarp();
+      smem_to_gmem_cell<K>(gc, cells + s * P, top, vec16, g);
+    }
+  }
+  if constexpr (TM != 0) {
+    // the cells written in shared memory become visible to the tensor copies, which have read
+    // them before shared memory is reused or released
+    fence_async_shared();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      const int ns = jd.nstore < nslots ? jd.nstore : nslots;
+      for (int s = 0; s < ns; s++)
+        tensor_store_cell(tm_st, int(jd.cell0 + int64_t(s) * jd.mstride), uint32_t(__cvta_generic_to_shared(cells + s * P)));
+      asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+    }
   }
   return true;
 }
@@ -682,10 +770,14 @@ __device__ __forceinline__ void prefetch_job_l2(const JobDesc &jd, const uint64_
 // A plain launch of independent single-CTA jobs as a persistent loop: CTA b runs jobs b, b + G,
 // b + 2 G, ... (G CTAs) and, while it works on one, prefetches the cells of its next one into L2,
 // so that the next job's loads overlap the current job's butterflies.
-template <int K, int MINB, bool FULL, bool SQ>
+// TM = 3: cells move through the tensor maps tm_ld / tm_st (CellMaps); TM = 0: the maps are
+// unused (see run_job).
+template <int K, int MINB, bool FULL, bool SQ, int TM>
 __global__ void __launch_bounds__(MINB == 3 ? 256 : 512, MINB) job_kernel_stream(uint64_t *__restrict__ x,
                                                   int64_t stride_limbs, const JobDesc *__restrict__ jobs, int njobs,
-                                                  int N, int ls, uint32_t mask, int prog_cap, uint32_t *fault) {
+                                                  int N, int ls, uint32_t mask, int prog_cap, uint32_t *fault,
+                                                  const __grid_constant__ CUtensorMap tm_ld,
+                                                  const __grid_constant__ CUtensorMap tm_st) {
   const KGeo kg = make_kgeo<K, FULL, SQ>(N, mask);
   const bool vec16 = ((reinterpret_cast<uintptr_t>(x) & 15) == 0) && ((stride_limbs & 1) == 0);
   for (int k = int(blockIdx.x); k < njobs; k += int(gridDim.x)) {
@@ -694,8 +786,9 @@ __global__ void __launch_bounds__(MINB == 3 ? 256 : 512, MINB) job_kernel_stream
     // the descriptor goes to registers first: passed as a reference into global memory, its fields
     // would be loaded again wherever the job body uses them
     const JobDesc jd = jobs[k];
-    run_job<K, SQ, true>(jd, x, stride_limbs, ls, 0, kg, prog_cap, fault);
-    __syncthreads();  // the job is done with shared memory
+    run_job<K, SQ, true, TM>(jd, x, stride_limbs, ls, 0, kg, prog_cap, fault, &tm_ld, &tm_st);
+    fence_async_shared();  // this job's shared-memory reads come before the next job's bulk copies
+    __syncthreads();       // the job is done with shared memory
   }
 }
 
@@ -713,7 +806,8 @@ __global__ void __launch_bounds__(MINB == 3 ? 256 : 512, MINB) job_kernel_fused(
   const int publisher = blockDim.x > 32 ? 32 : 0;
   uint32_t *done = nullptr;  // done flag of this CTA's previous job, not yet set
   for (;;) {
-    __syncthreads();  // the previous job is done with shared memory and with s_claim
+    fence_async_shared();  // the previous job's shared-memory reads come before the next bulk copies
+    __syncthreads();       // the previous job is done with shared memory and with s_claim
     if (int(threadIdx.x) == publisher && done) {
       __threadfence();
       st_release_u32(done, 1u);
@@ -736,7 +830,7 @@ __global__ void __launch_bounds__(MINB == 3 ? 256 : 512, MINB) job_kernel_fused(
 template <int K, int MINB, bool FULL, bool SQ, bool FUSED>
 static cudaError_t launch_km(const Launch &L, uint64_t *x, int64_t stride_limbs, const Ring &r, cudaStream_t s,
                       size_t smem, int prog_cap, uint32_t mask, int64_t reps, int64_t rep_cells, const FusedArgs &fa,
-                      uint32_t *fault) {
+                      uint32_t *fault, const CellMaps *cm) {
   static thread_local int configured[8] = {0, 0, 0, 0, 0, 0, 0, 0};
   int dev = 0;
   cudaGetDevice(&dev);
@@ -746,8 +840,12 @@ static cudaError_t launch_km(const Launch &L, uint64_t *x, int64_t stride_limbs,
       e = cudaFuncSetAttribute(job_kernel_fused<K, MINB, FULL, SQ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                int(kJobDynSmem));
       if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(job_kernel_stream<K, MINB, FULL, SQ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        e = cudaFuncSetAttribute(job_kernel_stream<K, MINB, FULL, SQ, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  int(kJobDynSmem));
+      if constexpr (K >= 8)
+        if (e == cudaSuccess)
+          e = cudaFuncSetAttribute(job_kernel_stream<K, MINB, FULL, SQ, 3>,
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize, int(kJobDynSmem));
     } else {
       e = cudaFuncSetAttribute(job_kernel<K, MINB, FULL, SQ, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                int(kJobDynSmem));
@@ -772,21 +870,24 @@ static cudaError_t launch_km(const Launch &L, uint64_t *x, int64_t stride_limbs,
     int per_sm = 0;
     cudaError_t e = fa.sync ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, job_kernel_fused<K, MINB, FULL, SQ>,
                                                                            L.nwarps * 32, smem)
-                            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, job_kernel_stream<K, MINB, FULL, SQ>,
+                            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, job_kernel_stream<K, MINB, FULL, SQ, 0>,
                                                                            L.nwarps * 32, smem);
     if (e != cudaSuccess) return e;
     int sms = 0;
     if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
     cfg.gridDim = dim3(unsigned(std::max(1, std::min(fa.njobs, std::max(1, per_sm) * sms))));
-    if (!fa.sync && fa.njobs < 0) {
-      // one CTA per job: the streaming kernel's loop runs once and prefetches nothing
-      cfg.gridDim = dim3(unsigned(-fa.njobs));
-      return cudaLaunchKernelEx(&cfg, job_kernel_stream<K, MINB, FULL, SQ>, x, stride_limbs, fa.jobs, -fa.njobs,
-                                int(r.N), L.ls, mask, prog_cap, fault);
+    if (!fa.sync) {
+      // one CTA per job (njobs < 0): the streaming kernel's loop runs once and prefetches nothing
+      const int nj = fa.njobs < 0 ? -fa.njobs : fa.njobs;
+      if (fa.njobs < 0) cfg.gridDim = dim3(unsigned(nj));
+      if constexpr (K >= 8)
+        if (cm && cm->mode == 3)
+          return cudaLaunchKernelEx(&cfg, job_kernel_stream<K, MINB, FULL, SQ, 3>, x, stride_limbs, fa.jobs, nj,
+                                    int(r.N), L.ls, mask, prog_cap, fault, cm->ld, cm->st);
+      static const CellMaps no_maps = {};
+      return cudaLaunchKernelEx(&cfg, job_kernel_stream<K, MINB, FULL, SQ, 0>, x, stride_limbs, fa.jobs, nj,
+                                int(r.N), L.ls, mask, prog_cap, fault, no_maps.ld, no_maps.st);
     }
-    if (!fa.sync)
-      return cudaLaunchKernelEx(&cfg, job_kernel_stream<K, MINB, FULL, SQ>, x, stride_limbs, fa.jobs, fa.njobs,
-                                int(r.N), L.ls, mask, prog_cap, fault);
     return cudaLaunchKernelEx(&cfg, job_kernel_fused<K, MINB, FULL, SQ>, x, stride_limbs, int(r.N), L.ls, mask,
                               prog_cap, fa, fault);
   } else {
@@ -824,7 +925,8 @@ static int sm_count() {
 
 template <int K, bool SQ, bool FUSED>
 static cudaError_t launch_k(const Launch &L, uint64_t *x, int64_t stride_limbs, const Ring &r, cudaStream_t s,
-                     int64_t reps, int64_t rep_cells, const FusedArgs &fa, uint32_t *fault) {
+                     int64_t reps, int64_t rep_cells, const FusedArgs &fa, uint32_t *fault,
+                     const CellMaps *cm = nullptr) {
   const int nslots = 1 << (L.ls - L.lc);
   // cells, their metadata, the load's mbarrier and the top limbs (job_stage_word)
   const size_t base_words = size_t(job_stage_word(nslots, r.pitch));
@@ -834,7 +936,8 @@ static cudaError_t launch_k(const Launch &L, uint64_t *x, int64_t stride_limbs, 
   // CTAs to fill the SMs three deep (a smaller launch gives each CTA all of its warps instead);
   // the program is staged in shared memory only if it fits beside the cells (else its ops are
   // read through the read-only path)
-  const size_t small_words = (75 * 1024 - 64) / 4;  // three per SM beside the static claim word
+  // three CTAs per SM: 228 KB less 1 KB reserved per CTA, beside the static claim word
+  const size_t small_words = (75 * 1024 - kJobStaticSmem) / 4;
   const int64_t ctas = (int64_t(L.njobs) << L.lc) * reps;
   if (base_words <= small_words && (L.nwarps <= 8 || ctas >= 3 * int64_t(sm_count()))) {
     Launch L8 = L;
@@ -844,10 +947,10 @@ static cudaError_t launch_k(const Launch &L, uint64_t *x, int64_t stride_limbs, 
     // (the persistent form is built for rings that fill all 32 lanes only)
     if constexpr (FUSED) {
       if (r.G != 32) return cudaErrorInvalidValue;
-      return launch_km<K, 3, true, SQ, FUSED>(L8, x, stride_limbs, r, s, smem, cap, mask, reps, rep_cells, fa, fault);
+      return launch_km<K, 3, true, SQ, FUSED>(L8, x, stride_limbs, r, s, smem, cap, mask, reps, rep_cells, fa, fault, cm);
     } else {
-      if (r.G == 32) return launch_km<K, 3, true, SQ, FUSED>(L8, x, stride_limbs, r, s, smem, cap, mask, reps, rep_cells, fa, fault);
-      return launch_km<K, 3, false, SQ, FUSED>(L8, x, stride_limbs, r, s, smem, cap, mask, reps, rep_cells, fa, fault);
+      if (r.G == 32) return launch_km<K, 3, true, SQ, FUSED>(L8, x, stride_limbs, r, s, smem, cap, mask, reps, rep_cells, fa, fault, cm);
+      return launch_km<K, 3, false, SQ, FUSED>(L8, x, stride_limbs, r, s, smem, cap, mask, reps, rep_cells, fa, fault, cm);
     }
   }
   const size_t max_words = kJobDynSmem / 4;
@@ -855,10 +958,10 @@ static cudaError_t launch_k(const Launch &L, uint64_t *x, int64_t stride_limbs, 
   const size_t smem = (base_words + size_t(prog_cap)) * 4;
   if constexpr (FUSED) {
     if (r.G != 32) return cudaErrorInvalidValue;
-    return launch_km<K, 1, true, SQ, FUSED>(L, x, stride_limbs, r, s, smem, prog_cap, mask, reps, rep_cells, fa, fault);
+    return launch_km<K, 1, true, SQ, FUSED>(L, x, stride_limbs, r, s, smem, prog_cap, mask, reps, rep_cells, fa, fault, cm);
   } else {
-    if (r.G == 32) return launch_km<K, 1, true, SQ, FUSED>(L, x, stride_limbs, r, s, smem, prog_cap, mask, reps, rep_cells, fa, fault);
-    return launch_km<K, 1, false, SQ, FUSED>(L, x, stride_limbs, r, s, smem, prog_cap, mask, reps, rep_cells, fa, fault);
+    if (r.G == 32) return launch_km<K, 1, true, SQ, FUSED>(L, x, stride_limbs, r, s, smem, prog_cap, mask, reps, rep_cells, fa, fault, cm);
+    return launch_km<K, 1, false, SQ, FUSED>(L, x, stride_limbs, r, s, smem, prog_cap, mask, reps, rep_cells, fa, fault, cm);
   }
 }
 
@@ -884,10 +987,16 @@ TFT_DECLARE_LAUNCHES(32, sq);
 #undef TFT_DECLARE_LAUNCHES
 // fa.sync null: the plain launch *plain (single-CTA jobs, no segments or replicas) in the
 // persistent streaming form (job_kernel_stream)
+// (cm: the call's tensor maps, or null)
 cudaError_t launch_fused_small(const TransformPlan &p, uint64_t *x, int64_t stride_limbs, cudaStream_t s,
-                               const FusedArgs &fa, uint32_t *fault, const Launch *plain = nullptr);  // K = 4, 8, 16
+                               const FusedArgs &fa, uint32_t *fault, const Launch *plain = nullptr,
+                               const CellMaps *cm = nullptr);  // K = 4, 8, 16
 cudaError_t launch_fused_k32(const TransformPlan &p, uint64_t *x, int64_t stride_limbs, cudaStream_t s,
-                             const FusedArgs &fa, uint32_t *fault, const Launch *plain = nullptr);
+                             const FusedArgs &fa, uint32_t *fault, const Launch *plain = nullptr,
+                             const CellMaps *cm = nullptr);
+// Tensor maps of the cells a plan touches in the buffer x (CellMaps); false (mode 0) when the
+// ring or the buffer does not qualify or the driver cannot encode them.
+bool make_cell_maps(const TransformPlan &p, uint64_t *x, int64_t stride_limbs, CellMaps *cm);
 
 // Definitions for the translation units above.
 // SQN: w2 for omega = 2, sq for omega = sqrt2 (SQ = false / true)
@@ -900,7 +1009,7 @@ cudaError_t launch_fused_k32(const TransformPlan &p, uint64_t *x, int64_t stride
 
 template <int K>
 cudaError_t launch_fused_as(const TransformPlan &p, uint64_t *x, int64_t stride_limbs, cudaStream_t s,
-                            const FusedArgs &fa, uint32_t *fault, const Launch *plain) {
+                            const FusedArgs &fa, uint32_t *fault, const Launch *plain, const CellMaps *cm) {
   Launch L;
   if (plain) {
     L = *plain;
@@ -911,8 +1020,8 @@ cudaError_t launch_fused_as(const TransformPlan &p, uint64_t *x, int64_t stride_
     L.njobs = p.f_njobs;
     L.prog_words = p.f_prog_words;
   }
-  return p.mode == RING_SQRT2 ? launch_k<K, true, true>(L, x, stride_limbs, p.ring, s, 1, 0, fa, fault)
-                              : launch_k<K, false, true>(L, x, stride_limbs, p.ring, s, 1, 0, fa, fault);
+  return p.mode == RING_SQRT2 ? launch_k<K, true, true>(L, x, stride_limbs, p.ring, s, 1, 0, fa, fault, cm)
+                              : launch_k<K, false, true>(L, x, stride_limbs, p.ring, s, 1, 0, fa, fault, cm);
 }
 
 }  // namespace tftgpu

@@ -75,7 +75,7 @@ bool config_valid(const Ring &r, const PlanConfig &c) {
                                    (size_t(1) << ls) * (size_t(r.pitch) + 1) * 4 <= kSmemBudget; };
   return fits(c.ls_max) && fits(c.ls_c) && c.ls_c <= c.ls_max + 1 && (c.max_warps == 8 || c.max_warps == 16) &&
          (c.split >= 0 && c.split <= 2) && (c.fused >= FUSED_NONE && c.fused <= FUSED_DIRECT) && c.max_lc >= 0 &&
-         c.max_lc <= kMaxClusterLog2;
+         c.max_lc <= kMaxClusterLog2 && (c.tma == 0 || c.tma == 1);
 }
 
 namespace {
@@ -573,8 +573,9 @@ const TransformPlan *get_transform_plan(int kind, int l, int64_t z, int64_t n, i
   const int64_t twoN = omega_order(N, mode);
   e = md(e, twoN);
   const PlanConfig cfg = plan_config(N);
-  const int cfg_key = cfg.ls_max | (cfg.ls_c << 5) | (cfg.max_warps << 10) | (cfg.split << 16) | (mode << 19) |
-                      (replicated ? 1 << 21 : 0) | (cfg.fused << 22) | (cfg.max_lc << 24);
+  // ls_max, ls_c, max_warps 5 bits each; split, mode, fused, max_lc 3 bits each
+  const int cfg_key = cfg.ls_max | (cfg.ls_c << 5) | (cfg.max_warps << 10) | (cfg.split << 15) | (mode << 18) |
+                      (replicated ? 1 << 21 : 0) | (cfg.fused << 22) | (cfg.max_lc << 25) | (cfg.tma << 28);
   auto key = std::make_tuple(dev, kind, l, z, n, f, N, e, scale, cfg_key);
   PlanCache &pc = plan_cache();
   {
@@ -632,11 +633,16 @@ const TransformPlan *get_transform_plan(int kind, int l, int64_t z, int64_t n, i
     g.second.d_jobs = d + g.first;
     plan->launches.push_back(g.second);
   }
+  for (const JobDesc &jd : flat) {
+    const int32_t m = std::max(jd.nload, jd.nstore);
+    if (m > 0) plan->cell_extent = std::max(plan->cell_extent, jd.cell0 + int64_t(m - 1) * jd.mstride + 1);
+  }
   (void)stride_limbs;
   // the fused form: every job single-CTA, more than one launch, not replicated
   plan->stream = (cfg.fused == FUSED_STREAM || cfg.fused == FUSED_DIRECT) && !replicated && P.ring.K >= 4 &&
                  P.ring.G == 32;
   plan->direct = cfg.fused == FUSED_DIRECT;
+  plan->tma = cfg.tma != 0;
   // (the persistent kernel is built for rings whose words fill all 32 lanes, four or more words
   // per lane: N a power of two from 4096 on)
   bool fusable = fused_for(cfg.fused, kind) && !replicated && plan->launches.size() > 1 && P.ring.K >= 4 &&

@@ -7,11 +7,11 @@
 namespace tftgpu {
 
 cudaError_t launch_fused_small(const TransformPlan &p, uint64_t *x, int64_t stride_limbs, cudaStream_t s,
-                               const FusedArgs &fa, uint32_t *fault, const Launch *plain) {
+                               const FusedArgs &fa, uint32_t *fault, const Launch *plain, const CellMaps *cm) {
   switch (p.ring.K) {
-    case 4: return launch_fused_as<4>(p, x, stride_limbs, s, fa, fault, plain);
-    case 8: return launch_fused_as<8>(p, x, stride_limbs, s, fa, fault, plain);
-    case 16: return launch_fused_as<16>(p, x, stride_limbs, s, fa, fault, plain);
+    case 4: return launch_fused_as<4>(p, x, stride_limbs, s, fa, fault, plain, cm);
+    case 8: return launch_fused_as<8>(p, x, stride_limbs, s, fa, fault, plain, cm);
+    case 16: return launch_fused_as<16>(p, x, stride_limbs, s, fa, fault, plain, cm);
     default: return cudaErrorInvalidValue;
   }
 }

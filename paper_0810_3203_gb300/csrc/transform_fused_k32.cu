@@ -5,8 +5,8 @@
 namespace tftgpu {
 
 cudaError_t launch_fused_k32(const TransformPlan &p, uint64_t *x, int64_t stride_limbs, cudaStream_t s,
-                             const FusedArgs &fa, uint32_t *fault, const Launch *plain) {
-  return launch_fused_as<32>(p, x, stride_limbs, s, fa, fault, plain);
+                             const FusedArgs &fa, uint32_t *fault, const Launch *plain, const CellMaps *cm) {
+  return launch_fused_as<32>(p, x, stride_limbs, s, fa, fault, plain, cm);
 }
 
 }  // namespace tftgpu

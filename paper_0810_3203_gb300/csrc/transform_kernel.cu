@@ -1,5 +1,9 @@
 // Per-pass launches of the sub-transform kernel (job_kernel.cuh) and the host entry points that
 // enqueue a plan: one launch per pass, or the plan's persistent form (transform_fused.cu).
+#include <cudaTypedefs.h>
+
+#include <climits>
+
 #include "job_kernel.cuh"
 
 namespace tftgpu {
@@ -17,6 +21,46 @@ static uint32_t *fault_word() {
   if (cudaGetSymbolAddress(&p, g_wait_fault) != cudaSuccess) return nullptr;
   if (dev < 8) addr[dev] = static_cast<uint32_t *>(p);
   return static_cast<uint32_t *>(p);
+}
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link-time dependency on
+// the driver library); null when the driver does not provide it
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static const PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
+    void *f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      f = nullptr;
+    return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+  }();
+  return fn;
+}
+
+bool make_cell_maps(const TransformPlan &p, uint64_t *x, int64_t stride_limbs, CellMaps *cm) {
+  cm->mode = 0;
+  const int NW = p.ring.NW, rows = NW / 32;
+  // rings of 8, 16 or 32 words per lane that fill all 32 lanes (rows of 36 words in multiples of
+  // 8 rows keep every cell 128-byte aligned in shared memory); 16-byte aligned cells whose stride
+  // leaves the limb after the top limb inside the cell's stride (the load box reads it)
+  if (!p.tma || p.ring.G != 32 || p.ring.K < 8 || (rows & 7) != 0 || p.cell_extent <= 0 ||
+      p.cell_extent > INT32_MAX)
+    return false;
+  if ((reinterpret_cast<uintptr_t>(x) & 15) != 0 || (stride_limbs & 1) != 0 || stride_limbs < NW / 2 + 2) return false;
+  const PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+  if (!enc) return false;
+  const cuuint64_t ext = cuuint64_t(p.cell_extent);
+  const cuuint64_t dims_ld[3] = {36, cuuint64_t(rows), ext}, dims_st[3] = {32, cuuint64_t(rows), ext};
+  const cuuint64_t strides[2] = {128, cuuint64_t(stride_limbs) * 8};
+  const cuuint32_t box[3] = {36, cuuint32_t(rows), 1}, elem[3] = {1, 1, 1};
+  if (enc(&cm->ld, CU_TENSOR_MAP_DATA_TYPE_UINT32, 3, x, dims_ld, strides, box, elem, CU_TENSOR_MAP_INTERLEAVE_NONE,
+          CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+    return false;
+  if (enc(&cm->st, CU_TENSOR_MAP_DATA_TYPE_UINT32, 3, x, dims_st, strides, box, elem, CU_TENSOR_MAP_INTERLEAVE_NONE,
+          CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+    return false;
+  cm->mode = 3;
+  return true;
 }
 
 // one launch of a plan's per-pass form, by the ring's words per lane
@@ -42,14 +86,16 @@ cudaError_t run_transform_reps(const TransformPlan &p, uint64_t *x, int64_t stri
   if (reps < 1) return cudaSuccess;
   uint32_t *fault = fault_word();
   if (!fault) return cudaErrorInvalidSymbol;
+  CellMaps cm;
+  const bool maps = p.stream && reps == 1 && make_cell_maps(p, x, stride_limbs, &cm);
   for (const Launch &L : p.launches) {
     if (reps > 1 && L.nsegs != 0) return cudaErrorInvalidValue;
     cudaError_t e;
     if (p.stream && reps == 1 && L.nsegs == 0 && L.lc == 0 && p.ring.K >= 4 && p.ring.G == 32) {
       // direct: sync is null and njobs negative, one CTA per job (see launch_km)
       const FusedArgs plain = {L.d_jobs, nullptr, nullptr, nullptr, p.direct ? -L.njobs : L.njobs};
-      e = p.ring.K == 32 ? launch_fused_k32(p, x, stride_limbs, s, plain, fault, &L)
-                         : launch_fused_small(p, x, stride_limbs, s, plain, fault, &L);
+      e = p.ring.K == 32 ? launch_fused_k32(p, x, stride_limbs, s, plain, fault, &L, maps ? &cm : nullptr)
+                         : launch_fused_small(p, x, stride_limbs, s, plain, fault, &L, maps ? &cm : nullptr);
     } else {
       e = launch_any(p, L, x, stride_limbs, s, reps, rep_cells, fault);
     }
@@ -73,8 +119,10 @@ cudaError_t run_transform(const TransformPlan &p, uint64_t *x, int64_t stride_li
   e = cudaMemsetAsync(sync, 0, bytes, s);
   if (e == cudaSuccess) {
     const FusedArgs fa = {p.f_jobs, p.f_dep_off, p.f_deps, sync, p.f_njobs};
-    e = p.ring.K == 32 ? launch_fused_k32(p, x, stride_limbs, s, fa, fault)
-                       : launch_fused_small(p, x, stride_limbs, s, fa, fault);
+    CellMaps cm;
+    const CellMaps *pm = make_cell_maps(p, x, stride_limbs, &cm) ? &cm : nullptr;
+    e = p.ring.K == 32 ? launch_fused_k32(p, x, stride_limbs, s, fa, fault, nullptr, pm)
+                       : launch_fused_small(p, x, stride_limbs, s, fa, fault, nullptr, pm);
   }
   const cudaError_t ef = cudaFreeAsync(sync, s);
   return e != cudaSuccess ? e : ef;

@@ -84,7 +84,7 @@ def test_tune_restores_buffer_and_keeps_fastest(tg, orc):
         back = d.cpu().numpy().view(np.uint64)
         assert np.array_equal(cells(back, n, W), cells(x, n, W))
         assert info["candidates"] >= 4 and info["best_ms"] > 0
-        assert tg.config_get(N) == {k: info[k] for k in ("ls_max", "ls_c", "max_warps", "split", "fused", "max_cluster_log2")}
+        assert tg.config_get(N) == {k: info[k] for k in ("ls_max", "ls_c", "max_warps", "split", "fused", "max_cluster_log2", "tma")}
         # the tuned configuration computes the same transform as the oracle
         ref = x.copy()
         orc.tft(ref, l, n, n, 0, N)
