@@ -11,7 +11,9 @@
  * Conventions shared by every entry point
  *   Ring element ("cell"): W = N/64 + 1 little-endian uint64 limbs holding the canonical residue
  *     in [0, 2^N] (the top limb is 0, or 1 only for 2^N = -1). Consecutive cells are
- *     stride_limbs >= W limbs apart; limbs past W in a cell are never read or written.
+ *     stride_limbs >= W limbs apart, and a buffer of k cells spans k * stride_limbs limbs. Limbs
+ *     past W in a cell are never written; when stride_limbs > W, the limb after a cell's top limb
+ *     may be read (loads move 16-byte vectors) and its value is ignored.
  *   omega = 2 (a principal 2N-th root of unity), so omega_L = 2^(2N/L) and L = 2^l must divide
  *     2N. A weight zeta = 2^e is passed as its exponent e (taken mod 2N), as in Sec. 6.
  *   Supported ring sizes: N a multiple of 64 with N <= 1024, or a multiple of 1024 up to 32768.

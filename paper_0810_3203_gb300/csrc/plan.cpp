@@ -302,6 +302,56 @@ struct Planner {
     depth--;
     return p - pass;
   }
+
+  // The recursions number passes in the order Algorithms 1 and 2 take their steps, one step
+  // after another. Steps that touch no common cell need not wait for each other (in Algorithm 2
+  // the last row's sub-transforms, for example, only need the rows and columns that feed them).
+  // relevel() renumbers the passes as levels of the dependency graph between them: a pass goes
+  // one level above every earlier pass that wrote a cell it reads or writes, and every earlier
+  // pass that read a cell it writes since that cell was last written. Running the levels in order
+  // keeps every such pair in order, and the passes of one level touch disjoint cells, so they
+  // share launches. Returns the number of levels.
+  int relevel() {
+    if (jobs.empty()) return 0;
+    int maxp = 0;
+    int64_t ncells = 0;
+    for (const JobRec &j : jobs) {
+      maxp = std::max(maxp, j.pass);
+      const int32_t m = std::max(j.d.nload, j.d.nstore);
+      if (m > 0) ncells = std::max(ncells, j.d.cell0 + int64_t(m - 1) * j.d.mstride + 1);
+    }
+    std::vector<std::vector<size_t>> by_pass(size_t(maxp) + 1);
+    for (size_t i = 0; i < jobs.size(); i++) by_pass[size_t(jobs[i].pass)].push_back(i);
+    std::vector<int> last_write(size_t(ncells), 0), last_read(size_t(ncells), 0), level(size_t(maxp) + 1, 0);
+    int top = 0;
+    for (int p = 0; p <= maxp; p++) {
+      int lev = 1;
+      for (size_t i : by_pass[size_t(p)]) {
+        const JobDesc &d = jobs[i].d;
+        for (int32_t m = 0; m < std::max(d.nload, d.nstore); m++) {
+          const size_t c = size_t(d.cell0 + int64_t(m) * d.mstride);
+          if (m < d.nload) lev = std::max(lev, last_write[c] + 1);
+          if (m < d.nstore) lev = std::max(lev, std::max(last_write[c], last_read[c]) + 1);
+        }
+      }
+      for (size_t i : by_pass[size_t(p)]) {
+        const JobDesc &d = jobs[i].d;
+        for (int32_t m = 0; m < std::max(d.nload, d.nstore); m++) {
+          const size_t c = size_t(d.cell0 + int64_t(m) * d.mstride);
+          if (m < d.nstore) {
+            last_write[c] = lev;
+            last_read[c] = 0;
+          } else {
+            last_read[c] = std::max(last_read[c], lev);
+          }
+        }
+      }
+      level[size_t(p)] = lev;
+      if (!by_pass[size_t(p)].empty()) top = std::max(top, lev);
+    }
+    for (JobRec &j : jobs) j.pass = level[size_t(j.pass)] - 1;
+    return top;
+  }
 };
 
 struct PlanCache {
@@ -472,13 +522,21 @@ int64_t zero_padded_outputs(int l, int64_t n, int64_t N) {
 
 int count_passes(int kind, int l, int64_t z, int64_t n, int f, int64_t N) {
   Planner P(N);
-  return kind == KIND_TFT ? P.tft(0, 0, 1, l, 0, z, n) : P.itft(0, 0, 1, l, 0, z, n, f, -1);
+  if (kind == KIND_TFT)
+    P.tft(0, 0, 1, l, 0, z, n);
+  else
+    P.itft(0, 0, 1, l, 0, z, n, f, -1);
+  return P.relevel();
 }
 
 void plan_shape(int kind, int l, int64_t z, int64_t n, int f, int64_t N, int *passes, int *launches,
                 int64_t *jobs, int *onchip_l, int *cluster_l) {
   Planner P(N);
-  *passes = kind == KIND_TFT ? P.tft(0, 0, 1, l, 0, z, n) : P.itft(0, 0, 1, l, 0, z, n, f, -1);
+  if (kind == KIND_TFT)
+    P.tft(0, 0, 1, l, 0, z, n);
+  else
+    P.itft(0, 0, 1, l, 0, z, n, f, -1);
+  *passes = P.relevel();
   std::sort(P.jobs.begin(), P.jobs.end(), launch_order);
   int nl = 0, lcmax = 0, lsmax = 0;
   for (size_t i = 0; i < P.jobs.size(); i++) {
@@ -503,8 +561,11 @@ void build_host_plan(int kind, int l, int64_t z, int64_t n, int f, int64_t N, in
   e = md(e, twoN);
   Planner P(N, nullptr, mode);
   out->ring = P.ring;
-  out->npasses = kind == KIND_TFT ? P.tft(0, 0, 1, l, e, z, n)
-                                  : P.itft(0, 0, 1, l, e, z, n, f, scale ? inv_l_exponent(l, twoN, mode) : -1);
+  if (kind == KIND_TFT)
+    P.tft(0, 0, 1, l, e, z, n);
+  else
+    P.itft(0, 0, 1, l, e, z, n, f, scale ? inv_l_exponent(l, twoN, mode) : -1);
+  out->npasses = P.relevel();
   std::map<std::tuple<int, int, int, int64_t, int64_t, int>, int> index;
   mark_raw_stores(P.jobs, l);
   std::stable_sort(P.jobs.begin(), P.jobs.end(), launch_order);
@@ -547,6 +608,7 @@ void build_host_schedule(int kind, int l, int64_t z, int64_t n, int f, int64_t N
     P.tft(0, 0, 1, l, e, z, n);
   else
     P.itft(0, 0, 1, l, e, z, n, f, scale ? inv_l_exponent(l, twoN, mode) : -1);
+  P.relevel();
   mark_raw_stores(P.jobs, l);
   std::stable_sort(P.jobs.begin(), P.jobs.end(), launch_order);
   int nl = 0;
@@ -585,11 +647,11 @@ const TransformPlan *get_transform_plan(int kind, int l, int64_t z, int64_t n, i
   }
   Planner P(N, &cfg, mode);
   P.whole_split = !replicated;
-  int npass;
   if (kind == KIND_TFT)
-    npass = P.tft(0, 0, 1, l, e, z, n);
+    P.tft(0, 0, 1, l, e, z, n);
   else
-    npass = P.itft(0, 0, 1, l, e, z, n, f, scale ? inv_l_exponent(l, twoN, mode) : -1);
+    P.itft(0, 0, 1, l, e, z, n, f, scale ? inv_l_exponent(l, twoN, mode) : -1);
+  const int npass = P.relevel();
 
   std::unique_ptr<TransformPlan> plan(new TransformPlan());
   plan->ring = P.ring;
@@ -727,7 +789,11 @@ const TransformPlan *get_sn_plan(int kind, int l, int64_t z, int64_t n, int f, i
   cfg.split = 0;
   Planner P(H, &cfg);
   // the final division by L: l halvings of every coefficient (escale counts them)
-  const int npass = kind == KIND_TFT ? P.tft(0, 0, 1, l, e, z, n) : P.itft(0, 0, 1, l, e, z, n, f, scale ? l : -1);
+  if (kind == KIND_TFT)
+    P.tft(0, 0, 1, l, e, z, n);
+  else
+    P.itft(0, 0, 1, l, e, z, n, f, scale ? l : -1);
+  const int npass = P.relevel();
   std::unique_ptr<TransformPlan> plan(new TransformPlan());
   plan->ring = make_ring(64);
   plan->ring.N = H;
@@ -786,7 +852,11 @@ void sn_plan_shape(int kind, int l, int64_t z, int64_t n, int f, int64_t H, int 
   cfg.max_warps = 8;
   cfg.split = 0;
   Planner P(H, &cfg);
-  *passes = kind == KIND_TFT ? P.tft(0, 0, 1, l, 0, z, n) : P.itft(0, 0, 1, l, 0, z, n, f, -1);
+  if (kind == KIND_TFT)
+    P.tft(0, 0, 1, l, 0, z, n);
+  else
+    P.itft(0, 0, 1, l, 0, z, n, f, -1);
+  *passes = P.relevel();
   std::sort(P.jobs.begin(), P.jobs.end(), launch_order);
   int nl = 0;
   for (size_t i = 0; i < P.jobs.size(); i++)
