@@ -282,6 +282,7 @@ struct BatchGroup {
   int64_t max_len = 0, max_n = 0;
   size_t pack_off = 0, pw_off = 0, lift_off = 0;
   std::vector<Launch> tft, itft;  // merged launches; d_segs hold descriptor-image byte offsets
+  int64_t cell_end = 0;           // the group's cells end here (cells of `stride` from the pool's start)
 };
 struct BatchLayout {
   size_t pool_bytes = 0;

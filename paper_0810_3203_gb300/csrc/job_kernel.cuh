@@ -718,13 +718,16 @@ __device__ __forceinline__ KGeo make_kgeo(int N, uint32_t mask) {
   return kg;
 }
 
-// One job per CTA (per cluster): a plain launch, a replicated one or a merged one.
-template <int K, int MINB, bool FULL, bool SQ, bool SINGLE>
+// One job per CTA (per cluster): a plain launch, a replicated one or a merged one. TM = 3 (single-CTA
+// launches only): the cells move through the tensor maps tm_ld / tm_st (see run_job).
+template <int K, int MINB, bool FULL, bool SQ, bool SINGLE, int TM>
 __global__ void __launch_bounds__(MINB == 3 ? 256 : 512, MINB) job_kernel(uint64_t *__restrict__ x, int64_t stride_limbs,
                                                   const JobDesc *__restrict__ jobs, int N, int ls, int lc,
                                                   uint32_t mask, int prog_cap,
                                                   const Segment *__restrict__ segs, int nsegs, int64_t rep_cells,
-                                                  int rep_ctas, uint32_t *fault) {
+                                                  int rep_ctas, uint32_t *fault,
+                                                  const __grid_constant__ CUtensorMap tm_ld,
+                                                  const __grid_constant__ CUtensorMap tm_st) {
   const KGeo kg = make_kgeo<K, FULL, SQ>(N, mask);
   JobDesc jd;
   if (nsegs == 0) {
@@ -751,7 +754,7 @@ __global__ void __launch_bounds__(MINB == 3 ? 256 : 512, MINB) job_kernel(uint64
     jd = sg.jobs[(int(blockIdx.x) - sg.first_cta) >> lc];
     jd.cell0 += sg.cell_off;
   }
-  run_job<K, SQ, SINGLE>(jd, x, stride_limbs, ls, lc, kg, prog_cap, fault);
+  run_job<K, SQ, SINGLE, TM>(jd, x, stride_limbs, ls, lc, kg, prog_cap, fault, &tm_ld, &tm_st);
 }
 
 // L2 prefetch of the input cells of a job (bulk prefetch, no shared memory): one cell per lane
@@ -847,13 +850,17 @@ static cudaError_t launch_km(const Launch &L, uint64_t *x, int64_t stride_limbs,
           e = cudaFuncSetAttribute(job_kernel_stream<K, MINB, FULL, SQ, 3>,
                                    cudaFuncAttributeMaxDynamicSharedMemorySize, int(kJobDynSmem));
     } else {
-      e = cudaFuncSetAttribute(job_kernel<K, MINB, FULL, SQ, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+      e = cudaFuncSetAttribute(job_kernel<K, MINB, FULL, SQ, true, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                int(kJobDynSmem));
       if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(job_kernel<K, MINB, FULL, SQ, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        e = cudaFuncSetAttribute(job_kernel<K, MINB, FULL, SQ, false, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  int(kJobDynSmem));
       if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(job_kernel<K, MINB, FULL, SQ, false>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        e = cudaFuncSetAttribute(job_kernel<K, MINB, FULL, SQ, false, 0>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+      if constexpr (K >= 8 && FULL)
+        if (e == cudaSuccess)
+          e = cudaFuncSetAttribute(job_kernel<K, MINB, FULL, SQ, true, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   int(kJobDynSmem));
     }
     if (e != cudaSuccess) return e;
     if (dev < 8) configured[dev] = 1;
@@ -901,13 +908,19 @@ static cudaError_t launch_km(const Launch &L, uint64_t *x, int64_t stride_limbs,
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = L.lc > 0 ? 1 : 0;
+    static const CellMaps no_maps = {};
+    if constexpr (K >= 8 && FULL)
+      if (L.lc == 0 && cm && cm->mode == 3)
+        return cudaLaunchKernelEx(&cfg, job_kernel<K, MINB, FULL, SQ, true, 3>, x, stride_limbs,
+                                  (const JobDesc *)L.d_jobs, int(r.N), L.ls, 0, mask, prog_cap, L.d_segs, L.nsegs,
+                                  rep_cells, reps > 1 ? int(per_rep) : 0, fault, cm->ld, cm->st);
     if (L.lc == 0)
-      return cudaLaunchKernelEx(&cfg, job_kernel<K, MINB, FULL, SQ, true>, x, stride_limbs, (const JobDesc *)L.d_jobs,
+      return cudaLaunchKernelEx(&cfg, job_kernel<K, MINB, FULL, SQ, true, 0>, x, stride_limbs, (const JobDesc *)L.d_jobs,
                                 int(r.N), L.ls, 0, mask, prog_cap, L.d_segs, L.nsegs, rep_cells,
-                                reps > 1 ? int(per_rep) : 0, fault);
-    return cudaLaunchKernelEx(&cfg, job_kernel<K, MINB, FULL, SQ, false>, x, stride_limbs, (const JobDesc *)L.d_jobs,
+                                reps > 1 ? int(per_rep) : 0, fault, no_maps.ld, no_maps.st);
+    return cudaLaunchKernelEx(&cfg, job_kernel<K, MINB, FULL, SQ, false, 0>, x, stride_limbs, (const JobDesc *)L.d_jobs,
                               int(r.N), L.ls, L.lc, mask, prog_cap, L.d_segs, L.nsegs, rep_cells,
-                              reps > 1 ? int(per_rep) : 0, fault);
+                              reps > 1 ? int(per_rep) : 0, fault, no_maps.ld, no_maps.st);
   }
 }
 
@@ -971,7 +984,8 @@ static cudaError_t launch_k(const Launch &L, uint64_t *x, int64_t stride_limbs, 
 // status word of the bounded waits.
 #define TFT_DECLARE_LAUNCHES(KK, SQN)                                                                       \
   cudaError_t launch_plain_k##KK##_##SQN(const TransformPlan &p, const Launch &L, uint64_t *x, int64_t stride_limbs, \
-                                        cudaStream_t s, int64_t reps, int64_t rep_cells, uint32_t *fault)
+                                        cudaStream_t s, int64_t reps, int64_t rep_cells, uint32_t *fault,       \
+                                        const CellMaps *cm)
 TFT_DECLARE_LAUNCHES(1, w2);
 TFT_DECLARE_LAUNCHES(1, sq);
 TFT_DECLARE_LAUNCHES(2, w2);
@@ -994,17 +1008,19 @@ cudaError_t launch_fused_small(const TransformPlan &p, uint64_t *x, int64_t stri
 cudaError_t launch_fused_k32(const TransformPlan &p, uint64_t *x, int64_t stride_limbs, cudaStream_t s,
                              const FusedArgs &fa, uint32_t *fault, const Launch *plain = nullptr,
                              const CellMaps *cm = nullptr);
-// Tensor maps of the cells a plan touches in the buffer x (CellMaps); false (mode 0) when the
-// ring or the buffer does not qualify or the driver cannot encode them.
-bool make_cell_maps(const TransformPlan &p, uint64_t *x, int64_t stride_limbs, CellMaps *cm);
+// Tensor maps of cells [0, ext) of the buffer x (CellMaps) for plan p's ring; false (mode 0) when
+// the plan asks for none (tma), the ring or the buffer does not qualify, or the driver cannot encode
+// them.
+bool make_cell_maps(const TransformPlan &p, uint64_t *x, int64_t stride_limbs, int64_t ext, CellMaps *cm);
 
 // Definitions for the translation units above.
 // SQN: w2 for omega = 2, sq for omega = sqrt2 (SQ = false / true)
 #define TFT_DEFINE_PLAIN(KK, SQN, SQB)                                                                      \
   cudaError_t launch_plain_k##KK##_##SQN(const TransformPlan &p, const Launch &L, uint64_t *x, int64_t stride_limbs, \
-                                        cudaStream_t s, int64_t reps, int64_t rep_cells, uint32_t *fault) {  \
+                                        cudaStream_t s, int64_t reps, int64_t rep_cells, uint32_t *fault,       \
+                                        const CellMaps *cm) {                                                   \
     const FusedArgs none = {nullptr, nullptr, nullptr, nullptr, 0};                                           \
-    return launch_k<KK, SQB, false>(L, x, stride_limbs, p.ring, s, reps, rep_cells, none, fault);             \
+    return launch_k<KK, SQB, false>(L, x, stride_limbs, p.ring, s, reps, rep_cells, none, fault, cm);         \
   }
 
 template <int K>

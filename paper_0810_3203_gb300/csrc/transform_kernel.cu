@@ -37,19 +37,18 @@ static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
   return fn;
 }
 
-bool make_cell_maps(const TransformPlan &p, uint64_t *x, int64_t stride_limbs, CellMaps *cm) {
+bool make_cell_maps(const TransformPlan &p, uint64_t *x, int64_t stride_limbs, int64_t ext_cells, CellMaps *cm) {
   cm->mode = 0;
   const int NW = p.ring.NW, rows = NW / 32;
   // rings of 8, 16 or 32 words per lane that fill all 32 lanes (rows of 36 words in multiples of
   // 8 rows keep every cell 128-byte aligned in shared memory); 16-byte aligned cells whose stride
   // leaves the limb after the top limb inside the cell's stride (the load box reads it)
-  if (!p.tma || p.ring.G != 32 || p.ring.K < 8 || (rows & 7) != 0 || p.cell_extent <= 0 ||
-      p.cell_extent > INT32_MAX)
+  if (!p.tma || p.ring.G != 32 || p.ring.K < 8 || (rows & 7) != 0 || ext_cells <= 0 || ext_cells > INT32_MAX)
     return false;
   if ((reinterpret_cast<uintptr_t>(x) & 15) != 0 || (stride_limbs & 1) != 0 || stride_limbs < NW / 2 + 2) return false;
   const PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
   if (!enc) return false;
-  const cuuint64_t ext = cuuint64_t(p.cell_extent);
+  const cuuint64_t ext = cuuint64_t(ext_cells);
   const cuuint64_t dims_ld[3] = {36, cuuint64_t(rows), ext}, dims_st[3] = {32, cuuint64_t(rows), ext};
   const cuuint64_t strides[2] = {128, cuuint64_t(stride_limbs) * 8};
   const cuuint32_t box[3] = {36, cuuint32_t(rows), 1}, elem[3] = {1, 1, 1};
@@ -65,10 +64,10 @@ bool make_cell_maps(const TransformPlan &p, uint64_t *x, int64_t stride_limbs, C
 
 // one launch of a plan's per-pass form, by the ring's words per lane
 static cudaError_t launch_any(const TransformPlan &p, const Launch &L, uint64_t *x, int64_t stride_limbs,
-                              cudaStream_t s, int64_t reps, int64_t rep_cells, uint32_t *fault) {
+                              cudaStream_t s, int64_t reps, int64_t rep_cells, uint32_t *fault, const CellMaps *cm) {
   const bool sq = p.mode == RING_SQRT2;
-#define TFT_PL(KK) (sq ? launch_plain_k##KK##_sq(p, L, x, stride_limbs, s, reps, rep_cells, fault) \
-                       : launch_plain_k##KK##_w2(p, L, x, stride_limbs, s, reps, rep_cells, fault))
+#define TFT_PL(KK) (sq ? launch_plain_k##KK##_sq(p, L, x, stride_limbs, s, reps, rep_cells, fault, cm) \
+                       : launch_plain_k##KK##_w2(p, L, x, stride_limbs, s, reps, rep_cells, fault, cm))
   switch (p.ring.K) {
     case 1: return TFT_PL(1);
     case 2: return TFT_PL(2);
@@ -86,8 +85,9 @@ cudaError_t run_transform_reps(const TransformPlan &p, uint64_t *x, int64_t stri
   if (reps < 1) return cudaSuccess;
   uint32_t *fault = fault_word();
   if (!fault) return cudaErrorInvalidSymbol;
+  // tensor maps over every cell the launches touch (replicas included)
   CellMaps cm;
-  const bool maps = p.stream && reps == 1 && make_cell_maps(p, x, stride_limbs, &cm);
+  const bool maps = make_cell_maps(p, x, stride_limbs, (reps - 1) * rep_cells + p.cell_extent, &cm);
   for (const Launch &L : p.launches) {
     if (reps > 1 && L.nsegs != 0) return cudaErrorInvalidValue;
     cudaError_t e;
@@ -97,7 +97,7 @@ cudaError_t run_transform_reps(const TransformPlan &p, uint64_t *x, int64_t stri
       e = p.ring.K == 32 ? launch_fused_k32(p, x, stride_limbs, s, plain, fault, &L, maps ? &cm : nullptr)
                          : launch_fused_small(p, x, stride_limbs, s, plain, fault, &L, maps ? &cm : nullptr);
     } else {
-      e = launch_any(p, L, x, stride_limbs, s, reps, rep_cells, fault);
+      e = launch_any(p, L, x, stride_limbs, s, reps, rep_cells, fault, maps ? &cm : nullptr);
     }
     if (e != cudaSuccess) return e;
   }
@@ -120,7 +120,7 @@ cudaError_t run_transform(const TransformPlan &p, uint64_t *x, int64_t stride_li
   if (e == cudaSuccess) {
     const FusedArgs fa = {p.f_jobs, p.f_dep_off, p.f_deps, sync, p.f_njobs};
     CellMaps cm;
-    const CellMaps *pm = make_cell_maps(p, x, stride_limbs, &cm) ? &cm : nullptr;
+    const CellMaps *pm = make_cell_maps(p, x, stride_limbs, p.cell_extent, &cm) ? &cm : nullptr;
     e = p.ring.K == 32 ? launch_fused_k32(p, x, stride_limbs, s, fa, fault, nullptr, pm)
                        : launch_fused_small(p, x, stride_limbs, s, fa, fault, nullptr, pm);
   }

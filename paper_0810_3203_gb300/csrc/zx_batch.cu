@@ -165,6 +165,7 @@ int layout_batch(const std::vector<BatchProduct> &items, const std::vector<int> 
       }
     }
     byte_off = size_t(cell_off) * cell_bytes;
+    gd.cell_end = cell_off;
     gd.pack_off = img.add(pk.data(), pk.size() * sizeof(PackItem));
     gd.pw_off = img.add(pw.data(), pw.size() * sizeof(PointwiseItem));
     gd.lift_off = img.add(lf.data(), lf.size() * sizeof(LiftItem));
@@ -182,6 +183,9 @@ cudaError_t enqueue_group(const BatchGroup &gd, unsigned char *d_desc, unsigned 
   TransformPlan tp, ip;
   tp.ring = ip.ring = gd.ring;
   tp.mode = ip.mode = gd.mode;
+  // the merged launches touch the group's cells only; tensor copies as the ring's configuration says
+  tp.cell_extent = ip.cell_extent = gd.cell_end;
+  tp.tma = ip.tma = plan_config(gd.ring.N).tma != 0;
   for (Launch L : gd.tft) {
     L.d_segs = rebase(L.d_segs, d_desc);
     tp.launches.push_back(L);

@@ -149,3 +149,46 @@ def test_the_setting_round_trips_through_the_configuration(tg):
     finally:
         tg.config_set(N, before)
     assert tg.config_get(N) == before
+
+
+def test_batched_products_on_large_rings_take_either_path(tg, orc):
+    """zx_mul_batch merges the transforms of many products into shared launches (job_kernel with
+    segment tables); these shapes (coefficients of about 3800 and 7800 bits) land on the rings
+    N = 8192 and 16384, whose 8 and 16 words per lane fill all 32 lanes, where the merged launches
+    use tensor copies. The batch must give the same words with tma on and off, the same as zx_mul
+    alone, and the oracle's schoolbook product for its smallest product."""
+    shapes = [(609, 1088, 3801, False), (959, 796, 3889, True), (1366, 814, 3829, True), (1338, 1130, 3995, False),
+              (652, 1242, 7799, False), (1471, 1340, 7986, False), (59, 138, 7935, True), (293, 1307, 7706, False),
+              (310, 1120, 7757, True), (1483, 1213, 4067, False)]
+    rings = [tg.zx_plan(lf, b, lg, b, s)["N"] for lf, lg, b, s in shapes]
+    assert set(rings) == {8192, 16384}, rings
+    results = {}
+    for tma in (1, 0):
+        with pinned_tma(tg, 8192, tma), pinned_tma(tg, 16384, tma):
+            items, host = [], []
+            for k, (lf, lg, bits, signed) in enumerate(shapes):
+                m = (bits + (1 if signed else 0) + 63) // 64
+                f = workloads.coefficients(500 + 2 * k, lf, bits, m, signed)
+                g = workloads.coefficients(501 + 2 * k, lg, bits, m, signed)
+                mh = tg.zx_plan(lf, bits, lg, bits, signed)["limbs_h"]
+                F = torch.from_numpy(f.view(np.int64)).cuda()
+                G = torch.from_numpy(g.view(np.int64)).cuda()
+                H = torch.full(((lf + lg - 1) * mh,), -1, dtype=torch.int64, device="cuda")
+                items.append((F, lf, m, G, lg, m, H, mh, signed, bits, bits))
+                host.append((f, g, m, mh))
+            tg.zx_mul_batch(items)
+            torch.cuda.synchronize()
+            results[tma] = [it[6].cpu().numpy().view(np.uint64).copy() for it in items]
+            if tma == 1:
+                for (F, lf, m, G, lg, _, H, mh, signed, bits, _), got in zip(items, results[1]):
+                    alone = torch.full_like(H, -1)
+                    tg.zx_mul(F, lf, m, G, lg, m, alone, mh, signed, bits, bits)
+                    torch.cuda.synchronize()
+                    assert np.array_equal(alone.cpu().numpy().view(np.uint64), got), (lf, lg, bits, signed)
+                smallest = sorted(range(len(shapes)), key=lambda k: shapes[k][0] * shapes[k][1])[:1]
+                for k in smallest:
+                    lf, lg, bits, signed = shapes[k]
+                    f, g, m, mh = host[k]
+                    assert np.array_equal(results[1][k], orc.zx_schoolbook(f, lf, m, g, lg, m, mh, signed))
+    for a, b in zip(results[1], results[0]):
+        assert np.array_equal(a, b)
