@@ -259,7 +259,7 @@ typedef struct {
                            persistent launch per transform (zx_transform_schedule), 2 the same
                            for the ITFT only; 3 one launch per pass as a persistent loop that
                            prefetches a CTA's next job into L2; 4 one launch per pass with one
-                           CTA per job through a kernel that needs no register spills (the
+                           CTA per job through the persistent kernels' job body (the
                            default). A persistent launch holds every CTA slot of the GPU until
                            it finishes, so transforms on concurrent streams stop overlapping;
                            it pays for a transform that runs alone */

@@ -55,9 +55,10 @@ Ring make_ring(int64_t N);
 //   3 one launch per pass as a persistent loop over its jobs that prefetches a CTA's next job into
 //     L2 while it computes the current one;
 //   4 one launch per pass, one CTA per job, through the persistent kernels' instantiation: the
-//     default. That job body fits the registers of three CTAs per SM without spilling (job_kernel
-//     spills about 170 bytes a thread, which the 30 KB of L1 beside the shared memory cannot hold),
-//     and it ran 4 % faster on GB300.
+//     default. With row copies that job body fit the registers of three CTAs per SM without
+//     spilling where job_kernel spilled (46 bytes a thread, which the L1 beside 225 KB of shared
+//     memory could not hold), and it ran 4 % faster on GB300; with tensor copies (tma) the two
+//     measure within 1 %.
 // Measured at l = 16, N = 32768: alone, the persistent ITFT is faster from n = 40000 on, the TFT
 // slower; with several transforms on concurrent streams, persistent launches hold every CTA slot
 // until they finish and the transforms stop overlapping (the five-stream benchmark step went from
