@@ -241,8 +241,9 @@ struct PackItem {
   int32_t is_signed, pad;
 };
 struct PointwiseItem {
-  int64_t a, b;  // limb offsets of the two cell arrays (a <- a * b)
+  int64_t a, b;   // limb offsets of the two cell arrays (a <- a * b)
   int64_t n;
+  int64_t first;  // the group's products before this item's (items in order, first ascending)
 };
 struct LiftItem {
   int64_t cells;  // limb offset
@@ -252,7 +253,7 @@ struct LiftItem {
 };
 cudaError_t launch_pack_batch(const PackItem *d_items, int count, int64_t max_len, int64_t stride_limbs,
                               const Ring &r, uint64_t *pool, cudaStream_t s);
-cudaError_t launch_pointwise_batch(const PointwiseItem *d_items, int count, int64_t max_n, int64_t stride_limbs,
+cudaError_t launch_pointwise_batch(const PointwiseItem *d_items, int count, int64_t total, int64_t stride_limbs,
                                    const Ring &r, uint64_t *pool, cudaStream_t s);
 cudaError_t launch_lift_batch(const LiftItem *d_items, int count, int64_t max_n, int64_t stride_limbs,
                               const Ring &r, uint64_t *pool, cudaStream_t s);
@@ -281,6 +282,7 @@ struct BatchGroup {
   int64_t stride = 0;
   int count = 0;
   int64_t max_len = 0, max_n = 0;
+  int64_t pw_total = 0;  // pointwise products of the group (the sum of its items' n)
   size_t pack_off = 0, pw_off = 0, lift_off = 0;
   std::vector<Launch> tft, itft;  // merged launches; d_segs hold descriptor-image byte offsets
   int64_t cell_end = 0;           // the group's cells end here (cells of `stride` from the pool's start)

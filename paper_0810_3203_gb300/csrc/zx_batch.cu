@@ -151,7 +151,8 @@ int layout_batch(const std::vector<BatchProduct> &items, const std::vector<int> 
       const int64_t F = cf * p.stride, G = cg * p.stride;  // limb offsets in the pool
       pk.push_back(PackItem{p.f, F, p.len_f, p.limbs_f, p.signed_f, 0});
       pk.push_back(PackItem{p.g, G, p.len_g, p.limbs_g, p.signed_g, 0});
-      pw.push_back(PointwiseItem{F, G, p.nf});
+      pw.push_back(PointwiseItem{F, G, p.nf, gd.pw_total});
+      gd.pw_total += p.nf;
       lf.push_back(LiftItem{F, p.h, p.n, p.limbs_h, p.sgn, 0});
       gd.max_len = std::max(gd.max_len, std::max(p.len_f, p.len_g));
       gd.max_n = std::max(gd.max_n, p.nf);
@@ -200,7 +201,7 @@ cudaError_t enqueue_group(const BatchGroup &gd, unsigned char *d_desc, unsigned 
   cudaError_t ce;
   if ((ce = launch_pack_batch(pk, 2 * gd.count, gd.max_len, gd.stride, gd.ring, x, s)) != cudaSuccess) return ce;
   if ((ce = run_transform(tp, x, gd.stride, s)) != cudaSuccess) return ce;
-  if ((ce = launch_pointwise_batch(pw, gd.count, gd.max_n, gd.stride, gd.ring, x, s)) != cudaSuccess) return ce;
+  if ((ce = launch_pointwise_batch(pw, gd.count, gd.pw_total, gd.stride, gd.ring, x, s)) != cudaSuccess) return ce;
   if ((ce = run_transform(ip, x, gd.stride, s)) != cudaSuccess) return ce;
   return launch_lift_batch(lf, gd.count, gd.max_n, gd.stride, gd.ring, x, s);
 }

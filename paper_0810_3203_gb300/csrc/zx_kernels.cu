@@ -312,19 +312,26 @@ __global__ void __launch_bounds__(kPointwiseWarps * 32)
     pointwise_one<K>(a + i * stride, b + i * stride, ws, g);
 }
 
+// The pointwise products of a batch group as one sequence of `total` products (item p holds
+// products first .. first + n - 1 of it): warps take them in a grid-stride loop, so a group's
+// longest product is spread over the whole grid instead of a per-item share of it. A warp's index
+// only grows, so its item cursor only moves forward.
 template <int K>
 __global__ void __launch_bounds__(kPointwiseWarps * 32)
-    pointwise_batch_kernel(const PointwiseItem *__restrict__ items, int64_t stride, int N, int warps_per_block,
-                           uint64_t *__restrict__ pool) {
+    pointwise_batch_kernel(const PointwiseItem *__restrict__ items, int count, int64_t total, int64_t stride, int N,
+                           int warps_per_block, uint64_t *__restrict__ pool) {
   extern __shared__ uint4 sm4[];
   uint32_t *sm = reinterpret_cast<uint32_t *>(sm4);
   const Geo g = make_geo(N, K);
   const int warp = threadIdx.x >> 5;
   uint32_t *ws = sm + size_t(warp) * pointwise_warp_words(g.NW);
-  const PointwiseItem it = items[blockIdx.y];
   const int64_t nwarps = int64_t(gridDim.x) * warps_per_block;
-  for (int64_t i = int64_t(blockIdx.x) * warps_per_block + warp; i < it.n; i += nwarps)
-    pointwise_one<K>(pool + it.a + i * stride, pool + it.b + i * stride, ws, g);
+  int p = 0;
+  for (int64_t t = int64_t(blockIdx.x) * warps_per_block + warp; t < total; t += nwarps) {
+    while (p + 1 < count && items[p + 1].first <= t) p++;
+    const int64_t i = t - items[p].first;
+    pointwise_one<K>(pool + items[p].a + i * stride, pool + items[p].b + i * stride, ws, g);
+  }
 }
 
 template <int K>
@@ -375,16 +382,14 @@ cudaError_t launch_lift(const uint64_t *cells, int64_t n, int64_t stride_limbs, 
 }
 
 template <int K>
-cudaError_t pointwise_batch_k(const PointwiseItem *items, int count, int64_t max_n, int64_t stride,
+cudaError_t pointwise_batch_k(const PointwiseItem *items, int count, int64_t total, int64_t stride,
                               const Ring &r, uint64_t *pool, cudaStream_t s) {
   const int wpb = kPointwiseWarps;
   const size_t smem = size_t(pointwise_warp_words(r.NW)) * 4 * wpb;
-  int64_t bx = (max_n + wpb - 1) / wpb;
-  int64_t cap = std::max<int64_t>(1, (152 * 16) / std::max(1, count));
-  if (bx > cap) bx = cap;
-  if (bx < 1) bx = 1;
-  pointwise_batch_kernel<K><<<dim3(unsigned(bx), unsigned(count)), wpb * 32, smem, s>>>(items, stride, int(r.N), wpb,
-                                                                                      pool);
+  int64_t blocks = (total + wpb - 1) / wpb;
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  if (blocks < 1) blocks = 1;
+  pointwise_batch_kernel<K><<<unsigned(blocks), wpb * 32, smem, s>>>(items, count, total, stride, int(r.N), wpb, pool);
   return cudaGetLastError();
 }
 
@@ -411,10 +416,10 @@ cudaError_t launch_lift_batch(const LiftItem *d_items, int count, int64_t max_n,
   return cudaGetLastError();
 }
 
-cudaError_t launch_pointwise_batch(const PointwiseItem *d_items, int count, int64_t max_n, int64_t stride_limbs,
+cudaError_t launch_pointwise_batch(const PointwiseItem *d_items, int count, int64_t total, int64_t stride_limbs,
                                    const Ring &r, uint64_t *pool, cudaStream_t s) {
-  if (count <= 0 || max_n <= 0) return cudaSuccess;
-  TFT_DISPATCH_K(r.K, return pointwise_batch_k<KK>(d_items, count, max_n, stride_limbs, r, pool, s));
+  if (count <= 0 || total <= 0) return cudaSuccess;
+  TFT_DISPATCH_K(r.K, return pointwise_batch_k<KK>(d_items, count, total, stride_limbs, r, pool, s));
   return cudaSuccess;
 }
 
