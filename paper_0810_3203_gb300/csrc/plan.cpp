@@ -113,6 +113,68 @@ int64_t md(int64_t a, int64_t m) {
   return r < 0 ? r + m : r;
 }
 
+// Device memory of the plan caches (job lists, job images, persistent schedules). Plans are made
+// while other streams run (a serving loop plans each new product shape as it arrives), and a
+// device allocation or a copy on the legacy default stream between two launches of different
+// streams keeps those launches from overlapping. So plans take their memory from chunks
+// allocated ahead (64 MiB at a time per device; the caches keep every plan, so nothing is
+// freed) and upload on a non-blocking stream of their own, synchronising only that stream.
+struct PlanMemory {
+  std::mutex mu;
+  struct Chunk {
+    unsigned char *base = nullptr;
+    size_t size = 0, used = 0;
+  };
+  std::map<int, Chunk> chunk;         // per device: the chunk plans are taken from
+  std::map<int, cudaStream_t> stream;  // per device: the upload stream
+};
+
+PlanMemory &plan_memory() {
+  static PlanMemory *m = new PlanMemory();
+  return *m;
+}
+
+// 256-byte aligned device memory for a cached plan; nullptr when the device has none left
+void *plan_alloc(size_t bytes) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  PlanMemory &pm = plan_memory();
+  std::lock_guard<std::mutex> lk(pm.mu);
+  PlanMemory::Chunk &c = pm.chunk[dev];
+  bytes = std::max<size_t>(256, (bytes + 255) & ~size_t(255));
+  if (!c.base || c.used + bytes > c.size) {
+    const size_t size = std::max<size_t>(size_t(64) << 20, bytes);
+    unsigned char *p = nullptr;
+    if (cudaMalloc(reinterpret_cast<void **>(&p), size) != cudaSuccess) return nullptr;
+    c = PlanMemory::Chunk{p, size, 0};  // the previous chunk keeps the plans it holds
+  }
+  void *r = c.base + c.used;
+  c.used += bytes;
+  return r;
+}
+
+// Host -> device copy of a plan on the upload stream; returns when the copy has landed.
+cudaError_t plan_upload(void *dst, const void *src, size_t bytes) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  PlanMemory &pm = plan_memory();
+  cudaStream_t s = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(pm.mu);
+    auto it = pm.stream.find(dev);
+    if (it == pm.stream.end()) {
+      const cudaError_t e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+      if (e != cudaSuccess) return e;
+      pm.stream[dev] = s;
+    } else {
+      s = it->second;
+    }
+  }
+  cudaError_t e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  return e;
+}
+
 // device copies of job images, keyed by (device, kind, ls, lc, z, n, f, N)
 struct ImageCache {
   std::mutex mu;
@@ -134,13 +196,12 @@ struct ImageCache {
     auto it = images.find(key);
     if (it != images.end()) return it->second;
     std::vector<uint32_t> img = build_job_image(kind, ls, lc, z, n, f, N, nullptr, mode);
-    uint32_t *d = nullptr;
-    if (cudaMalloc(&d, img.size() * 4) != cudaSuccess) {
+    uint32_t *d = static_cast<uint32_t *>(plan_alloc(img.size() * 4));
+    if (!d) {
       *err = ZX_ENOMEM;
       return nullptr;
     }
-    if (cudaMemcpy(d, img.data(), img.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess) {
-      cudaFree(d);
+    if (plan_upload(d, img.data(), img.size() * 4) != cudaSuccess) {
       *err = ZX_ECUDA;
       return nullptr;
     }
@@ -681,13 +742,12 @@ const TransformPlan *get_transform_plan(int kind, int l, int64_t z, int64_t n, i
     for (size_t t = i; t < k; t++) flat.push_back(P.jobs[t].d);
     i = k;
   }
-  JobDesc *d = nullptr;
-  if (cudaMalloc(&d, std::max<size_t>(1, flat.size()) * sizeof(JobDesc)) != cudaSuccess) {
+  JobDesc *d = static_cast<JobDesc *>(plan_alloc(std::max<size_t>(1, flat.size()) * sizeof(JobDesc)));
+  if (!d) {
     *err = ZX_ENOMEM;
     return nullptr;
   }
-  if (cudaMemcpy(d, flat.data(), flat.size() * sizeof(JobDesc), cudaMemcpyHostToDevice) != cudaSuccess) {
-    cudaFree(d);
+  if (plan_upload(d, flat.data(), flat.size() * sizeof(JobDesc)) != cudaSuccess) {
     *err = ZX_ECUDA;
     return nullptr;
   }
@@ -722,13 +782,12 @@ const TransformPlan *get_transform_plan(int kind, int l, int64_t z, int64_t n, i
     int32_t *ho = reinterpret_cast<int32_t *>(hj + nj);
     std::memcpy(ho, fs.dep_off.data(), fs.dep_off.size() * sizeof(int32_t));
     std::memcpy(ho + fs.dep_off.size(), fs.deps.data(), fs.deps.size() * sizeof(int32_t));
-    unsigned char *dblob = nullptr;
-    if (cudaMalloc(&dblob, bytes) != cudaSuccess) {
+    unsigned char *dblob = static_cast<unsigned char *>(plan_alloc(bytes));
+    if (!dblob) {
       *err = ZX_ENOMEM;
       return nullptr;
     }
-    if (cudaMemcpy(dblob, blob.data(), bytes, cudaMemcpyHostToDevice) != cudaSuccess) {
-      cudaFree(dblob);
+    if (plan_upload(dblob, blob.data(), bytes) != cudaSuccess) {
       *err = ZX_ECUDA;
       return nullptr;
     }
@@ -824,13 +883,12 @@ const TransformPlan *get_sn_plan(int kind, int l, int64_t z, int64_t n, int f, i
     for (size_t t = i; t < k; t++) flat.push_back(P.jobs[t].d);
     i = k;
   }
-  JobDesc *d = nullptr;
-  if (cudaMalloc(&d, std::max<size_t>(1, flat.size()) * sizeof(JobDesc)) != cudaSuccess) {
+  JobDesc *d = static_cast<JobDesc *>(plan_alloc(std::max<size_t>(1, flat.size()) * sizeof(JobDesc)));
+  if (!d) {
     *err = ZX_ENOMEM;
     return nullptr;
   }
-  if (cudaMemcpy(d, flat.data(), flat.size() * sizeof(JobDesc), cudaMemcpyHostToDevice) != cudaSuccess) {
-    cudaFree(d);
+  if (plan_upload(d, flat.data(), flat.size() * sizeof(JobDesc)) != cudaSuccess) {
     *err = ZX_ECUDA;
     return nullptr;
   }
