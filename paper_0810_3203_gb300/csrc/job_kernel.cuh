@@ -718,6 +718,16 @@ __device__ __forceinline__ KGeo make_kgeo(int N, uint32_t mask) {
   return kg;
 }
 
+// Programmatic dependent launch (launches of single-CTA jobs carry the attribute): this grid lets
+// the stream's next launch place its CTAs as this grid's CTAs finish, and waits until the launch
+// before it has completed, its writes visible, before it touches a cell (the plan's job lists and
+// programs were written long before). For a launch without the attribute, or after a predecessor
+// that is not a kernel of this file, the wait returns at once or the stream order holds as usual.
+__device__ __forceinline__ void grid_dependency_enter() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
 // One job per CTA (per cluster): a plain launch, a replicated one or a merged one. TM = 3 (single-CTA
 // launches only): the cells move through the tensor maps tm_ld / tm_st (see run_job).
 template <int K, int MINB, bool FULL, bool SQ, bool SINGLE, int TM>
@@ -728,6 +738,7 @@ __global__ void __launch_bounds__(MINB == 3 ? 256 : 512, MINB) job_kernel(uint64
                                                   int rep_ctas, uint32_t *fault,
                                                   const __grid_constant__ CUtensorMap tm_ld,
                                                   const __grid_constant__ CUtensorMap tm_st) {
+  grid_dependency_enter();
   const KGeo kg = make_kgeo<K, FULL, SQ>(N, mask);
   JobDesc jd;
   if (nsegs == 0) {
@@ -781,6 +792,7 @@ __global__ void __launch_bounds__(MINB == 3 ? 256 : 512, MINB) job_kernel_stream
                                                   int N, int ls, uint32_t mask, int prog_cap, uint32_t *fault,
                                                   const __grid_constant__ CUtensorMap tm_ld,
                                                   const __grid_constant__ CUtensorMap tm_st) {
+  grid_dependency_enter();
   const KGeo kg = make_kgeo<K, FULL, SQ>(N, mask);
   const bool vec16 = ((reinterpret_cast<uintptr_t>(x) & 15) == 0) && ((stride_limbs & 1) == 0);
   for (int k = int(blockIdx.x); k < njobs; k += int(gridDim.x)) {
@@ -887,6 +899,11 @@ static cudaError_t launch_km(const Launch &L, uint64_t *x, int64_t stride_limbs,
       // one CTA per job (njobs < 0): the streaming kernel's loop runs once and prefetches nothing
       const int nj = fa.njobs < 0 ? -fa.njobs : fa.njobs;
       if (fa.njobs < 0) cfg.gridDim = dim3(unsigned(nj));
+      cudaLaunchAttribute pdl[1];
+      pdl[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+      pdl[0].val.programmaticStreamSerializationAllowed = 1;
+      cfg.attrs = pdl;
+      cfg.numAttrs = 1;
       if constexpr (K >= 8)
         if (cm && cm->mode == 3)
           return cudaLaunchKernelEx(&cfg, job_kernel_stream<K, MINB, FULL, SQ, 3>, x, stride_limbs, fa.jobs, nj,
@@ -902,12 +919,18 @@ static cudaError_t launch_km(const Launch &L, uint64_t *x, int64_t stride_limbs,
     cfg.dynamicSmemBytes = smem;
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = 1u << L.lc;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
+    if (L.lc > 0) {
+      attr[0].id = cudaLaunchAttributeClusterDimension;
+      attr[0].val.clusterDim.x = 1u << L.lc;
+      attr[0].val.clusterDim.y = 1;
+      attr[0].val.clusterDim.z = 1;
+    } else {
+      // single-CTA jobs: programmatic dependent launch (grid_dependency_enter)
+      attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+      attr[0].val.programmaticStreamSerializationAllowed = 1;
+    }
     cfg.attrs = attr;
-    cfg.numAttrs = L.lc > 0 ? 1 : 0;
+    cfg.numAttrs = 1;
     static const CellMaps no_maps = {};
     if constexpr (K >= 8 && FULL)
       if (L.lc == 0 && cm && cm->mode == 3)
