@@ -718,16 +718,6 @@ __device__ __forceinline__ KGeo make_kgeo(int N, uint32_t mask) {
   return kg;
 }
 
-// Programmatic dependent launch (launches of single-CTA jobs carry the attribute): this grid lets
-// the stream's next launch place its CTAs as this grid's CTAs finish, and waits until the launch
-// before it has completed, its writes visible, before it touches a cell (the plan's job lists and
-// programs were written long before). For a launch without the attribute, or after a predecessor
-// that is not a kernel of this file, the wait returns at once or the stream order holds as usual.
-__device__ __forceinline__ void grid_dependency_enter() {
-  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-  asm volatile("griddepcontrol.wait;" ::: "memory");
-}
-
 // One job per CTA (per cluster): a plain launch, a replicated one or a merged one. TM = 3 (single-CTA
 // launches only): the cells move through the tensor maps tm_ld / tm_st (see run_job).
 template <int K, int MINB, bool FULL, bool SQ, bool SINGLE, int TM>

@@ -6,6 +6,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <utility>
 
 #include "common.h"
 #include "host.h"
@@ -46,6 +47,7 @@ __device__ __forceinline__ void pack_one(const uint64_t *coef, int64_t limbs, in
 template <int K>
 __global__ void pack_kernel(const uint64_t *__restrict__ coef, int64_t len, int64_t limbs, int sgn,
                             uint64_t *__restrict__ cells, int64_t stride, int N) {
+  grid_dependency_enter();
   const Geo g = make_geo(N, K);
   const int64_t nwarps = int64_t(gridDim.x) * (blockDim.x >> 5);
   for (int64_t i = int64_t(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5); i < len; i += nwarps)
@@ -55,6 +57,7 @@ __global__ void pack_kernel(const uint64_t *__restrict__ coef, int64_t len, int6
 template <int K>
 __global__ void pack_batch_kernel(const PackItem *__restrict__ items, int64_t stride, int N,
                                   uint64_t *__restrict__ pool) {
+  grid_dependency_enter();
   const Geo g = make_geo(N, K);
   const PackItem it = items[blockIdx.y];
   const int64_t nwarps = int64_t(gridDim.x) * (blockDim.x >> 5);
@@ -112,6 +115,7 @@ __device__ __forceinline__ void lift_one(const uint64_t *cell, int sgn, uint64_t
 template <int K>
 __global__ void lift_kernel(const uint64_t *__restrict__ cells, int64_t n, int64_t stride, int sgn,
                             uint64_t *__restrict__ out, int64_t limbs_out, int N) {
+  grid_dependency_enter();
   const Geo g = make_geo(N, K);
   const int64_t nwarps = int64_t(gridDim.x) * (blockDim.x >> 5);
   for (int64_t i = int64_t(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5); i < n; i += nwarps)
@@ -121,6 +125,7 @@ __global__ void lift_kernel(const uint64_t *__restrict__ cells, int64_t n, int64
 template <int K>
 __global__ void lift_batch_kernel(const LiftItem *__restrict__ items, int64_t stride, int N,
                                   const uint64_t *__restrict__ pool) {
+  grid_dependency_enter();
   const Geo g = make_geo(N, K);
   const LiftItem it = items[blockIdx.y];
   const int64_t nwarps = int64_t(gridDim.x) * (blockDim.x >> 5);
@@ -294,6 +299,25 @@ __device__ __forceinline__ void pointwise_one(uint64_t *acell, const uint64_t *b
   __syncwarp();
 }
 
+// Launch with programmatic dependent launch (every kernel of this file calls grid_dependency_enter
+// first), so that the launches of a product's chain (pack, transforms, pointwise, lift) start
+// their CTAs as the previous launch's last wave finishes.
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                       Args &&...args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute a[1];
+  a[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  a[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = a;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
+
 constexpr int kPointwiseWarps = 4;
 
 __host__ __device__ constexpr int pointwise_warp_words(int NW) { return (NW + 3) & ~3; }
@@ -302,6 +326,7 @@ template <int K>
 __global__ void __launch_bounds__(kPointwiseWarps * 32)
     pointwise_kernel(uint64_t *__restrict__ a, const uint64_t *__restrict__ b, int64_t n, int64_t stride, int N,
                      int warps_per_block) {
+  grid_dependency_enter();
   extern __shared__ uint4 sm4[];
   uint32_t *sm = reinterpret_cast<uint32_t *>(sm4);
   const Geo g = make_geo(N, K);
@@ -320,6 +345,7 @@ template <int K>
 __global__ void __launch_bounds__(kPointwiseWarps * 32)
     pointwise_batch_kernel(const PointwiseItem *__restrict__ items, int count, int64_t total, int64_t stride, int N,
                            int warps_per_block, uint64_t *__restrict__ pool) {
+  grid_dependency_enter();
   extern __shared__ uint4 sm4[];
   uint32_t *sm = reinterpret_cast<uint32_t *>(sm4);
   const Geo g = make_geo(N, K);
@@ -342,8 +368,8 @@ cudaError_t pointwise_k(uint64_t *a, const uint64_t *b, int64_t n, int64_t strid
   int64_t blocks = (n + wpb - 1) / wpb;
   if (blocks > 152 * 16) blocks = 152 * 16;
   if (blocks < 1) blocks = 1;
-  pointwise_kernel<K><<<int(blocks), wpb * 32, smem, s>>>(a, b, n, stride, int(r.N), wpb);
-  return cudaGetLastError();
+  return launch_pdl(pointwise_kernel<K>, dim3(unsigned(blocks)), dim3(unsigned(wpb * 32)), smem, s, a, b, n, stride,
+                    int(r.N), wpb);
 }
 
 int grid_for(int64_t items, int warps_per_block) {
@@ -368,17 +394,19 @@ int grid_for(int64_t items, int warps_per_block) {
 cudaError_t launch_pack(const uint64_t *coef, int64_t len, int64_t limbs, int is_signed, uint64_t *cells,
                         int64_t stride_limbs, const Ring &r, cudaStream_t s) {
   if (len <= 0) return cudaSuccess;
-  TFT_DISPATCH_K(r.K, (pack_kernel<KK><<<grid_for(len, 8), 256, 0, s>>>(coef, len, limbs, is_signed, cells,
-                                                                         stride_limbs, int(r.N))));
-  return cudaGetLastError();
+  const dim3 grid(unsigned(grid_for(len, 8)));
+  TFT_DISPATCH_K(r.K, return launch_pdl(pack_kernel<KK>, grid, dim3(256), 0, s, coef, len, limbs, is_signed, cells,
+                                        stride_limbs, int(r.N)));
+  return cudaSuccess;
 }
 
 cudaError_t launch_lift(const uint64_t *cells, int64_t n, int64_t stride_limbs, int is_signed, uint64_t *out,
                         int64_t limbs_out, const Ring &r, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
-  TFT_DISPATCH_K(r.K, (lift_kernel<KK><<<grid_for(n, 8), 256, 0, s>>>(cells, n, stride_limbs, is_signed, out,
-                                                                       limbs_out, int(r.N))));
-  return cudaGetLastError();
+  const dim3 grid(unsigned(grid_for(n, 8)));
+  TFT_DISPATCH_K(r.K, return launch_pdl(lift_kernel<KK>, grid, dim3(256), 0, s, cells, n, stride_limbs, is_signed, out,
+                                        limbs_out, int(r.N)));
+  return cudaSuccess;
 }
 
 template <int K>
@@ -389,8 +417,8 @@ cudaError_t pointwise_batch_k(const PointwiseItem *items, int count, int64_t tot
   int64_t blocks = (total + wpb - 1) / wpb;
   if (blocks > 152 * 16) blocks = 152 * 16;
   if (blocks < 1) blocks = 1;
-  pointwise_batch_kernel<K><<<unsigned(blocks), wpb * 32, smem, s>>>(items, count, total, stride, int(r.N), wpb, pool);
-  return cudaGetLastError();
+  return launch_pdl(pointwise_batch_kernel<K>, dim3(unsigned(blocks)), dim3(unsigned(wpb * 32)), smem, s, items, count,
+                    total, stride, int(r.N), wpb, pool);
 }
 
 int grid_x_for(int64_t max_items, int count, int warps_per_block) {
@@ -404,16 +432,18 @@ cudaError_t launch_pack_batch(const PackItem *d_items, int count, int64_t max_le
                               const Ring &r, uint64_t *pool, cudaStream_t s) {
   if (count <= 0 || max_len <= 0) return cudaSuccess;
   const dim3 grid(unsigned(grid_x_for(max_len, count, 8)), unsigned(count));
-  TFT_DISPATCH_K(r.K, (pack_batch_kernel<KK><<<grid, 256, 0, s>>>(d_items, stride_limbs, int(r.N), pool)));
-  return cudaGetLastError();
+  TFT_DISPATCH_K(r.K, return launch_pdl(pack_batch_kernel<KK>, grid, dim3(256), 0, s, d_items, stride_limbs, int(r.N),
+                                        pool));
+  return cudaSuccess;
 }
 
 cudaError_t launch_lift_batch(const LiftItem *d_items, int count, int64_t max_n, int64_t stride_limbs,
                               const Ring &r, uint64_t *pool, cudaStream_t s) {
   if (count <= 0 || max_n <= 0) return cudaSuccess;
   const dim3 grid(unsigned(grid_x_for(max_n, count, 8)), unsigned(count));
-  TFT_DISPATCH_K(r.K, (lift_batch_kernel<KK><<<grid, 256, 0, s>>>(d_items, stride_limbs, int(r.N), pool)));
-  return cudaGetLastError();
+  TFT_DISPATCH_K(r.K, return launch_pdl(lift_batch_kernel<KK>, grid, dim3(256), 0, s, d_items, stride_limbs, int(r.N),
+                                        pool));
+  return cudaSuccess;
 }
 
 cudaError_t launch_pointwise_batch(const PointwiseItem *d_items, int count, int64_t total, int64_t stride_limbs,
