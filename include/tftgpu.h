@@ -409,7 +409,9 @@ int zx_transform_schedule(int kind, int l, int64_t z, int64_t n, int f, int64_t 
  * read on request:
  *   zx_wait_status  synchronises `stream`, then reads and clears the status word of the current
  *                   device (atomically). ZX_OK when no wait gave up since the last read,
- *                   ZX_ETIMEOUT when one did, ZX_ECUDA on a CUDA error.
+ *                   ZX_ETIMEOUT when one did (or when a job that moves cells by tensor copies
+ *                   found its shared memory misaligned and ran nothing, which the kernel's
+ *                   declaration rules out), ZX_ECUDA on a CUDA error.
  *   zx_wait_probe   enqueues one warp that waits on an mbarrier that nothing completes until
  *                   limit_us microseconds (1 .. 10^6, else ZX_EINVAL) have passed, and reports
  *                   it as the transform kernel does: the error path, taken without a fault.

@@ -695,7 +695,9 @@ int zx_wait_status(void *stream) {
   uint32_t fault = 0;
   const cudaError_t ce = read_wait_status(&fault, cudaStream_t(stream));
   if (ce != cudaSuccess) return cuda_fail(ce, "reading the wait status");
-  if (fault) return fail(ZX_ETIMEOUT, "a bounded device-side wait gave up (outputs of that call are unspecified)");
+  if (fault)
+    return fail(ZX_ETIMEOUT, (fault & 4u) ? "a tensor-copy job found its shared memory misaligned (outputs unspecified)"
+                                          : "a bounded device-side wait gave up (outputs of that call are unspecified)");
   return ZX_OK;
 }
 
