@@ -226,6 +226,12 @@ struct JobRec {
   JobDesc d;
 };
 
+// Job lists and the planner's scratch arrays run to hundreds of kilobytes; allocated afresh for
+// every plan, their pages fault in again each time (most of a plan's host time). Each thread
+// keeps its largest buffers for the next plan instead.
+thread_local std::vector<JobRec> t_jobs_spare, t_jobs_sorted;
+thread_local std::vector<int32_t> t_cells_scratch;
+
 struct Planner {
   Ring ring;
   int64_t twoN;
@@ -245,7 +251,14 @@ struct Planner {
     ls_max = cfg.ls_max;
     ls_c = cfg.ls_c;
     split = cfg.split;
+    jobs.swap(t_jobs_spare);
+    jobs.clear();
   }
+  ~Planner() {
+    if (jobs.capacity() > t_jobs_spare.capacity()) jobs.swap(t_jobs_spare);
+  }
+  Planner(const Planner &) = delete;
+  Planner &operator=(const Planner &) = delete;
   int top_l1(int l) const {
     if (split == 2) return fewest_pass_l1(l);
     return split ? l - l / 2 : l / 2;
@@ -372,43 +385,61 @@ struct Planner {
   // pass that read a cell it writes since that cell was last written. Running the levels in order
   // keeps every such pair in order, and the passes of one level touch disjoint cells, so they
   // share launches. Returns the number of levels.
+  //
+  // A plan of Algorithm 1 alone is already levelled: a sub-transform reads all of its inputs in
+  // its first pass (a leaf loads its z cells; the columns of a split share the first pass and
+  // load the inputs between them), so the rows' first pass reads the deepest column's last
+  // output, and every pass reads a cell the pass before it wrote.
   int relevel() {
     if (jobs.empty()) return 0;
     int maxp = 0;
     int64_t ncells = 0;
+    bool all_tft = true;
     for (const JobRec &j : jobs) {
       maxp = std::max(maxp, j.pass);
+      all_tft = all_tft && j.kind == KIND_TFT;
       const int32_t m = std::max(j.d.nload, j.d.nstore);
       if (m > 0) ncells = std::max(ncells, j.d.cell0 + int64_t(m - 1) * j.d.mstride + 1);
     }
-    std::vector<std::vector<size_t>> by_pass(size_t(maxp) + 1);
-    for (size_t i = 0; i < jobs.size(); i++) by_pass[size_t(jobs[i].pass)].push_back(i);
-    std::vector<int> last_write(size_t(ncells), 0), last_read(size_t(ncells), 0), level(size_t(maxp) + 1, 0);
+    if (all_tft) return maxp + 1;
+    // job indices grouped by pass
+    std::vector<int32_t> first(size_t(maxp) + 2, 0), order(jobs.size());
+    for (const JobRec &j : jobs) first[size_t(j.pass) + 1]++;
+    for (int p = 0; p <= maxp; p++) first[size_t(p) + 1] += first[size_t(p)];
+    {
+      std::vector<int32_t> at(first.begin(), first.end() - 1);
+      for (size_t i = 0; i < jobs.size(); i++) order[size_t(at[size_t(jobs[i].pass)]++)] = int32_t(i);
+    }
+    // per cell: the level of its last store, the highest level that read it since
+    std::vector<int32_t> &seen = t_cells_scratch;
+    seen.assign(size_t(2 * ncells), 0);
+    std::vector<int> level(size_t(maxp) + 1, 0);
+    int32_t *lw = seen.data(), *lr = seen.data() + 1;  // cell c at 2c
     int top = 0;
     for (int p = 0; p <= maxp; p++) {
+      const int32_t b = first[size_t(p)], en = first[size_t(p) + 1];
       int lev = 1;
-      for (size_t i : by_pass[size_t(p)]) {
-        const JobDesc &d = jobs[i].d;
-        for (int32_t m = 0; m < std::max(d.nload, d.nstore); m++) {
-          const size_t c = size_t(d.cell0 + int64_t(m) * d.mstride);
-          if (m < d.nload) lev = std::max(lev, last_write[c] + 1);
-          if (m < d.nstore) lev = std::max(lev, std::max(last_write[c], last_read[c]) + 1);
-        }
+      for (int32_t t = b; t < en; t++) {
+        const JobDesc &d = jobs[size_t(order[size_t(t)])].d;
+        const int64_t c0 = d.cell0, ms = d.mstride;
+        const int32_t ns = d.nstore, span = std::max(d.nload, d.nstore);
+        int32_t m = 0;
+        for (; m < ns; m++) lev = std::max(lev, std::max(lw[2 * (c0 + m * ms)], lr[2 * (c0 + m * ms)]) + 1);  // stored
+        for (; m < span; m++) lev = std::max(lev, lw[2 * (c0 + m * ms)] + 1);                           // loaded only
       }
-      for (size_t i : by_pass[size_t(p)]) {
-        const JobDesc &d = jobs[i].d;
-        for (int32_t m = 0; m < std::max(d.nload, d.nstore); m++) {
-          const size_t c = size_t(d.cell0 + int64_t(m) * d.mstride);
-          if (m < d.nstore) {
-            last_write[c] = lev;
-            last_read[c] = 0;
-          } else {
-            last_read[c] = std::max(last_read[c], lev);
-          }
+      for (int32_t t = b; t < en; t++) {
+        const JobDesc &d = jobs[size_t(order[size_t(t)])].d;
+        const int64_t c0 = d.cell0, ms = d.mstride;
+        const int32_t ns = d.nstore, span = std::max(d.nload, d.nstore);
+        int32_t m = 0;
+        for (; m < ns; m++) {
+          lw[2 * (c0 + m * ms)] = lev;
+          lr[2 * (c0 + m * ms)] = 0;
         }
+        for (; m < span; m++) lr[2 * (c0 + m * ms)] = std::max(lr[2 * (c0 + m * ms)], lev);
       }
       level[size_t(p)] = lev;
-      if (!by_pass[size_t(p)].empty()) top = std::max(top, lev);
+      if (en > b) top = std::max(top, lev);
     }
     for (JobRec &j : jobs) j.pass = level[size_t(j.pass)] - 1;
     return top;
@@ -441,6 +472,31 @@ bool launch_order(const JobRec &a, const JobRec &b) {
   return a.ls < b.ls;
 }
 
+// Stable reorder into launch order: a counting sort over the packed key (pass, lc, ls), whose
+// range the plans keep small; a comparison sort otherwise.
+void sort_launch_order(std::vector<JobRec> &jobs) {
+  if (jobs.size() < 2) return;
+  int maxp = 0;
+  bool small = true;
+  for (const JobRec &j : jobs) {
+    maxp = std::max(maxp, j.pass);
+    small = small && j.pass >= 0 && j.lc >= 0 && j.lc < 8 && j.ls >= 0 && j.ls < 32;
+  }
+  const size_t range = (size_t(maxp) + 1) * 256;
+  if (!small || range > 4 * jobs.size() + 65536) {
+    std::stable_sort(jobs.begin(), jobs.end(), launch_order);
+    return;
+  }
+  auto key = [](const JobRec &j) { return (size_t(j.pass) * 8 + size_t(j.lc)) * 32 + size_t(j.ls); };
+  std::vector<int32_t> at(range + 1, 0);
+  for (const JobRec &j : jobs) at[key(j) + 1]++;
+  for (size_t k = 0; k < range; k++) at[k + 1] += at[k];
+  std::vector<JobRec> &out = t_jobs_sorted;
+  out.resize(jobs.size());
+  for (const JobRec &j : jobs) out[size_t(at[key(j)]++)] = j;
+  jobs.swap(out);  // the scratch keeps the old list's buffer
+}
+
 }  // namespace
 
 // Flag the jobs whose every stored cell is stored again by a later pass (JOB_RAW_STORE): they
@@ -450,16 +506,22 @@ bool launch_order(const JobRec &a, const JobRec &b) {
 static void mark_raw_stores(std::vector<JobRec> &jobs, int l) {
   if (l > 22 || jobs.empty()) return;
   const int64_t L = int64_t(1) << l;
-  std::vector<int> last(size_t(L), -1);
-  for (const JobRec &j : jobs)
-    for (int64_t m = 0; m < j.d.nstore; m++) {
-      const int64_t c = j.d.cell0 + m * j.d.mstride;
-      if (c < 0 || c >= L) return;  // not a plan over [0, L): leave every store canonical
-      last[size_t(c)] = std::max(last[size_t(c)], j.pass);
-    }
+  std::vector<int32_t> &last = t_cells_scratch;
+  last.assign(size_t(L), -1);
+  int32_t *lp = last.data();
+  for (const JobRec &j : jobs) {
+    const int64_t c0 = j.d.cell0, ms = j.d.mstride, ns = j.d.nstore;
+    if (ns <= 0) continue;
+    if (c0 < 0 || c0 >= L || c0 + (ns - 1) * ms < 0 || c0 + (ns - 1) * ms >= L)
+      return;  // not a plan over [0, L): leave every store canonical
+    const int pass = j.pass;
+    for (int64_t m = 0; m < ns; m++) lp[c0 + m * ms] = std::max(lp[c0 + m * ms], pass);
+  }
   for (JobRec &j : jobs) {
-    bool raw = j.d.nstore > 0;
-    for (int64_t m = 0; m < j.d.nstore && raw; m++) raw = last[size_t(j.d.cell0 + m * j.d.mstride)] > j.pass;
+    const int64_t c0 = j.d.cell0, ms = j.d.mstride, ns = j.d.nstore;
+    const int pass = j.pass;
+    bool raw = ns > 0;
+    for (int64_t m = 0; m < ns && raw; m++) raw = lp[c0 + m * ms] > pass;
     if (raw) j.d.pad |= JOB_RAW_STORE;
   }
 }
@@ -598,7 +660,7 @@ void plan_shape(int kind, int l, int64_t z, int64_t n, int f, int64_t N, int *pa
   else
     P.itft(0, 0, 1, l, 0, z, n, f, -1);
   *passes = P.relevel();
-  std::sort(P.jobs.begin(), P.jobs.end(), launch_order);
+  sort_launch_order(P.jobs);
   int nl = 0, lcmax = 0, lsmax = 0;
   for (size_t i = 0; i < P.jobs.size(); i++) {
     if (i == 0 || !same_launch(P.jobs[i], P.jobs[i - 1])) nl++;
@@ -629,7 +691,7 @@ void build_host_plan(int kind, int l, int64_t z, int64_t n, int f, int64_t N, in
   out->npasses = P.relevel();
   std::map<std::tuple<int, int, int, int64_t, int64_t, int>, int> index;
   mark_raw_stores(P.jobs, l);
-  std::stable_sort(P.jobs.begin(), P.jobs.end(), launch_order);
+  sort_launch_order(P.jobs);
   for (size_t i = 0; i < P.jobs.size();) {
     size_t k = i;
     while (k < P.jobs.size() && same_launch(P.jobs[k], P.jobs[i])) k++;
@@ -671,7 +733,7 @@ void build_host_schedule(int kind, int l, int64_t z, int64_t n, int f, int64_t N
     P.itft(0, 0, 1, l, e, z, n, f, scale ? inv_l_exponent(l, twoN, mode) : -1);
   P.relevel();
   mark_raw_stores(P.jobs, l);
-  std::stable_sort(P.jobs.begin(), P.jobs.end(), launch_order);
+  sort_launch_order(P.jobs);
   int nl = 0;
   bool single = true;
   for (size_t i = 0; i < P.jobs.size(); i++) {
@@ -720,12 +782,20 @@ const TransformPlan *get_transform_plan(int kind, int l, int64_t z, int64_t n, i
   plan->npasses = npass;
   plan->njobs = int64_t(P.jobs.size());
   // resolve job images, then group jobs by (pass, ls, lc) in pass order
+  // neighbouring jobs mostly share a shape: look an image up once per run of equal shapes
+  const JobRec *prev = nullptr;
   for (JobRec &j : P.jobs) {
-    j.d.image = image_cache().get(j.kind, j.ls, j.lc, j.z, j.n, j.f, N, err, mode);
-    if (!j.d.image) return nullptr;
+    if (prev && prev->kind == j.kind && prev->ls == j.ls && prev->lc == j.lc && prev->z == j.z &&
+        prev->n == j.n && prev->f == j.f) {
+      j.d.image = prev->d.image;
+    } else {
+      j.d.image = image_cache().get(j.kind, j.ls, j.lc, j.z, j.n, j.f, N, err, mode);
+      if (!j.d.image) return nullptr;
+    }
+    prev = &j;
   }
   mark_raw_stores(P.jobs, l);
-  std::stable_sort(P.jobs.begin(), P.jobs.end(), launch_order);
+  sort_launch_order(P.jobs);
   std::vector<JobDesc> flat;
   std::vector<std::pair<size_t, Launch>> groups;
   for (size_t i = 0; i < P.jobs.size();) {
@@ -737,7 +807,9 @@ const TransformPlan *get_transform_plan(int kind, int l, int64_t z, int64_t n, i
     L.lc = P.jobs[i].lc;
     L.njobs = int(k - i);
     L.nwarps = warps_for_job(L.ls, L.lc, P.cfg.max_warps);
-    for (size_t t = i; t < k; t++) L.prog_words = std::max(L.prog_words, image_cache().max_prog(P.jobs[t].d.image));
+    for (size_t t = i; t < k; t++)
+      if (t == i || P.jobs[t].d.image != P.jobs[t - 1].d.image)
+        L.prog_words = std::max(L.prog_words, image_cache().max_prog(P.jobs[t].d.image));
     groups.push_back({flat.size(), L});
     for (size_t t = i; t < k; t++) flat.push_back(P.jobs[t].d);
     i = k;
@@ -866,7 +938,7 @@ const TransformPlan *get_sn_plan(int kind, int l, int64_t z, int64_t n, int f, i
     j.d.image = image_cache().get(j.kind, j.ls, j.lc, j.z, j.n, j.f, H, err, RING_SN);
     if (!j.d.image) return nullptr;
   }
-  std::stable_sort(P.jobs.begin(), P.jobs.end(), launch_order);
+  sort_launch_order(P.jobs);
   std::vector<JobDesc> flat;
   std::vector<std::pair<size_t, Launch>> groups;
   for (size_t i = 0; i < P.jobs.size();) {
@@ -878,7 +950,9 @@ const TransformPlan *get_sn_plan(int kind, int l, int64_t z, int64_t n, int f, i
     L.lc = 0;
     L.njobs = int(k - i);
     L.nwarps = warps_for_job(L.ls, 0, cfg.max_warps);
-    for (size_t t = i; t < k; t++) L.prog_words = std::max(L.prog_words, image_cache().max_prog(P.jobs[t].d.image));
+    for (size_t t = i; t < k; t++)
+      if (t == i || P.jobs[t].d.image != P.jobs[t - 1].d.image)
+        L.prog_words = std::max(L.prog_words, image_cache().max_prog(P.jobs[t].d.image));
     groups.push_back({flat.size(), L});
     for (size_t t = i; t < k; t++) flat.push_back(P.jobs[t].d);
     i = k;
@@ -915,7 +989,7 @@ void sn_plan_shape(int kind, int l, int64_t z, int64_t n, int f, int64_t H, int 
   else
     P.itft(0, 0, 1, l, 0, z, n, f, -1);
   *passes = P.relevel();
-  std::sort(P.jobs.begin(), P.jobs.end(), launch_order);
+  sort_launch_order(P.jobs);
   int nl = 0;
   for (size_t i = 0; i < P.jobs.size(); i++)
     if (i == 0 || !same_launch(P.jobs[i], P.jobs[i - 1])) nl++;
