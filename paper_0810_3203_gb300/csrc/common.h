@@ -24,6 +24,13 @@ __device__ __forceinline__ void grid_dependency_enter() {
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   asm volatile("griddepcontrol.wait;" ::: "memory");
 }
+// The two halves, for a kernel that signals late: the next launch's CTAs then take SM slots
+// only as this grid's last CTAs end, instead of waiting there from the start of the grid's last
+// wave while CTAs of launches on other streams could have used the slots.
+__device__ __forceinline__ void grid_dependency_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void grid_dependents_launch() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
 #endif
 
 // ---------------------------------------------------------------- on-chip programs
