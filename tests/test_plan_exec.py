@@ -235,6 +235,32 @@ def test_plan_safety_sweep(tg):
         check_plan_safety(plan, 1 << l, range(n if kind == 0 else n + f))
 
 
+def test_tft_plans_come_levelled(tg):
+    """The planner takes an Algorithm 1 plan's passes as its dependency levels without
+    relevelling them: a sub-transform reads all of its inputs in its first pass, so each pass
+    reads a cell the pass before it stored. Checked here from the outside on plans of single-CTA
+    jobs (one launch per pass), and no launch may be empty."""
+    rng = random.Random(77)
+    checked = 0
+    for N, lmax in ((64, 7), (1024, 11), (4096, 12), (32768, 13)):
+        for l in range(2, lmax + 1):
+            L = 1 << l
+            for _ in range(4 if l < 10 else 2):
+                z, n = rng.randint(1, L), rng.randint(1, L)
+                plan = tg.transform_jobs(0, l, z, n, N)
+                launches = plan["launches"]
+                if any(launch["lc"] for launch in launches):
+                    continue
+                assert len(launches) == plan["passes"], (l, z, n, N)
+                assert all(launch["jobs"] for launch in launches)
+                for prev, cur in zip(launches, launches[1:]):
+                    stored = {jd["cell0"] + m * jd["mstride"] for jd in prev["jobs"] for m in range(jd["nstore"])}
+                    read = {jd["cell0"] + m * jd["mstride"] for jd in cur["jobs"] for m in range(jd["nload"])}
+                    assert stored & read, (l, z, n, N)
+                checked += 1
+    assert checked > 60
+
+
 def test_the_fewest_pass_plan_at_the_benchmark_size(tg):
     """split 2 with clusters of at most 4 CTAs and 16 cells per cluster CTA: the l = 16 TFT at
     N = 32768 takes three global-memory passes (64-cell column jobs on 4-CTA clusters, then rows
