@@ -471,14 +471,16 @@ def run_gpu(args):
 
     # end to end through the C ABI with host buffers: per n, H2D of its n input cells from
     # pinned memory, TFT, ITFT, D2H of its n result cells (the other L - n cells of a buffer are
-    # the transforms' scratch and stay on the device). The copies run on their own streams and
-    # each n's transforms on its stream of the timed step, so the copies of one n overlap the
+    # the transforms' scratch and stay on the device). The H2D copies run in order on one stream
+    # and each n's D2H on a stream of its own, so that no result waits behind another n's; each
+    # n's transforms run on its stream of the timed step, so the copies of one n overlap the
     # transforms of the others; a buffer is refilled only after its previous results have left.
     span = {n: n * stride for n in ns}  # limbs of the n cells
     pinned = {n: torch.from_numpy(host[n].view(np.int64)[:span[n]].copy()).pin_memory() for n in ns}
     outp = {n: torch.empty_like(pinned[n]).pin_memory() for n in ns}
     h2d = sum(pinned[n].numel() * 8 for n in ns)
-    s_in, s_out = torch.cuda.Stream(device), torch.cuda.Stream(device)
+    s_in = torch.cuda.Stream(device)
+    s_out = {n: torch.cuda.Stream(device) for n in ns}
     drained = {}
 
     def e2e_step():
@@ -494,11 +496,11 @@ def run_gpu(args):
             tg.itft_ex(dev[n], l, n, n, 0, N, 0, stride, 1, stream=lanes[n])
             done = torch.cuda.Event()
             done.record(lanes[n])
-            s_out.wait_event(done)
-            with torch.cuda.stream(s_out):
+            s_out[n].wait_event(done)
+            with torch.cuda.stream(s_out[n]):
                 outp[n].copy_(dev[n][:span[n]], non_blocking=True)
             drained[n] = torch.cuda.Event()
-            drained[n].record(s_out)
+            drained[n].record(s_out[n])
 
     e2e_secs = timed_steps(e2e_step, max(1, args.steps // 2), 1, sync, device)
     e2e_value = sb * max(1, args.steps // 2) * ws / e2e_secs / 1e9
