@@ -261,6 +261,18 @@ def test_tft_plans_come_levelled(tg):
     assert checked > 60
 
 
+def test_snake_order_only_in_plans_larger_than_half_of_l2(tg):
+    """Plans whose cells exceed 64 MB take every other launch's jobs in reverse order, so that a
+    pass starts on the cells the pass before it stored last; smaller plans (they fit in L2) keep
+    the sorted order. The l = 16 TFT at n = 40000, N = 32768 spans 40960 cells of 4104 bytes."""
+    big = tg.transform_jobs(0, 16, 40000, 40000, 32768)["launches"]
+    firsts = [launch["jobs"][0]["cell0"] for launch in big]
+    lasts = [launch["jobs"][-1]["cell0"] for launch in big]
+    assert [f < l for f, l in zip(firsts, lasts)] == [True, False, True, False], (firsts, lasts)
+    small = tg.transform_jobs(0, 13, 6000, 6000, 8192)["launches"]
+    assert all(launch["jobs"][0]["cell0"] <= launch["jobs"][-1]["cell0"] for launch in small)
+
+
 def test_the_fewest_pass_plan_at_the_benchmark_size(tg):
     """split 2 with clusters of at most 4 CTAs and 16 cells per cluster CTA: the l = 16 TFT at
     N = 32768 takes three global-memory passes (64-cell column jobs on 4-CTA clusters, then rows
