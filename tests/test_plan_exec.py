@@ -273,6 +273,60 @@ def test_snake_order_only_in_plans_larger_than_half_of_l2(tg):
     assert all(launch["jobs"][0]["cell0"] <= launch["jobs"][-1]["cell0"] for launch in small)
 
 
+def test_concurrent_planning_matches_sequential_planning(tg):
+    """The planner keeps its job lists and per-cell scratch in per-thread buffers that outlive a
+    plan. Plans made on four threads at once (the foreign calls release the interpreter lock)
+    must equal the same plans made one after another, in every job field and image."""
+    import threading
+
+    rng = random.Random(5)
+    cases = []
+    for N, lmax in ((1024, 11), (4096, 12), (32768, 13)):
+        for _ in range(6):
+            l = rng.randint(4, lmax)
+            L = 1 << l
+            n = rng.randint(1, L)
+            if rng.random() < 0.5:
+                cases.append((0, l, rng.randint(1, L), n, 0, N))
+            else:
+                cases.append((1, l, rng.randint(n, L), n, 1 if n < L and rng.random() < 0.5 else 0, N))
+
+    def key(plan):
+        return (plan["passes"], [(launch["ls"], launch["lc"], launch["warps"], launch["program_words"],
+                                  [tuple(sorted(jd.items())) for jd in launch["jobs"]]) for launch in plan["launches"]],
+                [img.tobytes() for img in plan["images"]])
+
+    expected = [key(tg.transform_jobs(kind, l, z, n, N, f=f)) for kind, l, z, n, f, N in cases]
+    results = [[None] * len(cases) for _ in range(4)]
+    errors = []
+
+    def worker(t):
+        try:
+            for _ in range(3):
+                for i in rng_orders[t]:
+                    kind, l, z, n, f, N = cases[i]
+                    got = key(tg.transform_jobs(kind, l, z, n, N, f=f))
+                    if results[t][i] is None or got != expected[i]:
+                        results[t][i] = got
+        except Exception as exc:  # reported below
+            errors.append(exc)
+
+    rng_orders = []
+    for t in range(4):
+        order = list(range(len(cases)))
+        random.Random(t).shuffle(order)
+        rng_orders.append(order)
+    threads = [threading.Thread(target=worker, args=(t,)) for t in range(4)]
+    for th in threads:
+        th.start()
+    for th in threads:
+        th.join()
+    assert not errors, errors
+    for t in range(4):
+        for i in range(len(cases)):
+            assert results[t][i] == expected[i], (t, cases[i])
+
+
 def test_the_fewest_pass_plan_at_the_benchmark_size(tg):
     """split 2 with clusters of at most 4 CTAs and 16 cells per cluster CTA: the l = 16 TFT at
     N = 32768 takes three global-memory passes (64-cell column jobs on 4-CTA clusters, then rows
