@@ -192,6 +192,29 @@ cudaError_t helper_stream(cudaStream_t *s, cudaEvent_t *fork, cudaEvent_t *join)
   return cudaSuccess;
 }
 
+// zx_mul_batch: a product with a transform of 2^13 cells or more (at least 512 jobs of 16 cells
+// a pass, more than the 456 CTA slots of a GB300) fills the GPU on its own, so it runs as its own
+// launch chain (zx_mul) on one of kChainStreams streams forked from the caller's; the smaller
+// ones share merged launches. On 512 mixed products (lengths 200-20000, 64-1024 bits), dealing
+// every product onto 4 streams measured 4.5 % faster than merging all of them (1738 against
+// 1662 products/s).
+constexpr int kChainMinL = 13;
+constexpr int kChainStreams = 4;
+
+static cudaError_t chain_streams(cudaStream_t (&out)[kChainStreams]) {
+  static thread_local cudaStream_t per_dev[16][kChainStreams] = {};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 16) return cudaErrorInvalidDevice;
+  for (int k = 0; k < kChainStreams; k++) {
+    if (!per_dev[dev][k] && (e = cudaStreamCreateWithFlags(&per_dev[dev][k], cudaStreamNonBlocking)) != cudaSuccess)
+      return e;
+    out[k] = per_dev[dev][k];
+  }
+  return cudaSuccess;
+}
+
 // Pointwise method for ring N: 1 (schoolbook) or 2 (recursive, with *rp filled). Auto picks the
 // recursion when its estimated word operations fall below kRecAutoRatio of the schoolbook's
 // NW^2 word products. Measured on GB300 (10^4 products at N = 32768: 9.27 ms recursive, 1.38 ms
@@ -448,9 +471,54 @@ int zx_mul_batch(const zx_poly *fs, const zx_poly *gs, zx_poly *hs, int count, v
     }
   }
   for (int i = 0; i < count; i++) hs[i].is_signed = items[size_t(i)].sgn;
+  // products whose transforms fill the GPU on their own run as their own launch chains, dealt
+  // largest first onto forked streams; the others share the merged launches
+  std::vector<BatchProduct> merged;
+  std::vector<int> chained;
+  for (int i = 0; i < count; i++) {
+    if (items[size_t(i)].l >= kChainMinL)
+      chained.push_back(i);
+    else
+      merged.push_back(items[size_t(i)]);
+  }
+  std::stable_sort(chained.begin(), chained.end(), [&](int a, int b) {
+    const BatchProduct &x = items[size_t(a)], &y = items[size_t(b)];
+    return (x.stride << x.l) > (y.stride << y.l);
+  });
+  cudaStream_t s = cudaStream_t(stream);
+  cudaStream_t cs[kChainStreams] = {};
+  cudaEvent_t fork = nullptr;
+  cudaError_t ce = cudaSuccess;
+  if (!chained.empty()) {
+    if ((ce = chain_streams(cs)) != cudaSuccess || (ce = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming)) != cudaSuccess ||
+        (ce = cudaEventRecord(fork, s)) != cudaSuccess) {
+      if (fork) cudaEventDestroy(fork);
+      return cuda_fail(ce, "batch streams");
+    }
+    for (int k = 0; k < kChainStreams; k++) cudaStreamWaitEvent(cs[k], fork, 0);
+    cudaEventDestroy(fork);
+  }
   std::string msg;
-  int rc = run_mul_batch(items, cudaStream_t(stream), &msg);
-  if (rc) return fail(rc, msg);
+  int rc = run_mul_batch(merged, s, &msg);
+  std::string chain_msg;
+  for (size_t j = 0; j < chained.size() && rc == ZX_OK; j++) {
+    const int i = chained[j];
+    if ((rc = zx_mul(fs + i, gs + i, hs + i, cs[j % kChainStreams])) != ZX_OK)
+      chain_msg = "product " + std::to_string(i) + ": " + g_last_error;
+  }
+  if (!chained.empty()) {
+    // the caller's stream waits for every chain, also after an error (before the caller frees)
+    for (int k = 0; k < kChainStreams; k++) {
+      cudaEvent_t join = nullptr;
+      if (cudaEventCreateWithFlags(&join, cudaEventDisableTiming) == cudaSuccess) {
+        if (cudaEventRecord(join, cs[k]) == cudaSuccess) cudaStreamWaitEvent(s, join, 0);
+        cudaEventDestroy(join);
+      } else {
+        cudaStreamSynchronize(cs[k]);
+      }
+    }
+  }
+  if (rc) return fail(rc, chain_msg.empty() ? msg : chain_msg);
   return ZX_OK;
 }
 
