@@ -159,10 +159,14 @@ int zx_mul(const zx_poly *f, const zx_poly *g, zx_poly *h, void *stream);
 
 /*
  * count independent products hs[i] = fs[i] * gs[i], each with its own ring and length, all
- * operands in device memory. The products run concurrently: every pass of every product is
- * one job of a shared per-pass launch, so short products share SMs with long ones instead of
- * leaving them idle. Same per-product rules as zx_mul (first failing index is reported by
- * zx_last_error()).
+ * operands in device memory. The products run concurrently. A product whose transforms have
+ * 2^13 cells or more fills the GPU on its own: it runs as its own launch chain (as zx_mul), the
+ * largest first, on one of 4 streams of the calling thread forked from `stream`. The smaller
+ * products share merged launches, where every pass of every product is one job of a shared
+ * per-pass launch, so short products share SMs instead of leaving them idle. All of the call's
+ * work is ordered after the work already on `stream` and before anything enqueued on it later,
+ * also when the call fails. Same per-product rules as zx_mul (the first failing index is
+ * reported by zx_last_error()).
  */
 int zx_mul_batch(const zx_poly *fs, const zx_poly *gs, zx_poly *hs, int count, void *stream);
 
